@@ -1,0 +1,197 @@
+"""FP64 CPU oracle of the GlassNet per-pixel forward pass (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU baseline
+and reference arm may import this module.  It shares no code with the CUDA
+library: it reads the float32 weights and buffers produced by ``gen.synth``,
+upcasts them to float64 and evaluates the network as written, in concat form,
+with no folding, fusion, blocking or reordering.
+
+The network (paper Sec. 3.3-3.4, Fig. 2; widths of the per-pixel MLP form):
+  sigma = F(s)                      scene encoder, run once per scene
+  v_k   = h([b_k ; sigma])          shared per-layer network, Eq. 5
+  pool  = [max_k v_k ; mean_k v_k]  symmetric function g over the valid layers
+  r     = rho(pool), r = 0 when the pixel has no valid layer
+  y     = B([g_p ; r ; sigma])      final blending network
+  rgb   = R(y)                      rendering network, sigmoid output
+
+Readings where the paper is silent (each is listed with its reason in the
+design notes): ReLU after every linear layer except the last one of R, which
+is a sigmoid; the mean divides by the number of valid layers; an empty layer
+set gives r = 0; input concat orders are [b ; sigma] and [g ; r ; sigma];
+pool order is [max ; mean].
+
+Every function below is pinned by ``tests/test_oracle_pins.py`` (hand-worked
+closed forms, brute force, invariants and library routines).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _f64(a) -> np.ndarray:
+    return np.asarray(a, dtype=np.float64)
+
+
+def linear(x, W, b) -> np.ndarray:
+    """Affine layer ``y = W x + b`` on the last axis; W is [out][in]."""
+    return _f64(x) @ _f64(W).T + _f64(b)
+
+
+def relu(x) -> np.ndarray:
+    return np.maximum(_f64(x), 0.0)
+
+
+def sigmoid(x) -> np.ndarray:
+    """Logistic function 1 / (1 + e^-x)."""
+    x = _f64(x)
+    with np.errstate(over="ignore"):
+        return 1.0 / (1.0 + np.exp(-x))
+
+
+def scene_encoder(weights, s) -> np.ndarray:
+    """Scene encoder F (Sec. 3.4): sigma = ReLU(F2 ReLU(F1 s + b1) + b2)."""
+    h1 = relu(linear(s, *weights["F1"]))
+    return relu(linear(h1, *weights["F2"]))
+
+
+def per_layer_h(weights, b_k, sigma) -> np.ndarray:
+    """Shared per-layer network h(b_i, sigma) of Eq. 5.
+
+    ``b_k`` is [..., n_t] (one transparency layer per row); sigma is
+    broadcast to every row and appended after the layer's channels.
+    """
+    b_k = _f64(b_k)
+    sig = np.broadcast_to(_f64(sigma), b_k.shape[:-1] + (np.shape(sigma)[-1],))
+    x = np.concatenate([b_k, sig], axis=-1)
+    u = relu(linear(x, *weights["phi1"]))
+    return relu(linear(u, *weights["phi2"]))
+
+
+def set_pool(V) -> np.ndarray | None:
+    """Symmetric function g over a set of per-layer vectors V [c][H].
+
+    Returns [max ; mean] (length 2H), or None for the empty set.  The sum is
+    taken over each channel's values sorted ascending, a canonical order that
+    makes the result exactly independent of the order of the layers (Eq. 5,
+    Table 4).
+    """
+    V = _f64(V)
+    c = V.shape[0]
+    if c == 0:
+        return None
+    mx = V.max(axis=0)
+    srt = np.sort(V, axis=0)
+    s = np.zeros(V.shape[1])
+    for k in range(c):
+        s = s + srt[k]
+    return np.concatenate([mx, s / c])
+
+
+def post_pool_rho(weights, pool) -> np.ndarray:
+    """Post-pooling network rho: r = ReLU(W_rho pool + b_rho)."""
+    return relu(linear(pool, *weights["rho"]))
+
+
+def final_blend_B(weights, g, r, sigma) -> np.ndarray:
+    """Final blending network B (Sec. 3.4) on [g ; r ; sigma]."""
+    g, r = _f64(g), _f64(r)
+    sig = np.broadcast_to(_f64(sigma), g.shape[:-1] + (np.shape(sigma)[-1],))
+    x = np.concatenate([g, r, sig], axis=-1)
+    y = relu(linear(x, *weights["B1"]))
+    return relu(linear(y, *weights["B2"]))
+
+
+def render_R(weights, y) -> np.ndarray:
+    """Rendering network R (Sec. 3.4): rgb = sigmoid(R2 ReLU(R1 y + b) + b)."""
+    q = relu(linear(y, *weights["R1"]))
+    return sigmoid(linear(q, *weights["R2"]))
+
+
+def render_pixel(weights, sigma, g, layers) -> np.ndarray:
+    """One pixel: ``g`` [n_g] opaque G-buffer, ``layers`` [c][n_t] valid layers."""
+    layers = _f64(layers).reshape(-1, np.shape(weights["phi1"][0])[1] - np.shape(sigma)[-1])
+    H = np.shape(weights["phi2"][0])[0]
+    if layers.shape[0] == 0:
+        r = np.zeros(H)
+    else:
+        V = np.stack([per_layer_h(weights, layers[k], sigma) for k in range(layers.shape[0])])
+        r = post_pool_rho(weights, set_pool(V))
+    y = final_blend_B(weights, g, r, sigma)
+    return render_R(weights, y)
+
+
+def render_opaque_only(weights, sigma, gbuf_rows) -> np.ndarray:
+    """Opaque-only path: B and R with the rho input removed.
+
+    Written independently of ``render_pixel``: B1's columns that multiply r
+    are dropped instead of multiplying a zero vector.  ``gbuf_rows`` is [P][n_g].
+    """
+    W1, b1 = weights["B1"]
+    W1 = _f64(W1)
+    n_g = np.shape(gbuf_rows)[-1]
+    Z = np.shape(sigma)[-1]
+    keep = np.r_[0:n_g, W1.shape[1] - Z:W1.shape[1]]
+    x = np.concatenate([_f64(gbuf_rows),
+                        np.broadcast_to(_f64(sigma), np.shape(gbuf_rows)[:-1] + (Z,))], axis=-1)
+    y = relu(x @ W1[:, keep].T + _f64(b1))
+    y = relu(linear(y, *weights["B2"]))
+    return render_R(weights, y)
+
+
+def render_frame(weights, scene, gbuf, tbuf, counts, chunk: int = 16384) -> np.ndarray:
+    """Whole frame, vectorised over pixels; returns rgb float64 [3][h][w].
+
+    ``gbuf`` [n_g][h][w], ``tbuf`` [K][n_t][h][w], ``counts`` [h][w].  Slots
+    ``k >= counts`` are never read into the result.  Pixels are processed in
+    chunks only to bound memory; every pixel's arithmetic is the same as
+    ``render_pixel``.
+    """
+    sigma = scene_encoder(weights, scene)
+    n_g, h, w = np.shape(gbuf)
+    K, n_t = np.shape(tbuf)[0], np.shape(tbuf)[1]
+    P = h * w
+    G = np.asarray(gbuf).reshape(n_g, P)
+    T = np.asarray(tbuf).reshape(K, n_t, P)
+    C = np.asarray(counts).reshape(P).astype(np.int64)
+    H = np.shape(weights["phi2"][0])[0]
+    out = np.empty((3, P))
+    for p0 in range(0, P, chunk):
+        p1 = min(P, p0 + chunk)
+        n = p1 - p0
+        c = C[p0:p1]
+        if np.any(c > K) or np.any(c < 0):
+            raise ValueError("layer count outside 0..K")
+        V = np.zeros((K, n, H))
+        for k in range(K):
+            idx = np.nonzero(c > k)[0]
+            if idx.size:
+                V[k, idx] = per_layer_h(weights, _f64(T[k][:, p0 + idx]).T, sigma)
+        mask = np.arange(K)[:, None] < c[None, :]
+        mx = np.where(mask[:, :, None], V, -np.inf).max(axis=0) if K else np.zeros((n, H))
+        srt = np.sort(np.where(mask[:, :, None], V, np.inf), axis=0)
+        s = np.zeros((n, H))
+        for k in range(K):
+            s = s + np.where((k < c)[:, None], srt[k], 0.0)
+        has = c > 0
+        r = np.zeros((n, H))
+        if np.any(has):
+            pool = np.concatenate([mx[has], s[has] / c[has][:, None]], axis=1)
+            r[has] = post_pool_rho(weights, pool)
+        y = final_blend_B(weights, _f64(G[:, p0:p1]).T, r, sigma)
+        out[:, p0:p1] = render_R(weights, y).T
+    return out.reshape(3, h, w)
+
+
+def alpha_blend(colors, alphas) -> np.ndarray:
+    """Order-dependent alpha compositing of Eq. 3-4 (a negative control).
+
+    ``colors`` [t][3], ``alphas`` [t]; T = sum_i alpha_i C_i z_i with
+    z_t = 1 and z_i = prod_{j=1}^{t-i} (1 - alpha_j) otherwise.
+    """
+    C, a = _f64(colors), _f64(alphas)
+    t = a.shape[0]
+    out = np.zeros(C.shape[1])
+    for i in range(1, t + 1):
+        z = 1.0 if i == t else float(np.prod(1.0 - a[: t - i]))
+        out += a[i - 1] * C[i - 1] * z
+    return out

@@ -1,0 +1,58 @@
+"""Hand-worked one-pixel GlassNet cases with widths shrunk to 2.
+
+Widths: scene 2, latent Z = 2, transparency channels 2, G-buffer channels 2,
+hidden H = 2, output 3.  Weights are small integers chosen so that every
+weight block, every bias, both concat orders and both halves of the pool reach
+the output with distinct values.  Each step below was worked by hand; the
+expected logits are exact integers, so the expected RGB is the logistic
+function of an integer (checked against scipy's ``expit``).
+"""
+import numpy as np
+
+W = {
+    # F1: [[1, 1], [0, -1]] s + [0, 3]; s = [1, 2] -> [3, 1] -> ReLU [3, 1]
+    "F1": (np.array([[1, 1], [0, -1]], np.float32), np.array([0, 3], np.float32)),
+    # F2: [[1, -1], [0, 2]] [3, 1] + [0, -1] -> [2, 1] -> sigma = [2, 1]
+    "F2": (np.array([[1, -1], [0, 2]], np.float32), np.array([0, -1], np.float32)),
+    # phi1 on [t0, t1, z0, z1]:
+    #   t = [1, 0]: [1 + 2, 0 - 1 + 2] = [3, 1]
+    #   t = [0, 1]: [0 + 2, 1 - 1 + 2] = [2, 2]
+    "phi1": (np.array([[1, 0, 1, 0], [0, 1, 0, -1]], np.float32), np.array([0, 2], np.float32)),
+    # phi2: [[1, 1], [-1, 2]] u + [1, 0]
+    #   u = [3, 1]: [5, -1] -> v = [5, 0]   (ReLU clips)
+    #   u = [2, 2]: [5, 2]  -> v = [5, 2]
+    "phi2": (np.array([[1, 1], [-1, 2]], np.float32), np.array([1, 0], np.float32)),
+    # rho on [max0, max1, mean0, mean1] with bias [0, 1]:
+    #   one layer  t=[1,0]:        pool [5, 0, 5, 0] -> [5 - 0, 0 + 5 + 1] = [5, 6]
+    #   two layers t=[1,0],[0,1]:  max [5, 2], mean [5, 1]
+    #                              pool [5, 2, 5, 1] -> [5 - 1, 2 + 5 + 1] = [4, 8]
+    "rho": (np.array([[1, 0, 0, -1], [0, 1, 1, 0]], np.float32), np.array([0, 1], np.float32)),
+    # B1 on [g0, g1, r0, r1, z0, z1], g = [1, -1], bias [0, 1]:
+    #   row 0 = g0 + r0 + z1, row 1 = 2 g1 + r1 + z0 + 1
+    #   one layer  r = [5, 6]: [1 + 5 + 1, -2 + 6 + 2 + 1] = [7, 7]
+    #   two layers r = [4, 8]: [1 + 4 + 1, -2 + 8 + 2 + 1] = [6, 9]
+    #   no layer   r = [0, 0]: [1 + 0 + 1, -2 + 0 + 2 + 1] = [2, 1]
+    "B1": (np.array([[1, 0, 1, 0, 0, 1], [0, 2, 0, 1, 1, 0]], np.float32),
+           np.array([0, 1], np.float32)),
+    # B2: [[2, -1], [1, 0]] y + [0, -1]
+    #   [7, 7] -> [7, 6];  [6, 9] -> [3, 5];  [2, 1] -> [3, 1]
+    "B2": (np.array([[2, -1], [1, 0]], np.float32), np.array([0, -1], np.float32)),
+    # R1: [[1, 0], [-1, 1]] y + [0, 3]
+    #   [7, 6] -> [7, 2];  [3, 5] -> [3, 5];  [3, 1] -> [3, 1]
+    "R1": (np.array([[1, 0], [-1, 1]], np.float32), np.array([0, 3], np.float32)),
+    # R2: [[1, -1], [0, 1], [-1, 0]] q + [0, 0, 1]
+    #   [7, 2] -> [5, 2, -6];  [3, 5] -> [-2, 5, -2];  [3, 1] -> [2, 1, -2]
+    "R2": (np.array([[1, -1], [0, 1], [-1, 0]], np.float32), np.array([0, 0, 1], np.float32)),
+}
+
+SCENE = np.array([1, 2], np.float32)
+SIGMA = np.array([2.0, 1.0])
+G = np.array([1, -1], np.float32)
+LAYER_A = np.array([1, 0], np.float32)
+LAYER_B = np.array([0, 1], np.float32)
+
+# Expected pre-sigmoid outputs (exact integers) for each case.
+LOGITS_ONE_LAYER = np.array([5.0, 2.0, -6.0])
+LOGITS_TWO_LAYERS = np.array([-2.0, 5.0, -2.0])
+LOGITS_NO_LAYER = np.array([2.0, 1.0, -2.0])
+POOL_TWO_LAYERS = np.array([5.0, 2.0, 5.0, 1.0])

@@ -1,0 +1,326 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each pin is one of: a hand-worked closed form (tests/hand_cases.py), brute
+force on tiny inputs, a library routine, or an invariant the paper states
+(Eq. 5 order independence, Table 4, the empty set of Eq. 5).  The mutation
+tests at the end plant plausible mistakes in a copy of the oracle and check
+that some pin catches each one.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import expit
+
+import oracle
+from oracle import glassnet_oracle as O
+from gen import synth
+from tests import hand_cases as hc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _tiny_weights(seed, bias="uniform", H=4, Z=3):
+    """Random model with small widths but the real channel counts."""
+    rng = np.random.default_rng(seed)
+    shapes = {
+        "F1": (Z, synth.SCENE_DIM), "F2": (Z, Z), "phi1": (H, synth.TBUF_CHANNELS + Z),
+        "phi2": (H, H), "rho": (H, 2 * H), "B1": (H, synth.GBUF_CHANNELS + H + Z),
+        "B2": (H, H), "R1": (H, H), "R2": (3, H),
+    }
+    w = {}
+    for k, (o, i) in shapes.items():
+        W = rng.standard_normal((o, i)).astype(np.float32)
+        b = (rng.uniform(-0.5, 0.5, o) if bias == "uniform" else np.zeros(o)).astype(np.float32)
+        w[k] = (W, b)
+    return w
+
+
+# ---------------------------------------------------------------- primitives
+
+def test_linear_matches_brute_force_loops():
+    rng = np.random.default_rng(1)
+    for (n, i, o) in [(1, 1, 1), (3, 5, 2), (4, 7, 6)]:
+        x = rng.standard_normal((n, i))
+        W = rng.standard_normal((o, i))
+        b = rng.standard_normal(o)
+        got = O.linear(x, W, b)
+        for r in range(n):
+            for j in range(o):
+                acc = float(b[j])
+                for k in range(i):
+                    acc += float(W[j, k]) * float(x[r, k])
+                assert abs(got[r, j] - acc) < 1e-12
+
+
+def test_relu_special_values():
+    np.testing.assert_array_equal(O.relu([-2.0, -0.0, 0.0, 3.5]), [0.0, 0.0, 0.0, 3.5])
+
+
+def test_sigmoid_closed_forms_and_library():
+    assert O.sigmoid(0.0) == 0.5
+    assert abs(O.sigmoid(math.log(3.0)) - 0.75) < 1e-15
+    x = np.linspace(-30, 30, 601)
+    np.testing.assert_allclose(O.sigmoid(x) + O.sigmoid(-x), 1.0, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(O.sigmoid(x), expit(x), rtol=1e-14, atol=0)
+    assert O.sigmoid(-1000.0) == 0.0 and O.sigmoid(1000.0) == 1.0
+
+
+# ------------------------------------------------------------ hand-worked cases
+
+def test_hand_scene_encoder():
+    np.testing.assert_array_equal(O.scene_encoder(hc.W, hc.SCENE), hc.SIGMA)
+
+
+def test_hand_per_layer_network():
+    np.testing.assert_array_equal(O.per_layer_h(hc.W, hc.LAYER_A, hc.SIGMA), [5.0, 0.0])
+    np.testing.assert_array_equal(O.per_layer_h(hc.W, hc.LAYER_B, hc.SIGMA), [5.0, 2.0])
+
+
+def test_hand_pool_two_layers():
+    V = np.stack([O.per_layer_h(hc.W, hc.LAYER_A, hc.SIGMA),
+                  O.per_layer_h(hc.W, hc.LAYER_B, hc.SIGMA)])
+    np.testing.assert_array_equal(O.set_pool(V), hc.POOL_TWO_LAYERS)
+    assert O.set_pool(np.zeros((0, 2))) is None
+
+
+@pytest.mark.parametrize("layers,logits", [
+    ([hc.LAYER_A], hc.LOGITS_ONE_LAYER),
+    ([hc.LAYER_A, hc.LAYER_B], hc.LOGITS_TWO_LAYERS),
+    ([hc.LAYER_B, hc.LAYER_A], hc.LOGITS_TWO_LAYERS),
+    ([], hc.LOGITS_NO_LAYER),
+])
+def test_hand_render_pixel(layers, logits):
+    sigma = O.scene_encoder(hc.W, hc.SCENE)
+    L = np.array(layers, np.float32).reshape(len(layers), 2)
+    got = O.render_pixel(hc.W, sigma, hc.G, L)
+    np.testing.assert_allclose(got, expit(logits), rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("K", [2, 3, 5])
+def test_hand_render_frame_matches_closed_forms(K):
+    """2x2 frame through the vectorised path; K > c checks the mean divides by c."""
+    counts = np.array([[1, 2], [0, 2]], np.uint8)
+    gbuf = np.broadcast_to(hc.G[:, None, None], (2, 2, 2)).copy()
+    tbuf = np.full((K, 2, 2, 2), np.nan, np.float32)
+    tbuf[0, :, 0, 0] = hc.LAYER_A
+    tbuf[0, :, 0, 1] = hc.LAYER_A
+    tbuf[1, :, 0, 1] = hc.LAYER_B
+    tbuf[0, :, 1, 1] = hc.LAYER_B
+    tbuf[1, :, 1, 1] = hc.LAYER_A
+    rgb = O.render_frame(hc.W, hc.SCENE, gbuf, tbuf, counts)
+    np.testing.assert_allclose(rgb[:, 0, 0], expit(hc.LOGITS_ONE_LAYER), rtol=1e-15)
+    np.testing.assert_allclose(rgb[:, 0, 1], expit(hc.LOGITS_TWO_LAYERS), rtol=1e-15)
+    np.testing.assert_allclose(rgb[:, 1, 0], expit(hc.LOGITS_NO_LAYER), rtol=1e-15)
+    np.testing.assert_allclose(rgb[:, 1, 1], expit(hc.LOGITS_TWO_LAYERS), rtol=1e-15)
+
+
+# ------------------------------------------------------------------- invariants
+
+def _table4_bound():
+    with open(os.path.join(GOLDEN, "table4_order_invariance.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    return max(float(r[3]) for r in rows)
+
+
+@pytest.mark.parametrize("c", [1, 2, 3, 4, 5])
+def test_permutation_invariance_every_order(c):
+    """Eq. 5 / Table 4: every order of the valid layers gives the same output."""
+    bound = _table4_bound()
+    assert bound == 0.0
+    w = _tiny_weights(10 + c)
+    rng = np.random.default_rng(c)
+    sigma = O.scene_encoder(w, rng.standard_normal(synth.SCENE_DIM))
+    g = rng.standard_normal(synth.GBUF_CHANNELS)
+    L = rng.standard_normal((c, synth.TBUF_CHANNELS))
+    ref = O.render_pixel(w, sigma, g, L)
+    for perm in itertools.permutations(range(c)):
+        got = O.render_pixel(w, sigma, g, L[list(perm)])
+        assert np.max(np.abs(got - ref)) <= bound
+
+
+def test_canonical_sum_agrees_with_plain_sum():
+    rng = np.random.default_rng(7)
+    V = rng.standard_normal((6, 9)) * 10
+    pool = O.set_pool(V)
+    np.testing.assert_allclose(pool[9:], V.sum(axis=0) / 6, rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(pool[:9], V.max(axis=0))
+
+
+def test_duplication_invariance_of_max_mean():
+    """max and mean of {a, b} equal those of {a, a, b, b}."""
+    rng = np.random.default_rng(3)
+    w = _tiny_weights(3)
+    sigma = O.scene_encoder(w, rng.standard_normal(synth.SCENE_DIM))
+    g = rng.standard_normal(synth.GBUF_CHANNELS)
+    a, b = rng.standard_normal((2, synth.TBUF_CHANNELS))
+    one = O.render_pixel(w, sigma, g, np.stack([a, b]))
+    two = O.render_pixel(w, sigma, g, np.stack([a, a, b, b]))
+    np.testing.assert_allclose(one, two, rtol=0, atol=1e-14)
+
+
+def test_empty_set_equals_independent_opaque_only_path():
+    rng = np.random.default_rng(4)
+    w = _tiny_weights(4)
+    s = rng.standard_normal(synth.SCENE_DIM)
+    sigma = O.scene_encoder(w, s)
+    gb = rng.standard_normal((5, synth.GBUF_CHANNELS))
+    ref = O.render_opaque_only(w, sigma, gb)
+    for i in range(5):
+        got = O.render_pixel(w, sigma, gb[i], np.zeros((0, synth.TBUF_CHANNELS)))
+        np.testing.assert_allclose(got, ref[i], rtol=0, atol=1e-14)
+
+
+def test_invalid_slots_never_read():
+    w = _tiny_weights(5)
+    f = synth.make_frame(6, 5, 4, counts="uniform", seed=5)
+    a = O.render_frame(w, synth.make_scene(5), f.gbuf, f.tbuf, f.counts)
+    t2 = f.tbuf.copy()
+    c = f.counts.reshape(-1)
+    t2r = t2.reshape(4, synth.TBUF_CHANNELS, -1)
+    for k in range(4):
+        t2r[k][:, c <= k] = np.float32(3.0e38)
+    b = O.render_frame(w, synth.make_scene(5), f.gbuf, t2, f.counts)
+    assert np.all(np.isfinite(a))
+    np.testing.assert_array_equal(a, b)
+
+
+def test_frame_matches_per_pixel_definition():
+    """Vectorised frame path equals the per-pixel definition (SoA indexing p = y*w + x)."""
+    w = _tiny_weights(6)
+    f = synth.make_frame(3, 4, 3, counts="uniform", seed=6)
+    s = synth.make_scene(6)
+    rgb = O.render_frame(w, s, f.gbuf, f.tbuf, f.counts)
+    sigma = O.scene_encoder(w, s)
+    for y in range(3):
+        for x in range(4):
+            c = int(f.counts[y, x])
+            L = f.tbuf[:c, :, y, x]
+            ref = O.render_pixel(w, sigma, f.gbuf[:, y, x], L)
+            np.testing.assert_allclose(rgb[:, y, x], ref, rtol=0, atol=1e-13)
+
+
+def test_frame_permutation_bit_identical():
+    w = _tiny_weights(8)
+    f = synth.make_frame(8, 8, 5, counts="uniform", seed=8)
+    s = synth.make_scene(8)
+    ref = O.render_frame(w, s, f.gbuf, f.tbuf, f.counts)
+    for seed in range(1, 4):
+        fp = synth.permute_layers(f, seed)
+        assert not np.array_equal(np.nan_to_num(fp.tbuf), np.nan_to_num(f.tbuf))
+        np.testing.assert_array_equal(O.render_frame(w, s, fp.gbuf, fp.tbuf, fp.counts), ref)
+
+
+def test_fold_identity():
+    """Splitting phi1 and B1 into a sigma-independent part plus a folded bias is exact
+    algebra: W [b ; sigma] + c = W_b b + (W_sigma sigma + c)."""
+    w = _tiny_weights(9)
+    rng = np.random.default_rng(9)
+    sigma = O.scene_encoder(w, rng.standard_normal(synth.SCENE_DIM))
+    t = rng.standard_normal((7, synth.TBUF_CHANNELS))
+    W1, b1 = (np.float64(a) for a in w["phi1"])
+    n_t = synth.TBUF_CHANNELS
+    folded = t @ W1[:, :n_t].T + (W1[:, n_t:] @ sigma + b1)
+    concat = O.linear(np.concatenate([t, np.broadcast_to(sigma, (7, sigma.size))], 1), W1, b1)
+    np.testing.assert_allclose(folded, concat, rtol=0, atol=1e-12)
+
+
+def test_alpha_blending_is_order_dependent_negative_control():
+    """Eq. 3-4 changes when the layers are reordered; the network's pool does not."""
+    C = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0]])
+    a = np.array([0.5, 0.25, 0.75])
+    fwd = O.alpha_blend(C, a)
+    rev = O.alpha_blend(C[::-1], a[::-1])
+    assert np.max(np.abs(fwd - rev)) > 0.1
+    # one layer: alpha * C
+    np.testing.assert_allclose(O.alpha_blend(C[:1], a[:1]), [0.5, 0, 0])
+
+
+# --------------------------------------------------------------- mutation tests
+
+def _pins_pass(mod):
+    """Run the hand-case pins against a (possibly mutated) oracle module."""
+    try:
+        sigma = mod.scene_encoder(hc.W, hc.SCENE)
+        cases = [([hc.LAYER_A], hc.LOGITS_ONE_LAYER),
+                 ([hc.LAYER_A, hc.LAYER_B], hc.LOGITS_TWO_LAYERS),
+                 ([], hc.LOGITS_NO_LAYER)]
+        for layers, logits in cases:
+            L = np.array(layers, np.float32).reshape(len(layers), 2)
+            got = mod.render_pixel(hc.W, sigma, hc.G, L)
+            if not np.allclose(got, expit(logits), rtol=1e-12, atol=0):
+                return False
+        counts = np.array([[2]], np.uint8)
+        tbuf = np.full((3, 2, 1, 1), np.nan, np.float32)
+        tbuf[0, :, 0, 0] = hc.LAYER_A
+        tbuf[1, :, 0, 0] = hc.LAYER_B
+        gbuf = hc.G.reshape(2, 1, 1)
+        rgb = mod.render_frame(hc.W, hc.SCENE, gbuf, tbuf, counts)
+        return bool(np.allclose(rgb[:, 0, 0], expit(hc.LOGITS_TWO_LAYERS), rtol=1e-12, atol=0))
+    except Exception:
+        return False
+
+
+def _mutant(monkeypatch, name, fn):
+    monkeypatch.setattr(O, name, fn)
+    return O
+
+
+def test_unmutated_oracle_passes_pins():
+    assert _pins_pass(O)
+
+
+MUTATIONS = {
+    "pool order [mean; max]": ("set_pool", lambda V: (lambda p: None if p is None else
+                                np.concatenate([p[len(p) // 2:], p[:len(p) // 2]]))(
+                                    _ORIG["set_pool"](V))),
+    "drop phi1 bias": ("per_layer_h", lambda w, b, s: _ORIG["per_layer_h"](
+        {**w, "phi1": (w["phi1"][0], 0 * w["phi1"][1])}, b, s)),
+    "sigma before layer channels": ("per_layer_h", lambda w, b, s: O.relu(O.linear(O.relu(O.linear(
+        np.concatenate([np.broadcast_to(np.float64(s), np.shape(b)[:-1] + (np.shape(s)[-1],)),
+                        np.float64(b)], -1), *w["phi1"])), *w["phi2"]))),
+    "transposed phi2": ("per_layer_h", lambda w, b, s: _ORIG["per_layer_h"](
+        {**w, "phi2": (w["phi2"][0].T, w["phi2"][1])}, b, s)),
+    "no ReLU after phi2": ("per_layer_h", lambda w, b, s: O.linear(O.relu(O.linear(
+        np.concatenate([np.float64(b), np.broadcast_to(np.float64(s), np.shape(b)[:-1] + (np.shape(s)[-1],))], -1),
+        *w["phi1"])), *w["phi2"])),
+    "B input [r; g; sigma]": ("final_blend_B", lambda w, g, r, s: _ORIG["final_blend_B"](w, r, g, s)),
+    "wrong sign B2 bias": ("final_blend_B", lambda w, g, r, s: _ORIG["final_blend_B"](
+        {**w, "B2": (w["B2"][0], -w["B2"][1])}, g, r, s)),
+    "transposed F1": ("scene_encoder", lambda w, s: _ORIG["scene_encoder"](
+        {**w, "F1": (w["F1"][0].T, w["F1"][1])}, s)),
+    "rho drops bias": ("post_pool_rho", lambda w, p: O.relu(np.float64(p) @ np.float64(w["rho"][0]).T)),
+    "R1 transposed": ("render_R", lambda w, y: _ORIG["render_R"](
+        {**w, "R1": (w["R1"][0].T, w["R1"][1])}, y)),
+    "sigmoid(-x)": ("sigmoid", lambda x: 1.0 / (1.0 + np.exp(np.float64(x)))),
+}
+_ORIG = {n: getattr(O, n) for n in ("set_pool", "per_layer_h", "final_blend_B",
+                                     "scene_encoder", "post_pool_rho", "render_R", "sigmoid")}
+
+
+@pytest.mark.parametrize("label", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(monkeypatch, label):
+    name, fn = MUTATIONS[label]
+    assert not _pins_pass(_mutant(monkeypatch, name, fn)), label
+
+
+def test_mean_over_slots_instead_of_valid_layers_is_caught():
+    """A mean that divides by K instead of the valid count fails the K=3 frame pin."""
+    counts = np.array([[2]], np.uint8)
+    tbuf = np.full((3, 2, 1, 1), 0.0, np.float32)
+    tbuf[0, :, 0, 0] = hc.LAYER_A
+    tbuf[1, :, 0, 0] = hc.LAYER_B
+    sigma = O.scene_encoder(hc.W, hc.SCENE)
+    V = np.stack([O.per_layer_h(hc.W, tbuf[k, :, 0, 0], sigma) for k in range(3)])
+    wrong = np.concatenate([V[:2].max(0), V[:2].sum(0) / 3])
+    right = O.set_pool(V[:2])
+    assert not np.allclose(wrong, right)
+    np.testing.assert_array_equal(right, hc.POOL_TWO_LAYERS)
+
+
+def test_oracle_package_exports():
+    for n in oracle.__all__ if hasattr(oracle, "__all__") else []:
+        assert hasattr(oracle, n)
+    assert callable(oracle.render_frame)
