@@ -1,0 +1,209 @@
+/*
+ * glassnet.h — C ABI of the GlassNet per-pixel forward pass on sm_103a.
+ *
+ * Method: Zhang & Simo-Serra, "Neural Scene Baking for Permutation Invariant
+ * Transparency Rendering with Real-time Global Illumination" (arXiv
+ * 2405.19056).  The network (Sec. 3.3-3.4, Fig. 2) in its per-pixel MLP form:
+ *
+ *   sigma = F(s)                          scene encoder, once per scene
+ *   v_k   = h([b_k ; sigma])              shared per-layer network (Eq. 5)
+ *   pool  = [max_k v_k ; mean_k v_k]      symmetric function over valid layers
+ *   r     = rho(pool)   (r = 0 when a pixel has no valid layer)
+ *   y     = B([g ; r ; sigma])            final blending network
+ *   rgb   = sigmoid(R(y))                 rendering network
+ *
+ * Widths: hidden H, latent Z with (H, Z) = (64, 128) or (128, 256); scene
+ * vector 32 floats; transparency layer 12 channels; opaque G-buffer 14
+ * channels; 3 output channels.  Every linear layer is followed by ReLU except
+ * the last one of R, which is followed by a sigmoid.
+ *
+ * Conventions for every entry point:
+ *  - Return value: GN_OK or a negative gn_status.  Nothing is thrown across
+ *    the ABI and nothing aborts.  glassnet_last_error() gives a message for the
+ *    last failure on the calling thread.
+ *  - Arguments are validated on the host before any launch; a call that
+ *    returns an error has enqueued no work.
+ *  - Buffers are owned by the caller; gn_model and gn_latent objects are owned
+ *    by the library and released with the matching free function.
+ *  - Device work is asynchronous on the given stream (0 = legacy default
+ *    stream).  Conditions only the device can see (a layer count above K, an
+ *    exact-sum overflow, a device-side wait that timed out) set sticky bits in
+ *    the model's error word; glassnet_check() synchronises the stream and
+ *    returns them as GN_EINVAL, GN_ERANGE or GN_ETIMEOUT.
+ *  - Image buffers are structure-of-arrays, row-major pixels p = y*w + x:
+ *      gbuf        float [14][h][w]      opaque G-buffer (device)
+ *      tbuf        float [K][12][h][w]   transparency layers (device);
+ *                  slots k >= layer_count[p] are never read into the result
+ *                  and may hold any bits, including NaN
+ *      layer_count uint8 [h][w]          valid layers per pixel, 0..K (device)
+ *      out         float [3][h][w]       RGB in (0, 1) (device)
+ *    All pointers must be 4-byte aligned (uint8 counts: any alignment).
+ */
+#ifndef GLASSNET_H_
+#define GLASSNET_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gn_status {
+  GN_OK = 0,
+  GN_EINVAL = -1,       /* bad argument, or a layer count above K seen on device */
+  GN_ENOMEM = -2,       /* device or host allocation failed */
+  GN_ECUDA = -3,        /* a CUDA runtime call failed */
+  GN_EFORMAT = -4,      /* weight blob: bad magic, version, sizes or checksum */
+  GN_ETIMEOUT = -5,     /* a device-side wait exceeded its time limit */
+  GN_EUNSUPPORTED = -6, /* widths or precision this build does not provide */
+  GN_ERANGE = -7        /* exact set-sum left its fixed-point range (see below) */
+} gn_status;
+
+typedef enum gn_precision {
+  GN_FP32_PLAIN = 0, /* unfused concat form, one kernel per layer, FP32 CUDA cores */
+  GN_BF16_FUSED = 1, /* one fused tcgen05 kernel, BF16 operands, FP32 accumulate */
+  GN_FP8_FUSED = 2   /* fused kernel with E4M3 operands and FP32 scales */
+} gn_precision;
+
+typedef struct gn_model gn_model;   /* device weights of one network */
+typedef struct gn_latent gn_latent; /* one encoded scene: sigma and folded biases */
+
+/* ------------------------------------------------------------------------
+ * Weight blob.  A 48-byte header followed by float32 tensors, each W as
+ * [out][in] row-major (y = W x + b) followed by its b [out], in the order
+ * F1, F2, phi1, phi2, rho, B1, B2, R1, R2 with shapes (concat form):
+ *   F1 [Z][32]   F2 [Z][Z]   phi1 [H][12+Z]   phi2 [H][H]   rho [H][2H]
+ *   B1 [H][14+H+Z]   B2 [H][H]   R1 [H][H]   R2 [3][H]
+ * phi1's input is [layer ; sigma]; B1's input is [gbuf ; r ; sigma]; rho's
+ * input is [max ; mean].  checksum = FNV-1a 64 over the payload bytes.
+ * ---------------------------------------------------------------------- */
+#define GN_BLOB_MAGIC 0x544E4C47u /* bytes "GLNT" */
+#define GN_BLOB_VERSION 1u
+
+typedef struct gn_blob_header {
+  uint32_t magic;
+  uint32_t version;
+  uint32_t hidden;        /* H */
+  uint32_t latent;        /* Z */
+  uint32_t scene_dim;     /* 32 */
+  uint32_t tbuf_channels; /* 12 */
+  uint32_t gbuf_channels; /* 14 */
+  uint32_t out_channels;  /* 3 */
+  uint64_t payload_floats;
+  uint64_t checksum;
+} gn_blob_header;
+
+/*
+ * Validates a weight blob (host memory) and uploads it for one precision.
+ * The network's weights are trained jointly (Sec. 3.4); the blob is the
+ * trained (or synthetic) parameter set.  For GN_BF16_FUSED the weights are
+ * rounded to BF16 (round to nearest even) and packed into the tensor-core
+ * operand layout; GN_FP32_PLAIN keeps them as given.
+ * Errors: GN_EINVAL (null pointers, unknown precision), GN_EFORMAT (size,
+ * magic, version, channel counts or checksum), GN_EUNSUPPORTED ((H, Z) not
+ * (64, 128) or (128, 256)), GN_ENOMEM, GN_ECUDA.  Synchronous.
+ */
+int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_model** out);
+
+/* Widths and precision of a loaded model (any pointer may be NULL). */
+int glassnet_model_info(const gn_model* model, int* hidden, int* latent, int* precision);
+
+/*
+ * Scene encoder F (Sec. 3.4) on one scene vector, and the per-scene folded
+ * biases c_phi = W_phi1[:, 12:] sigma + b_phi1 and c_B = W_B1[:, 14+H:] sigma
+ * + b_B1 (exact algebra of the concat form).  `scene` is 32 floats in host
+ * memory, copied before the call returns.  Allocates the latent (device
+ * memory) and enqueues the encoder on `stream`.
+ * Errors: GN_EINVAL, GN_ENOMEM, GN_ECUDA.
+ */
+int glassnet_encode_scene(gn_model* model, const float* scene, gn_latent** out,
+                          cudaStream_t stream);
+
+/* Re-encodes into an existing latent from a device scene vector (32 floats);
+ * allocates nothing. */
+int glassnet_encode_scene_device(gn_model* model, const float* scene_dev, gn_latent* latent,
+                                 cudaStream_t stream);
+
+/* Copies sigma (Z floats) or the folded biases (H floats each) of a latent
+ * to device buffers, enqueued on `stream`.  Any destination may be NULL. */
+int glassnet_latent_read(const gn_latent* latent, float* sigma_dev, float* c_phi_dev,
+                         float* c_b_dev, cudaStream_t stream);
+
+/*
+ * Renders one frame: the per-pixel network over every pixel (Sec. 3.2-3.4).
+ * K is the number of layer slots in tbuf (0..8); K = 0 renders the
+ * opaque-only path (r = 0) and tbuf may be NULL.  h, w >= 1, h*w < 2^31.
+ * Precision is the model's.  GN_BF16_FUSED: one kernel launch, output
+ * bit-identical under any permutation of each pixel's valid layers.
+ * GN_FP32_PLAIN: one kernel per layer with intermediates in a workspace the
+ * model owns and grows on demand (a growing call synchronises the device);
+ * concurrent FP32 renders of one model on different streams must use
+ * glassnet_render_ws with separate workspaces.
+ * Errors: GN_EINVAL (bad sizes, NULL pointers, misalignment, latent of another
+ * width), GN_ENOMEM, GN_ECUDA.
+ */
+int glassnet_render(const gn_model* model, const gn_latent* latent, const float* gbuf,
+                    const float* tbuf, const uint8_t* layer_count, int K, int h, int w, float* out,
+                    cudaStream_t stream);
+
+/* Workspace bytes glassnet_render_ws needs for this model and frame size
+ * (0 for the fused precisions). */
+int glassnet_workspace_bytes(const gn_model* model, int K, int h, int w, size_t* bytes);
+
+/* glassnet_render with a caller-owned device workspace of at least
+ * glassnet_workspace_bytes() bytes (256-byte aligned). */
+int glassnet_render_ws(const gn_model* model, const gn_latent* latent, const float* gbuf,
+                       const float* tbuf, const uint8_t* layer_count, int K, int h, int w,
+                       float* out, void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * End-to-end render from HOST buffers (same layouts as glassnet_render):
+ * copies gbuf, the K slots of tbuf and the counts to device staging owned by
+ * the model, renders, copies RGB back to `out_host` and synchronises
+ * `stream`.  Host buffers should be page-locked for full copy bandwidth.
+ * Staging grows on demand.  Not safe to call concurrently on one model.
+ */
+int glassnet_render_host(gn_model* model, const gn_latent* latent, const float* gbuf_host,
+                         const float* tbuf_host, const uint8_t* count_host, int K, int h, int w,
+                         float* out_host, cudaStream_t stream);
+
+/* One frame of a batched launch. */
+typedef struct gn_frame {
+  const gn_latent* latent;
+  const float* gbuf;
+  const float* tbuf;
+  const uint8_t* layer_count;
+  int K, h, w;
+  float* out;
+} gn_frame;
+
+/*
+ * Renders n frames of mixed sizes, layer counts and scenes in one persistent
+ * launch of the fused kernel (fused precisions only).  `frames` is host
+ * memory; the descriptor table is copied into a model-owned device buffer,
+ * so one model must not run two batches concurrently.  Each frame's output
+ * equals glassnet_render of that frame alone, bit for bit.
+ */
+int glassnet_render_batch(const gn_model* model, const gn_frame* frames, int n,
+                          cudaStream_t stream);
+
+/*
+ * Synchronises `stream`, then returns and clears the model's device error
+ * bits: GN_EINVAL (a layer count above K), GN_ERANGE (a pixel's exact set-sum
+ * reached 2^11 and lost exactness), GN_ETIMEOUT (a device wait gave up), or
+ * GN_OK.  GN_ECUDA if the stream reports a CUDA error.
+ */
+int glassnet_check(const gn_model* model, cudaStream_t stream);
+
+void glassnet_free_latent(gn_latent* latent);
+void glassnet_free_model(gn_model* model);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* glassnet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLASSNET_H_ */

@@ -1,0 +1,399 @@
+// C ABI of the GlassNet library: argument checks, weight-blob validation and
+// packing, model / latent objects, and dispatch to the kernels.
+#include <cuda_bf16.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(GN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+uint64_t fnv1a64(const uint8_t* p, size_t n) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+// Round-to-nearest-even float -> bf16 bits (host).
+uint16_t bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;  // NaN
+  const uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);
+  return static_cast<uint16_t>(r >> 16);
+}
+
+// Element (n, k) of an N x K operand in the [K/8][N][8] core-matrix layout.
+inline size_t core_idx(int N, int n, int k) {
+  return (static_cast<size_t>(k / 8) * N + n) * 8 + (k % 8);
+}
+
+template <int H>
+std::vector<uint8_t> pack_fused_bf16(const float* w, const gn::WeightIndex& wi) {
+  using L = gn::FusedLayout<H>;
+  std::vector<uint8_t> img(L::bytes, 0);
+  auto put = [&](uint32_t off, int N, int n, int k, float v) {
+    uint16_t b = bf16_rne(v);
+    std::memcpy(img.data() + off + core_idx(N, n, k) * 2, &b, 2);
+  };
+  auto W = [&](int l, int n, int j) { return w[wi.w[l] + static_cast<size_t>(n) * wi.in[l] + j]; };
+  for (int n = 0; n < H; ++n) {
+    for (int k = 0; k < gn::kTC; ++k) put(L::phi1, H, n, k, W(gn::LPHI1, n, k));
+    for (int k = 0; k < H; ++k) put(L::phi2, H, n, k, W(gn::LPHI2, n, k));
+    for (int k = 0; k < 2 * H; ++k) put(L::rho, H, n, k, W(gn::LRHO, n, k));
+    for (int k = 0; k < gn::kGC; ++k) put(L::b1, H, n, k, W(gn::LB1, n, k));
+    for (int k = 0; k < H; ++k) put(L::b1, H, n, 16 + k, W(gn::LB1, n, gn::kGC + k));
+    for (int k = 0; k < H; ++k) put(L::b2, H, n, k, W(gn::LB2, n, k));
+    for (int k = 0; k < H; ++k) put(L::r1, H, n, k, W(gn::LR1, n, k));
+  }
+  for (int n = 0; n < gn::kOut; ++n)
+    for (int k = 0; k < H; ++k) put(L::r2, 16, n, k, W(gn::LR2, n, k));
+  float* bias = reinterpret_cast<float*>(img.data() + L::bias);
+  for (int n = 0; n < H; ++n) {
+    bias[n] = w[wi.b[gn::LPHI2] + n];
+    bias[H + n] = w[wi.b[gn::LRHO] + n];
+    bias[2 * H + n] = w[wi.b[gn::LB2] + n];
+    bias[3 * H + n] = w[wi.b[gn::LR1] + n];
+  }
+  for (int n = 0; n < gn::kOut; ++n) bias[4 * H + n] = w[wi.b[gn::LR2] + n];
+  return img;
+}
+
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+int check_frame(const gn_model* m, const gn_latent* lat, const float* gbuf, const float* tbuf,
+                const uint8_t* cnt, int K, int h, int w, const float* out) {
+  if (!m) return fail(GN_EINVAL, "model is NULL");
+  if (!lat) return fail(GN_EINVAL, "latent is NULL");
+  if (lat->H != m->H || lat->Z != m->Z)
+    return fail(GN_EINVAL, "latent widths (%d, %d) do not match the model (%d, %d)", lat->H,
+                lat->Z, m->H, m->Z);
+  if (K < 0 || K > gn::kMaxK) return fail(GN_EINVAL, "K = %d outside 0..%d", K, gn::kMaxK);
+  if (h < 1 || w < 1) return fail(GN_EINVAL, "frame %d x %d is empty", h, w);
+  if (static_cast<long long>(h) * w * (K > 0 ? K : 1) >= (1ll << 31))
+    return fail(GN_EINVAL, "frame %d x %d x K=%d too large (K*h*w must be < 2^31)", h, w, K);
+  if (!gbuf || !cnt || !out) return fail(GN_EINVAL, "gbuf, layer_count and out must be non-NULL");
+  if (K > 0 && !tbuf) return fail(GN_EINVAL, "tbuf is NULL with K = %d", K);
+  if (!aligned4(gbuf) || !aligned4(out) || (tbuf && !aligned4(tbuf)))
+    return fail(GN_EINVAL, "gbuf, tbuf and out must be 4-byte aligned");
+  return GN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* glassnet_last_error(void) { return g_last_error.c_str(); }
+
+int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_model** out) {
+  if (!blob || !out) return fail(GN_EINVAL, "blob and out must be non-NULL");
+  *out = nullptr;
+  if (precision != GN_FP32_PLAIN && precision != GN_BF16_FUSED && precision != GN_FP8_FUSED)
+    return fail(GN_EINVAL, "unknown precision %d", precision);
+  if (nbytes < sizeof(gn_blob_header))
+    return fail(GN_EFORMAT, "blob of %zu bytes is shorter than its header", nbytes);
+  gn_blob_header hd;
+  std::memcpy(&hd, blob, sizeof(hd));
+  if (hd.magic != GN_BLOB_MAGIC) return fail(GN_EFORMAT, "bad magic 0x%08x", hd.magic);
+  if (hd.version != GN_BLOB_VERSION) return fail(GN_EFORMAT, "unsupported version %u", hd.version);
+  if (hd.scene_dim != gn::kScene || hd.tbuf_channels != gn::kTC || hd.gbuf_channels != gn::kGC ||
+      hd.out_channels != gn::kOut)
+    return fail(GN_EFORMAT, "channel counts (%u, %u, %u, %u) differ from (32, 12, 14, 3)",
+                hd.scene_dim, hd.tbuf_channels, hd.gbuf_channels, hd.out_channels);
+  if (hd.hidden > 4096 || hd.latent > 4096) return fail(GN_EFORMAT, "implausible widths");
+  gn::WeightIndex wi;
+  wi.build(static_cast<int>(hd.hidden), static_cast<int>(hd.latent));
+  if (hd.payload_floats != wi.total)
+    return fail(GN_EFORMAT, "payload holds %llu floats, widths (%u, %u) need %zu",
+                static_cast<unsigned long long>(hd.payload_floats), hd.hidden, hd.latent, wi.total);
+  if (nbytes != sizeof(gn_blob_header) + wi.total * sizeof(float))
+    return fail(GN_EFORMAT, "blob size %zu != %zu", nbytes,
+                sizeof(gn_blob_header) + wi.total * sizeof(float));
+  const uint8_t* payload = static_cast<const uint8_t*>(blob) + sizeof(gn_blob_header);
+  if (fnv1a64(payload, wi.total * sizeof(float)) != hd.checksum)
+    return fail(GN_EFORMAT, "payload checksum mismatch");
+  const bool ok_widths = (hd.hidden == 64 && hd.latent == 128) || (hd.hidden == 128 && hd.latent == 256);
+  if (!ok_widths)
+    return fail(GN_EUNSUPPORTED, "widths (H, Z) = (%u, %u); this build has (64, 128), (128, 256)",
+                hd.hidden, hd.latent);
+  if (precision == GN_FP8_FUSED) return fail(GN_EUNSUPPORTED, "FP8 fused path is not built");
+
+  std::vector<float> w(wi.total);
+  std::memcpy(w.data(), payload, wi.total * sizeof(float));
+  gn_model* m = new (std::nothrow) gn_model();
+  if (!m) return fail(GN_ENOMEM, "host allocation failed");
+  m->H = wi.H;
+  m->Z = wi.Z;
+  m->precision = precision;
+  m->wi = wi;
+  cudaGetDevice(&m->device);
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->w32, wi.total * sizeof(float))) != cudaSuccess) {
+    glassnet_free_model(m);
+    return fail(GN_ENOMEM, "cudaMalloc weights: %s", cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpy(m->w32, w.data(), wi.total * sizeof(float), cudaMemcpyHostToDevice)) !=
+      cudaSuccess) {
+    glassnet_free_model(m);
+    return cuda_fail(e, "upload weights");
+  }
+  if ((e = cudaMalloc(&m->err, 256)) != cudaSuccess ||
+      (e = cudaMemset(m->err, 0, 256)) != cudaSuccess) {
+    glassnet_free_model(m);
+    return fail(GN_ENOMEM, "cudaMalloc error word: %s", cudaGetErrorString(e));
+  }
+  if (precision == GN_BF16_FUSED) {
+    std::vector<uint8_t> img =
+        wi.H == 128 ? pack_fused_bf16<128>(w.data(), wi) : pack_fused_bf16<64>(w.data(), wi);
+    m->fused_bytes = img.size();
+    if ((e = cudaMalloc(&m->fused, img.size())) != cudaSuccess) {
+      glassnet_free_model(m);
+      return fail(GN_ENOMEM, "cudaMalloc packed weights: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpy(m->fused, img.data(), img.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess) {
+      glassnet_free_model(m);
+      return cuda_fail(e, "upload packed weights");
+    }
+  }
+  *out = m;
+  return GN_OK;
+}
+
+int glassnet_model_info(const gn_model* m, int* hidden, int* latent, int* precision) {
+  if (!m) return fail(GN_EINVAL, "model is NULL");
+  if (hidden) *hidden = m->H;
+  if (latent) *latent = m->Z;
+  if (precision) *precision = m->precision;
+  return GN_OK;
+}
+
+int glassnet_encode_scene_device(gn_model* m, const float* scene_dev, gn_latent* lat,
+                                 cudaStream_t s) {
+  if (!m || !scene_dev || !lat) return fail(GN_EINVAL, "model, scene and latent must be non-NULL");
+  if (lat->H != m->H || lat->Z != m->Z) return fail(GN_EINVAL, "latent widths differ from model");
+  cudaError_t e = gn::launch_encode(m->w32, m->wi, scene_dev, lat->d, s);
+  if (e != cudaSuccess) return cuda_fail(e, "encode launch");
+  return GN_OK;
+}
+
+int glassnet_encode_scene(gn_model* m, const float* scene, gn_latent** out, cudaStream_t s) {
+  if (!m || !scene || !out) return fail(GN_EINVAL, "model, scene and out must be non-NULL");
+  *out = nullptr;
+  gn_latent* lat = new (std::nothrow) gn_latent();
+  if (!lat) return fail(GN_ENOMEM, "host allocation failed");
+  lat->H = m->H;
+  lat->Z = m->Z;
+  const size_t n = static_cast<size_t>(m->Z) + 2 * m->H + gn::kScene;
+  cudaError_t e = cudaMalloc(&lat->d, n * sizeof(float));
+  if (e != cudaSuccess) {
+    delete lat;
+    return fail(GN_ENOMEM, "cudaMalloc latent: %s", cudaGetErrorString(e));
+  }
+  // The scene vector travels with the latent; a synchronous copy so the
+  // caller's host buffer may be reused as soon as this returns.
+  if ((e = cudaMemcpyAsync(lat->scene(), scene, gn::kScene * sizeof(float),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    glassnet_free_latent(lat);
+    return cuda_fail(e, "upload scene");
+  }
+  int rc = glassnet_encode_scene_device(m, lat->scene(), lat, s);
+  if (rc != GN_OK) {
+    glassnet_free_latent(lat);
+    return rc;
+  }
+  *out = lat;
+  return GN_OK;
+}
+
+int glassnet_latent_read(const gn_latent* lat, float* sigma, float* c_phi, float* c_b,
+                         cudaStream_t s) {
+  if (!lat) return fail(GN_EINVAL, "latent is NULL");
+  cudaError_t e = cudaSuccess;
+  if (sigma && e == cudaSuccess)
+    e = cudaMemcpyAsync(sigma, lat->d, lat->Z * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (c_phi && e == cudaSuccess)
+    e = cudaMemcpyAsync(c_phi, lat->d + lat->Z, lat->H * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (c_b && e == cudaSuccess)
+    e = cudaMemcpyAsync(c_b, lat->d + lat->Z + lat->H, lat->H * sizeof(float),
+                        cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "latent copy");
+  return GN_OK;
+}
+
+int glassnet_workspace_bytes(const gn_model* m, int K, int h, int w, size_t* bytes) {
+  if (!m || !bytes) return fail(GN_EINVAL, "model and bytes must be non-NULL");
+  if (K < 0 || K > gn::kMaxK || h < 1 || w < 1) return fail(GN_EINVAL, "bad frame size");
+  *bytes = m->precision == GN_FP32_PLAIN ? gn::plain_workspace_bytes(m->H, K, h * w) : 0;
+  return GN_OK;
+}
+
+int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbuf,
+                       const float* tbuf, const uint8_t* cnt, int K, int h, int w, float* out,
+                       void* ws, size_t ws_bytes, cudaStream_t s) {
+  int rc = check_frame(m, lat, gbuf, tbuf, cnt, K, h, w, out);
+  if (rc != GN_OK) return rc;
+  const int P = h * w;
+  cudaError_t e;
+  if (m->precision == GN_FP32_PLAIN) {
+    const size_t need = gn::plain_workspace_bytes(m->H, K, P);
+    if (!ws || ws_bytes < need)
+      return fail(GN_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, need);
+    if (reinterpret_cast<uintptr_t>(ws) & 255u)
+      return fail(GN_EINVAL, "workspace must be 256-byte aligned");
+    e = gn::launch_plain_fp32(m->w32, m->wi, lat->d, gbuf, tbuf, cnt, K, P, out, ws, m->err, s);
+    if (e != cudaSuccess) return cuda_fail(e, "FP32 plain launch");
+    return GN_OK;
+  }
+  gn::FusedParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nframes = 1;
+  p.total_tiles = (P + gn::kTile - 1) / gn::kTile;
+  p.err = m->err;
+  p.f[0] = gn::FusedFrame{gbuf, tbuf, cnt, out, lat->fold(), K, P, 0, 0};
+  e = gn::launch_fused_bf16(m->H, m->fused, p, s);
+  if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+  return GN_OK;
+}
+
+int glassnet_render(const gn_model* m, const gn_latent* lat, const float* gbuf, const float* tbuf,
+                    const uint8_t* cnt, int K, int h, int w, float* out, cudaStream_t s) {
+  int rc = check_frame(m, lat, gbuf, tbuf, cnt, K, h, w, out);
+  if (rc != GN_OK) return rc;
+  if (m->precision != GN_FP32_PLAIN)
+    return glassnet_render_ws(m, lat, gbuf, tbuf, cnt, K, h, w, out, nullptr, 0, s);
+  gn_model* mm = const_cast<gn_model*>(m);
+  const size_t need = gn::plain_workspace_bytes(m->H, K, h * w);
+  if (mm->ws_bytes < need) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before workspace growth");
+    if (mm->ws) cudaFree(mm->ws);
+    mm->ws = nullptr;
+    mm->ws_bytes = 0;
+    if ((e = cudaMalloc(&mm->ws, need)) != cudaSuccess)
+      return fail(GN_ENOMEM, "cudaMalloc workspace (%zu bytes): %s", need, cudaGetErrorString(e));
+    mm->ws_bytes = need;
+  }
+  return glassnet_render_ws(m, lat, gbuf, tbuf, cnt, K, h, w, out, mm->ws, mm->ws_bytes, s);
+}
+
+int glassnet_render_host(gn_model* m, const gn_latent* lat, const float* gbuf_h,
+                         const float* tbuf_h, const uint8_t* cnt_h, int K, int h, int w,
+                         float* out_h, cudaStream_t s) {
+  int rc = check_frame(m, lat, gbuf_h, tbuf_h, cnt_h, K, h, w, out_h);
+  if (rc != GN_OK) return rc;
+  const size_t P = static_cast<size_t>(h) * w;
+  const size_t b_g = P * gn::kGC * 4, b_t = P * gn::kTC * 4 * K, b_o = P * gn::kOut * 4;
+  const size_t b_c = (P + 255) / 256 * 256;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t need = up(b_g) + up(b_t) + up(b_o) + b_c;
+  cudaError_t e;
+  if (m->stage_bytes < need) {
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "synchronise");
+    if (m->stage) cudaFree(m->stage);
+    m->stage = nullptr;
+    m->stage_bytes = 0;
+    if ((e = cudaMalloc(&m->stage, need)) != cudaSuccess)
+      return fail(GN_ENOMEM, "cudaMalloc staging (%zu bytes): %s", need, cudaGetErrorString(e));
+    m->stage_bytes = need;
+  }
+  uint8_t* base = static_cast<uint8_t*>(m->stage);
+  float* d_g = reinterpret_cast<float*>(base);
+  float* d_t = reinterpret_cast<float*>(base + up(b_g));
+  float* d_o = reinterpret_cast<float*>(base + up(b_g) + up(b_t));
+  uint8_t* d_c = base + up(b_g) + up(b_t) + up(b_o);
+  if ((e = cudaMemcpyAsync(d_g, gbuf_h, b_g, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (K > 0 && (e = cudaMemcpyAsync(d_t, tbuf_h, b_t, cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+      (e = cudaMemcpyAsync(d_c, cnt_h, P, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "host to device copy");
+  rc = glassnet_render(m, lat, d_g, K > 0 ? d_t : nullptr, d_c, K, h, w, d_o, s);
+  if (rc != GN_OK) return rc;
+  if ((e = cudaMemcpyAsync(out_h, d_o, b_o, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "device to host copy");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "synchronise");
+  return GN_OK;
+}
+
+int glassnet_render_batch(const gn_model* m, const gn_frame* frames, int n, cudaStream_t s) {
+  if (!m || !frames) return fail(GN_EINVAL, "model and frames must be non-NULL");
+  if (n < 1 || n > gn::kMaxBatch) return fail(GN_EINVAL, "batch of %d frames outside 1..%d", n, gn::kMaxBatch);
+  if (m->precision == GN_FP32_PLAIN) return fail(GN_EUNSUPPORTED, "batched launch needs a fused precision");
+  gn::FusedParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nframes = n;
+  p.err = m->err;
+  long long tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    const gn_frame& f = frames[i];
+    int rc = check_frame(m, f.latent, f.gbuf, f.tbuf, f.layer_count, f.K, f.h, f.w, f.out);
+    if (rc != GN_OK) return fail(rc, "frame %d: %s", i, g_last_error.c_str());
+    const int P = f.h * f.w;
+    p.f[i] = gn::FusedFrame{f.gbuf, f.tbuf, f.layer_count, f.out, f.latent->fold(), f.K, P,
+                            static_cast<int>(tiles), 0};
+    tiles += (P + gn::kTile - 1) / gn::kTile;
+    if (tiles >= (1ll << 31)) return fail(GN_EINVAL, "batch too large");
+  }
+  p.total_tiles = static_cast<int>(tiles);
+  cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s);
+  if (e != cudaSuccess) return cuda_fail(e, "batched fused launch");
+  return GN_OK;
+}
+
+int glassnet_check(const gn_model* m, cudaStream_t s) {
+  if (!m) return fail(GN_EINVAL, "model is NULL");
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "stream");
+  uint32_t bits = 0;
+  if ((e = cudaMemcpy(&bits, m->err, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "read error word");
+  if (bits) {
+    if ((e = cudaMemset(m->err, 0, 4)) != cudaSuccess) return cuda_fail(e, "clear error word");
+  }
+  if (bits & gn::kErrTimeout) return fail(GN_ETIMEOUT, "a device-side wait timed out");
+  if (bits & gn::kErrCount) return fail(GN_EINVAL, "a layer count exceeded K");
+  if (bits & gn::kErrRange) return fail(GN_ERANGE, "an exact set-sum left its fixed-point range");
+  return GN_OK;
+}
+
+void glassnet_free_latent(gn_latent* lat) {
+  if (!lat) return;
+  if (lat->d) cudaFree(lat->d);
+  delete lat;
+}
+
+void glassnet_free_model(gn_model* m) {
+  if (!m) return;
+  if (m->w32) cudaFree(m->w32);
+  if (m->fused) cudaFree(m->fused);
+  if (m->err) cudaFree(m->err);
+  if (m->ws) cudaFree(m->ws);
+  if (m->stage) cudaFree(m->stage);
+  delete m;
+}
+
+}  // extern "C"

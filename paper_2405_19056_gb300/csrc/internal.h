@@ -1,0 +1,118 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/glassnet.h"
+
+namespace gn {
+
+constexpr int kScene = 32;     // scene-parameter vector
+constexpr int kTC = 12;        // transparency-layer channels
+constexpr int kGC = 14;        // opaque G-buffer channels
+constexpr int kOut = 3;        // RGB
+constexpr int kMaxK = 8;       // layer slots per pixel
+constexpr int kTile = 128;     // pixels per fused tile (tcgen05 M)
+
+// Sticky device error bits (model error word).
+constexpr uint32_t kErrCount = 1u;    // layer count above K
+constexpr uint32_t kErrRange = 2u;    // exact set-sum left its fixed-point range
+constexpr uint32_t kErrTimeout = 4u;  // a device wait gave up
+
+// Linear layers in blob order.
+enum Layer { LF1 = 0, LF2, LPHI1, LPHI2, LRHO, LB1, LB2, LR1, LR2, kLayers };
+
+// Offsets (in floats) of each W and b inside the concat-form f32 weights.
+struct WeightIndex {
+  int H = 0, Z = 0;
+  size_t w[kLayers] = {}, b[kLayers] = {};
+  int out[kLayers] = {}, in[kLayers] = {};
+  size_t total = 0;
+  void build(int H_, int Z_);
+};
+
+// Packed operand image of the fused kernels: B operands (weights, [N][K]) in
+// the K-major no-swizzle core-matrix layout [K/8][N][8] bf16, then the f32
+// biases that are added in epilogues.  The same bytes are copied verbatim
+// into each CTA's shared memory.
+//   phi1 [16][H]    K = 12 channels, 2 folded-bias columns (per scene), 2 zero
+//   phi2 [H][H]     rho [2H][H]  (K = [max ; mean])
+//   B1   [16+H][H]  K = 14 channels, 2 folded-bias columns, then r (H)
+//   B2, R1 [H][H]   R2 [H][16]   (N = 3 outputs + 13 zero rows)
+//   bias f32: phi2[H], rho[H], B2[H], R1[H], R2[16]
+template <int H>
+struct FusedLayout {
+  static constexpr int KT = 16;
+  static constexpr int KB1 = 16 + H;
+  static constexpr int NR2 = 16;
+  static constexpr uint32_t phi1 = 0;
+  static constexpr uint32_t phi2 = phi1 + KT * H * 2;
+  static constexpr uint32_t rho = phi2 + H * H * 2;
+  static constexpr uint32_t b1 = rho + 2 * H * H * 2;
+  static constexpr uint32_t b2 = b1 + KB1 * H * 2;
+  static constexpr uint32_t r1 = b2 + H * H * 2;
+  static constexpr uint32_t r2 = r1 + H * H * 2;
+  static constexpr uint32_t bias = r2 + H * NR2 * 2;
+  static constexpr uint32_t bias_phi2 = bias;
+  static constexpr uint32_t bias_rho = bias + H * 4;
+  static constexpr uint32_t bias_b2 = bias + 2 * H * 4;
+  static constexpr uint32_t bias_r1 = bias + 3 * H * 4;
+  static constexpr uint32_t bias_r2 = bias + 4 * H * 4;
+  static constexpr uint32_t bytes = bias + (4 * H + 16) * 4;
+};
+
+// One frame as the fused kernel sees it.
+struct FusedFrame {
+  const float* gbuf;
+  const float* tbuf;
+  const uint8_t* counts;
+  float* out;
+  const float* fold;  // c_phi [H] then c_B [H]
+  int K;
+  int P;      // pixels
+  int tile0;  // first global tile index of this frame
+  int pad;
+};
+
+constexpr int kMaxBatch = 64;
+
+struct FusedParams {
+  FusedFrame f[kMaxBatch];
+  int nframes;
+  int total_tiles;
+  uint32_t* err;
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_encode(const float* w32, const WeightIndex& wi, const float* scene_dev,
+                          float* latent_dev, cudaStream_t s);
+cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& p, cudaStream_t s);
+size_t plain_workspace_bytes(int H, int K, int P);
+cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const float* latent,
+                              const float* gbuf, const float* tbuf, const uint8_t* counts, int K,
+                              int P, float* out, void* ws, uint32_t* err, cudaStream_t s);
+int device_sm_count();
+
+}  // namespace gn
+
+struct gn_model {
+  int H = 0, Z = 0, precision = 0, device = 0;
+  gn::WeightIndex wi;
+  float* w32 = nullptr;     // concat-form f32 weights (device)
+  void* fused = nullptr;    // packed operand image (device)
+  size_t fused_bytes = 0;
+  uint32_t* err = nullptr;  // sticky error word (device)
+  void* ws = nullptr;       // FP32 plain workspace (device), grown on demand
+  size_t ws_bytes = 0;
+  void* stage = nullptr;    // glassnet_render_host staging (device)
+  size_t stage_bytes = 0;
+};
+
+struct gn_latent {
+  int H = 0, Z = 0;
+  // device: sigma [Z], c_phi [H], c_B [H], scene [32]
+  float* d = nullptr;
+  float* scene() const { return d + Z + 2 * H; }
+  float* fold() const { return d + Z; }
+};

@@ -1,0 +1,115 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point the header declares, and rejects bad arguments and bad
+weight blobs before touching the device."""
+import ctypes
+import os
+import re
+import struct
+
+import numpy as np
+import pytest
+
+from gen import synth
+from paper_2405_19056_gb300 import glassnet as gl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "glassnet.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return gl.load_library()
+
+
+def _declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(glassnet_\w+)\s*\(", text)))
+
+
+def test_header_declarations_are_bound():
+    decl = _declared_symbols()
+    assert len(decl) >= 14
+    assert set(decl) == set(gl._SIGNATURES), set(decl) ^ set(gl._SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_last_error_starts_empty_or_string(lib):
+    assert isinstance(gl.glassnet_last_error(), str)
+
+
+def _blob(widths=synth.BASE_WIDTHS):
+    return gl.pack_blob(synth.make_weights(widths, seed=0))
+
+
+def _load(lib, blob, precision=gl.GN_BF16_FUSED):
+    out = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    rc = lib.glassnet_load_weights(buf, len(blob), precision, ctypes.byref(out))
+    return rc, out.value
+
+
+def test_blob_header_layout():
+    blob = _blob()
+    fields = struct.unpack(gl.HEADER_FMT, blob[:48])
+    assert fields[0] == 0x544E4C47 and blob[:4] == b"GLNT"
+    assert fields[1:8] == (1, 64, 128, 32, 12, 14, 3)
+    assert fields[8] * 4 == len(blob) - 48
+
+
+def test_blob_checksum_is_fnv1a64():
+    blob = _blob()
+    payload = blob[48:]
+    h = 0xCBF29CE484222325
+    for byte in payload:
+        h ^= byte
+        h = (h * 0x100000001B3) % (1 << 64)
+    assert struct.unpack("<Q", blob[40:48])[0] == h
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda b: b[:20], gl.GN_EFORMAT),                                   # truncated header
+    (lambda b: b"XXXX" + b[4:], gl.GN_EFORMAT),                          # magic
+    (lambda b: b[:4] + struct.pack("<I", 9) + b[8:], gl.GN_EFORMAT),     # version
+    (lambda b: b[:-4], gl.GN_EFORMAT),                                   # truncated payload
+    (lambda b: b[:100] + bytes([b[100] ^ 1]) + b[101:], gl.GN_EFORMAT),  # checksum
+    (lambda b: b[:16] + struct.pack("<I", 13) + b[20:], gl.GN_EFORMAT),  # scene dim
+])
+def test_corrupt_blobs_rejected(lib, mutate, code):
+    rc, handle = _load(lib, mutate(_blob()))
+    assert rc == code and not handle
+    assert gl.glassnet_last_error()
+
+
+def test_unsupported_widths_rejected(lib):
+    w = synth.make_weights(synth.Widths(hidden=32, latent=64), seed=0)
+    rc, handle = _load(lib, gl.pack_blob(w))
+    assert rc == gl.GN_EUNSUPPORTED and not handle
+
+
+def test_unknown_precision_rejected(lib):
+    rc, _ = _load(lib, _blob(), precision=7)
+    assert rc == gl.GN_EINVAL
+
+
+def test_null_arguments_rejected(lib):
+    out = ctypes.c_void_p()
+    assert lib.glassnet_load_weights(None, 10, 1, ctypes.byref(out)) == gl.GN_EINVAL
+    assert lib.glassnet_render(None, None, None, None, None, 1, 8, 8, None, None) == gl.GN_EINVAL
+    assert lib.glassnet_render_batch(None, None, 1, None) == gl.GN_EINVAL
+    assert lib.glassnet_encode_scene(None, None, ctypes.byref(out), None) == gl.GN_EINVAL
+    assert lib.glassnet_check(None, None) == gl.GN_EINVAL
+    n = ctypes.c_size_t()
+    assert lib.glassnet_workspace_bytes(None, 1, 1, 1, ctypes.byref(n)) == gl.GN_EINVAL
+    lib.glassnet_free_model(None)
+    lib.glassnet_free_latent(None)
+
+
+def test_python_binding_raises_with_message(lib):
+    with pytest.raises(gl.GlassNetError) as ei:
+        gl.glassnet_load_weights(b"short", gl.GN_BF16_FUSED)
+    assert ei.value.code == gl.GN_EFORMAT
