@@ -197,6 +197,36 @@ int glassnet_render_batch(const gn_model* model, const gn_frame* frames, int n,
  */
 int glassnet_check(const gn_model* model, cudaStream_t stream);
 
+/*
+ * The FP32 plain render with no device allocation.  The paper has no
+ * counterpart; this is an ABI convenience.  glassnet_render grows a
+ * model-owned workspace with cudaMalloc (synchronising the device) when it
+ * meets a larger frame, and glassnet_render_ws needs a workspace allocated by
+ * the caller.  Callers that cannot allocate device memory at render time (a
+ * program whose device memory is all handed out up front by its own pooling
+ * allocator, a frame loop that must never block in the allocator) use this
+ * entry point instead: its scratch is a 48 MiB array in device memory that
+ * the library defines statically, so every GPU that loads the library holds
+ * those 48 MiB until the process exits.
+ *  - The model must have precision GN_FP32_PLAIN.  Other arguments and the
+ *    result are those of glassnet_render.
+ *  - Frames whose plain-path scratch (glassnet_workspace_bytes) exceeds
+ *    48 MiB are rejected with GN_EINVAL and a message giving both sizes, e.g.
+ *    base widths K = 4 fit up to about 14,000 pixels, doubled widths K = 8 up
+ *    to about 4,400 pixels.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.  Later calls only launch kernels.
+ *  - All calls on a device share the one array, and it keeps the previous
+ *    call's contents (every call overwrites all scratch it reads).  Calls
+ *    whose work overlaps on the GPU (different streams, no ordering between
+ *    them) race on the scratch and give wrong results: serialise them.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ */
+int glassnet_render_fp32_static(const gn_model* model, const gn_latent* latent, const float* gbuf,
+                                const float* tbuf, const uint8_t* layer_count, int K, int h, int w,
+                                float* out, cudaStream_t stream);
+
 void glassnet_free_latent(gn_latent* latent);
 void glassnet_free_model(gn_model* model);
 

@@ -105,6 +105,11 @@ int check_frame(const gn_model* m, const gn_latent* lat, const float* gbuf, cons
 
 }  // namespace
 
+namespace gn {
+// Records an error message for glassnet_last_error() from other translation units.
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace gn
+
 extern "C" {
 
 const char* glassnet_last_error(void) { return g_last_error.c_str(); }

@@ -48,6 +48,7 @@ _SIGNATURES = {
     "glassnet_render_host": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P]),
     "glassnet_render_batch": (_I, [_P, _P, _I, _P]),
     "glassnet_check": (_I, [_P, _P]),
+    "glassnet_render_fp32_static": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P]),
     "glassnet_free_latent": (None, [_P]),
     "glassnet_free_model": (None, [_P]),
     "glassnet_last_error": (ctypes.c_char_p, []),
@@ -198,6 +199,14 @@ def glassnet_render_batch(model, frames, stream=None):
         arr[i] = GnFrame(f["latent"], _ptr(f["gbuf"]), _ptr(f.get("tbuf")), _ptr(f["layer_count"]),
                          f["K"], f["h"], f["w"], _ptr(f["out"]))
     _check(_lib().glassnet_render_batch(model, arr, len(frames), _stream(stream)))
+
+
+def glassnet_render_fp32_static(model, latent, gbuf, tbuf, layer_count, K, h, w, out,
+                                stream=None):
+    """FP32 plain render whose scratch is the library's static device array (no allocation)."""
+    _check(_lib().glassnet_render_fp32_static(model, latent, _ptr(gbuf), _ptr(tbuf),
+                                              _ptr(layer_count), K, h, w, _ptr(out),
+                                              _stream(stream)))
 
 
 def glassnet_check(model, stream=None):
