@@ -134,7 +134,7 @@ int glassnet_latent_read(const gn_latent* latent, float* sigma_dev, float* c_phi
 /*
  * Renders one frame: the per-pixel network over every pixel (Sec. 3.2-3.4).
  * K is the number of layer slots in tbuf (0..8); K = 0 renders the
- * opaque-only path (r = 0) and tbuf may be NULL.  h, w >= 1, h*w < 2^31.
+ * opaque-only path (r = 0) and tbuf may be NULL.  h, w >= 1, 12*max(K,1)*h*w < 2^31.
  * Precision is the model's.  GN_BF16_FUSED: one kernel launch, output
  * bit-identical under any permutation of each pixel's valid layers.
  * GN_FP32_PLAIN: one kernel per layer with intermediates in a workspace the

@@ -5,8 +5,8 @@
 // biases (c_phi, c_B) that enter the GEMMs through two constant-one input
 // columns (a hi/lo BF16 split of each bias, so the fold keeps ~16 bits):
 //   for each layer slot k < max count in the tile:
-//     U   = ReLU([t_k, 1, 1, 0, 0] W_phi1')              (K = 16)
-//     V   = U W_phi2^T + b_phi2                          (K = H)
+//     U   = ReLU([t_k, 1, 1, 0, 0] W_phi1'^T)            (K = 16)
+//     V   = [U, 1, 1, 0..] [W_phi2, b_phi2 hi, lo]^T     (K = H + 16)
 //     max = max(max, V);  sum += ReLU(V)   for pixels with k < c_p
 //   pool  = [max ; mean], mean = sum / c_p               (exact, see below)
 //   r     = ReLU(pool W_rho^T + b_rho), r = 0 if c_p = 0
@@ -15,20 +15,40 @@
 //   rgb   = sigmoid(q W_R2^T + b_R2)                     (N padded to 16)
 //
 // Exact, order-independent set pooling: the running max starts at 0 (which is
-// also the ReLU), and the sum is a fixed-point accumulator held in an FP32
-// significand: s starts at 2^11 and every addition is rounded toward zero, so
-// while s < 2^12 each add contributes exactly floor(ReLU(v) / 2^-12) quanta,
-// whatever the order of the layers.  mean = (s - 2^11 + c 2^-13) / c (the
-// c 2^-13 term centres the truncation).  A pixel whose sum reaches 2^12 sets
-// the range error bit.  Hence the output is bit-identical under any
-// permutation of a pixel's valid layers.
+// also the ReLU) and is kept as bf16 pairs (rounding is monotonic, so the max
+// of the rounded values is the rounded max that the rho GEMM consumes); the
+// sum is a fixed-point accumulator held in an FP32 significand: s starts at
+// 2^11 and every addition is rounded toward zero, so while s < 2^12 each add
+// contributes exactly floor(ReLU(v) / 2^-12) quanta, whatever the order of the
+// layers.  mean = (s - 2^11 + c 2^-13) * (1/c) (the c 2^-13 term centres the
+// truncation).  A pixel whose sum reaches 2^12 sets the range error bit.
+// Hence the output is bit-identical under any permutation of a pixel's valid
+// layers.
 //
-// Threads: 16 warps.  Warp w serves TMEM lane quadrant q = w % 4 (pixel rows
-// 32q..32q+31) and output-column chunk g = w / 4 (H/4 columns), so the 128x H
-// accumulator of every GEMM is read by all 16 warps in parallel.  Thread 0
-// issues the MMAs.  Operands: weights resident in shared memory (copied once
-// per CTA by bulk copies), activations and inputs in TMEM (A operand from
-// TMEM), accumulators in TMEM.
+// Warp roles (11 warps, at most three per SM sub-partition, so every thread
+// may hold 168 registers):
+//  - warps 0-7 (epilogue): warp w serves TMEM lane quadrant q = w % 4 (pixel
+//    rows 32q..32q+31) and accumulator columns [g H/2, (g+1) H/2), g = w / 4.
+//    They run every epilogue (ReLU, pooling, biases, sigmoid) and hold the
+//    pool state (H/2 sums and H/4 packed maxima per thread) in registers.
+//  - warp 8 (MMA): allocates TMEM, patches the per-scene bias rows, issues
+//    every tcgen05.mma from lane 0.
+//  - warps 9-10 (loaders, 64 pixel rows each): read each tile's layer counts,
+//    G-buffer and layers (coalesced: 32 consecutive pixels per load
+//    instruction), convert them to BF16 and write the shared-memory A
+//    operands, running up to two layer slots ahead of the tensor core.
+// Hand-offs are mbarriers: the MMA warp commits accumulators and consumed
+// operands (tcgen05.commit); the epilogue warps arrive once per warp when an
+// A operand is written or an accumulator has been read; the loader arrives
+// when an operand is filled.  phi1(k+1) is issued before phi2(k), so its
+// epilogue overlaps phi2(k) on the tensor core.
+//
+// Buffers: phi2's accumulator is double buffered in TMEM (slot k uses buffer k
+// mod 2); U is double buffered in TMEM; the two layer operands of phi1, the
+// constant-one operand of phi2's bias and B1's G-buffer block live in shared
+// memory next to the weights.  Every device-side wait gives up after 1 s,
+// sets the timeout error bit and makes all warps leave through the common
+// exit.
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -37,24 +57,50 @@
 namespace gn {
 namespace {
 
-constexpr int kThreadsF = 512;
+constexpr int kEpiWarps = 8;
+constexpr int kMmaWarp = 8;
+constexpr int kLoadWarp0 = 9;  // warps 9 and 10
+constexpr int kThreadsF = 11 * 32;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per device-side wait
 constexpr float kSumBase = 2048.0f;          // 2^11: quantum 2^-12 in [2^11, 2^12)
 constexpr float kSumLimit = 4096.0f;
 constexpr float kHalfQuantum = 1.0f / 8192.0f;
 
-// TMEM column map (128 lanes x NCOLS columns of 32 bits).
+// mbarrier slots.
+enum : int {
+  B_W = 0,      // weights copied (transaction count)
+  B_IN = 1,     // an A operand in TMEM is complete (epilogue warps arrive)
+  B_D1 = 2,     // phi1 accumulator ready (commit)
+  B_DR2 = 3,    // R2 accumulator ready (commit)
+  B_DP = 4,     // per-pixel layer accumulator ready (commit)
+  B_AG_F = 5,   // B1's G-buffer operand written (loader)
+  B_AG_E = 6,   // B1's G-buffer operand consumed (commit)
+  B_D2 = 7,     // + buffer: phi2 accumulator ready (commit)
+  B_E2 = 9,     // + buffer: phi2 accumulator read (epilogue warps arrive)
+  B_AT_F = 11,  // + buffer: layer operand written (loader)
+  B_AT_E = 13,  // + buffer: layer operand consumed (commit)
+  B_TILE = 15,  // + tile parity: counts and slot count published (loader)
+  B_COUNT = 17
+};
+
+// TMEM column map (128 lanes x 512 columns of 32 bits).  The per-pixel
+// layers reuse the phi-loop regions once the loop is over.
 template <int H>
 struct TMap {
-  static constexpr uint32_t DA = 0;               // D: phi1, rho, B2 (H cols)
-  static constexpr uint32_t DB = H;               // D: phi2, B1, R1 (H cols)
-  static constexpr uint32_t AX = 2 * H;           // A: U, pool (H cols), y, y2, q
-  static constexpr uint32_t AT = 3 * H;           // A: transparency layer (8 cols)
-  static constexpr uint32_t AG = 3 * H + 8;       // A: [g, 1, 1] (8 cols) ...
-  static constexpr uint32_t AR = 3 * H + 16;      // ... followed by r (H/2 cols)
-  static constexpr uint32_t DR2 = 3 * H + 16 + H / 2;  // D: R2 (16 cols)
-  static constexpr uint32_t NCOLS = H == 128 ? 512 : 256;
-  static_assert(DR2 + 16 <= NCOLS, "TMEM map overflows the allocation");
+  static constexpr uint32_t D1 = 0;              // phi1 D; per-pixel D (rho, B1, B2, R1)
+  static constexpr uint32_t D2A = H;             // phi2 D, even slots
+  static constexpr uint32_t D2B = 2 * H;         // phi2 D, odd slots
+  static constexpr uint32_t AU0 = 3 * H;         // phi2 A (U), double buffered
+  static constexpr uint32_t AU1 = 3 * H + H / 2;
+  // per-pixel stage
+  static constexpr uint32_t APOOL = AU0;         // rho A: [max ; mean] (H columns)
+  static constexpr uint32_t AR = D2A;            // B1 A after its G-buffer block: r
+  static constexpr uint32_t DR2 = D2A + H / 2;   // R2 D (16 columns)
+  static constexpr uint32_t AY = D2B;            // B2 A (y), R2 A (q)
+  static constexpr uint32_t AY2 = D2B + H / 2;   // R1 A (y2)
+  static constexpr uint32_t NCOLS = 512;
+  static_assert(AU1 + H / 2 <= NCOLS, "TMEM map overflows the allocation");
+  static_assert(DR2 % 16 == 0 && DR2 + 16 <= D2B, "R2 accumulator misplaced");
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) {
@@ -65,43 +111,250 @@ __device__ __forceinline__ float bf16_value(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
 }
 
-// D = A (TMEM, K/2 columns from a_col) x B^T (smem [K/8][N][8] bf16 at b_smem).
-__device__ __forceinline__ void issue_gemm(uint32_t tbase, uint32_t d_col, uint32_t a_col,
-                                           uint32_t b_smem, int N, int K, uint32_t idesc) {
-  for (int ks = 0; ks < K / 16; ++ks) {
-    const uint64_t bdesc = make_sdesc(b_smem + ks * 2 * N * 16, N * 16, 128);
-    mma_f16_ts(tbase + d_col, tbase + a_col + ks * 8, bdesc, idesc, ks > 0 ? 1u : 0u);
+// (a0, a1) + (b0, b1), round to nearest even / toward zero, two lanes per op.
+__device__ __forceinline__ void fadd2_rn(float& r0, float& r1, float a0, float a1, float b0,
+                                         float b1) {
+  asm("{.reg .b64 p, q, r;\n\tmov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
+      "add.rn.f32x2 r, p, q;\n\tmov.b64 {%0, %1}, r;}"
+      : "=f"(r0), "=f"(r1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fadd2_rz(float& r0, float& r1, float a0, float a1, float b0,
+                                         float b1) {
+  asm("{.reg .b64 p, q, r;\n\tmov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
+      "add.rz.f32x2 r, p, q;\n\tmov.b64 {%0, %1}, r;}"
+      : "=f"(r0), "=f"(r1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ uint32_t bmax2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("max.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                       uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+
+// Bounded wait shared by a whole warp: every lane waits, then the warp agrees.
+// On a timeout the CTA-wide abort flag is raised and every later wait fails
+// at once, so all warps reach the common exit.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  bool ok = mbar_try_wait(bar, parity);
+  if (!ok) {
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+      if (mbar_try_wait(bar, parity)) {
+        ok = true;
+        break;
+      }
+      if (*abort_flag) break;
+      if (globaltimer_ns() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        break;
+      }
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+// D (+)= A (TMEM, K/2 columns from a_tmem) x B^T, B stored [K/8][N][8] bf16
+// and described by `d0` (its K = 0 column).  Each K step of 16 advances the
+// start address by two core-matrix columns (2 N 16 bytes), i.e. (2 N 16) >> 4
+// in the descriptor's 14-bit address field (shared-memory addresses stay
+// < 256 KB, so the field never carries into the next one).  Fully unrolled:
+// the issuing thread blocks until the tensor core accepts each MMA, so
+// nothing but the MMA itself may sit between two issues.
+template <int N, int K>
+__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, uint32_t a_tmem, uint64_t d0,
+                                           uint32_t idesc, bool accumulate = false) {
+  constexpr uint64_t step = static_cast<uint64_t>((2 * N * 16) >> 4);
+#pragma unroll
+  for (int ks = 0; ks < K / 16; ++ks)
+    mma_f16_ts(d_tmem, a_tmem + ks * 8, d0 + step * ks, idesc, (ks > 0 || accumulate) ? 1u : 0u);
+}
+
+// Frame that owns global tile `tile`.
+__device__ __forceinline__ const FusedFrame& frame_of(const FusedParams& prm, int tile) {
+  int fi = 0;
+  while (fi + 1 < prm.nframes && tile >= prm.f[fi + 1].tile0) ++fi;
+  return prm.f[fi];
+}
+
+// ---------------------------------------------------------------- loader
+// Shared-memory bookkeeping written by the loader warps.
+struct LoaderShared {
+  uint8_t cnt[2][kTile];  // layer counts of a tile (by tile parity), clamped to K
+  int ns[2][2];           // per loader warp: max count over its 64 rows
+};
+
+constexpr int kLoadWarps = 2;
+constexpr int kRowsPerLoadLane = kTile / (kLoadWarps * 32);  // 2
+
+// Layer k of rows row0 + 32 i (i < kRowsPerLoadLane): 12 channels each, zeros
+// where the slot is not valid.  One load instruction covers 32 consecutive
+// pixels of one channel plane.  Element offsets fit in 32 bits: the host
+// requires 12 K h w < 2^31.
+__device__ __forceinline__ void load_slot(const FusedFrame& F, int p0, int row0, int k,
+                                          const int (&cnt)[kRowsPerLoadLane],
+                                          float (&x)[kRowsPerLoadLane][kTC]) {
+  const uint32_t P = static_cast<uint32_t>(F.P);
+#pragma unroll
+  for (int i = 0; i < kRowsPerLoadLane; ++i) {
+    const uint32_t pix = static_cast<uint32_t>(p0 + row0 + 32 * i);
+    const bool v = k < cnt[i];
+    const uint32_t o = static_cast<uint32_t>(k) * kTC * P + pix;
+#pragma unroll
+    for (int ch = 0; ch < kTC; ++ch) x[i][ch] = v ? __ldg(F.tbuf + (o + ch * P)) : 0.0f;
   }
 }
 
+// Writes rows row0 + 32 i of a [2][128][8] bf16 operand: K entries 0..11 from
+// x, then the constant-one columns [1, 1, 0, 0].
+__device__ __forceinline__ void store_slot(uint32_t base, int row0,
+                                           const float (&x)[kRowsPerLoadLane][kTC]) {
+  const uint32_t one = pack_bf16(1.0f, 1.0f);
+#pragma unroll
+  for (int i = 0; i < kRowsPerLoadLane; ++i) {
+    const uint32_t r = base + static_cast<uint32_t>(row0 + 32 * i) * 16u;
+    sts128(r, pack_bf16(x[i][0], x[i][1]), pack_bf16(x[i][2], x[i][3]), pack_bf16(x[i][4], x[i][5]),
+           pack_bf16(x[i][6], x[i][7]));
+    sts128(r + 2048u, pack_bf16(x[i][8], x[i][9]), pack_bf16(x[i][10], x[i][11]), one, 0u);
+  }
+}
+
+// Loader warps: per tile, publish the counts and the slot count, then fill the
+// layer operands slot by slot (two buffers, released by the MMAs that read
+// them) and B1's G-buffer operand (released by B1 of the previous tile).
+template <int H>
+__device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sbase,
+                                            uint32_t bar_base, LoaderShared& ls,
+                                            volatile int* abort_flag, int li, int lane) {
+  using L = FusedLayout<H>;
+  auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
+  const int row0 = li * 64 + lane;
+  uint32_t lc = 0, n_ag = 0, tb = 0;
+  for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++tb) {
+    const FusedFrame& F = frame_of(prm, tile);
+    const int p0 = (tile - F.tile0) * kTile;
+    int cnt[kRowsPerLoadLane];
+    int cmax = 0;
+#pragma unroll
+    for (int i = 0; i < kRowsPerLoadLane; ++i) {
+      const int pix = p0 + row0 + 32 * i;
+      int c = pix < F.P ? static_cast<int>(F.counts[pix]) : 0;
+      if (c > F.K) {
+        atomicOr(prm.err, kErrCount);
+        c = F.K;
+      }
+      cnt[i] = c;
+      cmax = max(cmax, c);
+      ls.cnt[tb & 1][row0 + 32 * i] = static_cast<uint8_t>(c);
+    }
+    const int wmax = __reduce_max_sync(0xffffffffu, cmax);
+    if (lane == 0) ls.ns[tb & 1][li] = wmax;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar(B_TILE + (tb & 1)));
+    // the tile's slot count is the max over both loader warps
+    if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
+    const int ns = max(ls.ns[tb & 1][0], ls.ns[tb & 1][1]);
+
+    // G-buffer block [g0..g13, 1, 1] of rows row0 + 32 i, loads in flight now
+    float gv[kRowsPerLoadLane][kGC];
+    {
+      const uint32_t P = static_cast<uint32_t>(F.P);
+#pragma unroll
+      for (int i = 0; i < kRowsPerLoadLane; ++i) {
+        const int pix = p0 + row0 + 32 * i;
+        const bool v = pix < F.P;
+#pragma unroll
+        for (int ch = 0; ch < kGC; ++ch)
+          gv[i][ch] = v ? __ldg(F.gbuf + (static_cast<uint32_t>(ch) * P + pix)) : 0.0f;
+      }
+    }
+    auto put_ag = [&]() -> bool {
+      if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
+      ++n_ag;
+      const uint32_t one = pack_bf16(1.0f, 1.0f);
+#pragma unroll
+      for (int i = 0; i < kRowsPerLoadLane; ++i) {
+        const uint32_t r = sbase + L::ag + static_cast<uint32_t>(row0 + 32 * i) * 16u;
+        sts128(r, pack_bf16(gv[i][0], gv[i][1]), pack_bf16(gv[i][2], gv[i][3]),
+               pack_bf16(gv[i][4], gv[i][5]), pack_bf16(gv[i][6], gv[i][7]));
+        sts128(r + 2048u, pack_bf16(gv[i][8], gv[i][9]), pack_bf16(gv[i][10], gv[i][11]),
+               pack_bf16(gv[i][12], gv[i][13]), one);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_AG_F));
+      return true;
+    };
+
+    float x[kRowsPerLoadLane][kTC], y[kRowsPerLoadLane][kTC];
+    if (ns > 0) load_slot(F, p0, row0, 0, cnt, x);
+    const int ag_after = min(ns, 2) - 1;  // B1's operand after the first slots
+    if (ag_after < 0 && !put_ag()) return;
+    for (int k = 0; k < ns; ++k, ++lc) {
+      if (k + 1 < ns) load_slot(F, p0, row0, k + 1, cnt, y);
+      const int b = lc & 1;
+      if (!warp_wait(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
+      store_slot(sbase + (b ? L::at1 : L::at0), row0, x);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_AT_F + b));
+      if (k == ag_after && !put_ag()) return;
+#pragma unroll
+      for (int i = 0; i < kRowsPerLoadLane; ++i)
+#pragma unroll
+        for (int ch = 0; ch < kTC; ++ch) x[i][ch] = y[i][ch];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ kernel
 template <int H>
 __global__ void __launch_bounds__(kThreadsF, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   using L = FusedLayout<H>;
   using T = TMap<H>;
-  constexpr int CH = H / 4;    // accumulator columns per thread
+  constexpr int CH = H / 2;    // accumulator columns per epilogue thread
   constexpr int CHC = CH / 2;  // TMEM columns of CH bf16 values
+  constexpr int LB = 16;       // TMEM load block of the phi-loop epilogues
+  constexpr int PB = 32;       // TMEM load block of the per-pixel epilogues
+  static_assert(CH % PB == 0, "accumulator columns per thread must be a multiple of 32");
 
-  extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bar_w;
-  __shared__ __align__(8) uint64_t bar_a;  // phi2, rho, B1, B2, R1, R2 completion
-  __shared__ __align__(8) uint64_t bar_b;  // phi1 completion
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[B_COUNT];
   __shared__ uint32_t s_tmem;
-  __shared__ int s_qmax[4];
+  __shared__ LoaderShared s_ld;
+  __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q = warp & 3, g = warp >> 2;
-  const int row = q * 32 + lane;
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t bw = smem_u32(&bar_w), ba = smem_u32(&bar_a), bb = smem_u32(&bar_b);
+  const uint32_t bar_base = smem_u32(&bars[0]);
+  auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
 
   if (tid == 0) {
-    mbar_init(bw, 1);
-    mbar_init(ba, 1);
-    mbar_init(bb, 1);
+    mbar_init(bar(B_W), 1);
+    mbar_init(bar(B_IN), kEpiWarps);
+    mbar_init(bar(B_D1), 1);
+    mbar_init(bar(B_DR2), 1);
+    mbar_init(bar(B_DP), 1);
+    mbar_init(bar(B_AG_F), kLoadWarps);
+    mbar_init(bar(B_AG_E), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(B_D2 + b), 1);
+      mbar_init(bar(B_E2 + b), kEpiWarps);
+      mbar_init(bar(B_AT_F + b), kLoadWarps);
+      mbar_init(bar(B_AT_E + b), 1);
+      mbar_init(bar(B_TILE + b), kLoadWarps);
+    }
+    s_abort = 0;
     fence_mbar_init();
   }
-  if (warp == 0) {
+  if (warp == kMmaWarp) {
     tmem_alloc(smem_u32(&s_tmem), T::NCOLS);
     tmem_relinquish();
   }
@@ -109,317 +362,304 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = s_tmem;
-  const uint32_t tl = tbase + (static_cast<uint32_t>(q * 32) << 16);  // this warp's lanes
 
-  if (tid == 0) {
-    mbar_arrive_expect_tx(bw, L::bytes);
-    for (uint32_t off = 0; off < L::bytes; off += 32768u) {
-      const uint32_t n = L::bytes - off < 32768u ? L::bytes - off : 32768u;
-      bulk_g2s(sbase + off, wimg + off, n, bw);
+  if (warp >= kLoadWarp0) {
+    // the constant [1, 1, 0, ...] operand that multiplies phi2's bias rows
+    for (int r = (warp - kLoadWarp0) * 32 + lane; r < kTile; r += kLoadWarps * 32) {
+      sts128(sbase + L::aone + r * 16u, pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
+      sts128(sbase + L::aone + 2048u + r * 16u, 0u, 0u, 0u, 0u);
     }
-  }
-  int abort = !mbar_wait(bw, 0, kWaitNs);
-  if (abort) atomicOr(prm.err, kErrTimeout);
-
-  const float* b_phi2 = reinterpret_cast<const float*>(smem + L::bias_phi2) + g * CH;
-  const float* b_rho = reinterpret_cast<const float*>(smem + L::bias_rho) + g * CH;
-  const float* b_b2 = reinterpret_cast<const float*>(smem + L::bias_b2) + g * CH;
-  const float* b_r1 = reinterpret_cast<const float*>(smem + L::bias_r1) + g * CH;
-  const float* b_r2 = reinterpret_cast<const float*>(smem + L::bias_r2);
-  constexpr uint32_t idH = make_idesc(128, H, kFmtBF16);
-  constexpr uint32_t id16 = make_idesc(128, 16, kFmtBF16);
-  uint32_t ph_a = 0, ph_b = 0;
-  const float* cur_fold = nullptr;
-
-  for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x) {
-    abort = __syncthreads_or(abort);
-    if (abort) break;
-    int fi = 0;
-    while (fi + 1 < prm.nframes && tile >= prm.f[fi + 1].tile0) ++fi;
-    const FusedFrame& F = prm.f[fi];
-    const int P = F.P, K = F.K;
-    const int pix = (tile - F.tile0) * kTile + row;
-    const bool ok = pix < P;
-
-    // Per-scene folded biases -> the constant-one rows of phi1 and B1.  No
-    // MMA is in flight here: the previous tile waited for its last GEMM.
-    if (F.fold != cur_fold) {
-      if (tid < 2 * H) {
-        const int n = tid < H ? tid : tid - H;
-        const float c = F.fold[tid];
-        const float hi = bf16_value(c);
-        const uint32_t packed = static_cast<uint32_t>(bf16_bits(hi)) |
-                                (static_cast<uint32_t>(bf16_bits(c - hi)) << 16);
-        const uint32_t off = tid < H ? L::phi1 + ((H + n) * 8 + 4) * 2
-                                     : L::b1 + ((H + n) * 8 + 6) * 2;
-        *reinterpret_cast<uint32_t*>(smem + off) = packed;
-      }
-      fence_proxy_async_smem();
-      cur_fold = F.fold;
-    }
-
-    int c = 0;
-    if (ok) {
-      c = F.counts[pix];
-      if (c > K) {
-        if (g == 0) atomicOr(prm.err, kErrCount);
-        c = K;
+    fence_proxy_async_smem();
+    loader_loop<H>(prm, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
+  } else if (warp == kMmaWarp) {
+    // ------------------------------------------------------------ MMA warp
+    if (lane == 0) {
+      mbar_arrive_expect_tx(bar(B_W), L::bytes);
+      for (uint32_t off = 0; off < L::bytes; off += 32768u) {
+        const uint32_t n = L::bytes - off < 32768u ? L::bytes - off : 32768u;
+        bulk_g2s(sbase + off, wimg + off, n, bar(B_W));
       }
     }
-    // A_g = [g0..g13, 1, 1] (bf16), columns 2g, 2g+1 of the 8-column block.
-    {
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      if (ok) {
-        if (g < 3) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) x[j] = F.gbuf[static_cast<size_t>(4 * g + j) * P + pix];
-        } else {
-          x[0] = F.gbuf[static_cast<size_t>(12) * P + pix];
-          x[1] = F.gbuf[static_cast<size_t>(13) * P + pix];
-          x[2] = 1.0f;
-          x[3] = 1.0f;
-        }
+    __syncwarp();
+    constexpr uint32_t idH = make_idesc(128, H, kFmtBF16);
+    constexpr uint32_t id16 = make_idesc(128, 16, kFmtBF16);
+    const uint64_t dsc_phi1 = make_sdesc(sbase + L::phi1, H * 16, 128);
+    const uint64_t dsc_phi2 = make_sdesc(sbase + L::phi2, H * 16, 128);
+    const uint64_t dsc_phi2b = make_sdesc(sbase + L::phi2b, H * 16, 128);
+    const uint64_t dsc_rho = make_sdesc(sbase + L::rho, H * 16, 128);
+    const uint64_t dsc_b1 = make_sdesc(sbase + L::b1, H * 16, 128);
+    const uint64_t dsc_b2 = make_sdesc(sbase + L::b2, H * 16, 128);
+    const uint64_t dsc_r1 = make_sdesc(sbase + L::r1, H * 16, 128);
+    const uint64_t dsc_r2 = make_sdesc(sbase + L::r2, 16 * 16, 128);
+    const uint64_t dsc_at0 = make_sdesc(sbase + L::at0, 128 * 16, 128);
+    const uint64_t dsc_at1 = make_sdesc(sbase + L::at1, 128 * 16, 128);
+    const uint64_t dsc_one = make_sdesc(sbase + L::aone, 128 * 16, 128);
+    const uint64_t dsc_ag = make_sdesc(sbase + L::ag, 128 * 16, 128);
+    // B1's weights for r start after its 16-wide G-buffer block
+    const uint64_t dsc_b1r = dsc_b1 + static_cast<uint64_t>((2 * H * 16) >> 4);
+    uint32_t n_in = 0, gs = 0, lc = 0, n_agf = 0, tb = 0;
+    const float* cur_fold = nullptr;
+    // phi1 for the next global layer slot (its operand filled by the loader)
+    auto phi1 = [&]() -> bool {
+      const int b = lc & 1;
+      if (!warp_wait(bar(B_AT_F + b), (lc >> 1) & 1, &s_abort)) return false;
+      tc_fence_after();
+      if (lane == 0) {
+        mma_f16_ss(tbase + T::D1, b ? dsc_at1 : dsc_at0, dsc_phi1, idH, 0u);
+        mma_commit(bar(B_D1));
+        mma_commit(bar(B_AT_E + b));
       }
-      const uint32_t v[2] = {pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3])};
-      tmem_st2(tl + T::AG + 2 * g, v);
-    }
-    // Transparency layer k -> [t0..t11, 1, 1, 0, 0]; zeros for k >= c.
-    auto load_layer = [&](int k, float (&x)[4]) {
-      if (g == 3) {
-        x[0] = 1.0f;
-        x[1] = 1.0f;
-        x[2] = 0.0f;
-        x[3] = 0.0f;
-      } else if (ok && k < c) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          x[j] = F.tbuf[(static_cast<size_t>(k) * kTC + 4 * g + j) * P + pix];
-      } else {
-        x[0] = x[1] = x[2] = x[3] = 0.0f;
-      }
+      __syncwarp();
+      ++lc;
+      return true;
     };
-    float nx[4];
-    load_layer(0, nx);
-    {
-      const uint32_t v[2] = {pack_bf16(nx[0], nx[1]), pack_bf16(nx[2], nx[3])};
-      tmem_st2(tl + T::AT + 2 * g, v);
-    }
-    const int wmax = __reduce_max_sync(0xffffffffu, c);
-    if (g == 0 && lane == 0) s_qmax[q] = wmax;
-    tmem_wait_st();
-    tc_fence_before();
-    abort = __syncthreads_or(abort);
-    if (abort) break;
-    const int ns = max(max(s_qmax[0], s_qmax[1]), max(s_qmax[2], s_qmax[3]));
-    if (ns > 1) load_layer(1, nx);
-
-    float mx[CH], sm[CH];
-#pragma unroll
-    for (int j = 0; j < CH; ++j) {
-      mx[j] = 0.0f;
-      sm[j] = kSumBase;
-    }
-    if (ns > 0 && tid == 0) {
-      tc_fence_after();
-      issue_gemm(tbase, T::DA, T::AT, sbase + L::phi1, H, 16, idH);
-      mma_commit(bb);
-    }
-    for (int k = 0; k < ns; ++k) {
-      // phi1(k) done -> U = ReLU(D) as bf16 into AX; next layer into AT.
-      if (!mbar_wait(bb, ph_b, kWaitNs)) abort = 1;
-      ph_b ^= 1;
-      tc_fence_after();
-      {
-        uint32_t r[CH], u[CHC];
-        tmem_ld<CH>(tl + T::DA + g * CH, r);
-#pragma unroll
-        for (int j = 0; j < CHC; ++j)
-          u[j] = pack_bf16_relu(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-        tmem_st<CHC>(tl + T::AX + g * CHC, u);
+    if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+    for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++tb) {
+      if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
+      const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
+      const FusedFrame& F = frame_of(prm, tile);
+      if (F.fold != cur_fold) {
+        // Per-scene folded biases -> the constant-one rows of phi1 and B1,
+        // once no MMA of the previous tile can still read them.
+        if (tb > 0 && !warp_wait(bar(B_DR2), (tb - 1) & 1, &s_abort)) goto done;
+        for (int i = lane; i < 2 * H; i += 32) {
+          const int n = i < H ? i : i - H;
+          const float cv = F.fold[i];
+          const float hi = bf16_value(cv);
+          const uint32_t packed = static_cast<uint32_t>(bf16_bits(hi)) |
+                                  (static_cast<uint32_t>(bf16_bits(cv - hi)) << 16);
+          const uint32_t off = i < H ? L::phi1 + ((H + n) * 8 + 4) * 2
+                                     : L::b1 + ((H + n) * 8 + 6) * 2;
+          *reinterpret_cast<uint32_t*>(smem + off) = packed;
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        cur_fold = F.fold;
       }
-      if (k + 1 < ns) {
-        const uint32_t v[2] = {pack_bf16(nx[0], nx[1]), pack_bf16(nx[2], nx[3])};
-        tmem_st2(tl + T::AT + 2 * g, v);
+      if (ns > 0 && !phi1()) goto done;
+      for (int k = 0; k < ns; ++k, ++gs) {
+        if (!warp_wait(bar(B_IN), n_in & 1, &s_abort)) goto done;  // U(k) written, D1 read
+        ++n_in;
+        tc_fence_after();
+        if (k + 1 < ns && !phi1()) goto done;
+        const int b = gs & 1;
+        // the buffer's previous accumulator (slot gs - 2) has been read
+        if (!warp_wait(bar(B_E2 + b), ((gs >> 1) & 1) ^ 1, &s_abort)) goto done;
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t d = tbase + (b ? T::D2B : T::D2A);
+          issue_gemm<H, H>(d, tbase + (k & 1 ? T::AU1 : T::AU0), dsc_phi2, idH);
+          mma_f16_ss(d, dsc_one, dsc_phi2b, idH, 1u);
+          mma_commit(bar(B_D2 + b));
+        }
+        __syncwarp();
       }
+      // Per-pixel layers rho, B1, B2, R1 into D1, then R2.
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        if (!warp_wait(bar(B_IN), n_in & 1, &s_abort)) goto done;
+        ++n_in;
+        if (l == 1) {
+          if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+          ++n_agf;
+        }
+        tc_fence_after();
+        if (lane == 0) {
+          if (l == 0) issue_gemm<H, 2 * H>(tbase + T::D1, tbase + T::APOOL, dsc_rho, idH);
+          if (l == 1) {
+            mma_f16_ss(tbase + T::D1, dsc_ag, dsc_b1, idH, 0u);
+            issue_gemm<H, H>(tbase + T::D1, tbase + T::AR, dsc_b1r, idH, true);
+          }
+          if (l == 2) issue_gemm<H, H>(tbase + T::D1, tbase + T::AY, dsc_b2, idH);
+          if (l == 3) issue_gemm<H, H>(tbase + T::D1, tbase + T::AY2, dsc_r1, idH);
+          mma_commit(bar(B_DP));
+          if (l == 1) mma_commit(bar(B_AG_E));
+        }
+        __syncwarp();
+      }
+      if (!warp_wait(bar(B_IN), n_in & 1, &s_abort)) goto done;
+      ++n_in;
+      tc_fence_after();
+      if (lane == 0) {
+        issue_gemm<16, H>(tbase + T::DR2, tbase + T::AY, dsc_r2, id16);
+        mma_commit(bar(B_DR2));
+      }
+      __syncwarp();
+    }
+  } else {
+    // ------------------------------------------------------- epilogue warps
+    const int q = warp & 3, g = warp >> 2;
+    const int row = q * 32 + lane;
+    const uint32_t tl = tbase + (static_cast<uint32_t>(q * 32) << 16);
+    const float* b_rho = reinterpret_cast<const float*>(smem + L::bias_rho) + g * CH;
+    const float* b_b2 = reinterpret_cast<const float*>(smem + L::bias_b2) + g * CH;
+    const float* b_r1 = reinterpret_cast<const float*>(smem + L::bias_r1) + g * CH;
+    const float* b_r2 = reinterpret_cast<const float*>(smem + L::bias_r2);
+    uint32_t n_d1 = 0, n_dp = 0, gs = 0, tb = 0;
+    auto arrive = [&](int b) {
       tmem_wait_st();
       tc_fence_before();
-      abort = __syncthreads_or(abort);
-      if (abort) break;
-      if (tid == 0) {
-        tc_fence_after();
-        issue_gemm(tbase, T::DB, T::AX, sbase + L::phi2, H, H, idH);
-        mma_commit(ba);
-        if (k + 1 < ns) {
-          issue_gemm(tbase, T::DA, T::AT, sbase + L::phi1, H, 16, idH);
-          mma_commit(bb);
-        }
-      }
-      if (k + 2 < ns) load_layer(k + 2, nx);
-      if (!mbar_wait(ba, ph_a, kWaitNs)) abort = 1;
-      ph_a ^= 1;
-      tc_fence_after();
-      {
-        uint32_t r[CH];
-        tmem_ld<CH>(tl + T::DB + g * CH, r);
-        if (k < c) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(b));
+    };
+    if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+
+    for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++tb) {
+      if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
+      const int c = s_ld.cnt[tb & 1][row];
+      const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
+
+      uint32_t mx[CHC];  // running max, bf16 pairs
+      float sm[CH];      // fixed-point sums
 #pragma unroll
-          for (int j = 0; j < CH; ++j) {
-            const float v = __uint_as_float(r[j]) + b_phi2[j];
-            mx[j] = fmaxf(mx[j], v);
-            sm[j] = __fadd_rz(sm[j], fmaxf(v, 0.0f));
+      for (int j = 0; j < CHC; ++j) mx[j] = 0u;
+#pragma unroll
+      for (int j = 0; j < CH; ++j) sm[j] = kSumBase;
+
+      // phi1(j) accumulator -> U(j) = ReLU as bf16.
+      auto epi1 = [&](int j) -> bool {
+        if (!warp_wait(bar(B_D1), n_d1 & 1, &s_abort)) return false;
+        ++n_d1;
+        tc_fence_after();
+#pragma unroll
+        for (int hh = 0; hh < CH / LB; ++hh) {
+          uint32_t r[LB], u[LB / 2];
+          tmem_ld<LB>(tl + T::D1 + g * CH + hh * LB, r);
+#pragma unroll
+          for (int i = 0; i < LB / 2; ++i)
+            u[i] = pack_bf16_relu(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+          tmem_st<LB / 2>(tl + (j & 1 ? T::AU1 : T::AU0) + g * CHC + hh * (LB / 2), u);
+        }
+        arrive(B_IN);
+        return true;
+      };
+
+      if (ns > 0 && !epi1(0)) goto done;
+      for (int k = 0; k < ns; ++k, ++gs) {
+        if (k + 1 < ns && !epi1(k + 1)) goto done;
+        const int b = gs & 1;
+        if (!warp_wait(bar(B_D2 + b), (gs >> 1) & 1, &s_abort)) goto done;
+        tc_fence_after();
+        const uint32_t d2 = tl + (b ? T::D2B : T::D2A) + g * CH;
+#pragma unroll
+        for (int hh = 0; hh < CH / LB; ++hh) {
+          uint32_t r[LB];
+          tmem_ld<LB>(d2 + hh * LB, r);
+          if (hh == CH / LB - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(B_E2 + b));
+          }
+          if (k < c) {
+#pragma unroll
+            for (int i = 0; i < LB; i += 2) {
+              const int j = hh * LB + i;
+              const float v0 = __uint_as_float(r[i]), v1 = __uint_as_float(r[i + 1]);
+              mx[j / 2] = bmax2(mx[j / 2], pack_bf16_relu(v0, v1));
+              float s0, s1;
+              fadd2_rz(s0, s1, sm[j], sm[j + 1], fmaxf(v0, 0.0f), fmaxf(v1, 0.0f));
+              sm[j] = s0;
+              sm[j + 1] = s1;
+            }
           }
         }
       }
-      tc_fence_before();
-    }
-    // (a local timeout from the last wait is made uniform by the next barrier)
 
-    // pool = [max ; mean] -> AX (H columns: max in the first H/2).
-    {
-      uint32_t pm[CHC], pa[CHC];
-      bool range = false;
+      // pool = [max ; mean] -> APOOL (bf16, 2H values = H columns).
+      {
+        const float rcp = c > 0 ? __frcp_rn(static_cast<float>(c)) : 0.0f;
+        const float off = kSumBase - static_cast<float>(c) * kHalfQuantum;
+        bool over = false;
 #pragma unroll
-      for (int j = 0; j < CHC; ++j) {
-        float m2[2];
+        for (int hh = 0; hh < CHC / 16; ++hh) {
+          uint32_t pa[16], pm[16];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float s = sm[2 * j + h];
-          range |= !(s < kSumLimit);
-          m2[h] = c > 0 ? __fdiv_rn((s - kSumBase) + static_cast<float>(c) * kHalfQuantum,
-                                    static_cast<float>(c))
-                        : 0.0f;
+          for (int j = 0; j < 16; ++j) {
+            const int jj = hh * 16 + j;
+            over |= !(fmaxf(sm[2 * jj], sm[2 * jj + 1]) < kSumLimit);
+            float a0, a1;
+            fadd2_rn(a0, a1, sm[2 * jj], sm[2 * jj + 1], -off, -off);
+            pa[j] = pack_bf16(a0 * rcp, a1 * rcp);
+            pm[j] = mx[jj];
+          }
+          tmem_st16(tl + T::APOOL + g * CHC + hh * 16, pm);
+          tmem_st16(tl + T::APOOL + H / 2 + g * CHC + hh * 16, pa);
         }
-        pm[j] = pack_bf16(mx[2 * j], mx[2 * j + 1]);
-        pa[j] = pack_bf16(m2[0], m2[1]);
+        if (over && c > 0) atomicOr(prm.err, kErrRange);
       }
-      if (range && c > 0) atomicOr(prm.err, kErrRange);
-      tmem_st<CHC>(tl + T::AX + g * CHC, pm);
-      tmem_st<CHC>(tl + T::AX + H / 2 + g * CHC, pa);
-    }
-    tmem_wait_st();
-    tc_fence_before();
-    abort = __syncthreads_or(abort);
-    if (abort) break;
-    // rho
-    if (tid == 0) {
-      tc_fence_after();
-      issue_gemm(tbase, T::DA, T::AX, sbase + L::rho, H, 2 * H, idH);
-      mma_commit(ba);
-    }
-    if (!mbar_wait(ba, ph_a, kWaitNs)) abort = 1;
-    ph_a ^= 1;
-    tc_fence_after();
-    {
-      uint32_t r[CH], u[CHC];
-      tmem_ld<CH>(tl + T::DA + g * CH, r);
+      arrive(B_IN);
+
+      // rho -> r (zero without layers) -> AR;  B1 -> y -> AY;
+      // B2 -> y2 -> AY2;  R1 -> q -> AY.
+#pragma unroll 1
+      for (int l = 0; l < 4; ++l) {
+        if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
+        ++n_dp;
+        tc_fence_after();
+        const float* bl = l == 0 ? b_rho : (l == 2 ? b_b2 : b_r1);
+        const uint32_t dst = l == 0 ? T::AR : (l == 2 ? T::AY2 : T::AY);
 #pragma unroll
-      for (int j = 0; j < CHC; ++j)
-        u[j] = c > 0 ? pack_bf16_relu(__uint_as_float(r[2 * j]) + b_rho[2 * j],
-                                      __uint_as_float(r[2 * j + 1]) + b_rho[2 * j + 1])
-                     : 0u;
-      tmem_st<CHC>(tl + T::AR + g * CHC, u);
-    }
-    tmem_wait_st();
-    tc_fence_before();
-    abort = __syncthreads_or(abort);
-    if (abort) break;
-    // B1 on [g, 1, 1, r]
-    if (tid == 0) {
-      tc_fence_after();
-      issue_gemm(tbase, T::DB, T::AG, sbase + L::b1, H, 16 + H, idH);
-      mma_commit(ba);
-    }
-    if (!mbar_wait(ba, ph_a, kWaitNs)) abort = 1;
-    ph_a ^= 1;
-    tc_fence_after();
-    {
-      uint32_t r[CH], u[CHC];
-      tmem_ld<CH>(tl + T::DB + g * CH, r);
+        for (int hh = 0; hh < CH / PB; ++hh) {
+          uint32_t r[PB], u[PB / 2];
+          tmem_ld<PB>(tl + T::D1 + g * CH + hh * PB, r);
+          if (l == 1) {
 #pragma unroll
-      for (int j = 0; j < CHC; ++j)
-        u[j] = pack_bf16_relu(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-      tmem_st<CHC>(tl + T::AX + g * CHC, u);
-    }
-    tmem_wait_st();
-    tc_fence_before();
-    abort = __syncthreads_or(abort);
-    if (abort) break;
-    // B2
-    if (tid == 0) {
-      tc_fence_after();
-      issue_gemm(tbase, T::DA, T::AX, sbase + L::b2, H, H, idH);
-      mma_commit(ba);
-    }
-    if (!mbar_wait(ba, ph_a, kWaitNs)) abort = 1;
-    ph_a ^= 1;
-    tc_fence_after();
-    {
-      uint32_t r[CH], u[CHC];
-      tmem_ld<CH>(tl + T::DA + g * CH, r);
+            for (int i = 0; i < PB / 2; ++i)
+              u[i] = pack_bf16_relu(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+          } else {
 #pragma unroll
-      for (int j = 0; j < CHC; ++j)
-        u[j] = pack_bf16_relu(__uint_as_float(r[2 * j]) + b_b2[2 * j],
-                              __uint_as_float(r[2 * j + 1]) + b_b2[2 * j + 1]);
-      tmem_st<CHC>(tl + T::AX + g * CHC, u);
-    }
-    tmem_wait_st();
-    tc_fence_before();
-    abort = __syncthreads_or(abort);
-    if (abort) break;
-    // R1
-    if (tid == 0) {
-      tc_fence_after();
-      issue_gemm(tbase, T::DB, T::AX, sbase + L::r1, H, H, idH);
-      mma_commit(ba);
-    }
-    if (!mbar_wait(ba, ph_a, kWaitNs)) abort = 1;
-    ph_a ^= 1;
-    tc_fence_after();
-    {
-      uint32_t r[CH], u[CHC];
-      tmem_ld<CH>(tl + T::DB + g * CH, r);
+            for (int i = 0; i < PB / 2; ++i) {
+              float v0, v1;
+              fadd2_rn(v0, v1, __uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]),
+                       bl[hh * PB + 2 * i], bl[hh * PB + 2 * i + 1]);
+              u[i] = (l == 0 && c == 0) ? 0u : pack_bf16_relu(v0, v1);
+            }
+          }
+          tmem_st<PB / 2>(tl + dst + g * CHC + hh * (PB / 2), u);
+        }
+        arrive(B_IN);
+      }
+      // R2 + sigmoid -> out (column group 0 stores).  Every warp waits for R2:
+      // it was issued after all warps' last B_IN arrival of this tile, so no
+      // warp's next-tile arrival can complete a phase of this tile.
+      if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
+      if (g == 0) {
+        tc_fence_after();
+        const FusedFrame& F = frame_of(prm, tile);
+        const int pix = (tile - F.tile0) * kTile + row;
+        uint32_t r[4];
+        tmem_ld4(tl + T::DR2, r);
+        if (pix < F.P) {
 #pragma unroll
-      for (int j = 0; j < CHC; ++j)
-        u[j] = pack_bf16_relu(__uint_as_float(r[2 * j]) + b_r1[2 * j],
-                              __uint_as_float(r[2 * j + 1]) + b_r1[2 * j + 1]);
-      tmem_st<CHC>(tl + T::AX + g * CHC, u);
-    }
-    tmem_wait_st();
-    tc_fence_before();
-    abort = __syncthreads_or(abort);
-    if (abort) break;
-    // R2 (N = 16, outputs 0..2) + sigmoid
-    if (tid == 0) {
-      tc_fence_after();
-      issue_gemm(tbase, T::DR2, T::AX, sbase + L::r2, 16, H, id16);
-      mma_commit(ba);
-    }
-    if (!mbar_wait(ba, ph_a, kWaitNs)) abort = 1;
-    ph_a ^= 1;
-    tc_fence_after();
-    if (g == 0) {
-      uint32_t r[4];
-      tmem_ld4(tl + T::DR2, r);
-      if (ok) {
-#pragma unroll
-        for (int j = 0; j < kOut; ++j) {
-          const float y = __uint_as_float(r[j]) + b_r2[j];
-          F.out[static_cast<size_t>(j) * P + pix] = 1.0f / (1.0f + expf(-y));
+          for (int j = 0; j < kOut; ++j) {
+            const float y = __uint_as_float(r[j]) + b_r2[j];
+            F.out[static_cast<size_t>(j) * F.P + pix] = 1.0f / (1.0f + expf(-y));
+          }
         }
       }
     }
-    tc_fence_before();
   }
-  if (abort) atomicOr(prm.err, kErrTimeout);
+done:
+  if (s_abort && tid == 0) atomicOr(prm.err, kErrTimeout);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
-    tmem_dealloc(tbase, T::NCOLS);
+    tmem_dealloc(tbase, TMap<H>::NCOLS);
   }
 }
 
 int g_sm_count = 0;
+
+template <int H>
+cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
+  constexpr int smem = FusedLayout<H>::smem_bytes;
+  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  fused_bf16_kernel<H><<<grid, kThreadsF, smem, s>>>(p, static_cast<const uint8_t*>(wimg));
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -436,21 +676,7 @@ int device_sm_count() {
 cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& p, cudaStream_t s) {
   if (p.total_tiles <= 0) return cudaSuccess;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
-  cudaError_t e;
-  if (H == 128) {
-    constexpr int smem = FusedLayout<128>::bytes;
-    e = cudaFuncSetAttribute(fused_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-    if (e != cudaSuccess) return e;
-    fused_bf16_kernel<128><<<grid, kThreadsF, smem, s>>>(p, static_cast<const uint8_t*>(wimg));
-  } else {
-    constexpr int smem = FusedLayout<64>::bytes;
-    e = cudaFuncSetAttribute(fused_bf16_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-    if (e != cudaSuccess) return e;
-    fused_bf16_kernel<64><<<grid, kThreadsF, smem, s>>>(p, static_cast<const uint8_t*>(wimg));
-  }
-  return cudaGetLastError();
+  return H == 128 ? launch_h<128>(wimg, p, s, grid) : launch_h<64>(wimg, p, s, grid);
 }
 
 }  // namespace gn

@@ -72,6 +72,15 @@ std::vector<uint8_t> pack_fused_bf16(const float* w, const gn::WeightIndex& wi) 
   }
   for (int n = 0; n < gn::kOut; ++n)
     for (int k = 0; k < H; ++k) put(L::r2, 16, n, k, W(gn::LR2, n, k));
+  for (int n = 0; n < H; ++n) {  // phi2 bias as hi + lo BF16 rows of a K = 16 operand
+    const float b = w[wi.b[gn::LPHI2] + n];
+    uint16_t hb = bf16_rne(b);
+    uint32_t hu = static_cast<uint32_t>(hb) << 16;
+    float hf;
+    std::memcpy(&hf, &hu, 4);
+    put(L::phi2b, H, n, 0, hf);
+    put(L::phi2b, H, n, 1, b - hf);
+  }
   float* bias = reinterpret_cast<float*>(img.data() + L::bias);
   for (int n = 0; n < H; ++n) {
     bias[n] = w[wi.b[gn::LPHI2] + n];
@@ -94,8 +103,8 @@ int check_frame(const gn_model* m, const gn_latent* lat, const float* gbuf, cons
                 lat->Z, m->H, m->Z);
   if (K < 0 || K > gn::kMaxK) return fail(GN_EINVAL, "K = %d outside 0..%d", K, gn::kMaxK);
   if (h < 1 || w < 1) return fail(GN_EINVAL, "frame %d x %d is empty", h, w);
-  if (static_cast<long long>(h) * w * (K > 0 ? K : 1) >= (1ll << 31))
-    return fail(GN_EINVAL, "frame %d x %d x K=%d too large (K*h*w must be < 2^31)", h, w, K);
+  if (static_cast<long long>(h) * w * gn::kTC * (K > 0 ? K : 1) >= (1ll << 31))
+    return fail(GN_EINVAL, "frame %d x %d x K=%d too large (12*K*h*w must be < 2^31)", h, w, K);
   if (!gbuf || !cnt || !out) return fail(GN_EINVAL, "gbuf, layer_count and out must be non-NULL");
   if (K > 0 && !tbuf) return fail(GN_EINVAL, "tbuf is NULL with K = %d", K);
   if (!aligned4(gbuf) || !aligned4(out) || (tbuf && !aligned4(tbuf)))

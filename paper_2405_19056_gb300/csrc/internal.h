@@ -40,6 +40,9 @@ struct WeightIndex {
 //   phi2 [H][H]     rho [2H][H]  (K = [max ; mean])
 //   B1   [16+H][H]  K = 14 channels, 2 folded-bias columns, then r (H)
 //   B2, R1 [H][H]   R2 [H][16]   (N = 3 outputs + 13 zero rows)
+//   phi2b [16][H]   phi2's bias as a K = 16 operand: k = 0 / 1 hold the bias
+//                   split into a high and a low BF16 part, k >= 2 zero; the
+//                   GEMM multiplies it by a constant [1, 1, 0, ...] A column
 //   bias f32: phi2[H], rho[H], B2[H], R1[H], R2[16]
 template <int H>
 struct FusedLayout {
@@ -53,13 +56,23 @@ struct FusedLayout {
   static constexpr uint32_t b2 = b1 + KB1 * H * 2;
   static constexpr uint32_t r1 = b2 + H * H * 2;
   static constexpr uint32_t r2 = r1 + H * H * 2;
-  static constexpr uint32_t bias = r2 + H * NR2 * 2;
+  static constexpr uint32_t phi2b = r2 + H * NR2 * 2;
+  static constexpr uint32_t bias = phi2b + 16 * H * 2;
   static constexpr uint32_t bias_phi2 = bias;
   static constexpr uint32_t bias_rho = bias + H * 4;
   static constexpr uint32_t bias_b2 = bias + 2 * H * 4;
   static constexpr uint32_t bias_r1 = bias + 3 * H * 4;
   static constexpr uint32_t bias_r2 = bias + 4 * H * 4;
   static constexpr uint32_t bytes = bias + (4 * H + 16) * 4;
+  // Shared memory beyond the weights, each a [2][128][8] bf16 A operand
+  // (K = 16 for 128 rows): two layer operands of phi1, the constant
+  // [1, 1, 0, ...] operand that multiplies phi2b, and the G-buffer block
+  // [g0..g13, 1, 1] of B1.
+  static constexpr uint32_t at0 = (bytes + 127) / 128 * 128;
+  static constexpr uint32_t at1 = at0 + 4096;
+  static constexpr uint32_t aone = at1 + 4096;
+  static constexpr uint32_t ag = aone + 4096;
+  static constexpr uint32_t smem_bytes = ag + 4096;
 };
 
 // One frame as the fused kernel sees it.
