@@ -25,15 +25,15 @@
 // Hence the output is bit-identical under any permutation of a pixel's valid
 // layers.
 //
-// Warp roles (11 warps, at most three per SM sub-partition, so every thread
-// may hold 168 registers):
-//  - warps 0-7 (epilogue): warp w serves TMEM lane quadrant q = w % 4 (pixel
-//    rows 32q..32q+31) and accumulator columns [g H/2, (g+1) H/2), g = w / 4.
-//    They run every epilogue (ReLU, pooling, biases, sigmoid) and hold the
-//    pool state (H/2 sums and H/4 packed maxima per thread) in registers.
-//  - warp 8 (MMA): allocates TMEM, patches the per-scene bias rows, issues
+// Warp roles (4 EW + 3 warps, EW = 2 or 4 epilogue warps per lane quadrant):
+//  - warps 0 .. 4 EW - 1 (epilogue): warp w serves TMEM lane quadrant
+//    q = w % 4 (pixel rows 32q..32q+31) and accumulator columns
+//    [g H/EW, (g+1) H/EW), g = w / 4.  They run every epilogue (ReLU,
+//    pooling, biases, sigmoid) and hold the pool state (H/EW sums and H/2EW
+//    packed maxima per thread) in registers.
+//  - warp 4 EW (MMA): allocates TMEM, patches the per-scene bias rows, issues
 //    every tcgen05.mma from lane 0.
-//  - warps 9-10 (loaders, 64 pixel rows each): read each tile's layer counts,
+//  - the last two warps (loaders, 64 pixel rows each): read each tile's layer counts,
 //    G-buffer and layers (coalesced: 32 consecutive pixels per load
 //    instruction), convert them to BF16 and write the shared-memory A
 //    operands, running up to two layer slots ahead of the tensor core.
@@ -57,10 +57,15 @@
 namespace gn {
 namespace {
 
-constexpr int kEpiWarps = 8;
-constexpr int kMmaWarp = 8;
-constexpr int kLoadWarp0 = 9;  // warps 9 and 10
-constexpr int kThreadsF = 11 * 32;
+// EW epilogue warps per TMEM lane quadrant (2 or 4): warps 0 .. 4 EW - 1 are
+// epilogue warps, then the MMA warp, then the two loader warps.
+template <int EW>
+struct Roles {
+  static constexpr int kEpiWarps = 4 * EW;
+  static constexpr int kMmaWarp = 4 * EW;
+  static constexpr int kLoadWarp0 = 4 * EW + 1;
+  static constexpr int kThreads = (4 * EW + 3) * 32;
+};
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per device-side wait
 constexpr float kSumBase = 2048.0f;          // 2^11: quantum 2^-12 in [2^11, 2^12)
 constexpr float kSumLimit = 4096.0f;
@@ -314,16 +319,17 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 }
 
 // ------------------------------------------------------------------ kernel
-template <int H>
-__global__ void __launch_bounds__(kThreadsF, 1)
+template <int H, int EW>
+__global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   using L = FusedLayout<H>;
   using T = TMap<H>;
-  constexpr int CH = H / 2;    // accumulator columns per epilogue thread
+  constexpr int kEpiWarps = Roles<EW>::kEpiWarps;
+  constexpr int kMmaWarp = Roles<EW>::kMmaWarp;
+  constexpr int kLoadWarp0 = Roles<EW>::kLoadWarp0;
+  constexpr int CH = H / EW;   // accumulator columns per epilogue thread
   constexpr int CHC = CH / 2;  // TMEM columns of CH bf16 values
-  constexpr int LB = 16;       // TMEM load block of the phi-loop epilogues
-  constexpr int PB = 32;       // TMEM load block of the per-pixel epilogues
-  static_assert(CH % PB == 0, "accumulator columns per thread must be a multiple of 32");
+  static_assert(CH % 16 == 0, "accumulator columns per thread must be a multiple of 16");
 
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[B_COUNT];
@@ -516,19 +522,28 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 #pragma unroll
       for (int j = 0; j < CH; ++j) sm[j] = kSumBase;
 
-      // phi1(j) accumulator -> U(j) = ReLU as bf16.
+      // phi1(j) accumulator -> U(j) = ReLU as bf16.  16-column TMEM loads
+      // are double buffered: block hh + 1 is in flight while hh is packed.
       auto epi1 = [&](int j) -> bool {
         if (!warp_wait(bar(B_D1), n_d1 & 1, &s_abort)) return false;
         ++n_d1;
         tc_fence_after();
+        const uint32_t src = tl + T::D1 + g * CH;
+        const uint32_t dst = tl + (j & 1 ? T::AU1 : T::AU0) + g * CHC;
+        uint32_t ra[16], rb[16];
+        tmem_ld16_async(src, ra);
+        tmem_wait_ld_tied(ra);
 #pragma unroll
-        for (int hh = 0; hh < CH / LB; ++hh) {
-          uint32_t r[LB], u[LB / 2];
-          tmem_ld<LB>(tl + T::D1 + g * CH + hh * LB, r);
+        for (int hh = 0; hh < CH / 16; ++hh) {
+          uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
+          uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
+          if (hh + 1 < CH / 16) tmem_ld16_async(src + (hh + 1) * 16, nxt);
+          uint32_t u[8];
 #pragma unroll
-          for (int i = 0; i < LB / 2; ++i)
-            u[i] = pack_bf16_relu(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
-          tmem_st<LB / 2>(tl + (j & 1 ? T::AU1 : T::AU0) + g * CHC + hh * (LB / 2), u);
+          for (int i = 0; i < 8; ++i)
+            u[i] = pack_bf16_relu(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
+          tmem_st8(dst + hh * 8, u);
+          if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
         }
         arrive(B_IN);
         return true;
@@ -541,20 +556,26 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         if (!warp_wait(bar(B_D2 + b), (gs >> 1) & 1, &s_abort)) goto done;
         tc_fence_after();
         const uint32_t d2 = tl + (b ? T::D2B : T::D2A) + g * CH;
+        uint32_t ra[16], rb[16];
+        tmem_ld16_async(d2, ra);
+        tmem_wait_ld_tied(ra);
 #pragma unroll
-        for (int hh = 0; hh < CH / LB; ++hh) {
-          uint32_t r[LB];
-          tmem_ld<LB>(d2 + hh * LB, r);
-          if (hh == CH / LB - 1) {
+        for (int hh = 0; hh < CH / 16; ++hh) {
+          uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
+          uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
+          if (hh + 1 < CH / 16) {
+            tmem_ld16_async(d2 + (hh + 1) * 16, nxt);
+          } else {
+            // every column of this buffer is in registers: release it
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(B_E2 + b));
           }
           if (k < c) {
 #pragma unroll
-            for (int i = 0; i < LB; i += 2) {
-              const int j = hh * LB + i;
-              const float v0 = __uint_as_float(r[i]), v1 = __uint_as_float(r[i + 1]);
+            for (int i = 0; i < 16; i += 2) {
+              const int j = hh * 16 + i;
+              const float v0 = __uint_as_float(cur[i]), v1 = __uint_as_float(cur[i + 1]);
               mx[j / 2] = bmax2(mx[j / 2], pack_bf16_relu(v0, v1));
               float s0, s1;
               fadd2_rz(s0, s1, sm[j], sm[j + 1], fmaxf(v0, 0.0f), fmaxf(v1, 0.0f));
@@ -562,6 +583,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
               sm[j + 1] = s1;
             }
           }
+          if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
         }
       }
 
@@ -571,19 +593,19 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const float off = kSumBase - static_cast<float>(c) * kHalfQuantum;
         bool over = false;
 #pragma unroll
-        for (int hh = 0; hh < CHC / 16; ++hh) {
-          uint32_t pa[16], pm[16];
+        for (int hh = 0; hh < CHC / 8; ++hh) {
+          uint32_t pa[8], pm[8];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int jj = hh * 16 + j;
+          for (int j = 0; j < 8; ++j) {
+            const int jj = hh * 8 + j;
             over |= !(fmaxf(sm[2 * jj], sm[2 * jj + 1]) < kSumLimit);
             float a0, a1;
             fadd2_rn(a0, a1, sm[2 * jj], sm[2 * jj + 1], -off, -off);
             pa[j] = pack_bf16(a0 * rcp, a1 * rcp);
             pm[j] = mx[jj];
           }
-          tmem_st16(tl + T::APOOL + g * CHC + hh * 16, pm);
-          tmem_st16(tl + T::APOOL + H / 2 + g * CHC + hh * 16, pa);
+          tmem_st8(tl + T::APOOL + g * CHC + hh * 8, pm);
+          tmem_st8(tl + T::APOOL + H / 2 + g * CHC + hh * 8, pa);
         }
         if (over && c > 0) atomicOr(prm.err, kErrRange);
       }
@@ -597,25 +619,32 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         ++n_dp;
         tc_fence_after();
         const float* bl = l == 0 ? b_rho : (l == 2 ? b_b2 : b_r1);
-        const uint32_t dst = l == 0 ? T::AR : (l == 2 ? T::AY2 : T::AY);
+        const uint32_t src = tl + T::D1 + g * CH;
+        const uint32_t dst = tl + (l == 0 ? T::AR : (l == 2 ? T::AY2 : T::AY)) + g * CHC;
+        uint32_t ra[16], rb[16];
+        tmem_ld16_async(src, ra);
+        tmem_wait_ld_tied(ra);
 #pragma unroll
-        for (int hh = 0; hh < CH / PB; ++hh) {
-          uint32_t r[PB], u[PB / 2];
-          tmem_ld<PB>(tl + T::D1 + g * CH + hh * PB, r);
+        for (int hh = 0; hh < CH / 16; ++hh) {
+          uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
+          uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
+          if (hh + 1 < CH / 16) tmem_ld16_async(src + (hh + 1) * 16, nxt);
+          uint32_t u[8];
           if (l == 1) {
 #pragma unroll
-            for (int i = 0; i < PB / 2; ++i)
-              u[i] = pack_bf16_relu(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+            for (int i = 0; i < 8; ++i)
+              u[i] = pack_bf16_relu(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
           } else {
 #pragma unroll
-            for (int i = 0; i < PB / 2; ++i) {
+            for (int i = 0; i < 8; ++i) {
               float v0, v1;
-              fadd2_rn(v0, v1, __uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]),
-                       bl[hh * PB + 2 * i], bl[hh * PB + 2 * i + 1]);
+              fadd2_rn(v0, v1, __uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]),
+                       bl[hh * 16 + 2 * i], bl[hh * 16 + 2 * i + 1]);
               u[i] = (l == 0 && c == 0) ? 0u : pack_bf16_relu(v0, v1);
             }
           }
-          tmem_st<PB / 2>(tl + dst + g * CHC + hh * (PB / 2), u);
+          tmem_st8(dst + hh * 8, u);
+          if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
         }
         arrive(B_IN);
       }
@@ -651,13 +680,20 @@ done:
 
 int g_sm_count = 0;
 
+// Epilogue warps per lane quadrant (compile-time tuning knob: 2 or 4).
+#ifndef GN_FUSED_EW
+#define GN_FUSED_EW 2
+#endif
+
 template <int H>
 cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
+  constexpr int EW = GN_FUSED_EW;
   constexpr int smem = FusedLayout<H>::smem_bytes;
-  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H>,
+  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, EW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  fused_bf16_kernel<H><<<grid, kThreadsF, smem, s>>>(p, static_cast<const uint8_t*>(wimg));
+  fused_bf16_kernel<H, EW>
+      <<<grid, Roles<EW>::kThreads, smem, s>>>(p, static_cast<const uint8_t*>(wimg));
   return cudaGetLastError();
 }
 

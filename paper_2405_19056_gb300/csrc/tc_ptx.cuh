@@ -152,6 +152,39 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* r) {
   if constexpr (N == 32) tmem_ld32(taddr, r);
   else tmem_ld16(taddr, r);
 }
+// Split-phase loads: tmem_ld16_async issues the load and returns; the
+// destination registers hold the data only after tmem_wait_ld_tied(r), which
+// runs tcgen05.wait::ld and then "rewrites" every register in empty volatile
+// asm statements, so no use of them can be moved above the wait (volatile asm
+// statements keep their order).  Other loads may be issued in between; the
+// wait covers all of them.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_tie16(uint32_t (&r)[16]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+}
+__device__ __forceinline__ void tmem_wait_ld_tied(uint32_t (&r)[16]) {
+  tmem_wait_ld();
+  tmem_tie16(r);
+}
+// Two 16-column halves issued back to back, one wait for both.
+__device__ __forceinline__ void tmem_wait_ld_tied(uint32_t (&a)[16], uint32_t (&b)[16]) {
+  tmem_wait_ld();
+  tmem_tie16(a);
+  tmem_tie16(b);
+}
+
 __device__ __forceinline__ void tmem_st2(uint32_t taddr, const uint32_t (&r)[2]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(r[0]),
                "r"(r[1])
