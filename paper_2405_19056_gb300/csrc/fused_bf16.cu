@@ -1,5 +1,6 @@
-// Fused GlassNet forward pass on sm_103a: one persistent kernel, 128-pixel
-// tiles, every layer a tcgen05 BF16 GEMM with FP32 accumulators in TMEM.
+// Fused GlassNet forward pass on sm_103a: a count-sorting plan kernel, then
+// one persistent kernel over 128-pixel tiles in which every layer is a
+// tcgen05 BF16 GEMM with FP32 accumulators in TMEM.
 //
 // Per tile (Sec. 3.3-3.4, Eq. 5), with the scene latent folded into per-scene
 // biases (c_phi, c_B) that enter the GEMMs through two constant-one input
@@ -7,46 +8,63 @@
 //   for each layer slot k < max count in the tile:
 //     U   = ReLU([t_k, 1, 1, 0, 0] W_phi1'^T)            (K = 16)
 //     V   = [U, 1, 1, 0..] [W_phi2, b_phi2 hi, lo]^T     (K = H + 16)
-//     max = max(max, V);  sum += ReLU(V)   for pixels with k < c_p
+//     u   = bf16(ReLU(V));  max = max(max, u);  sum += u   for pixels with k < c_p
 //   pool  = [max ; mean], mean = sum / c_p               (exact, see below)
 //   r     = ReLU(pool W_rho^T + b_rho), r = 0 if c_p = 0
 //   y     = ReLU([g, 1, 1, r] W_B1'^T)                   (K = 16 + H)
 //   y2    = ReLU(y W_B2^T + b_B2);  q = ReLU(y2 W_R1^T + b_R1)
 //   rgb   = sigmoid(q W_R2^T + b_R2)                     (N padded to 16)
 //
-// Exact, order-independent set pooling: the running max starts at 0 (which is
-// also the ReLU) and is kept as bf16 pairs (rounding is monotonic, so the max
-// of the rounded values is the rounded max that the rho GEMM consumes); the
-// sum is a fixed-point accumulator held in an FP32 significand: s starts at
-// 2^11 and every addition is rounded toward zero, so while s < 2^12 each add
-// contributes exactly floor(ReLU(v) / 2^-12) quanta, whatever the order of the
-// layers.  mean = (s - 2^11 + c 2^-13) * (1/c) (the c 2^-13 term centres the
+// Tile plan and schedule.  Eq. 5 pools over each pixel's own layers, so a
+// tile must run as many layer slots as its largest count.  The plan kernel
+// sorts the pixels of every window of 4 tiles (512 pixels) by layer count,
+// largest first (stable in pixel index), so the tiles of a window hold pixels
+// of similar counts and the slots run per tile come closer to the mean count.
+// A pixel's result does not depend on its tile or row, so the order changes
+// nothing but the work.  Tiles are handed out dynamically (a global counter),
+// in plan order: tiles of very different cost then balance over the CTAs, and
+// the tiles of one window, which gather from the same 512-pixel stretch of
+// every plane, run at about the same time.  Small windows trade some
+// compaction for gathers that stay within fewer cache lines (measured at 512^2,
+// K = 8, Poisson(3) counts: 4 tiles beat 8, 16 and 32).
+//
+// Exact, order-independent set pooling: each valid layer contributes
+// u = bf16(ReLU(V)); the running max starts at 0 (which is also the ReLU) and
+// is kept as bf16 pairs; the sum is a fixed-point accumulator held in an FP32
+// significand: s starts at 2^11 and every addition of u (exact in FP32) is
+// rounded toward zero, so while s < 2^12 each add contributes exactly
+// floor(u / 2^-12) quanta, whatever the order of the layers.
+// mean = (s - 2^11 + c 2^-13) * (1/c) (the c 2^-13 term centres the
 // truncation).  A pixel whose sum reaches 2^12 sets the range error bit.
 // Hence the output is bit-identical under any permutation of a pixel's valid
-// layers.
+// layers.  The adds use the mixed-precision add.rz.f32.bf16 (FMA pipe), the
+// max uses max.bf16x2 on the pair that the ReLU conversion produced.
 //
-// Warp roles (4 EW + 3 warps, EW = 2 or 4 epilogue warps per lane quadrant):
-//  - warps 0 .. 4 EW - 1 (epilogue): warp w serves TMEM lane quadrant
-//    q = w % 4 (pixel rows 32q..32q+31) and accumulator columns
-//    [g H/EW, (g+1) H/EW), g = w / 4.  They run every epilogue (ReLU,
-//    pooling, biases, sigmoid) and hold the pool state (H/EW sums and H/2EW
-//    packed maxima per thread) in registers.
-//  - warp 4 EW (MMA): allocates TMEM, patches the per-scene bias rows, issues
+// Warp roles (11 warps, at most three per SM sub-partition, 168 registers):
+//  - warps 0-7 (epilogue): warp w serves TMEM lane quadrant q = w % 4 (pixel
+//    rows 32q..32q+31) and accumulator columns [g H/2, (g+1) H/2), g = w / 4.
+//    They run every epilogue (ReLU, pooling, biases, sigmoid) and hold the
+//    pool state (H/2 sums and H/4 packed maxima per thread) in registers.
+//  - warp 8 (MMA): allocates TMEM, patches the per-scene bias rows, issues
 //    every tcgen05.mma from lane 0.
-//  - the last two warps (loaders, 64 pixel rows each): read each tile's layer counts,
-//    G-buffer and layers (coalesced: 32 consecutive pixels per load
-//    instruction), convert them to BF16 and write the shared-memory A
-//    operands, running up to two layer slots ahead of the tensor core.
+//  - warps 9-10 (loaders, 64 pixel rows each): read each tile's plan entries,
+//    gather its G-buffer and layers, convert them to BF16 and write the
+//    shared-memory A operands, running up to two layer slots ahead.
+//
+// Layer-slot pipeline.  Three TMEM accumulator buffers rotate over the global
+// sequence of layer slots: phi1(k) writes buffer k mod 3, the epilogue turns
+// it into U(k) (TMEM, double buffered), then phi2(k) overwrites the same
+// buffer.  The MMA warp issues phi1 two slots ahead of phi2, so the tensor
+// pipe always holds the next phi1 while the epilogue works:
+//   tensor pipe:  phi2(k-1) phi1(k+1) phi2(k) phi1(k+2) ...
+//   epilogue:     epi1(k+1) epi2(k) epi1(k+2) epi2(k+1) ...
 // Hand-offs are mbarriers: the MMA warp commits accumulators and consumed
 // operands (tcgen05.commit); the epilogue warps arrive once per warp when an
-// A operand is written or an accumulator has been read; the loader arrives
-// when an operand is filled.  phi1(k+1) is issued before phi2(k), so its
-// epilogue overlaps phi2(k) on the tensor core.
-//
-// Buffers: phi2's accumulator is double buffered in TMEM (slot k uses buffer k
-// mod 2); U is double buffered in TMEM; the two layer operands of phi1, the
-// constant-one operand of phi2's bias and B1's G-buffer block live in shared
-// memory next to the weights.  Every device-side wait gives up after 1 s,
+// A operand is written (two alternating barriers, so a warp that runs ahead
+// cannot complete the phase of a slower one) or an accumulator has been read;
+// the loaders arrive when an operand is filled.  After the last slot the
+// per-pixel layers reuse the three buffers; the next tile's first two phi1
+// are issued right behind R2.  Every device-side wait gives up after 1 s,
 // sets the timeout error bit and makes all warps leave through the common
 // exit.
 #include <cuda_bf16.h>
@@ -57,15 +75,11 @@
 namespace gn {
 namespace {
 
-// EW epilogue warps per TMEM lane quadrant (2 or 4): warps 0 .. 4 EW - 1 are
-// epilogue warps, then the MMA warp, then the two loader warps.
-template <int EW>
-struct Roles {
-  static constexpr int kEpiWarps = 4 * EW;
-  static constexpr int kMmaWarp = 4 * EW;
-  static constexpr int kLoadWarp0 = 4 * EW + 1;
-  static constexpr int kThreads = (4 * EW + 3) * 32;
-};
+constexpr int kEpiWarps = 8;
+constexpr int kMmaWarp = 8;
+constexpr int kLoadWarp0 = 9;  // warps 9 and 10
+constexpr int kLoadWarps = 2;
+constexpr int kThreadsF = 11 * 32;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per device-side wait
 constexpr float kSumBase = 2048.0f;          // 2^11: quantum 2^-12 in [2^11, 2^12)
 constexpr float kSumLimit = 4096.0f;
@@ -73,39 +87,50 @@ constexpr float kHalfQuantum = 1.0f / 8192.0f;
 
 // mbarrier slots.
 enum : int {
-  B_W = 0,      // weights copied (transaction count)
-  B_IN = 1,     // an A operand in TMEM is complete (epilogue warps arrive)
-  B_D1 = 2,     // phi1 accumulator ready (commit)
-  B_DR2 = 3,    // R2 accumulator ready (commit)
-  B_DP = 4,     // per-pixel layer accumulator ready (commit)
-  B_AG_F = 5,   // B1's G-buffer operand written (loader)
-  B_AG_E = 6,   // B1's G-buffer operand consumed (commit)
-  B_D2 = 7,     // + buffer: phi2 accumulator ready (commit)
-  B_E2 = 9,     // + buffer: phi2 accumulator read (epilogue warps arrive)
-  B_AT_F = 11,  // + buffer: layer operand written (loader)
-  B_AT_E = 13,  // + buffer: layer operand consumed (commit)
-  B_TILE = 15,  // + tile parity: counts and slot count published (loader)
-  B_COUNT = 17
+  B_W = 0,       // weights copied (transaction count)
+  B_IN = 1,      // + (n & 1): an A operand in TMEM written (epilogue warps arrive)
+  B_DP = 3,      // per-pixel layer accumulator ready (commit)
+  B_DR2 = 4,     // R2 accumulator ready (commit)
+  B_AG_F = 5,    // B1's G-buffer operand written (loaders)
+  B_AG_E = 6,    // B1's G-buffer operand consumed (commit)
+  B_D1 = 7,      // + buffer (3): phi1 accumulator ready (commit)
+  B_D2 = 10,     // + buffer (3): phi2 accumulator ready (commit)
+  B_BE = 13,     // + buffer (3): phi2 accumulator read (epilogue warps arrive)
+  B_AT_F = 16,   // + buffer (2): layer operand written (loaders)
+  B_AT_E = 18,   // + buffer (2): layer operand consumed (commit)
+  B_TILE = 20,   // + tile parity: tile index and slot count published (loaders)
+  B_SCHED = 22,  // + tile parity: tile index taken (loader warp 0)
+  B_COUNT = 24
 };
 
-// TMEM column map (128 lanes x 512 columns of 32 bits).  The per-pixel
-// layers reuse the phi-loop regions once the loop is over.
+// TMEM column map (128 lanes x 4H columns of 32 bits): three accumulator
+// buffers of H columns, then U (H bf16 = H/2 columns) double buffered.  The
+// per-pixel layers of a tile use, with r = (first global slot of the next
+// tile) mod 3:  X = buffer r (their accumulator), Y = buffer r + 1 (r, then y
+// and q), Z = buffer r + 2 (y2, and R2's accumulator), and the U region for
+// the pooled [max ; mean].  The next tile's phi1 for its first two slots
+// write X and Y, issued after R2 (which reads Y); Z is written again only
+// after every epilogue warp has read R2.
 template <int H>
 struct TMap {
-  static constexpr uint32_t D1 = 0;              // phi1 D; per-pixel D (rho, B1, B2, R1)
-  static constexpr uint32_t D2A = H;             // phi2 D, even slots
-  static constexpr uint32_t D2B = 2 * H;         // phi2 D, odd slots
-  static constexpr uint32_t AU0 = 3 * H;         // phi2 A (U), double buffered
+  static constexpr uint32_t AU0 = 3 * H;
   static constexpr uint32_t AU1 = 3 * H + H / 2;
-  // per-pixel stage
-  static constexpr uint32_t APOOL = AU0;         // rho A: [max ; mean] (H columns)
-  static constexpr uint32_t AR = D2A;            // B1 A after its G-buffer block: r
-  static constexpr uint32_t DR2 = D2A + H / 2;   // R2 D (16 columns)
-  static constexpr uint32_t AY = D2B;            // B2 A (y), R2 A (q)
-  static constexpr uint32_t AY2 = D2B + H / 2;   // R1 A (y2)
-  static constexpr uint32_t NCOLS = 512;
-  static_assert(AU1 + H / 2 <= NCOLS, "TMEM map overflows the allocation");
-  static_assert(DR2 % 16 == 0 && DR2 + 16 <= D2B, "R2 accumulator misplaced");
+  static constexpr uint32_t APOOL = AU0;  // rho A: [max ; mean] (H columns)
+  static constexpr uint32_t NCOLS = 4 * H;
+  static __device__ __forceinline__ uint32_t buf(uint32_t b) { return b * H; }
+  static_assert(NCOLS == 256 || NCOLS == 512, "TMEM allocation must be a power of two");
+};
+
+// Position in the rotating sequence of layer slots: buffer b = g mod 3 and
+// use u = g / 3 (the phase parity of the buffer's barriers is u & 1).
+struct SlotPos {
+  uint32_t b = 0, u = 0;
+  __device__ __forceinline__ void next() {
+    if (++b == 3) {
+      b = 0;
+      ++u;
+    }
+  }
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) {
@@ -116,7 +141,7 @@ __device__ __forceinline__ float bf16_value(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
 }
 
-// (a0, a1) + (b0, b1), round to nearest even / toward zero, two lanes per op.
+// (a0, a1) + (b0, b1), round to nearest even, two lanes per op.
 __device__ __forceinline__ void fadd2_rn(float& r0, float& r1, float a0, float a1, float b0,
                                          float b1) {
   asm("{.reg .b64 p, q, r;\n\tmov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
@@ -124,12 +149,13 @@ __device__ __forceinline__ void fadd2_rn(float& r0, float& r1, float a0, float a
       : "=f"(r0), "=f"(r1)
       : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
-__device__ __forceinline__ void fadd2_rz(float& r0, float& r1, float a0, float a1, float b0,
-                                         float b1) {
-  asm("{.reg .b64 p, q, r;\n\tmov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
-      "add.rz.f32x2 r, p, q;\n\tmov.b64 {%0, %1}, r;}"
-      : "=f"(r0), "=f"(r1)
-      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+// s0 += low bf16 of p, s1 += high bf16 of p, each rounded toward zero (the
+// bf16 value is exact in FP32, so only the sum is rounded).
+__device__ __forceinline__ void add_bf16x2_rz(float& s0, float& s1, uint32_t p) {
+  asm("{.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+      "add.rz.f32.bf16 %0, lo, %0;\n\tadd.rz.f32.bf16 %1, hi, %1;}"
+      : "+f"(s0), "+f"(s1)
+      : "r"(p));
 }
 __device__ __forceinline__ uint32_t bmax2(uint32_t a, uint32_t b) {
   uint32_t r;
@@ -169,16 +195,23 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
 // and described by `d0` (its K = 0 column).  Each K step of 16 advances the
 // start address by two core-matrix columns (2 N 16 bytes), i.e. (2 N 16) >> 4
 // in the descriptor's 14-bit address field (shared-memory addresses stay
-// < 256 KB, so the field never carries into the next one).  Fully unrolled:
-// the issuing thread blocks until the tensor core accepts each MMA, so
-// nothing but the MMA itself may sit between two issues.
+// < 256 KB, so the field never carries into the next one).  Issued by the
+// whole warp (one elected lane), eight K steps per statement.
 template <int N, int K>
 __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, uint32_t a_tmem, uint64_t d0,
                                            uint32_t idesc, bool accumulate = false) {
-  constexpr uint64_t step = static_cast<uint64_t>((2 * N * 16) >> 4);
+  constexpr uint32_t step = (2 * N * 16) >> 4;
+  if constexpr (K % 128 == 0) {
 #pragma unroll
-  for (int ks = 0; ks < K / 16; ++ks)
-    mma_f16_ts(d_tmem, a_tmem + ks * 8, d0 + step * ks, idesc, (ks > 0 || accumulate) ? 1u : 0u);
+    for (int kb = 0; kb < K / 128; ++kb)
+      mma8_f16_ts_e<step>(d_tmem, a_tmem + kb * 64, d0 + static_cast<uint64_t>(8 * step) * kb,
+                          idesc, (kb > 0 || accumulate) ? 1u : 0u);
+  } else {
+#pragma unroll
+    for (int ks = 0; ks < K / 16; ++ks)
+      mma_f16_ts_e(d_tmem, a_tmem + ks * 8, d0 + static_cast<uint64_t>(step) * ks, idesc,
+                   (ks > 0 || accumulate) ? 1u : 0u);
+  }
 }
 
 // Frame that owns global tile `tile`.
@@ -188,29 +221,115 @@ __device__ __forceinline__ const FusedFrame& frame_of(const FusedParams& prm, in
   return prm.f[fi];
 }
 
+// ------------------------------------------------------------- tile plan
+#ifndef GN_WIN_TILES
+#define GN_WIN_TILES 4
+#endif
+constexpr int kWinTiles = GN_WIN_TILES;  // tiles per count-sorting window
+constexpr int kPlanThreads = 256;
+static_assert(kWinTiles * kTile % kPlanThreads == 0, "window must split evenly over the threads");
+constexpr int kPlanPer = kWinTiles * kTile / kPlanThreads;  // pixels per thread
+constexpr int kClasses = kMaxK + 1;                          // counts 0..8
+
+// One CTA per window of up to kWinTiles tiles of one frame.  Every pixel of the
+// window gets the entry pixel | count << 28 at its sorted position: counts in
+// descending order, pixel index ascending within a count.  Rows past the
+// frame's last pixel get kPlanEmpty.  Counts above K are clamped to K and set
+// the count error bit.
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(const __grid_constant__ FusedParams prm) {
+  __shared__ int s_tot[kPlanThreads / 32][kClasses];
+  int fi = 0;
+  while (fi + 1 < prm.nframes && static_cast<int>(blockIdx.x) >= prm.f[fi + 1].win0) ++fi;
+  const FusedFrame& F = prm.f[fi];
+  const int lw = static_cast<int>(blockIdx.x) - F.win0;
+  const int tiles_f = (F.P + kTile - 1) / kTile;
+  const int rows = min(kWinTiles, tiles_f - lw * kWinTiles) * kTile;  // rows of this window
+  const int p0 = lw * kWinTiles * kTile;                              // first pixel
+  uint32_t* out = prm.plan + static_cast<size_t>(F.tile0 + lw * kWinTiles) * kTile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (blockIdx.x == 0 && tid == 0) *prm.next_tile = 0u;
+
+  int c[kPlanPer];
+  int pre[kClasses];
+#pragma unroll
+  for (int b = 0; b < kClasses; ++b) pre[b] = 0;
+  bool over = false;
+#pragma unroll
+  for (int i = 0; i < kPlanPer; ++i) {
+    const int p = p0 + tid * kPlanPer + i;
+    int v = -1;
+    if (p < F.P) {
+      v = F.counts[p];
+      if (v > F.K) {
+        over = true;
+        v = F.K;
+      }
+    }
+    c[i] = v;
+#pragma unroll
+    for (int b = 0; b < kClasses; ++b) pre[b] += v == b ? 1 : 0;
+  }
+  if (over) atomicOr(prm.err, kErrCount);
+  // exclusive prefix of every class over the threads, and the class totals
+#pragma unroll
+  for (int b = 0; b < kClasses; ++b) {
+    int x = pre[b];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) s_tot[warp][b] = x;
+    pre[b] = x - pre[b];
+  }
+  __syncthreads();
+  int base = 0;  // classes 8, 7, ..., 0 in turn
+#pragma unroll
+  for (int b = kClasses - 1; b >= 0; --b) {
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kPlanThreads / 32; ++w) {
+      const int t = s_tot[w][b];
+      before += w < warp ? t : 0;
+      total += t;
+    }
+    pre[b] += base + before;
+    base += total;
+  }
+#pragma unroll
+  for (int i = 0; i < kPlanPer; ++i) {
+    const uint32_t p = static_cast<uint32_t>(p0 + tid * kPlanPer + i);
+#pragma unroll
+    for (int b = 0; b < kClasses; ++b) {
+      if (c[i] == b) {
+        out[pre[b]] = p | (static_cast<uint32_t>(b) << 28);
+        ++pre[b];
+      }
+    }
+  }
+  for (int r = base + tid; r < rows; r += kPlanThreads) out[r] = kPlanEmpty;
+}
+
 // ---------------------------------------------------------------- loader
-// Shared-memory bookkeeping written by the loader warps.
+// Slot count of the tile of each parity, per loader warp (max over its rows).
 struct LoaderShared {
-  uint8_t cnt[2][kTile];  // layer counts of a tile (by tile parity), clamped to K
-  int ns[2][2];           // per loader warp: max count over its 64 rows
+  int ns[2][kLoadWarps];
+  int tile[2];
 };
 
-constexpr int kLoadWarps = 2;
 constexpr int kRowsPerLoadLane = kTile / (kLoadWarps * 32);  // 2
 
-// Layer k of rows row0 + 32 i (i < kRowsPerLoadLane): 12 channels each, zeros
-// where the slot is not valid.  One load instruction covers 32 consecutive
-// pixels of one channel plane.  Element offsets fit in 32 bits: the host
-// requires 12 K h w < 2^31.
-__device__ __forceinline__ void load_slot(const FusedFrame& F, int p0, int row0, int k,
+// Layer k of the lane's rows: 12 channels each, zeros where the slot is not
+// valid.  Element offsets fit in 32 bits: the host requires 12 K h w < 2^31.
+__device__ __forceinline__ void load_slot(const FusedFrame& F, int k,
+                                          const uint32_t (&pix)[kRowsPerLoadLane],
                                           const int (&cnt)[kRowsPerLoadLane],
                                           float (&x)[kRowsPerLoadLane][kTC]) {
   const uint32_t P = static_cast<uint32_t>(F.P);
 #pragma unroll
   for (int i = 0; i < kRowsPerLoadLane; ++i) {
-    const uint32_t pix = static_cast<uint32_t>(p0 + row0 + 32 * i);
     const bool v = k < cnt[i];
-    const uint32_t o = static_cast<uint32_t>(k) * kTC * P + pix;
+    const uint32_t o = static_cast<uint32_t>(k) * kTC * P + pix[i];
 #pragma unroll
     for (int ch = 0; ch < kTC; ++ch) x[i][ch] = v ? __ldg(F.tbuf + (o + ch * P)) : 0.0f;
   }
@@ -230,9 +349,10 @@ __device__ __forceinline__ void store_slot(uint32_t base, int row0,
   }
 }
 
-// Loader warps: per tile, publish the counts and the slot count, then fill the
-// layer operands slot by slot (two buffers, released by the MMAs that read
-// them) and B1's G-buffer operand (released by B1 of the previous tile).
+// Loader warps: per tile, read the plan entries of their rows and publish the
+// slot count, then fill the layer operands slot by slot (two buffers, released
+// by the phi1 MMAs that read them) and B1's G-buffer operand (released by B1
+// of the previous tile).
 template <int H>
 __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sbase,
                                             uint32_t bar_base, LoaderShared& ls,
@@ -240,23 +360,40 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
   using L = FusedLayout<H>;
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
   const int row0 = li * 64 + lane;
-  uint32_t lc = 0, n_ag = 0, tb = 0;
-  for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++tb) {
+  uint32_t lc = 0, n_ag = 0;
+  for (uint32_t tb = 0;; ++tb) {
+    // Dynamic schedule: loader warp 0 takes the next tile from the global
+    // counter (which the plan kernel zeroed) and hands it to loader warp 1;
+    // an index past the last tile ends every role's loop.
+    int tile;
+    if (li == 0) {
+      if (lane == 0) ls.tile[tb & 1] = static_cast<int>(atomicAdd(prm.next_tile, 1u));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_SCHED + (tb & 1)));
+    } else if (!warp_wait(bar(B_SCHED + (tb & 1)), (tb >> 1) & 1, abort_flag)) {
+      return;
+    }
+    tile = *reinterpret_cast<volatile int*>(&ls.tile[tb & 1]);
+    if (tile >= prm.total_tiles) {
+      if (lane == 0) {
+        ls.ns[tb & 1][li] = 0;
+        mbar_arrive(bar(B_TILE + (tb & 1)));
+      }
+      return;
+    }
     const FusedFrame& F = frame_of(prm, tile);
-    const int p0 = (tile - F.tile0) * kTile;
+    const uint32_t* ent = prm.plan + static_cast<size_t>(tile) * kTile;
+    uint32_t pix[kRowsPerLoadLane];
     int cnt[kRowsPerLoadLane];
+    bool has[kRowsPerLoadLane];
     int cmax = 0;
 #pragma unroll
     for (int i = 0; i < kRowsPerLoadLane; ++i) {
-      const int pix = p0 + row0 + 32 * i;
-      int c = pix < F.P ? static_cast<int>(F.counts[pix]) : 0;
-      if (c > F.K) {
-        atomicOr(prm.err, kErrCount);
-        c = F.K;
-      }
-      cnt[i] = c;
-      cmax = max(cmax, c);
-      ls.cnt[tb & 1][row0 + 32 * i] = static_cast<uint8_t>(c);
+      const uint32_t e = __ldg(ent + row0 + 32 * i);
+      has[i] = e != kPlanEmpty;
+      pix[i] = has[i] ? (e & kPlanPixelMask) : 0u;
+      cnt[i] = has[i] ? static_cast<int>(e >> 28) : 0;
+      cmax = max(cmax, cnt[i]);
     }
     const int wmax = __reduce_max_sync(0xffffffffu, cmax);
     if (lane == 0) ls.ns[tb & 1][li] = wmax;
@@ -266,18 +403,15 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
     const int ns = max(ls.ns[tb & 1][0], ls.ns[tb & 1][1]);
 
-    // G-buffer block [g0..g13, 1, 1] of rows row0 + 32 i, loads in flight now
+    // G-buffer block [g0..g13, 1, 1] of the lane's rows, loads in flight now
     float gv[kRowsPerLoadLane][kGC];
     {
       const uint32_t P = static_cast<uint32_t>(F.P);
 #pragma unroll
-      for (int i = 0; i < kRowsPerLoadLane; ++i) {
-        const int pix = p0 + row0 + 32 * i;
-        const bool v = pix < F.P;
+      for (int i = 0; i < kRowsPerLoadLane; ++i)
 #pragma unroll
         for (int ch = 0; ch < kGC; ++ch)
-          gv[i][ch] = v ? __ldg(F.gbuf + (static_cast<uint32_t>(ch) * P + pix)) : 0.0f;
-      }
+          gv[i][ch] = has[i] ? __ldg(F.gbuf + (static_cast<uint32_t>(ch) * P + pix[i])) : 0.0f;
     }
     auto put_ag = [&]() -> bool {
       if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
@@ -298,11 +432,11 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     };
 
     float x[kRowsPerLoadLane][kTC], y[kRowsPerLoadLane][kTC];
-    if (ns > 0) load_slot(F, p0, row0, 0, cnt, x);
+    if (ns > 0) load_slot(F, 0, pix, cnt, x);
     const int ag_after = min(ns, 2) - 1;  // B1's operand after the first slots
     if (ag_after < 0 && !put_ag()) return;
     for (int k = 0; k < ns; ++k, ++lc) {
-      if (k + 1 < ns) load_slot(F, p0, row0, k + 1, cnt, y);
+      if (k + 1 < ns) load_slot(F, k + 1, pix, cnt, y);
       const int b = lc & 1;
       if (!warp_wait(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
       store_slot(sbase + (b ? L::at1 : L::at0), row0, x);
@@ -319,15 +453,12 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 }
 
 // ------------------------------------------------------------------ kernel
-template <int H, int EW>
-__global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
+template <int H>
+__global__ void __launch_bounds__(kThreadsF, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   using L = FusedLayout<H>;
   using T = TMap<H>;
-  constexpr int kEpiWarps = Roles<EW>::kEpiWarps;
-  constexpr int kMmaWarp = Roles<EW>::kMmaWarp;
-  constexpr int kLoadWarp0 = Roles<EW>::kLoadWarp0;
-  constexpr int CH = H / EW;   // accumulator columns per epilogue thread
+  constexpr int CH = H / 2;    // accumulator columns per epilogue thread
   constexpr int CHC = CH / 2;  // TMEM columns of CH bf16 values
   static_assert(CH % 16 == 0, "accumulator columns per thread must be a multiple of 16");
 
@@ -344,18 +475,21 @@ __global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
 
   if (tid == 0) {
     mbar_init(bar(B_W), 1);
-    mbar_init(bar(B_IN), kEpiWarps);
-    mbar_init(bar(B_D1), 1);
-    mbar_init(bar(B_DR2), 1);
     mbar_init(bar(B_DP), 1);
+    mbar_init(bar(B_DR2), 1);
     mbar_init(bar(B_AG_F), kLoadWarps);
     mbar_init(bar(B_AG_E), 1);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(bar(B_D2 + b), 1);
-      mbar_init(bar(B_E2 + b), kEpiWarps);
+      mbar_init(bar(B_IN + b), kEpiWarps);
       mbar_init(bar(B_AT_F + b), kLoadWarps);
       mbar_init(bar(B_AT_E + b), 1);
       mbar_init(bar(B_TILE + b), kLoadWarps);
+      mbar_init(bar(B_SCHED + b), 1);
+    }
+    for (int b = 0; b < 3; ++b) {
+      mbar_init(bar(B_D1 + b), 1);
+      mbar_init(bar(B_D2 + b), 1);
+      mbar_init(bar(B_BE + b), kEpiWarps);
     }
     s_abort = 0;
     fence_mbar_init();
@@ -403,25 +537,36 @@ __global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
     const uint64_t dsc_ag = make_sdesc(sbase + L::ag, 128 * 16, 128);
     // B1's weights for r start after its 16-wide G-buffer block
     const uint64_t dsc_b1r = dsc_b1 + static_cast<uint64_t>((2 * H * 16) >> 4);
-    uint32_t n_in = 0, gs = 0, lc = 0, n_agf = 0, tb = 0;
+    SlotPos p1, p2;  // next phi1 / phi2 buffer
+    uint32_t g1 = 0, n_in = 0, n_agf = 0, tb = 0;
     const float* cur_fold = nullptr;
-    // phi1 for the next global layer slot (its operand filled by the loader)
+    // phi1 for the next global layer slot, into its rotating buffer
     auto phi1 = [&]() -> bool {
-      const int b = lc & 1;
-      if (!warp_wait(bar(B_AT_F + b), (lc >> 1) & 1, &s_abort)) return false;
+      // the buffer's previous phi2 accumulator has been read
+      if (!warp_wait(bar(B_BE + p1.b), (p1.u & 1) ^ 1, &s_abort)) return false;
+      const int a = g1 & 1;
+      if (!warp_wait(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
       tc_fence_after();
-      if (lane == 0) {
-        mma_f16_ss(tbase + T::D1, b ? dsc_at1 : dsc_at0, dsc_phi1, idH, 0u);
-        mma_commit(bar(B_D1));
-        mma_commit(bar(B_AT_E + b));
-      }
+      mma_f16_ss_e(tbase + T::buf(p1.b), a ? dsc_at1 : dsc_at0, dsc_phi1, idH, 0u);
+      mma_commit_e(bar(B_D1 + p1.b));
+      mma_commit_e(bar(B_AT_E + a));
       __syncwarp();
-      ++lc;
+      ++g1;
+      p1.next();
+      return true;
+    };
+    // the epilogue warps have written the next A operand in TMEM
+    auto wait_in = [&]() -> bool {
+      if (!warp_wait(bar(B_IN + (n_in & 1)), (n_in >> 1) & 1, &s_abort)) return false;
+      ++n_in;
+      tc_fence_after();
       return true;
     };
     if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
-    for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++tb) {
+    for (;; ++tb) {
       if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
+      const int tile = *reinterpret_cast<volatile int*>(&s_ld.tile[tb & 1]);
+      if (tile >= prm.total_tiles) break;
       const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
       const FusedFrame& F = frame_of(prm, tile);
       if (F.fold != cur_fold) {
@@ -442,54 +587,46 @@ __global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
         __syncwarp();
         cur_fold = F.fold;
       }
-      if (ns > 0 && !phi1()) goto done;
-      for (int k = 0; k < ns; ++k, ++gs) {
-        if (!warp_wait(bar(B_IN), n_in & 1, &s_abort)) goto done;  // U(k) written, D1 read
-        ++n_in;
-        tc_fence_after();
-        if (k + 1 < ns && !phi1()) goto done;
-        const int b = gs & 1;
-        // the buffer's previous accumulator (slot gs - 2) has been read
-        if (!warp_wait(bar(B_E2 + b), ((gs >> 1) & 1) ^ 1, &s_abort)) goto done;
-        tc_fence_after();
-        if (lane == 0) {
-          const uint32_t d = tbase + (b ? T::D2B : T::D2A);
+      for (int k = 0; k < ns && k < 2; ++k)
+        if (!phi1()) goto done;
+      for (int k = 0; k < ns; ++k) {
+        if (!wait_in()) goto done;  // U(k) written, its buffer read
+        {
+          const uint32_t d = tbase + T::buf(p2.b);
           issue_gemm<H, H>(d, tbase + (k & 1 ? T::AU1 : T::AU0), dsc_phi2, idH);
-          mma_f16_ss(d, dsc_one, dsc_phi2b, idH, 1u);
-          mma_commit(bar(B_D2 + b));
+          mma_f16_ss_e(d, dsc_one, dsc_phi2b, idH, 1u);
+          mma_commit_e(bar(B_D2 + p2.b));
         }
         __syncwarp();
+        p2.next();
+        if (k + 2 < ns && !phi1()) goto done;
       }
-      // Per-pixel layers rho, B1, B2, R1 into D1, then R2.
+      // Per-pixel layers rho, B1, B2, R1 into X, then R2 into Z + H/2.
+      const uint32_t X = tbase + T::buf(p1.b);
+      const uint32_t Y = tbase + T::buf(p1.b == 2 ? 0 : p1.b + 1);
+      const uint32_t Z = tbase + T::buf(p1.b == 0 ? 2 : p1.b - 1);
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
-        if (!warp_wait(bar(B_IN), n_in & 1, &s_abort)) goto done;
-        ++n_in;
+        if (!wait_in()) goto done;
         if (l == 1) {
           if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
           ++n_agf;
+          tc_fence_after();
         }
-        tc_fence_after();
-        if (lane == 0) {
-          if (l == 0) issue_gemm<H, 2 * H>(tbase + T::D1, tbase + T::APOOL, dsc_rho, idH);
-          if (l == 1) {
-            mma_f16_ss(tbase + T::D1, dsc_ag, dsc_b1, idH, 0u);
-            issue_gemm<H, H>(tbase + T::D1, tbase + T::AR, dsc_b1r, idH, true);
-          }
-          if (l == 2) issue_gemm<H, H>(tbase + T::D1, tbase + T::AY, dsc_b2, idH);
-          if (l == 3) issue_gemm<H, H>(tbase + T::D1, tbase + T::AY2, dsc_r1, idH);
-          mma_commit(bar(B_DP));
-          if (l == 1) mma_commit(bar(B_AG_E));
+        if (l == 0) issue_gemm<H, 2 * H>(X, tbase + T::APOOL, dsc_rho, idH);
+        if (l == 1) {
+          mma_f16_ss_e(X, dsc_ag, dsc_b1, idH, 0u);
+          issue_gemm<H, H>(X, Y, dsc_b1r, idH, true);
         }
+        if (l == 2) issue_gemm<H, H>(X, Y + H / 2, dsc_b2, idH);
+        if (l == 3) issue_gemm<H, H>(X, Z, dsc_r1, idH);
+        mma_commit_e(bar(B_DP));
+        if (l == 1) mma_commit_e(bar(B_AG_E));
         __syncwarp();
       }
-      if (!warp_wait(bar(B_IN), n_in & 1, &s_abort)) goto done;
-      ++n_in;
-      tc_fence_after();
-      if (lane == 0) {
-        issue_gemm<16, H>(tbase + T::DR2, tbase + T::AY, dsc_r2, id16);
-        mma_commit(bar(B_DR2));
-      }
+      if (!wait_in()) goto done;
+      issue_gemm<16, H>(Z + H / 2, Y + H / 2, dsc_r2, id16);
+      mma_commit_e(bar(B_DR2));
       __syncwarp();
     }
   } else {
@@ -501,19 +638,24 @@ __global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
     const float* b_b2 = reinterpret_cast<const float*>(smem + L::bias_b2) + g * CH;
     const float* b_r1 = reinterpret_cast<const float*>(smem + L::bias_r1) + g * CH;
     const float* b_r2 = reinterpret_cast<const float*>(smem + L::bias_r2);
-    uint32_t n_d1 = 0, n_dp = 0, gs = 0, tb = 0;
-    auto arrive = [&](int b) {
+    uint32_t gs = 0;  // global index of the tile's first layer slot
+    uint32_t n_in = 0, n_dp = 0, tb = 0;
+    auto arrive_in = [&]() {
       tmem_wait_st();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar(b));
+      if (lane == 0) mbar_arrive(bar(B_IN + (n_in & 1)));
+      ++n_in;
     };
     if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
 
-    for (int tile = blockIdx.x; tile < prm.total_tiles; tile += gridDim.x, ++tb) {
+    for (;; ++tb) {
       if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
-      const int c = s_ld.cnt[tb & 1][row];
+      const int tile = *reinterpret_cast<volatile int*>(&s_ld.tile[tb & 1]);
+      if (tile >= prm.total_tiles) break;
+      const uint32_t ent = __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row);
       const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
+      const int c = ent != kPlanEmpty ? static_cast<int>(ent >> 28) : 0;
 
       uint32_t mx[CHC];  // running max, bf16 pairs
       float sm[CH];      // fixed-point sums
@@ -522,14 +664,14 @@ __global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
 #pragma unroll
       for (int j = 0; j < CH; ++j) sm[j] = kSumBase;
 
-      // phi1(j) accumulator -> U(j) = ReLU as bf16.  16-column TMEM loads
+      // phi1(k) accumulator -> U(k) = ReLU as bf16.  16-column TMEM loads
       // are double buffered: block hh + 1 is in flight while hh is packed.
-      auto epi1 = [&](int j) -> bool {
-        if (!warp_wait(bar(B_D1), n_d1 & 1, &s_abort)) return false;
-        ++n_d1;
+      auto epi1 = [&](int k) -> bool {
+        const uint32_t gk = gs + k, b = gk % 3u;
+        if (!warp_wait(bar(B_D1 + b), (gk / 3u) & 1, &s_abort)) return false;
         tc_fence_after();
-        const uint32_t src = tl + T::D1 + g * CH;
-        const uint32_t dst = tl + (j & 1 ? T::AU1 : T::AU0) + g * CHC;
+        const uint32_t src = tl + T::buf(b) + g * CH;
+        const uint32_t dst = tl + (k & 1 ? T::AU1 : T::AU0) + g * CHC;
         uint32_t ra[16], rb[16];
         tmem_ld16_async(src, ra);
         tmem_wait_ld_tied(ra);
@@ -545,46 +687,49 @@ __global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
           tmem_st8(dst + hh * 8, u);
           if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
         }
-        arrive(B_IN);
+        arrive_in();
         return true;
       };
-
-      if (ns > 0 && !epi1(0)) goto done;
-      for (int k = 0; k < ns; ++k, ++gs) {
-        if (k + 1 < ns && !epi1(k + 1)) goto done;
-        const int b = gs & 1;
-        if (!warp_wait(bar(B_D2 + b), (gs >> 1) & 1, &s_abort)) goto done;
+      // phi2(k) accumulator -> pool update for pixels with k < c.
+      auto epi2 = [&](int k) -> bool {
+        const uint32_t gk = gs + k, b = gk % 3u;
+        if (!warp_wait(bar(B_D2 + b), (gk / 3u) & 1, &s_abort)) return false;
         tc_fence_after();
-        const uint32_t d2 = tl + (b ? T::D2B : T::D2A) + g * CH;
+        const uint32_t src = tl + T::buf(b) + g * CH;
         uint32_t ra[16], rb[16];
-        tmem_ld16_async(d2, ra);
+        tmem_ld16_async(src, ra);
         tmem_wait_ld_tied(ra);
 #pragma unroll
         for (int hh = 0; hh < CH / 16; ++hh) {
           uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
           uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
           if (hh + 1 < CH / 16) {
-            tmem_ld16_async(d2 + (hh + 1) * 16, nxt);
+            tmem_ld16_async(src + (hh + 1) * 16, nxt);
           } else {
             // every column of this buffer is in registers: release it
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar(B_E2 + b));
+            if (lane == 0) mbar_arrive(bar(B_BE + b));
           }
           if (k < c) {
 #pragma unroll
             for (int i = 0; i < 16; i += 2) {
               const int j = hh * 16 + i;
-              const float v0 = __uint_as_float(cur[i]), v1 = __uint_as_float(cur[i + 1]);
-              mx[j / 2] = bmax2(mx[j / 2], pack_bf16_relu(v0, v1));
-              float s0, s1;
-              fadd2_rz(s0, s1, sm[j], sm[j + 1], fmaxf(v0, 0.0f), fmaxf(v1, 0.0f));
-              sm[j] = s0;
-              sm[j + 1] = s1;
+              const uint32_t u =
+                  pack_bf16_relu(__uint_as_float(cur[i]), __uint_as_float(cur[i + 1]));
+              mx[j / 2] = bmax2(mx[j / 2], u);
+              add_bf16x2_rz(sm[j], sm[j + 1], u);
             }
           }
           if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
         }
+        return true;
+      };
+
+      if (ns > 0 && !epi1(0)) goto done;
+      for (int k = 0; k < ns; ++k) {
+        if (k + 1 < ns && !epi1(k + 1)) goto done;
+        if (!epi2(k)) goto done;
       }
 
       // pool = [max ; mean] -> APOOL (bf16, 2H values = H columns).
@@ -609,18 +754,23 @@ __global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
         }
         if (over && c > 0) atomicOr(prm.err, kErrRange);
       }
-      arrive(B_IN);
+      arrive_in();
 
-      // rho -> r (zero without layers) -> AR;  B1 -> y -> AY;
-      // B2 -> y2 -> AY2;  R1 -> q -> AY.
+      // rho -> r (zero without layers) -> Y;  B1 -> y -> Y + H/2;
+      // B2 -> y2 -> Z;  R1 -> q -> Y + H/2.  Accumulator X.
+      gs += ns;
+      const uint32_t r3 = gs % 3u;
+      const uint32_t X = tl + T::buf(r3);
+      const uint32_t Y = tl + T::buf(r3 == 2 ? 0 : r3 + 1);
+      const uint32_t Z = tl + T::buf(r3 == 0 ? 2 : r3 - 1);
 #pragma unroll 1
       for (int l = 0; l < 4; ++l) {
         if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
         ++n_dp;
         tc_fence_after();
         const float* bl = l == 0 ? b_rho : (l == 2 ? b_b2 : b_r1);
-        const uint32_t src = tl + T::D1 + g * CH;
-        const uint32_t dst = tl + (l == 0 ? T::AR : (l == 2 ? T::AY2 : T::AY)) + g * CHC;
+        const uint32_t src = X + g * CH;
+        const uint32_t dst = (l == 0 ? Y : (l == 2 ? Z : Y + H / 2)) + g * CHC;
         uint32_t ra[16], rb[16];
         tmem_ld16_async(src, ra);
         tmem_wait_ld_tied(ra);
@@ -646,19 +796,19 @@ __global__ void __launch_bounds__(Roles<EW>::kThreads, 1)
           tmem_st8(dst + hh * 8, u);
           if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
         }
-        arrive(B_IN);
+        arrive_in();
       }
       // R2 + sigmoid -> out (column group 0 stores).  Every warp waits for R2:
-      // it was issued after all warps' last B_IN arrival of this tile, so no
-      // warp's next-tile arrival can complete a phase of this tile.
+      // the next tile's phi1 for its third slot writes Z, and it is issued
+      // only after every warp's first arrival of that tile.
       if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
       if (g == 0) {
         tc_fence_after();
-        const FusedFrame& F = frame_of(prm, tile);
-        const int pix = (tile - F.tile0) * kTile + row;
         uint32_t r[4];
-        tmem_ld4(tl + T::DR2, r);
-        if (pix < F.P) {
+        tmem_ld4(Z + H / 2, r);
+        if (ent != kPlanEmpty) {
+          const FusedFrame& F = frame_of(prm, tile);
+          const uint32_t pix = ent & kPlanPixelMask;
 #pragma unroll
           for (int j = 0; j < kOut; ++j) {
             const float y = __uint_as_float(r[j]) + b_r2[j];
@@ -680,20 +830,13 @@ done:
 
 int g_sm_count = 0;
 
-// Epilogue warps per lane quadrant (compile-time tuning knob: 2 or 4).
-#ifndef GN_FUSED_EW
-#define GN_FUSED_EW 2
-#endif
-
 template <int H>
 cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
-  constexpr int EW = GN_FUSED_EW;
   constexpr int smem = FusedLayout<H>::smem_bytes;
-  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, EW>,
+  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  fused_bf16_kernel<H, EW>
-      <<<grid, Roles<EW>::kThreads, smem, s>>>(p, static_cast<const uint8_t*>(wimg));
+  fused_bf16_kernel<H><<<grid, kThreadsF, smem, s>>>(p, static_cast<const uint8_t*>(wimg));
   return cudaGetLastError();
 }
 
@@ -709,8 +852,24 @@ int device_sm_count() {
   return g_sm_count;
 }
 
-cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& p, cudaStream_t s) {
-  if (p.total_tiles <= 0) return cudaSuccess;
+size_t fused_plan_bytes(long long tiles) {
+  return kPlanHeader + static_cast<size_t>(tiles) * kTile * sizeof(uint32_t);
+}
+
+cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& params,
+                              cudaStream_t s) {
+  if (params.total_tiles <= 0) return cudaSuccess;
+  FusedParams p = params;
+  int wins = 0;
+  for (int i = 0; i < p.nframes; ++i) {
+    p.f[i].win0 = wins;
+    const int t = (p.f[i].P + kTile - 1) / kTile;
+    wins += (t + kWinTiles - 1) / kWinTiles;
+  }
+  p.total_windows = wins;
+  plan_kernel<<<p.total_windows, kPlanThreads, 0, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
   return H == 128 ? launch_h<128>(wimg, p, s, grid) : launch_h<64>(wimg, p, s, grid);
 }

@@ -263,9 +263,39 @@ int glassnet_latent_read(const gn_latent* lat, float* sigma, float* c_phi, float
 int glassnet_workspace_bytes(const gn_model* m, int K, int h, int w, size_t* bytes) {
   if (!m || !bytes) return fail(GN_EINVAL, "model and bytes must be non-NULL");
   if (K < 0 || K > gn::kMaxK || h < 1 || w < 1) return fail(GN_EINVAL, "bad frame size");
-  *bytes = m->precision == GN_FP32_PLAIN ? gn::plain_workspace_bytes(m->H, K, h * w) : 0;
+  const long long tiles = (static_cast<long long>(h) * w + gn::kTile - 1) / gn::kTile;
+  *bytes = m->precision == GN_FP32_PLAIN ? gn::plain_workspace_bytes(m->H, K, h * w)
+                                         : gn::fused_plan_bytes(tiles);
   return GN_OK;
 }
+
+namespace {
+// Grows a model-owned device buffer to `need` bytes; a growing call
+// synchronises the device first (the old buffer may be in use).
+int grow_buffer(void*& buf, size_t& bytes, size_t need, const char* what) {
+  if (bytes >= need) return GN_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess)
+    return fail(GN_ECUDA, "synchronise before growing the %s: %s", what, cudaGetErrorString(e));
+  if (buf) cudaFree(buf);
+  buf = nullptr;
+  bytes = 0;
+  if ((e = cudaMalloc(&buf, need)) != cudaSuccess)
+    return fail(GN_ENOMEM, "cudaMalloc %s (%zu bytes): %s", what, need, cudaGetErrorString(e));
+  bytes = need;
+  return GN_OK;
+}
+
+// Fills the frame table's first-tile offsets and the tile total.
+void number_tiles(gn::FusedParams& p) {
+  long long tiles = 0;
+  for (int i = 0; i < p.nframes; ++i) {
+    p.f[i].tile0 = static_cast<int>(tiles);
+    tiles += (static_cast<long long>(p.f[i].P) + gn::kTile - 1) / gn::kTile;
+  }
+  p.total_tiles = static_cast<int>(tiles);
+}
+}  // namespace
 
 int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbuf,
                        const float* tbuf, const uint8_t* cnt, int K, int h, int w, float* out,
@@ -287,9 +317,16 @@ int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbu
   gn::FusedParams p;
   std::memset(&p, 0, sizeof(p));
   p.nframes = 1;
-  p.total_tiles = (P + gn::kTile - 1) / gn::kTile;
   p.err = m->err;
   p.f[0] = gn::FusedFrame{gbuf, tbuf, cnt, out, lat->fold(), K, P, 0, 0};
+  number_tiles(p);
+  const size_t need = gn::fused_plan_bytes(p.total_tiles);
+  if (!ws || ws_bytes < need)
+    return fail(GN_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, need);
+  if (reinterpret_cast<uintptr_t>(ws) & 255u)
+    return fail(GN_EINVAL, "workspace must be 256-byte aligned");
+  p.next_tile = static_cast<uint32_t*>(ws);
+  p.plan = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws) + gn::kPlanHeader);
   e = gn::launch_fused_bf16(m->H, m->fused, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "fused launch");
   return GN_OK;
@@ -299,20 +336,14 @@ int glassnet_render(const gn_model* m, const gn_latent* lat, const float* gbuf, 
                     const uint8_t* cnt, int K, int h, int w, float* out, cudaStream_t s) {
   int rc = check_frame(m, lat, gbuf, tbuf, cnt, K, h, w, out);
   if (rc != GN_OK) return rc;
-  if (m->precision != GN_FP32_PLAIN)
-    return glassnet_render_ws(m, lat, gbuf, tbuf, cnt, K, h, w, out, nullptr, 0, s);
   gn_model* mm = const_cast<gn_model*>(m);
-  const size_t need = gn::plain_workspace_bytes(m->H, K, h * w);
-  if (mm->ws_bytes < need) {
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_fail(e, "synchronise before workspace growth");
-    if (mm->ws) cudaFree(mm->ws);
-    mm->ws = nullptr;
-    mm->ws_bytes = 0;
-    if ((e = cudaMalloc(&mm->ws, need)) != cudaSuccess)
-      return fail(GN_ENOMEM, "cudaMalloc workspace (%zu bytes): %s", need, cudaGetErrorString(e));
-    mm->ws_bytes = need;
+  size_t need = 0;
+  glassnet_workspace_bytes(m, K, h, w, &need);
+  if (m->precision != GN_FP32_PLAIN) {
+    if ((rc = grow_buffer(mm->plan, mm->plan_bytes, need, "tile plan")) != GN_OK) return rc;
+    return glassnet_render_ws(m, lat, gbuf, tbuf, cnt, K, h, w, out, mm->plan, mm->plan_bytes, s);
   }
+  if ((rc = grow_buffer(mm->ws, mm->ws_bytes, need, "workspace")) != GN_OK) return rc;
   return glassnet_render_ws(m, lat, gbuf, tbuf, cnt, K, h, w, out, mm->ws, mm->ws_bytes, s);
 }
 
@@ -367,12 +398,16 @@ int glassnet_render_batch(const gn_model* m, const gn_frame* frames, int n, cuda
     int rc = check_frame(m, f.latent, f.gbuf, f.tbuf, f.layer_count, f.K, f.h, f.w, f.out);
     if (rc != GN_OK) return fail(rc, "frame %d: %s", i, g_last_error.c_str());
     const int P = f.h * f.w;
-    p.f[i] = gn::FusedFrame{f.gbuf, f.tbuf, f.layer_count, f.out, f.latent->fold(), f.K, P,
-                            static_cast<int>(tiles), 0};
+    p.f[i] = gn::FusedFrame{f.gbuf, f.tbuf, f.layer_count, f.out, f.latent->fold(), f.K, P, 0, 0};
     tiles += (P + gn::kTile - 1) / gn::kTile;
-    if (tiles >= (1ll << 31)) return fail(GN_EINVAL, "batch too large");
+    if (tiles >= (1ll << 24)) return fail(GN_EINVAL, "batch too large");
   }
-  p.total_tiles = static_cast<int>(tiles);
+  number_tiles(p);
+  gn_model* mm = const_cast<gn_model*>(m);
+  int rc = grow_buffer(mm->plan, mm->plan_bytes, gn::fused_plan_bytes(tiles), "tile plan");
+  if (rc != GN_OK) return rc;
+  p.next_tile = static_cast<uint32_t*>(mm->plan);
+  p.plan = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(mm->plan) + gn::kPlanHeader);
   cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "batched fused launch");
   return GN_OK;
@@ -407,6 +442,7 @@ void glassnet_free_model(gn_model* m) {
   if (m->err) cudaFree(m->err);
   if (m->ws) cudaFree(m->ws);
   if (m->stage) cudaFree(m->stage);
+  if (m->plan) cudaFree(m->plan);
   delete m;
 }
 

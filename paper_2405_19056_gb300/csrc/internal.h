@@ -15,6 +15,15 @@ constexpr int kOut = 3;        // RGB
 constexpr int kMaxK = 8;       // layer slots per pixel
 constexpr int kTile = 128;     // pixels per fused tile (tcgen05 M)
 
+// Fused tile plan: one entry per tile row, pixel | count << 28 (pixel indices
+// stay below 2^28 because 12 max(K, 1) P < 2^31), or kPlanEmpty for a row past
+// the frame's last pixel.
+constexpr uint32_t kPlanEmpty = 0xffffffffu;
+// The plan workspace starts with a 256-byte header holding the dynamic tile
+// counter; the entries follow.
+constexpr size_t kPlanHeader = 256;
+constexpr uint32_t kPlanPixelMask = 0x0fffffffu;
+
 // Sticky device error bits (model error word).
 constexpr uint32_t kErrCount = 1u;    // layer count above K
 constexpr uint32_t kErrRange = 2u;    // exact set-sum left its fixed-point range
@@ -85,7 +94,7 @@ struct FusedFrame {
   int K;
   int P;      // pixels
   int tile0;  // first global tile index of this frame
-  int pad;
+  int win0;   // first global plan window of this frame (set by the launcher)
 };
 
 constexpr int kMaxBatch = 64;
@@ -94,13 +103,18 @@ struct FusedParams {
   FusedFrame f[kMaxBatch];
   int nframes;
   int total_tiles;
+  int total_windows;    // set by the launcher
   uint32_t* err;
+  uint32_t* plan;       // total_tiles * kTile entries (device)
+  uint32_t* next_tile;  // dynamic tile counter (device), zeroed by the plan kernel
 };
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_encode(const float* w32, const WeightIndex& wi, const float* scene_dev,
                           float* latent_dev, cudaStream_t s);
+// Plan kernel, then the fused kernel.
 cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& p, cudaStream_t s);
+size_t fused_plan_bytes(long long tiles);
 size_t plain_workspace_bytes(int H, int K, int P);
 cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const float* latent,
                               const float* gbuf, const float* tbuf, const uint8_t* counts, int K,
@@ -120,6 +134,8 @@ struct gn_model {
   size_t ws_bytes = 0;
   void* stage = nullptr;    // glassnet_render_host staging (device)
   size_t stage_bytes = 0;
+  void* plan = nullptr;     // fused tile plan of glassnet_render / _batch (device)
+  size_t plan_bytes = 0;
 };
 
 struct gn_latent {
