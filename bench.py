@@ -299,10 +299,11 @@ def run_fused(args, world, rank, local):
         "fps": world * args.steps / (total_ms * 1e-3),
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "encode_scene_ms": encode_ms,
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,  # per step: tile-plan kernel + fused kernel
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
                      "kernel": "fused_bf16_kernel<128>",
+                     "duration": "CUDA events around the render call (plan kernel + fused kernel)",
                      "flops_per_launch": step_flops,
                      "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)"},
     }

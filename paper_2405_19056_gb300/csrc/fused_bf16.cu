@@ -226,28 +226,33 @@ __device__ __forceinline__ const FusedFrame& frame_of(const FusedParams& prm, in
 #define GN_WIN_TILES 4
 #endif
 constexpr int kWinTiles = GN_WIN_TILES;  // tiles per count-sorting window
-constexpr int kPlanThreads = 256;
-static_assert(kWinTiles * kTile % kPlanThreads == 0, "window must split evenly over the threads");
-constexpr int kPlanPer = kWinTiles * kTile / kPlanThreads;  // pixels per thread
-constexpr int kClasses = kMaxK + 1;                          // counts 0..8
+constexpr int kPlanWarps = 4;                         // windows per plan CTA
+constexpr int kPlanPer = kWinTiles * kTile / 32;        // pixels per lane
+constexpr int kClasses = kMaxK + 1;                     // counts 0..8
+static_assert(kPlanPer <= 32, "window too large for one warp");
 
-// One CTA per window of up to kWinTiles tiles of one frame.  Every pixel of the
-// window gets the entry pixel | count << 28 at its sorted position: counts in
-// descending order, pixel index ascending within a count.  Rows past the
-// frame's last pixel get kPlanEmpty.  Counts above K are clamped to K and set
-// the count error bit.
-__global__ void __launch_bounds__(kPlanThreads) plan_kernel(const __grid_constant__ FusedParams prm) {
-  __shared__ int s_tot[kPlanThreads / 32][kClasses];
+// One warp per window of up to kWinTiles tiles of one frame (lane l holds
+// pixels l * kPlanPer ..).  Every pixel of the window gets the entry
+// pixel | count << 28 at its sorted position: counts in descending order,
+// pixel index ascending within a count.  Rows past the frame's last pixel get
+// kPlanEmpty.  Counts above K are clamped to K and set the count error bit.
+// The fused kernel is launched as a programmatic dependent of this grid, so
+// it may start (and load its weights) before this grid ends; it waits on the
+// grid dependency before it reads the plan.
+__global__ void __launch_bounds__(kPlanWarps * 32) plan_kernel(const __grid_constant__ FusedParams prm) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int win = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
+  if (win == 0 && lane == 0) *prm.next_tile = 0u;
+  if (win >= prm.total_windows) return;
   int fi = 0;
-  while (fi + 1 < prm.nframes && static_cast<int>(blockIdx.x) >= prm.f[fi + 1].win0) ++fi;
+  while (fi + 1 < prm.nframes && win >= prm.f[fi + 1].win0) ++fi;
   const FusedFrame& F = prm.f[fi];
-  const int lw = static_cast<int>(blockIdx.x) - F.win0;
+  const int lw = win - F.win0;
   const int tiles_f = (F.P + kTile - 1) / kTile;
   const int rows = min(kWinTiles, tiles_f - lw * kWinTiles) * kTile;  // rows of this window
-  const int p0 = lw * kWinTiles * kTile;                              // first pixel
+  const int p0 = lw * kWinTiles * kTile + lane * kPlanPer;            // lane's first pixel
   uint32_t* out = prm.plan + static_cast<size_t>(F.tile0 + lw * kWinTiles) * kTile;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (blockIdx.x == 0 && tid == 0) *prm.next_tile = 0u;
 
   int c[kPlanPer];
   int pre[kClasses];
@@ -256,10 +261,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const __grid_constan
   bool over = false;
 #pragma unroll
   for (int i = 0; i < kPlanPer; ++i) {
-    const int p = p0 + tid * kPlanPer + i;
     int v = -1;
-    if (p < F.P) {
-      v = F.counts[p];
+    if (p0 + i < F.P) {
+      v = F.counts[p0 + i];
       if (v > F.K) {
         over = true;
         v = F.K;
@@ -270,35 +274,24 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const __grid_constan
     for (int b = 0; b < kClasses; ++b) pre[b] += v == b ? 1 : 0;
   }
   if (over) atomicOr(prm.err, kErrCount);
-  // exclusive prefix of every class over the threads, and the class totals
+  // exclusive prefix of every class over the lanes; classes 8, 7, ..., 0 are
+  // laid out one after the other
+  int base = 0;
 #pragma unroll
-  for (int b = 0; b < kClasses; ++b) {
+  for (int b = kClasses - 1; b >= 0; --b) {
     int x = pre[b];
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, d);
       if (lane >= d) x += y;
     }
-    if (lane == 31) s_tot[warp][b] = x;
-    pre[b] = x - pre[b];
-  }
-  __syncthreads();
-  int base = 0;  // classes 8, 7, ..., 0 in turn
-#pragma unroll
-  for (int b = kClasses - 1; b >= 0; --b) {
-    int before = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < kPlanThreads / 32; ++w) {
-      const int t = s_tot[w][b];
-      before += w < warp ? t : 0;
-      total += t;
-    }
-    pre[b] += base + before;
+    const int total = __shfl_sync(0xffffffffu, x, 31);
+    pre[b] = base + x - pre[b];
     base += total;
   }
 #pragma unroll
   for (int i = 0; i < kPlanPer; ++i) {
-    const uint32_t p = static_cast<uint32_t>(p0 + tid * kPlanPer + i);
+    const uint32_t p = static_cast<uint32_t>(p0 + i);
 #pragma unroll
     for (int b = 0; b < kClasses; ++b) {
       if (c[i] == b) {
@@ -307,7 +300,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const __grid_constan
       }
     }
   }
-  for (int r = base + tid; r < rows; r += kPlanThreads) out[r] = kPlanEmpty;
+  for (int r = base + lane; r < rows; r += 32) out[r] = kPlanEmpty;
 }
 
 // ---------------------------------------------------------------- loader
@@ -510,6 +503,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       sts128(sbase + L::aone + 2048u + r * 16u, 0u, 0u, 0u, 0u);
     }
     fence_proxy_async_smem();
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
     loader_loop<H>(prm, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA warp
@@ -521,6 +515,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       }
     }
     __syncwarp();
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
     constexpr uint32_t idH = make_idesc(128, H, kFmtBF16);
     constexpr uint32_t id16 = make_idesc(128, 16, kFmtBF16);
     const uint64_t dsc_phi1 = make_sdesc(sbase + L::phi1, H * 16, 128);
@@ -647,6 +642,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       if (lane == 0) mbar_arrive(bar(B_IN + (n_in & 1)));
       ++n_in;
     };
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
     if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
 
     for (;; ++tb) {
@@ -836,8 +832,19 @@ cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int
   cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  fused_bf16_kernel<H><<<grid, kThreadsF, smem, s>>>(p, static_cast<const uint8_t*>(wimg));
-  return cudaGetLastError();
+  // Programmatic dependent launch: the CTAs may start while the plan kernel
+  // is still running; they wait on the grid dependency before the plan reads.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreadsF);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H>, p, static_cast<const uint8_t*>(wimg));
 }
 
 }  // namespace
@@ -867,7 +874,7 @@ cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& params
     wins += (t + kWinTiles - 1) / kWinTiles;
   }
   p.total_windows = wins;
-  plan_kernel<<<p.total_windows, kPlanThreads, 0, s>>>(p);
+  plan_kernel<<<(p.total_windows + kPlanWarps - 1) / kPlanWarps, kPlanWarps * 32, 0, s>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
