@@ -311,6 +311,7 @@ def run_fused(args, world, rank, local):
         result["fp32_plain"] = fp32_plain_leg(dev, weights, scene, dframes, stream)
         result["fp32_plain"]["speedup_of_bf16_fused"] = value / world / result["fp32_plain"]["value"]
         result["e2e"] = e2e_leg(model, lat, frames, args, stream, world)
+        result["batch_16_frames"] = batch_leg(model, dev, stream)
     clocks = clk.summary()
     result["clocks"] = clocks
     if rank == 0 and not args.no_extras:
@@ -342,6 +343,50 @@ def fp32_plain_leg(dev, weights, scene, dframes, stream, steps=10):
     ms = e0.elapsed_time(e1) / steps
     return {"value": H_IMG * W_IMG / (ms * 1e-3) / 1e6, "unit": UNIT, "fps": 1e3 / ms,
             "ms_per_step": ms, "steps": steps, "dtype": "fp32"}
+
+
+def batch_leg(model, dev, stream, steps=20):
+    """The batched workload: 16 frames, sizes 128..1024 squared, K ~ U{2..8},
+    every slot valid, 4 scenes, one persistent launch per batch, replayed
+    from a CUDA graph (and the direct batched launch for comparison)."""
+    import torch
+    from gen import synth
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    specs = synth.batch_specs(16, synth.BATCH_SIZES_FULL, seed=0)
+    lats = [model.encode(synth.make_scene(100 + s), stream) for s in range(4)]
+    frames = []
+    for i, sp in enumerate(specs):
+        f = synth.make_frame(sp.h, sp.w, sp.K, counts="all", seed=i)
+        frames.append(dict(latent=lats[sp.scene].handle, gbuf=torch.from_numpy(f.gbuf).to(dev),
+                           tbuf=torch.from_numpy(f.tbuf).to(dev),
+                           layer_count=torch.from_numpy(f.counts).to(dev), K=sp.K, h=sp.h, w=sp.w,
+                           out=torch.empty((3, sp.h, sp.w), device=dev)))
+    px = sum(sp.h * sp.w for sp in specs)
+    graph = gl.glassnet_graph_create(model.handle, frames)
+    res = {"workload": "16 frames, sizes {128,256,512,1024}^2, K~U{2..8}, all slots valid, "
+                       "4 scenes, H=128 (batch seed 0)", "pixels_per_batch": px}
+    try:
+        for name, run in (("graph", lambda: gl.glassnet_graph_launch(graph, stream)),
+                          ("direct", lambda: gl.glassnet_render_batch(model.handle, frames, stream))):
+            for _ in range(3):
+                run()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                run()
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res[name] = {"ms_per_batch": ms, "value": px / (ms * 1e-3) / 1e6, "unit": "Mpixel/s",
+                         "steps": steps}
+        gl.glassnet_check(model.handle, stream)
+    finally:
+        gl.glassnet_graph_free(graph)
+    res["gpu_launches_per_batch"] = 2
+    return res
 
 
 def e2e_leg(model, lat, frames, args, stream, world, steps=20):

@@ -202,3 +202,28 @@ def permute_layers(frame: Frame, seed: int) -> Frame:
     tp = np.take_along_axis(t, idx, axis=0)
     return Frame(gbuf=frame.gbuf.copy(), tbuf=tp.reshape(K, TBUF_CHANNELS, h, w),
                  counts=frame.counts.copy())
+
+
+# Batched workload (16 frames of mixed size and layer count, a few scenes):
+# per frame a square resolution drawn uniformly from `sizes`, K ~ U{2..8} and
+# scene index i mod n_scenes; every slot of every pixel valid.
+BATCH_SIZES_FULL = (128, 256, 512, 1024)
+
+
+class BatchSpec:
+    def __init__(self, h: int, w: int, K: int, scene: int):
+        self.h, self.w, self.K, self.scene = h, w, K, scene
+
+    def __repr__(self):
+        return f"BatchSpec({self.h}x{self.w}, K={self.K}, scene={self.scene})"
+
+
+def batch_specs(n: int = 16, sizes=BATCH_SIZES_FULL, n_scenes: int = 4,
+                seed: int = 0) -> list[BatchSpec]:
+    rng = np.random.default_rng([seed, 5])
+    out = []
+    for i in range(n):
+        s = int(rng.choice(np.asarray(sizes)))
+        K = int(rng.integers(2, 9))
+        out.append(BatchSpec(s, s, K, i % n_scenes))
+    return out

@@ -190,6 +190,36 @@ int glassnet_render_batch(const gn_model* model, const gn_frame* frames, int n,
                           cudaStream_t stream);
 
 /*
+ * CUDA graphs of batched launches.  A graph holds the launch sequence of
+ * glassnet_render_batch (the tile-plan kernel and the fused kernel) for one
+ * batch shape: the number of frames and each frame's h, w and K.  The paper
+ * has no counterpart (its Sec. 5 times single frames); this is the serving
+ * layer's way to replay a shape bucket without rebuilding its launches.
+ *
+ * glassnet_graph_create validates the batch as glassnet_render_batch does,
+ * allocates the graph's own tile-plan workspace (device memory, so graphs of
+ * one model may replay concurrently on different streams) and captures the
+ * launches with the given buffers and latents.  Synchronous; call it outside
+ * any stream capture.  Errors: those of glassnet_render_batch, GN_ENOMEM,
+ * GN_ECUDA.
+ *
+ * glassnet_graph_launch replays the graph on `stream`: same buffers, same
+ * latents (whose contents may have changed), fresh contents read at replay.
+ * Each replay's output equals glassnet_render_batch of the same frames, bit
+ * for bit.  Replays of one graph must not overlap on the GPU (they share the
+ * graph's workspace).
+ *
+ * glassnet_graph_update rebinds the graph to other buffers and latents of
+ * the same shapes (n, and per frame h, w, K; GN_EINVAL otherwise).  Call it
+ * when no replay of the graph is in flight.
+ */
+typedef struct gn_graph gn_graph;
+int glassnet_graph_create(const gn_model* model, const gn_frame* frames, int n, gn_graph** out);
+int glassnet_graph_launch(gn_graph* graph, cudaStream_t stream);
+int glassnet_graph_update(gn_graph* graph, const gn_frame* frames, int n);
+void glassnet_graph_free(gn_graph* graph);
+
+/*
  * Synchronises `stream`, then returns and clears the model's device error
  * bits: GN_EINVAL (a layer count above K), GN_ERANGE (a pixel's exact set-sum
  * reached 2^11 and lost exactness), GN_ETIMEOUT (a device wait gave up), or

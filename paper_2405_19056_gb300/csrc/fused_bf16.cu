@@ -827,10 +827,20 @@ done:
 int g_sm_count = 0;
 
 template <int H>
+cudaError_t prepare_h() {
+  static bool done = false;  // per process: the attribute holds for every later launch
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       FusedLayout<H>::smem_bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int H>
 cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
   constexpr int smem = FusedLayout<H>::smem_bytes;
-  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = prepare_h<H>();
   if (e != cudaSuccess) return e;
   // Programmatic dependent launch: the CTAs may start while the plan kernel
   // is still running; they wait on the grid dependency before the plan reads.
@@ -857,6 +867,11 @@ int device_sm_count() {
     if (g_sm_count <= 0) g_sm_count = 1;
   }
   return g_sm_count;
+}
+
+cudaError_t prepare_fused_bf16(int H) {
+  device_sm_count();
+  return H == 128 ? prepare_h<128>() : prepare_h<64>();
 }
 
 size_t fused_plan_bytes(long long tiles) {

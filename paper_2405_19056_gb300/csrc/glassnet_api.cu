@@ -297,6 +297,45 @@ void number_tiles(gn::FusedParams& p) {
 }
 }  // namespace
 
+}  // extern "C"
+
+namespace gn {
+
+int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* out) {
+  if (!m || !frames || !out) return fail(GN_EINVAL, "model and frames must be non-NULL");
+  if (n < 1 || n > kMaxBatch) return fail(GN_EINVAL, "batch of %d frames outside 1..%d", n, kMaxBatch);
+  if (m->precision == GN_FP32_PLAIN)
+    return fail(GN_EUNSUPPORTED, "batched launch needs a fused precision");
+  FusedParams& p = *out;
+  std::memset(&p, 0, sizeof(p));
+  p.nframes = n;
+  p.err = m->err;
+  long long tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    const gn_frame& f = frames[i];
+    int rc = check_frame(m, f.latent, f.gbuf, f.tbuf, f.layer_count, f.K, f.h, f.w, f.out);
+    if (rc != GN_OK) {
+      const std::string msg = g_last_error;
+      return fail(rc, "frame %d: %s", i, msg.c_str());
+    }
+    const int P = f.h * f.w;
+    p.f[i] = FusedFrame{f.gbuf, f.tbuf, f.layer_count, f.out, f.latent->fold(), f.K, P, 0, 0};
+    tiles += (P + kTile - 1) / kTile;
+    if (tiles >= (1ll << 24)) return fail(GN_EINVAL, "batch too large");
+  }
+  number_tiles(p);
+  return GN_OK;
+}
+
+void bind_plan(FusedParams& p, void* ws) {
+  p.next_tile = static_cast<uint32_t*>(ws);
+  p.plan = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws) + kPlanHeader);
+}
+
+}  // namespace gn
+
+extern "C" {
+
 int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbuf,
                        const float* tbuf, const uint8_t* cnt, int K, int h, int w, float* out,
                        void* ws, size_t ws_bytes, cudaStream_t s) {
@@ -325,8 +364,7 @@ int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbu
     return fail(GN_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, need);
   if (reinterpret_cast<uintptr_t>(ws) & 255u)
     return fail(GN_EINVAL, "workspace must be 256-byte aligned");
-  p.next_tile = static_cast<uint32_t*>(ws);
-  p.plan = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws) + gn::kPlanHeader);
+  gn::bind_plan(p, ws);
   e = gn::launch_fused_bf16(m->H, m->fused, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "fused launch");
   return GN_OK;
@@ -385,29 +423,13 @@ int glassnet_render_host(gn_model* m, const gn_latent* lat, const float* gbuf_h,
 }
 
 int glassnet_render_batch(const gn_model* m, const gn_frame* frames, int n, cudaStream_t s) {
-  if (!m || !frames) return fail(GN_EINVAL, "model and frames must be non-NULL");
-  if (n < 1 || n > gn::kMaxBatch) return fail(GN_EINVAL, "batch of %d frames outside 1..%d", n, gn::kMaxBatch);
-  if (m->precision == GN_FP32_PLAIN) return fail(GN_EUNSUPPORTED, "batched launch needs a fused precision");
   gn::FusedParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.nframes = n;
-  p.err = m->err;
-  long long tiles = 0;
-  for (int i = 0; i < n; ++i) {
-    const gn_frame& f = frames[i];
-    int rc = check_frame(m, f.latent, f.gbuf, f.tbuf, f.layer_count, f.K, f.h, f.w, f.out);
-    if (rc != GN_OK) return fail(rc, "frame %d: %s", i, g_last_error.c_str());
-    const int P = f.h * f.w;
-    p.f[i] = gn::FusedFrame{f.gbuf, f.tbuf, f.layer_count, f.out, f.latent->fold(), f.K, P, 0, 0};
-    tiles += (P + gn::kTile - 1) / gn::kTile;
-    if (tiles >= (1ll << 24)) return fail(GN_EINVAL, "batch too large");
-  }
-  number_tiles(p);
-  gn_model* mm = const_cast<gn_model*>(m);
-  int rc = grow_buffer(mm->plan, mm->plan_bytes, gn::fused_plan_bytes(tiles), "tile plan");
+  int rc = gn::build_batch(m, frames, n, &p);
   if (rc != GN_OK) return rc;
-  p.next_tile = static_cast<uint32_t*>(mm->plan);
-  p.plan = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(mm->plan) + gn::kPlanHeader);
+  gn_model* mm = const_cast<gn_model*>(m);
+  rc = grow_buffer(mm->plan, mm->plan_bytes, gn::fused_plan_bytes(p.total_tiles), "tile plan");
+  if (rc != GN_OK) return rc;
+  gn::bind_plan(p, mm->plan);
   cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "batched fused launch");
   return GN_OK;

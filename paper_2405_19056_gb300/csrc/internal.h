@@ -114,6 +114,8 @@ cudaError_t launch_encode(const float* w32, const WeightIndex& wi, const float* 
                           float* latent_dev, cudaStream_t s);
 // Plan kernel, then the fused kernel.
 cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& p, cudaStream_t s);
+// Kernel attributes the fused launch needs; call once outside stream capture.
+cudaError_t prepare_fused_bf16(int H);
 size_t fused_plan_bytes(long long tiles);
 size_t plain_workspace_bytes(int H, int K, int P);
 cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const float* latent,
@@ -137,6 +139,16 @@ struct gn_model {
   void* plan = nullptr;     // fused tile plan of glassnet_render / _batch (device)
   size_t plan_bytes = 0;
 };
+
+namespace gn {
+// Validates a batch and fills the frame table (no plan binding); sets the
+// thread's error message on failure.
+int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* out);
+// Points the params at a plan workspace of fused_plan_bytes(p.total_tiles) bytes.
+void bind_plan(FusedParams& p, void* ws);
+// Sets the calling thread's glassnet_last_error message; returns `code`.
+int set_error(int code, const char* msg);
+}  // namespace gn
 
 struct gn_latent {
   int H = 0, Z = 0;

@@ -49,6 +49,10 @@ _SIGNATURES = {
     "glassnet_render_batch": (_I, [_P, _P, _I, _P]),
     "glassnet_check": (_I, [_P, _P]),
     "glassnet_render_fp32_static": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P]),
+    "glassnet_graph_create": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
+    "glassnet_graph_launch": (_I, [_P, _P]),
+    "glassnet_graph_update": (_I, [_P, _P, _I]),
+    "glassnet_graph_free": (None, [_P]),
     "glassnet_free_latent": (None, [_P]),
     "glassnet_free_model": (None, [_P]),
     "glassnet_last_error": (ctypes.c_char_p, []),
@@ -194,11 +198,34 @@ class GnFrame(ctypes.Structure):
 
 def glassnet_render_batch(model, frames, stream=None):
     """frames: list of dicts with latent, gbuf, tbuf, layer_count, K, h, w, out."""
+    _check(_lib().glassnet_render_batch(model, _frame_array(frames), len(frames), _stream(stream)))
+
+
+def _frame_array(frames):
     arr = (GnFrame * len(frames))()
     for i, f in enumerate(frames):
         arr[i] = GnFrame(f["latent"], _ptr(f["gbuf"]), _ptr(f.get("tbuf")), _ptr(f["layer_count"]),
                          f["K"], f["h"], f["w"], _ptr(f["out"]))
-    _check(_lib().glassnet_render_batch(model, arr, len(frames), _stream(stream)))
+    return arr
+
+
+def glassnet_graph_create(model, frames) -> int:
+    """Captures the batched launch of `frames` (same dicts as glassnet_render_batch)."""
+    out = ctypes.c_void_p()
+    _check(_lib().glassnet_graph_create(model, _frame_array(frames), len(frames), ctypes.byref(out)))
+    return out.value
+
+
+def glassnet_graph_launch(graph, stream=None):
+    _check(_lib().glassnet_graph_launch(graph, _stream(stream)))
+
+
+def glassnet_graph_update(graph, frames):
+    _check(_lib().glassnet_graph_update(graph, _frame_array(frames), len(frames)))
+
+
+def glassnet_graph_free(graph):
+    _lib().glassnet_graph_free(graph)
 
 
 def glassnet_render_fp32_static(model, latent, gbuf, tbuf, layer_count, K, h, w, out,

@@ -107,6 +107,11 @@ def test_null_arguments_rejected(lib):
     assert lib.glassnet_workspace_bytes(None, 1, 1, 1, ctypes.byref(n)) == gl.GN_EINVAL
     lib.glassnet_free_model(None)
     lib.glassnet_free_latent(None)
+    assert lib.glassnet_graph_create(None, None, 1, ctypes.byref(out)) == gl.GN_EINVAL
+    assert lib.glassnet_graph_create(None, None, 1, None) == gl.GN_EINVAL
+    assert lib.glassnet_graph_launch(None, None) == gl.GN_EINVAL
+    assert lib.glassnet_graph_update(None, None, 1) == gl.GN_EINVAL
+    lib.glassnet_graph_free(None)
 
 
 def test_python_binding_raises_with_message(lib):
