@@ -61,7 +61,7 @@ def algorithmic_flops(H: int, counts: np.ndarray) -> float:
 def kernel_digest() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2405_19056_gb300", "csrc")
-    for name in ("fused_bf16.cu", "tc_ptx.cuh", "internal.h"):
+    for name in ("fused_bf16.cu", "fused_common.cuh", "plan.cu", "tc_ptx.cuh", "internal.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()

@@ -190,6 +190,33 @@ int glassnet_render_batch(const gn_model* model, const gn_frame* frames, int n,
                           cudaStream_t stream);
 
 /*
+ * FP8 variant.  A model loaded with GN_FP8_FUSED runs every layer's GEMM with
+ * E4M3 operands and FP32 accumulation: weights are quantised per output
+ * channel (scale = channel |max| / 448), activations per tensor with static
+ * scales taken from one calibration render.  The per-scene folded biases
+ * stay exact (a BF16 hi/lo MMA), the set pooling stays exact and
+ * order-independent (it runs on the dequantised phi output).  The paper
+ * fixes no precision for the network; this is a deployment variant.
+ *
+ * glassnet_calibrate_fp8 renders the given frame with the FP32 plain path
+ * (intermediates in the model's FP32 workspace, grown on demand), takes the
+ * |max| of each layer input over it (t over valid slots, U, pool, [g ; r],
+ * y, y2, q), sets scale = 2 |max| / 448 (one binade of headroom against
+ * inputs beyond the calibration frame's range; 1 where the maximum is 0) and
+ * packs the E4M3 image.  Synchronous.  Until it has run, rendering with the model
+ * returns GN_EINVAL.  It may be called again to recalibrate (no render may be
+ * in flight).  Errors: GN_EINVAL (not an FP8 model, bad frame), GN_ENOMEM,
+ * GN_ECUDA.
+ *
+ * glassnet_fp8_scales copies the seven activation scales (the real value of a
+ * code x is x * scale), in the order above, to host memory.
+ */
+int glassnet_calibrate_fp8(gn_model* model, const gn_latent* latent, const float* gbuf,
+                           const float* tbuf, const uint8_t* layer_count, int K, int h, int w,
+                           cudaStream_t stream);
+int glassnet_fp8_scales(const gn_model* model, float* scales);
+
+/*
  * CUDA graphs of batched launches.  A graph holds the launch sequence of
  * glassnet_render_batch (the tile-plan kernel and the fused kernel) for one
  * batch shape: the number of frames and each frame's h, w and K.  The paper

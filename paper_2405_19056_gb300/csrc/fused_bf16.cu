@@ -69,39 +69,11 @@
 // exit.
 #include <cuda_bf16.h>
 
-#include "internal.h"
-#include "tc_ptx.cuh"
+#include "fused_common.cuh"
 
 namespace gn {
 namespace {
-
-constexpr int kEpiWarps = 8;
-constexpr int kMmaWarp = 8;
-constexpr int kLoadWarp0 = 9;  // warps 9 and 10
-constexpr int kLoadWarps = 2;
-constexpr int kThreadsF = 11 * 32;
-constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per device-side wait
-constexpr float kSumBase = 2048.0f;          // 2^11: quantum 2^-12 in [2^11, 2^12)
-constexpr float kSumLimit = 4096.0f;
-constexpr float kHalfQuantum = 1.0f / 8192.0f;
-
-// mbarrier slots.
-enum : int {
-  B_W = 0,       // weights copied (transaction count)
-  B_IN = 1,      // + (n & 1): an A operand in TMEM written (epilogue warps arrive)
-  B_DP = 3,      // per-pixel layer accumulator ready (commit)
-  B_DR2 = 4,     // R2 accumulator ready (commit)
-  B_AG_F = 5,    // B1's G-buffer operand written (loaders)
-  B_AG_E = 6,    // B1's G-buffer operand consumed (commit)
-  B_D1 = 7,      // + buffer (3): phi1 accumulator ready (commit)
-  B_D2 = 10,     // + buffer (3): phi2 accumulator ready (commit)
-  B_BE = 13,     // + buffer (3): phi2 accumulator read (epilogue warps arrive)
-  B_AT_F = 16,   // + buffer (2): layer operand written (loaders)
-  B_AT_E = 18,   // + buffer (2): layer operand consumed (commit)
-  B_TILE = 20,   // + tile parity: tile index and slot count published (loaders)
-  B_SCHED = 22,  // + tile parity: tile index taken (loader warp 0)
-  B_COUNT = 24
-};
+using namespace fused;
 
 // TMEM column map (128 lanes x 4H columns of 32 bits): three accumulator
 // buffers of H columns, then U (H bf16 = H/2 columns) double buffered.  The
@@ -120,76 +92,6 @@ struct TMap {
   static __device__ __forceinline__ uint32_t buf(uint32_t b) { return b * H; }
   static_assert(NCOLS == 256 || NCOLS == 512, "TMEM allocation must be a power of two");
 };
-
-// Position in the rotating sequence of layer slots: buffer b = g mod 3 and
-// use u = g / 3 (the phase parity of the buffer's barriers is u & 1).
-struct SlotPos {
-  uint32_t b = 0, u = 0;
-  __device__ __forceinline__ void next() {
-    if (++b == 3) {
-      b = 0;
-      ++u;
-    }
-  }
-};
-
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-  __nv_bfloat16 b = __float2bfloat16_rn(x);
-  return *reinterpret_cast<uint16_t*>(&b);
-}
-__device__ __forceinline__ float bf16_value(float x) {
-  return __bfloat162float(__float2bfloat16_rn(x));
-}
-
-// (a0, a1) + (b0, b1), round to nearest even, two lanes per op.
-__device__ __forceinline__ void fadd2_rn(float& r0, float& r1, float a0, float a1, float b0,
-                                         float b1) {
-  asm("{.reg .b64 p, q, r;\n\tmov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
-      "add.rn.f32x2 r, p, q;\n\tmov.b64 {%0, %1}, r;}"
-      : "=f"(r0), "=f"(r1)
-      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
-}
-// s0 += low bf16 of p, s1 += high bf16 of p, each rounded toward zero (the
-// bf16 value is exact in FP32, so only the sum is rounded).
-__device__ __forceinline__ void add_bf16x2_rz(float& s0, float& s1, uint32_t p) {
-  asm("{.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-      "add.rz.f32.bf16 %0, lo, %0;\n\tadd.rz.f32.bf16 %1, hi, %1;}"
-      : "+f"(s0), "+f"(s1)
-      : "r"(p));
-}
-__device__ __forceinline__ uint32_t bmax2(uint32_t a, uint32_t b) {
-  uint32_t r;
-  asm("max.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-  return r;
-}
-__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                       uint32_t d) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
-               "r"(d)
-               : "memory");
-}
-
-// Bounded wait shared by a whole warp: every lane waits, then the warp agrees.
-// On a timeout the CTA-wide abort flag is raised and every later wait fails
-// at once, so all warps reach the common exit.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  bool ok = mbar_try_wait(bar, parity);
-  if (!ok) {
-    const uint64_t t0 = globaltimer_ns();
-    while (true) {
-      if (mbar_try_wait(bar, parity)) {
-        ok = true;
-        break;
-      }
-      if (*abort_flag) break;
-      if (globaltimer_ns() - t0 > kWaitNs) {
-        *abort_flag = 1;
-        break;
-      }
-    }
-  }
-  return __all_sync(0xffffffffu, ok);
-}
 
 // D (+)= A (TMEM, K/2 columns from a_tmem) x B^T, B stored [K/8][N][8] bf16
 // and described by `d0` (its K = 0 column).  Each K step of 16 advances the
@@ -213,104 +115,6 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, uint32_t a_tmem, uin
                    (ks > 0 || accumulate) ? 1u : 0u);
   }
 }
-
-// Frame that owns global tile `tile`.
-__device__ __forceinline__ const FusedFrame& frame_of(const FusedParams& prm, int tile) {
-  int fi = 0;
-  while (fi + 1 < prm.nframes && tile >= prm.f[fi + 1].tile0) ++fi;
-  return prm.f[fi];
-}
-
-// ------------------------------------------------------------- tile plan
-#ifndef GN_WIN_TILES
-#define GN_WIN_TILES 4
-#endif
-constexpr int kWinTiles = GN_WIN_TILES;  // tiles per count-sorting window
-constexpr int kPlanWarps = 4;                         // windows per plan CTA
-constexpr int kPlanPer = kWinTiles * kTile / 32;        // pixels per lane
-constexpr int kClasses = kMaxK + 1;                     // counts 0..8
-static_assert(kPlanPer <= 32, "window too large for one warp");
-
-// One warp per window of up to kWinTiles tiles of one frame (lane l holds
-// pixels l * kPlanPer ..).  Every pixel of the window gets the entry
-// pixel | count << 28 at its sorted position: counts in descending order,
-// pixel index ascending within a count.  Rows past the frame's last pixel get
-// kPlanEmpty.  Counts above K are clamped to K and set the count error bit.
-// The fused kernel is launched as a programmatic dependent of this grid, so
-// it may start (and load its weights) before this grid ends; it waits on the
-// grid dependency before it reads the plan.
-__global__ void __launch_bounds__(kPlanWarps * 32) plan_kernel(const __grid_constant__ FusedParams prm) {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int lane = threadIdx.x & 31;
-  const int win = blockIdx.x * kPlanWarps + (threadIdx.x >> 5);
-  if (win == 0 && lane == 0) *prm.next_tile = 0u;
-  if (win >= prm.total_windows) return;
-  int fi = 0;
-  while (fi + 1 < prm.nframes && win >= prm.f[fi + 1].win0) ++fi;
-  const FusedFrame& F = prm.f[fi];
-  const int lw = win - F.win0;
-  const int tiles_f = (F.P + kTile - 1) / kTile;
-  const int rows = min(kWinTiles, tiles_f - lw * kWinTiles) * kTile;  // rows of this window
-  const int p0 = lw * kWinTiles * kTile + lane * kPlanPer;            // lane's first pixel
-  uint32_t* out = prm.plan + static_cast<size_t>(F.tile0 + lw * kWinTiles) * kTile;
-
-  int c[kPlanPer];
-  int pre[kClasses];
-#pragma unroll
-  for (int b = 0; b < kClasses; ++b) pre[b] = 0;
-  bool over = false;
-#pragma unroll
-  for (int i = 0; i < kPlanPer; ++i) {
-    int v = -1;
-    if (p0 + i < F.P) {
-      v = F.counts[p0 + i];
-      if (v > F.K) {
-        over = true;
-        v = F.K;
-      }
-    }
-    c[i] = v;
-#pragma unroll
-    for (int b = 0; b < kClasses; ++b) pre[b] += v == b ? 1 : 0;
-  }
-  if (over) atomicOr(prm.err, kErrCount);
-  // exclusive prefix of every class over the lanes; classes 8, 7, ..., 0 are
-  // laid out one after the other
-  int base = 0;
-#pragma unroll
-  for (int b = kClasses - 1; b >= 0; --b) {
-    int x = pre[b];
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= d) x += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, x, 31);
-    pre[b] = base + x - pre[b];
-    base += total;
-  }
-#pragma unroll
-  for (int i = 0; i < kPlanPer; ++i) {
-    const uint32_t p = static_cast<uint32_t>(p0 + i);
-#pragma unroll
-    for (int b = 0; b < kClasses; ++b) {
-      if (c[i] == b) {
-        out[pre[b]] = p | (static_cast<uint32_t>(b) << 28);
-        ++pre[b];
-      }
-    }
-  }
-  for (int r = base + lane; r < rows; r += 32) out[r] = kPlanEmpty;
-}
-
-// ---------------------------------------------------------------- loader
-// Slot count of the tile of each parity, per loader warp (max over its rows).
-struct LoaderShared {
-  int ns[2][kLoadWarps];
-  int tile[2];
-};
-
-constexpr int kRowsPerLoadLane = kTile / (kLoadWarps * 32);  // 2
 
 // Layer k of the lane's rows: 12 channels each, zeros where the slot is not
 // valid.  Element offsets fit in 32 bits: the host requires 12 K h w < 2^31.
@@ -824,8 +628,6 @@ done:
   }
 }
 
-int g_sm_count = 0;
-
 template <int H>
 cudaError_t prepare_h() {
   static bool done = false;  // per process: the attribute holds for every later launch
@@ -859,38 +661,16 @@ cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int
 
 }  // namespace
 
-int device_sm_count() {
-  if (g_sm_count == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sm_count <= 0) g_sm_count = 1;
-  }
-  return g_sm_count;
-}
-
 cudaError_t prepare_fused_bf16(int H) {
   device_sm_count();
   return H == 128 ? prepare_h<128>() : prepare_h<64>();
-}
-
-size_t fused_plan_bytes(long long tiles) {
-  return kPlanHeader + static_cast<size_t>(tiles) * kTile * sizeof(uint32_t);
 }
 
 cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& params,
                               cudaStream_t s) {
   if (params.total_tiles <= 0) return cudaSuccess;
   FusedParams p = params;
-  int wins = 0;
-  for (int i = 0; i < p.nframes; ++i) {
-    p.f[i].win0 = wins;
-    const int t = (p.f[i].P + kTile - 1) / kTile;
-    wins += (t + kWinTiles - 1) / kWinTiles;
-  }
-  p.total_windows = wins;
-  plan_kernel<<<(p.total_windows + kPlanWarps - 1) / kPlanWarps, kPlanWarps * 32, 0, s>>>(p);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_plan(p, s);
   if (e != cudaSuccess) return e;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
   return H == 128 ? launch_h<128>(wimg, p, s, grid) : launch_h<64>(wimg, p, s, grid);

@@ -1,0 +1,128 @@
+// Device-side pieces shared by the fused kernels (BF16 and FP8): warp roles,
+// mbarrier slots, the pooling arithmetic helpers, bounded waits, the frame
+// lookup and the loader's shared bookkeeping.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace gn {
+namespace fused {
+constexpr int kEpiWarps = 8;
+constexpr int kMmaWarp = 8;
+constexpr int kLoadWarp0 = 9;  // warps 9 and 10
+constexpr int kLoadWarps = 2;
+constexpr int kThreadsF = 11 * 32;
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per device-side wait
+constexpr float kSumBase = 2048.0f;          // 2^11: quantum 2^-12 in [2^11, 2^12)
+constexpr float kSumLimit = 4096.0f;
+constexpr float kHalfQuantum = 1.0f / 8192.0f;
+
+// mbarrier slots.
+enum : int {
+  B_W = 0,       // weights copied (transaction count)
+  B_IN = 1,      // + (n & 1): an A operand in TMEM written (epilogue warps arrive)
+  B_DP = 3,      // per-pixel layer accumulator ready (commit)
+  B_DR2 = 4,     // R2 accumulator ready (commit)
+  B_AG_F = 5,    // B1's G-buffer operand written (loaders)
+  B_AG_E = 6,    // B1's G-buffer operand consumed (commit)
+  B_D1 = 7,      // + buffer (3): phi1 accumulator ready (commit)
+  B_D2 = 10,     // + buffer (3): phi2 accumulator ready (commit)
+  B_BE = 13,     // + buffer (3): phi2 accumulator read (epilogue warps arrive)
+  B_AT_F = 16,   // + buffer (2): layer operand written (loaders)
+  B_AT_E = 18,   // + buffer (2): layer operand consumed (commit)
+  B_TILE = 20,   // + tile parity: tile index and slot count published (loaders)
+  B_SCHED = 22,  // + tile parity: tile index taken (loader warp 0)
+  B_COUNT = 24
+};
+
+
+// Position in the rotating sequence of layer slots: buffer b = g mod 3 and
+// use u = g / 3 (the phase parity of the buffer's barriers is u & 1).
+struct SlotPos {
+  uint32_t b = 0, u = 0;
+  __device__ __forceinline__ void next() {
+    if (++b == 3) {
+      b = 0;
+      ++u;
+    }
+  }
+};
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  __nv_bfloat16 b = __float2bfloat16_rn(x);
+  return *reinterpret_cast<uint16_t*>(&b);
+}
+__device__ __forceinline__ float bf16_value(float x) {
+  return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+// (a0, a1) + (b0, b1), round to nearest even, two lanes per op.
+__device__ __forceinline__ void fadd2_rn(float& r0, float& r1, float a0, float a1, float b0,
+                                         float b1) {
+  asm("{.reg .b64 p, q, r;\n\tmov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
+      "add.rn.f32x2 r, p, q;\n\tmov.b64 {%0, %1}, r;}"
+      : "=f"(r0), "=f"(r1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+// s0 += low bf16 of p, s1 += high bf16 of p, each rounded toward zero (the
+// bf16 value is exact in FP32, so only the sum is rounded).
+__device__ __forceinline__ void add_bf16x2_rz(float& s0, float& s1, uint32_t p) {
+  asm("{.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+      "add.rz.f32.bf16 %0, lo, %0;\n\tadd.rz.f32.bf16 %1, hi, %1;}"
+      : "+f"(s0), "+f"(s1)
+      : "r"(p));
+}
+__device__ __forceinline__ uint32_t bmax2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("max.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                       uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+
+// Bounded wait shared by a whole warp: every lane waits, then the warp agrees.
+// On a timeout the CTA-wide abort flag is raised and every later wait fails
+// at once, so all warps reach the common exit.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  bool ok = mbar_try_wait(bar, parity);
+  if (!ok) {
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+      if (mbar_try_wait(bar, parity)) {
+        ok = true;
+        break;
+      }
+      if (*abort_flag) break;
+      if (globaltimer_ns() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        break;
+      }
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Frame that owns global tile `tile`.
+__device__ __forceinline__ const FusedFrame& frame_of(const FusedParams& prm, int tile) {
+  int fi = 0;
+  while (fi + 1 < prm.nframes && tile >= prm.f[fi + 1].tile0) ++fi;
+  return prm.f[fi];
+}
+
+// ---------------------------------------------------------------- loader
+// Slot count of the tile of each parity, per loader warp (max over its rows).
+struct LoaderShared {
+  int ns[2][kLoadWarps];
+  int tile[2];
+};
+
+constexpr int kRowsPerLoadLane = kTile / (kLoadWarps * 32);  // 2
+
+}  // namespace fused
+}  // namespace gn

@@ -2,8 +2,11 @@
 // packing, model / latent objects, and dispatch to the kernels.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -92,6 +95,100 @@ std::vector<uint8_t> pack_fused_bf16(const float* w, const gn::WeightIndex& wi) 
   return img;
 }
 
+// Round-to-nearest-even float -> E4M3 code (1 sign, 4 exponent bits with bias
+// 7, 3 mantissa bits; largest finite 448, no infinities), saturating to
+// +-448 (the satfinite rule).  NaN -> 0x7f.
+uint8_t e4m3_rne(float f) {
+  if (std::isnan(f)) return 0x7f;
+  const uint8_t sign = std::signbit(f) ? 0x80 : 0x00;
+  const double a = std::fabs(static_cast<double>(f));
+  if (a >= 448.0) return sign | 0x7e;
+  int code;
+  if (a < std::ldexp(1.0, -6)) {
+    code = static_cast<int>(std::nearbyint(a / std::ldexp(1.0, -9)));  // subnormal steps of 2^-9
+  } else {
+    int e;
+    const double m = std::frexp(a, &e);  // a = m 2^e, m in [0.5, 1)
+    // a = (1 + f) 2^(e-1): mantissa steps of 2^(e-4)
+    double q = std::nearbyint(a / std::ldexp(1.0, e - 4));  // in [8, 16]
+    int ex = e - 1;
+    if (q >= 16.0) {
+      q = 8.0;
+      ex += 1;
+    }
+    const int field = ex + 7;
+    code = (field << 3) | (static_cast<int>(q) - 8);
+    (void)m;
+  }
+  if (code > 0x7e) code = 0x7e;
+  return sign | static_cast<uint8_t>(code);
+}
+
+// Element (n, k) of an N x K E4M3 operand in the [K/16][N][16] layout.
+inline size_t core_idx8(int N, int n, int k) {
+  return (static_cast<size_t>(k / 16) * N + n) * 16 + (k % 16);
+}
+
+// FP8 image (FusedLayoutF8) from the concat-form weights and the activation
+// scales act[kFp8Acts] = s of t, U, pool, [g ; r], y, y2, q.
+template <int H>
+std::vector<uint8_t> pack_fused_fp8(const float* w, const gn::WeightIndex& wi, const float* act) {
+  using L = gn::FusedLayoutF8<H>;
+  std::vector<uint8_t> img(L::bytes, 0);
+  auto W = [&](int l, int n, int j) { return w[wi.w[l] + static_cast<size_t>(n) * wi.in[l] + j]; };
+  auto Bv = [&](int l, int n) { return w[wi.b[l] + n]; };
+  // per-output-channel weight scale over the columns that stay in the GEMM
+  auto wscale = [&](int l, int n, int j0, int j1, int j2 = 0, int j3 = 0) {
+    float m = 0.0f;
+    for (int j = j0; j < j1; ++j) m = std::max(m, std::fabs(W(l, n, j)));
+    for (int j = j2; j < j3; ++j) m = std::max(m, std::fabs(W(l, n, j)));
+    return m > 0.0f ? m / 448.0f : 1.0f;
+  };
+  auto put = [&](uint32_t off, int N, int n, int k, float v) {
+    img[off + core_idx8(N, n, k)] = e4m3_rne(v);
+  };
+  const float s_t = act[0], s_u = act[1], s_pool = act[2], s_g = act[3], s_y = act[4],
+              s_y2 = act[5], s_q = act[6];
+  float* c = reinterpret_cast<float*>(img.data() + L::cst);
+  for (int n = 0; n < H; ++n) {
+    const float w1 = wscale(gn::LPHI1, n, 0, gn::kTC);
+    for (int k = 0; k < gn::kTC; ++k) put(L::phi1, H, n, k, W(gn::LPHI1, n, k) / w1);
+    c[L::S_PHI1 + n] = s_t * w1 / s_u;
+    c[L::U_PHI1 + n] = 1.0f / (s_t * w1);
+    const float w2 = wscale(gn::LPHI2, n, 0, H);
+    for (int k = 0; k < H; ++k) put(L::phi2, H, n, k, W(gn::LPHI2, n, k) / w2);
+    c[L::S_PHI2 + n] = s_u * w2;
+    c[L::B_PHI2 + n] = Bv(gn::LPHI2, n);
+    const float wr = wscale(gn::LRHO, n, 0, 2 * H);
+    for (int k = 0; k < 2 * H; ++k) put(L::rho, H, n, k, W(gn::LRHO, n, k) / wr);
+    c[L::S_RHO + n] = s_pool * wr / s_g;
+    c[L::B_RHO + n] = Bv(gn::LRHO, n) / s_g;
+    const float wb1 = wscale(gn::LB1, n, 0, gn::kGC + H);
+    for (int k = 0; k < gn::kGC; ++k) put(L::b1, H, n, k, W(gn::LB1, n, k) / wb1);
+    for (int k = 0; k < H; ++k) put(L::b1, H, n, 32 + k, W(gn::LB1, n, gn::kGC + k) / wb1);
+    c[L::S_B1 + n] = s_g * wb1 / s_y;
+    c[L::U_B1 + n] = 1.0f / (s_g * wb1);
+    const float wb2 = wscale(gn::LB2, n, 0, H);
+    for (int k = 0; k < H; ++k) put(L::b2, H, n, k, W(gn::LB2, n, k) / wb2);
+    c[L::S_B2 + n] = s_y * wb2 / s_y2;
+    c[L::B_B2 + n] = Bv(gn::LB2, n) / s_y2;
+    const float wq1 = wscale(gn::LR1, n, 0, H);
+    for (int k = 0; k < H; ++k) put(L::r1, H, n, k, W(gn::LR1, n, k) / wq1);
+    c[L::S_R1 + n] = s_y2 * wq1 / s_q;
+    c[L::B_R1 + n] = Bv(gn::LR1, n) / s_q;
+  }
+  for (int n = 0; n < gn::kOut; ++n) {
+    const float wq2 = wscale(gn::LR2, n, 0, H);
+    for (int k = 0; k < H; ++k) put(L::r2, 16, n, k, W(gn::LR2, n, k) / wq2);
+    c[L::S_R2 + n] = s_q * wq2;
+    c[L::B_R2 + n] = Bv(gn::LR2, n);
+  }
+  c[L::INV_S_T] = 1.0f / s_t;
+  c[L::INV_S_G] = 1.0f / s_g;
+  c[L::INV_S_POOL] = 1.0f / s_pool;
+  return img;
+}
+
 bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
 
 int check_frame(const gn_model* m, const gn_latent* lat, const float* gbuf, const float* tbuf,
@@ -154,7 +251,6 @@ int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_mod
   if (!ok_widths)
     return fail(GN_EUNSUPPORTED, "widths (H, Z) = (%u, %u); this build has (64, 128), (128, 256)",
                 hd.hidden, hd.latent);
-  if (precision == GN_FP8_FUSED) return fail(GN_EUNSUPPORTED, "FP8 fused path is not built");
 
   std::vector<float> w(wi.total);
   std::memcpy(w.data(), payload, wi.total * sizeof(float));
@@ -179,6 +275,15 @@ int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_mod
       (e = cudaMemset(m->err, 0, 256)) != cudaSuccess) {
     glassnet_free_model(m);
     return fail(GN_ENOMEM, "cudaMalloc error word: %s", cudaGetErrorString(e));
+  }
+  if (precision == GN_FP8_FUSED) {
+    // packed by glassnet_calibrate_fp8 once activation scales are known
+    m->host_w = static_cast<float*>(std::malloc(wi.total * sizeof(float)));
+    if (!m->host_w) {
+      glassnet_free_model(m);
+      return fail(GN_ENOMEM, "host allocation failed");
+    }
+    std::memcpy(m->host_w, w.data(), wi.total * sizeof(float));
   }
   if (precision == GN_BF16_FUSED) {
     std::vector<uint8_t> img =
@@ -306,6 +411,8 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
   if (n < 1 || n > kMaxBatch) return fail(GN_EINVAL, "batch of %d frames outside 1..%d", n, kMaxBatch);
   if (m->precision == GN_FP32_PLAIN)
     return fail(GN_EUNSUPPORTED, "batched launch needs a fused precision");
+  if (m->precision == GN_FP8_FUSED && !m->fp8_ready)
+    return fail(GN_EINVAL, "FP8 model is not calibrated (glassnet_calibrate_fp8)");
   FusedParams& p = *out;
   std::memset(&p, 0, sizeof(p));
   p.nframes = n;
@@ -325,6 +432,15 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
   }
   number_tiles(p);
   return GN_OK;
+}
+
+cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s) {
+  return m->precision == GN_FP8_FUSED ? launch_fused_fp8(m->H, m->fused, p, s)
+                                      : launch_fused_bf16(m->H, m->fused, p, s);
+}
+
+cudaError_t prepare_fused(const gn_model* m) {
+  return m->precision == GN_FP8_FUSED ? prepare_fused_fp8(m->H) : prepare_fused_bf16(m->H);
 }
 
 void bind_plan(FusedParams& p, void* ws) {
@@ -353,6 +469,8 @@ int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbu
     if (e != cudaSuccess) return cuda_fail(e, "FP32 plain launch");
     return GN_OK;
   }
+  if (m->precision == GN_FP8_FUSED && !m->fp8_ready)
+    return fail(GN_EINVAL, "FP8 model is not calibrated (glassnet_calibrate_fp8)");
   gn::FusedParams p;
   std::memset(&p, 0, sizeof(p));
   p.nframes = 1;
@@ -365,7 +483,7 @@ int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbu
   if (reinterpret_cast<uintptr_t>(ws) & 255u)
     return fail(GN_EINVAL, "workspace must be 256-byte aligned");
   gn::bind_plan(p, ws);
-  e = gn::launch_fused_bf16(m->H, m->fused, p, s);
+  e = gn::launch_fused(m, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "fused launch");
   return GN_OK;
 }
@@ -430,8 +548,68 @@ int glassnet_render_batch(const gn_model* m, const gn_frame* frames, int n, cuda
   rc = grow_buffer(mm->plan, mm->plan_bytes, gn::fused_plan_bytes(p.total_tiles), "tile plan");
   if (rc != GN_OK) return rc;
   gn::bind_plan(p, mm->plan);
-  cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s);
+  cudaError_t e = gn::launch_fused(m, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "batched fused launch");
+  return GN_OK;
+}
+
+// Activation scale = kFp8Headroom |max| / 448 over the calibration render.
+// E4M3's relative step is the same over its whole normal range, so one binade
+// of headroom costs precision only for values in the lowest binade, while it
+// keeps inputs up to twice the calibration maximum from saturating (measured:
+// with no headroom, frames other than the calibration frame showed clipped
+// outliers of up to 0.12 in RGB; with it, <= 0.056).
+constexpr float kFp8Headroom = 2.0f;
+
+int glassnet_calibrate_fp8(gn_model* m, const gn_latent* lat, const float* gbuf, const float* tbuf,
+                           const uint8_t* cnt, int K, int h, int w, cudaStream_t s) {
+  if (!m) return fail(GN_EINVAL, "model is NULL");
+  if (m->precision != GN_FP8_FUSED) return fail(GN_EINVAL, "model precision is not GN_FP8_FUSED");
+  const int P = h * w;
+  int rc = check_frame(m, lat, gbuf, tbuf, cnt, K, h, w, gbuf);
+  if (rc != GN_OK) return rc;
+  const size_t need = gn::plain_workspace_bytes(m->H, K, P);
+  if ((rc = grow_buffer(m->ws, m->ws_bytes, need, "workspace")) != GN_OK) return rc;
+  void* tmp = nullptr;  // RGB of the calibration render, then the amax words
+  const size_t out_bytes = (static_cast<size_t>(P) * gn::kOut * sizeof(float) + 255) / 256 * 256;
+  cudaError_t e = cudaMalloc(&tmp, out_bytes + 256);
+  if (e != cudaSuccess) return fail(GN_ENOMEM, "cudaMalloc calibration scratch");
+  float* out = static_cast<float*>(tmp);
+  uint32_t* amax = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(tmp) + out_bytes);
+  uint32_t bits[gn::kFp8Acts] = {};
+  e = gn::launch_plain_fp32(m->w32, m->wi, lat->d, gbuf, tbuf, cnt, K, P, out, m->ws, m->err, s);
+  if (e == cudaSuccess)
+    e = gn::launch_fp8_act_amax(m->ws, gbuf, tbuf, cnt, m->H, K, P, amax, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bits, amax, sizeof(bits), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "calibration render");
+  float act[gn::kFp8Acts];
+  for (int i = 0; i < gn::kFp8Acts; ++i) {
+    float a;
+    std::memcpy(&a, &bits[i], 4);
+    act[i] = (a > 0.0f && std::isfinite(a)) ? a * kFp8Headroom / 448.0f : 1.0f;
+  }
+  std::vector<uint8_t> img = m->H == 128 ? pack_fused_fp8<128>(m->host_w, m->wi, act)
+                                         : pack_fused_fp8<64>(m->host_w, m->wi, act);
+  if (!m->fused) {
+    if ((e = cudaMalloc(&m->fused, img.size())) != cudaSuccess)
+      return fail(GN_ENOMEM, "cudaMalloc packed weights: %s", cudaGetErrorString(e));
+    m->fused_bytes = img.size();
+  }
+  if ((e = cudaMemcpy(m->fused, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "upload packed FP8 weights");
+  std::memcpy(m->fp8_act, act, sizeof(act));
+  m->fp8_ready = true;
+  return GN_OK;
+}
+
+int glassnet_fp8_scales(const gn_model* m, float* scales) {
+  if (!m || !scales) return fail(GN_EINVAL, "model and scales must be non-NULL");
+  if (m->precision != GN_FP8_FUSED || !m->fp8_ready)
+    return fail(GN_EINVAL, "not a calibrated GN_FP8_FUSED model");
+  std::memcpy(scales, m->fp8_act, sizeof(m->fp8_act));
   return GN_OK;
 }
 
@@ -465,6 +643,7 @@ void glassnet_free_model(gn_model* m) {
   if (m->ws) cudaFree(m->ws);
   if (m->stage) cudaFree(m->stage);
   if (m->plan) cudaFree(m->plan);
+  std::free(m->host_w);
   delete m;
 }
 

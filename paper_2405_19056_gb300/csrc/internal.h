@@ -84,6 +84,55 @@ struct FusedLayout {
   static constexpr uint32_t smem_bytes = ag + 4096;
 };
 
+// Packed operand image of the FP8 fused kernel (E4M3 operands, FP32
+// accumulate), copied verbatim into shared memory.  E4M3 matrices use the
+// same K-major core matrices of 8 rows x 16 bytes, i.e. [K/16][N][16] bytes;
+// one MMA consumes K = 32.
+//   phi1  [32][H]     K = 12 channels + 20 zero
+//   phi1b [16][H]     BF16: the per-scene bias c_phi in accumulator units,
+//                     split hi / lo in rows k = 0 / 1 (written per frame)
+//   phi2  [H][H]      rho [2H][H]
+//   b1    [32+H][H]   K = 14 channels + 18 zero, then r (H)
+//   b1b   [16][H]     BF16: per-scene c_B in accumulator units (per frame)
+//   b2, r1 [H][H]     r2 [H][16]  (N = 3 outputs + 13 zero rows)
+//   FP32 constants (indices in floats from `cst`): per output column a
+//   dequantisation scale (accumulator -> next layer's quantised input, or
+//   real units where the result is not re-quantised) and a bias; u_phi1 and
+//   u_b1 turn c_phi / c_B into accumulator units; then three scalars: 1/s_t,
+//   1/s_g (the scale of B1's [g ; r] input) and 1/s_pool.
+//   A operands: at0, at1, ag ([2][128][16] bytes each, K block 1 zero) and
+//   the constant BF16 [1, 1, 0, ...] operand of the bias MMAs.
+template <int H>
+struct FusedLayoutF8 {
+  static constexpr uint32_t phi1 = 0;
+  static constexpr uint32_t phi1b = phi1 + 32 * H;
+  static constexpr uint32_t phi2 = phi1b + 16 * H * 2;
+  static constexpr uint32_t rho = phi2 + H * H;
+  static constexpr uint32_t b1 = rho + 2 * H * H;
+  static constexpr uint32_t b1b = b1 + (32 + H) * H;
+  static constexpr uint32_t b2 = b1b + 16 * H * 2;
+  static constexpr uint32_t r1 = b2 + H * H;
+  static constexpr uint32_t r2 = r1 + H * H;
+  static constexpr uint32_t cst = r2 + H * 16;
+  enum : int {
+    S_PHI1 = 0, S_PHI2 = H, B_PHI2 = 2 * H, S_RHO = 3 * H, B_RHO = 4 * H, S_B1 = 5 * H,
+    S_B2 = 6 * H, B_B2 = 7 * H, S_R1 = 8 * H, B_R1 = 9 * H, U_PHI1 = 10 * H, U_B1 = 11 * H,
+    S_R2 = 12 * H, B_R2 = 12 * H + 16, INV_S_T = 12 * H + 32, INV_S_G, INV_S_POOL, N_CST = 12 * H + 36
+  };
+  static constexpr uint32_t bytes = cst + N_CST * 4;
+  static constexpr uint32_t at0 = (bytes + 127) / 128 * 128;
+  static constexpr uint32_t at1 = at0 + 4096;
+  static constexpr uint32_t ag = at1 + 4096;
+  static constexpr uint32_t aone = ag + 4096;
+  static constexpr uint32_t smem_bytes = aone + 4096;
+  static_assert(bytes % 16 == 0, "bulk copy size must be a multiple of 16 bytes");
+};
+
+// Activation scales of the FP8 path (per-tensor, static): the real value of
+// an E4M3 code x is x * s.  Order: layer inputs t (phi1), U (phi2), pool
+// (rho), [g ; r] (B1), y (B2), y2 (R1), q (R2).
+constexpr int kFp8Acts = 7;
+
 // One frame as the fused kernel sees it.
 struct FusedFrame {
   const float* gbuf;
@@ -117,11 +166,23 @@ cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& p, cud
 // Kernel attributes the fused launch needs; call once outside stream capture.
 cudaError_t prepare_fused_bf16(int H);
 size_t fused_plan_bytes(long long tiles);
+// Numbers the plan windows of `p` (win0, total_windows) and launches the
+// tile-plan kernel that the fused kernels read.
+cudaError_t launch_plan(FusedParams& p, cudaStream_t s);
 size_t plain_workspace_bytes(int H, int K, int P);
 cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const float* latent,
                               const float* gbuf, const float* tbuf, const uint8_t* counts, int K,
                               int P, float* out, void* ws, uint32_t* err, cudaStream_t s);
 int device_sm_count();
+// FP8 fused path (fused_fp8.cu): plan kernel, then the fused E4M3 kernel.
+cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& p, cudaStream_t s);
+cudaError_t prepare_fused_fp8(int H);
+// Per-layer |activation| maxima of an FP32 plain render held in `ws` (the
+// workspace launch_plain_fp32 filled for the same frame), in the order of
+// the FP8 activation scales, as FP32 bit patterns in amax[kFp8Acts].
+cudaError_t launch_fp8_act_amax(const void* ws, const float* gbuf, const float* tbuf,
+                                const uint8_t* counts, int H, int K, int P, uint32_t* amax,
+                                cudaStream_t s);
 
 }  // namespace gn
 
@@ -138,12 +199,19 @@ struct gn_model {
   size_t stage_bytes = 0;
   void* plan = nullptr;     // fused tile plan of glassnet_render / _batch (device)
   size_t plan_bytes = 0;
+  float* host_w = nullptr;  // FP8 models: concat-form f32 weights kept for packing
+  bool fp8_ready = false;   // FP8 models: calibrated and packed
+  float fp8_act[gn::kFp8Acts] = {};  // FP8 activation scales (real value of a code = code * s)
 };
 
 namespace gn {
 // Validates a batch and fills the frame table (no plan binding); sets the
 // thread's error message on failure.
 int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* out);
+// Launches the fused path of the model's precision (plan + fused kernel), or
+// sets its kernel attributes (once, outside stream capture).
+cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s);
+cudaError_t prepare_fused(const gn_model* m);
 // Points the params at a plan workspace of fused_plan_bytes(p.total_tiles) bytes.
 void bind_plan(FusedParams& p, void* ws);
 // Sets the calling thread's glassnet_last_error message; returns `code`.

@@ -164,6 +164,38 @@ cudaError_t run_linear(const In& in, const float* W, const float* b, float* Y, i
 
 }  // namespace
 
+// |x| max of n floats into *slot (as ordered uint bits of a non-negative float).
+__global__ void amax_kernel(const float* __restrict__ x, size_t n, uint32_t* slot) {
+  float m = 0.0f;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, __float_as_uint(m));
+}
+// |t| max over the valid layer slots (k < c_p) of a transparency buffer.
+__global__ void amax_layers_kernel(const float* __restrict__ tbuf, const uint8_t* __restrict__ counts,
+                                   int K, int P, uint32_t* slot) {
+  float m = 0.0f;
+  const size_t n = static_cast<size_t>(K) * kTC * P;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int p = static_cast<int>(i % P);
+    const int k = static_cast<int>(i / (static_cast<size_t>(kTC) * P));
+    if (k < counts[p]) m = fmaxf(m, fabsf(tbuf[i]));
+  }
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, __float_as_uint(m));
+}
+
 size_t plain_workspace_bytes(int H, int K, int P) {
   const size_t rows = static_cast<size_t>(K) * P;
   // U, V: [K*P][H]; pool [P][2H]; R, Y1, Y2, Q: [P][H]
@@ -210,6 +242,37 @@ cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const flo
   e = run_linear<RowsIn, false>(RowsIn{Y2, nullptr, P, H}, W(LR1), B(LR1), Q, P, H, H, s);
   if (e != cudaSuccess) return e;
   return run_linear<RowsIn, true>(RowsIn{Q, nullptr, P, H}, W(LR2), B(LR2), out, P, kOut, H, s);
+}
+
+cudaError_t launch_fp8_act_amax(const void* ws, const float* gbuf, const float* tbuf,
+                                const uint8_t* counts, int H, int K, int P, uint32_t* amax,
+                                cudaStream_t s) {
+  const size_t rows = static_cast<size_t>(K) * P;
+  const float* U = static_cast<const float*>(ws);
+  const float* pool = U + 2 * rows * H;
+  const float* R = pool + static_cast<size_t>(P) * 2 * H;
+  const float* Y1 = R + static_cast<size_t>(P) * H;
+  const float* Y2 = Y1 + static_cast<size_t>(P) * H;
+  const float* Q = Y2 + static_cast<size_t>(P) * H;
+  cudaError_t e = cudaMemsetAsync(amax, 0, kFp8Acts * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  const size_t ph = static_cast<size_t>(P) * H;
+  auto run = [&](const float* x, size_t n, int slot) {
+    if (n == 0) return;
+    const unsigned blocks = static_cast<unsigned>(n / 256 + 1 < 2048 ? n / 256 + 1 : 2048);
+    amax_kernel<<<blocks, 256, 0, s>>>(x, n, amax + slot);
+  };
+  if (K > 0) {
+    amax_layers_kernel<<<1024, 256, 0, s>>>(tbuf, counts, K, P, amax + 0);
+    run(U, rows * H, 1);
+    run(pool, ph * 2, 2);
+  }
+  run(gbuf, static_cast<size_t>(kGC) * P, 3);
+  run(R, ph, 3);
+  run(Y1, ph, 4);
+  run(Y2, ph, 5);
+  run(Q, ph, 6);
+  return cudaGetLastError();
 }
 
 }  // namespace gn

@@ -24,7 +24,7 @@ int capture(const gn_model* m, const gn::FusedParams& p, cudaGraph_t* graph) {
   if (e != cudaSuccess) return cuda_err(e, "create capture stream");
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    const cudaError_t el = gn::launch_fused_bf16(m->H, m->fused, p, cs);
+    const cudaError_t el = gn::launch_fused(m, p, cs);
     e = cudaStreamEndCapture(cs, graph);
     if (el != cudaSuccess) e = el;
   }
@@ -57,7 +57,7 @@ int glassnet_graph_create(const gn_model* m, const gn_frame* frames, int n, gn_g
   gn::FusedParams p;
   int rc = gn::build_batch(m, frames, n, &p);
   if (rc != GN_OK) return rc;
-  cudaError_t e = gn::prepare_fused_bf16(m->H);
+  cudaError_t e = gn::prepare_fused(m);
   if (e != cudaSuccess) return cuda_err(e, "kernel attributes");
   gn_graph* g = new (std::nothrow) gn_graph();
   if (!g) return gn::set_error(GN_ENOMEM, "host allocation failed");

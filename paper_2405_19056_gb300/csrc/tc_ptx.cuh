@@ -344,7 +344,63 @@ __device__ __forceinline__ void mma8_f16_ts_e(uint32_t d_tmem, uint32_t a_tmem, 
       : "memory");
 }
 
+// E4M3 forms (kind::f8f6f4): one instruction consumes K = 32 (32 bytes of A
+// and B per row; in TMEM, 8 columns of 4 values).
+__device__ __forceinline__ void mma_f8_ss_e(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred e, p;\n\t.reg .b32 r;\n\telect.sync r|e, 0xffffffff;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_f8_ts_e(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred e, p;\n\t.reg .b32 r;\n\telect.sync r|e, 0xffffffff;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Four K steps (K = 128 e4m3) of D (+)= A[tmem] * B[smem]^T in one statement:
+// step j reads A from TMEM columns a + 8 j and B from descriptor b + j BSTEP.
+template <uint32_t BSTEP>
+__device__ __forceinline__ void mma4_f8_ts_e(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                             uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred e, p, q;\n\t.reg .b32 r, a1, a2, a3;\n\t.reg .b64 b1, b2, b3;\n\t"
+      "elect.sync r|e, 0xffffffff;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
+      "add.u32 a1, %1, 8;\n\tadd.u32 a2, %1, 16;\n\tadd.u32 a3, %1, 24;\n\t"
+      "add.s64 b1, %2, %5;\n\tadd.s64 b2, %2, %6;\n\tadd.s64 b3, %2, %7;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [a1], b1, %3, q;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [a2], b2, %3, q;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [a3], b3, %3, q;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(BSTEP), "n"(2 * BSTEP),
+      "n"(3 * BSTEP)
+      : "memory");
+}
+
 // ------------------------------------------------------------- conversions
+// Packs (lo, hi) into e4m3x2 (round to nearest even, saturating to +-448);
+// lo in bits 7..0.
+__device__ __forceinline__ uint16_t pack_e4m3(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// Same with ReLU applied to both values.
+__device__ __forceinline__ uint16_t pack_e4m3_relu(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+__device__ __forceinline__ uint32_t pack_u16x2(uint16_t lo, uint16_t hi) {
+  return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
 // Packs (lo, hi) into bf16x2 with round-to-nearest-even; lo in bits 15..0.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   uint32_t r;

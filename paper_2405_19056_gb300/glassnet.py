@@ -49,6 +49,8 @@ _SIGNATURES = {
     "glassnet_render_batch": (_I, [_P, _P, _I, _P]),
     "glassnet_check": (_I, [_P, _P]),
     "glassnet_render_fp32_static": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P]),
+    "glassnet_calibrate_fp8": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P]),
+    "glassnet_fp8_scales": (_I, [_P, _P]),
     "glassnet_graph_create": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
     "glassnet_graph_launch": (_I, [_P, _P]),
     "glassnet_graph_update": (_I, [_P, _P, _I]),
@@ -199,6 +201,17 @@ class GnFrame(ctypes.Structure):
 def glassnet_render_batch(model, frames, stream=None):
     """frames: list of dicts with latent, gbuf, tbuf, layer_count, K, h, w, out."""
     _check(_lib().glassnet_render_batch(model, _frame_array(frames), len(frames), _stream(stream)))
+
+
+def glassnet_calibrate_fp8(model, latent, gbuf, tbuf, layer_count, K, h, w, stream=None):
+    _check(_lib().glassnet_calibrate_fp8(model, latent, _ptr(gbuf), _ptr(tbuf), _ptr(layer_count),
+                                         K, h, w, _stream(stream)))
+
+
+def glassnet_fp8_scales(model) -> np.ndarray:
+    out = np.zeros(7, dtype=np.float32)
+    _check(_lib().glassnet_fp8_scales(model, out.ctypes.data))
+    return out
 
 
 def _frame_array(frames):

@@ -1,0 +1,180 @@
+"""FP8 (E4M3) fused path through the C ABI.
+
+Calibration renders one frame (seed 1, never a test seed) with the FP32
+plain path; every GEMM then runs with E4M3 operands and FP32 accumulation.
+Tolerance against the FP64 oracle (provisional, the paper fixes none):
+max |err| <= 6e-2, mean |err| <= 1e-2.  The exact pooling makes the output
+bit-identical under any permutation of each pixel's valid layers, as in the
+BF16 path.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gen import synth
+from paper_2405_19056_gb300 import glassnet as gl
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+FP8_MAX = 6e-2
+FP8_MEAN = 1e-2
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+CAL = dict(h=128, w=128, K=8, counts="poisson3", seed=1)
+
+
+class Fp8Net:
+    def __init__(self, widths, seed=0, bias="zero"):
+        self.w = synth.make_weights(widths, seed=seed, bias=bias)
+        self.model = gl.Model(self.w, gl.GN_FP8_FUSED)
+        self.cal = synth.make_frame(CAL["h"], CAL["w"], CAL["K"], counts=CAL["counts"],
+                                    seed=CAL["seed"])
+        lat = self.model.encode(synth.make_scene(0))
+        gl.glassnet_calibrate_fp8(self.model.handle, lat.handle, _dev(self.cal.gbuf),
+                                  _dev(self.cal.tbuf), _dev(self.cal.counts), CAL["K"], CAL["h"],
+                                  CAL["w"])
+        self.lats = {}
+
+    def latent(self, scene_seed):
+        if scene_seed not in self.lats:
+            self.lats[scene_seed] = self.model.encode(synth.make_scene(scene_seed))
+        return self.lats[scene_seed]
+
+    def render(self, frame, scene_seed=0, tbuf=None, counts=None):
+        t = frame.tbuf if tbuf is None else tbuf
+        c = frame.counts if counts is None else counts
+        out = torch.full((3, frame.h, frame.w), float("nan"), device=DEV)
+        self.model.render(self.latent(scene_seed), _dev(frame.gbuf), _dev(t) if t.shape[0] else None,
+                          _dev(c), out)
+        self.model.check()
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def base8(cuda_lib):
+    return Fp8Net(synth.BASE_WIDTHS, seed=0)
+
+
+@pytest.fixture(scope="module")
+def doubled8(cuda_lib):
+    return Fp8Net(synth.DOUBLED_WIDTHS, seed=0)
+
+
+@pytest.fixture(scope="module")
+def bias8(cuda_lib):
+    return Fp8Net(synth.DOUBLED_WIDTHS, seed=3, bias="uniform")
+
+
+def _ref(net, frame, scene_seed=0):
+    return oracle.render_frame(net.w, synth.make_scene(scene_seed), frame.gbuf, frame.tbuf,
+                               frame.counts)
+
+
+def test_uncalibrated_model_is_rejected(cuda_lib):
+    m = gl.Model(synth.make_weights(synth.BASE_WIDTHS, seed=0), gl.GN_FP8_FUSED)
+    lat = m.encode(synth.make_scene(0))
+    f = synth.make_frame(16, 16, 2, seed=0)
+    out = torch.empty((3, 16, 16), device=DEV)
+    with pytest.raises(gl.GlassNetError) as ei:
+        m.render(lat, _dev(f.gbuf), _dev(f.tbuf), _dev(f.counts), out)
+    assert ei.value.code == gl.GN_EINVAL
+    with pytest.raises(gl.GlassNetError):
+        gl.glassnet_fp8_scales(m.handle)
+
+
+def test_input_scale_is_twice_valid_layer_amax_over_448(base8):
+    s = gl.glassnet_fp8_scales(base8.model.handle)
+    f = base8.cal
+    valid = np.arange(f.tbuf.shape[0])[:, None, None] < f.counts[None, :, :]
+    amax_t = np.float32(np.abs(f.tbuf.transpose(1, 0, 2, 3)[:, valid]).max())
+    assert s[0] == np.float32(np.float32(2.0) * amax_t / np.float32(448.0))
+    amax_g = np.float32(np.abs(f.gbuf).max())
+    assert s[3] >= np.float32(np.float32(2.0) * amax_g / np.float32(448.0))
+    assert np.all(np.isfinite(s)) and np.all(s > 0)
+
+
+CASES = [
+    ("base8", 64, 64, 2, "all", 0),
+    ("base8", 256, 256, 4, "uniform", 1),
+    ("doubled8", 64, 64, 8, "poisson3", 2),
+    ("bias8", 96, 80, 3, "uniform", 3),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}x{c[2]}-K{c[3]}-{c[4]}")
+def test_fp8_fused_vs_oracle(case, request):
+    name, h, w, K, cd, seed = case
+    net = request.getfixturevalue(name)
+    f = synth.make_frame(h, w, K, counts=cd, seed=10 + seed)
+    err = np.abs(net.render(f, scene_seed=seed) - _ref(net, f, scene_seed=seed))
+    assert err.max() <= FP8_MAX and err.mean() <= FP8_MEAN, (err.max(), err.mean())
+
+
+def test_fp8_bit_identical_under_8_permutations(base8):
+    f = synth.make_frame(64, 64, 4, counts="uniform", seed=5)
+    first = base8.render(f)
+    for p in range(1, 9):
+        g = synth.permute_layers(f, seed=p)
+        assert np.array_equal(base8.render(g), first), p
+
+
+def test_fp8_empty_sets_match_opaque_only(bias8):
+    f = synth.make_frame(40, 40, 3, counts="uniform", seed=7)
+    zero = np.zeros_like(f.counts)
+    got = bias8.render(f, counts=zero)
+    sigma = oracle.scene_encoder(bias8.w, synth.make_scene(0))
+    exp = oracle.render_opaque_only(bias8.w, sigma, f.gbuf.reshape(14, -1).T).T.reshape(3, 40, 40)
+    err = np.abs(got - exp)
+    assert err.max() <= FP8_MAX and err.mean() <= FP8_MEAN, (err.max(), err.mean())
+
+
+def test_fp8_batch_and_graph_equal_single(doubled8):
+    m = doubled8.model
+    specs = synth.batch_specs(8, (32, 64, 128), seed=4)
+    frames, singles = [], []
+    for i, sp in enumerate(specs):
+        f = synth.make_frame(sp.h, sp.w, sp.K, counts="all", seed=60 + i)
+        singles.append(doubled8.render(f, scene_seed=sp.scene))
+        frames.append(dict(latent=doubled8.latent(sp.scene).handle, gbuf=_dev(f.gbuf),
+                           tbuf=_dev(f.tbuf), layer_count=_dev(f.counts), K=sp.K, h=sp.h, w=sp.w,
+                           out=torch.full((3, sp.h, sp.w), float("nan"), device=DEV)))
+    gl.glassnet_render_batch(m.handle, frames)
+    m.check()
+    for fr, single in zip(frames, singles):
+        assert np.array_equal(fr["out"].cpu().numpy().astype(np.float64), single)
+    g = gl.glassnet_graph_create(m.handle, frames)
+    try:
+        for fr in frames:
+            fr["out"].fill_(float("nan"))
+        gl.glassnet_graph_launch(g)
+        m.check()
+        for fr, single in zip(frames, singles):
+            assert np.array_equal(fr["out"].cpu().numpy().astype(np.float64), single)
+    finally:
+        gl.glassnet_graph_free(g)
+
+
+def test_fp8_full_512_K8_poisson_sampled(doubled8):
+    """The benchmark workload with the FP8 model: the 64x64 crop at rows and
+    columns 0..63 and 1024 sampled pixels against the oracle."""
+    frame = synth.make_frame(512, 512, 8, counts="poisson3", seed=0)
+    got = doubled8.render(frame)
+    crop = synth.Frame(gbuf=frame.gbuf[:, :64, :64].copy(), tbuf=frame.tbuf[:, :, :64, :64].copy(),
+                       counts=frame.counts[:64, :64].copy())
+    err = np.abs(got[:, :64, :64] - _ref(doubled8, crop))
+    assert err.max() <= FP8_MAX and err.mean() <= FP8_MEAN, (err.max(), err.mean())
+    rng = np.random.default_rng(0)
+    idx = rng.choice(512 * 512, 1024, replace=False)
+    ys, xs = idx // 512, idx % 512
+    samp = synth.Frame(gbuf=frame.gbuf[:, ys, xs][:, None, :].copy(),
+                       tbuf=frame.tbuf[:, :, ys, xs][:, :, None, :].copy(),
+                       counts=frame.counts[ys, xs][None, :].copy())
+    e2 = np.abs(got[:, ys, xs] - _ref(doubled8, samp)[:, 0, :])
+    assert e2.max() <= FP8_MAX and e2.mean() <= FP8_MEAN, (e2.max(), e2.mean())
