@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the e2e, FP32-plain and CPU-baseline legs")
+                    help="skip the e2e, FP32-plain, batched, FP8 and CPU-baseline legs")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8"],
+                    help="precision of the timed fused leg (fp8: calibrated on a seed-1 frame)")
     return ap.parse_args()
 
 
@@ -230,7 +232,8 @@ def run_fused(args, world, rank, local):
     dev = torch.device("cuda", local)
     gl.load_library()
     weights = synth.make_weights(synth.DOUBLED_WIDTHS, seed=0)
-    model = gl.Model(weights, gl.GN_BF16_FUSED)
+    fp8 = args.precision == "fp8"
+    model = gl.Model(weights, gl.GN_FP8_FUSED if fp8 else gl.GN_BF16_FUSED)
     scene = synth.make_scene(0)
     stream = torch.cuda.Stream(device=dev)
 
@@ -253,6 +256,11 @@ def run_fused(args, world, rank, local):
         t_enc1.record(stream)
     stream.synchronize()
     encode_ms = t_enc0.elapsed_time(t_enc1)
+    if fp8:
+        cal = synth.make_frame(256, 256, K_SLOTS, counts="poisson3", seed=1)
+        gl.glassnet_calibrate_fp8(model.handle, lat.handle, torch.from_numpy(cal.gbuf).to(dev),
+                                  torch.from_numpy(cal.tbuf).to(dev),
+                                  torch.from_numpy(cal.counts).to(dev), K_SLOTS, 256, 256, stream)
 
     def step(i):
         d = dframes[i % N_ROTATE]
@@ -282,17 +290,19 @@ def run_fused(args, world, rank, local):
     step_flops = sum(flops[i % N_ROTATE] for i in range(args.steps)) / args.steps
     avg_kernel_ms = statistics.mean(per)
     peak_tf, _, peak_src = measured_peaks()
+    if fp8:
+        peak_tf *= 2
     achieved_tf = step_flops / (avg_kernel_ms * 1e-3) / 1e12
     traffic = None
     if os.path.exists(PROFILE_TRAFFIC):
         with open(PROFILE_TRAFFIC) as f:
             prof = json.load(f)
-        if prof.get("kernel_sha256") == kernel_digest():
+        if not fp8 and prof.get("kernel_sha256") == kernel_digest():
             traffic = prof.get("dram_bytes_per_launch")
     result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC.replace("BF16", "FP8") if fp8 else METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if fp8 else "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_rotated": N_ROTATE,
                    "l2": "inputs rotate over 3 frames of 115 MB (> 129 MB L2 in total)",
                    "parallelism": f"replicas{world}", "weights": "Xavier-normal seed 0, zero bias"},
@@ -302,16 +312,19 @@ def run_fused(args, world, rank, local):
         "gpu_launches": 2 * args.steps,  # per step: tile-plan kernel + fused kernel
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
-                     "kernel": "fused_bf16_kernel<128>",
+                     "kernel": "fused_fp8_kernel<128>" if fp8 else "fused_bf16_kernel<128>",
                      "duration": "CUDA events around the render call (plan kernel + fused kernel)",
                      "flops_per_launch": step_flops,
-                     "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)"},
+                     "peak_source": (f"{peak_src} bf16 burst (MEASURED_PEAKS.json) x 2 (nominal "
+                                     "fp8/bf16 ratio)") if fp8 else
+                                    f"{peak_src} bf16 burst (MEASURED_PEAKS.json)"},
     }
     if not args.no_extras:
         result["fp32_plain"] = fp32_plain_leg(dev, weights, scene, dframes, stream)
         result["fp32_plain"]["speedup_of_bf16_fused"] = value / world / result["fp32_plain"]["value"]
         result["e2e"] = e2e_leg(model, lat, frames, args, stream, world)
         result["batch_16_frames"] = batch_leg(model, dev, stream)
+        result["fp8"] = fp8_leg(weights, scene, dframes, flops, stream, dev)
     clocks = clk.summary()
     result["clocks"] = clocks
     if rank == 0 and not args.no_extras:
@@ -343,6 +356,47 @@ def fp32_plain_leg(dev, weights, scene, dframes, stream, steps=10):
     ms = e0.elapsed_time(e1) / steps
     return {"value": H_IMG * W_IMG / (ms * 1e-3) / 1e6, "unit": UNIT, "fps": 1e3 / ms,
             "ms_per_step": ms, "steps": steps, "dtype": "fp32"}
+
+
+def fp8_leg(weights, scene, dframes, flops, stream, dev, steps=200):
+    """The same workload with the FP8 (E4M3) model, calibrated on one frame of
+    seed 1 (256x256, K=8, Poisson(3) counts) that is not a timed frame."""
+    import torch
+    from gen import synth
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    m8 = gl.Model(weights, gl.GN_FP8_FUSED)
+    lat = m8.encode(scene, stream)
+    cal = synth.make_frame(256, 256, K_SLOTS, counts="poisson3", seed=1)
+    gl.glassnet_calibrate_fp8(m8.handle, lat.handle, torch.from_numpy(cal.gbuf).to(dev),
+                              torch.from_numpy(cal.tbuf).to(dev), torch.from_numpy(cal.counts).to(dev),
+                              K_SLOTS, 256, 256, stream)
+
+    def step(i):
+        d = dframes[i % N_ROTATE]
+        gl.glassnet_render(m8.handle, lat.handle, d["gbuf"], d["tbuf"], d["counts"], K_SLOTS,
+                           H_IMG, W_IMG, d["out"], stream)
+
+    for i in range(5):
+        step(i)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        step(i)
+    e1.record(stream)
+    stream.synchronize()
+    gl.glassnet_check(m8.handle, stream)
+    ms = e0.elapsed_time(e1) / steps
+    peak_bf16, _, _ = measured_peaks()
+    step_flops = sum(flops[i % N_ROTATE] for i in range(steps)) / steps
+    achieved = step_flops / (ms * 1e-3) / 1e12
+    return {"value": H_IMG * W_IMG / (ms * 1e-3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms,
+            "steps": steps, "dtype": "e4m3 operands, fp32 accumulate",
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": 2 * peak_bf16,
+                         "unit": "TFLOP/s", "frac": achieved / (2 * peak_bf16),
+                         "peak_source": "measured bf16 burst x 2 (nominal fp8/bf16 ratio)"}}
 
 
 def batch_leg(model, dev, stream, steps=20):
