@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, FP32-plain, batched, FP8 and CPU-baseline legs")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serving leg at 50, 200 and 800 req/s with 2000 requests each "
+                         "(default: 200 and 800 req/s, 300 requests each)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8"],
                     help="precision of the timed fused leg (fp8: calibrated on a seed-1 frame)")
     return ap.parse_args()
@@ -325,6 +328,8 @@ def run_fused(args, world, rank, local):
         result["e2e"] = e2e_leg(model, lat, frames, args, stream, world)
         result["batch_16_frames"] = batch_leg(model, dev, stream)
         result["fp8"] = fp8_leg(weights, scene, dframes, flops, stream, dev)
+        result["serving"] = (serving_leg(model, (50, 200, 800), 2000) if args.serving_full
+                             else serving_leg(model, (200, 800), 300))
     clocks = clk.summary()
     result["clocks"] = clocks
     if rank == 0 and not args.no_extras:
@@ -397,6 +402,76 @@ def fp8_leg(weights, scene, dframes, flops, stream, dev, steps=200):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": 2 * peak_bf16,
                          "unit": "TFLOP/s", "frac": achieved / (2 * peak_bf16),
                          "peak_source": "measured bf16 burst x 2 (nominal fp8/bf16 ratio)"}}
+
+
+def serving_leg(model, rates, n_requests, n_streams=4, seed=0):
+    """Requests arriving as a Poisson process (rate per second), resolution
+    256, 512 or 1024 squared with probabilities 0.5 / 0.35 / 0.15, K ~ U{1..8}
+    with every slot valid, 8 resident scenes, host buffers (page-locked) in
+    and out, through glassnet_server_*: p50 / p99 latency from submission to
+    the image in host memory, and the throughput achieved."""
+    import time
+    import torch
+    from gen import synth
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    sizes, probs = (256, 512, 1024), (0.5, 0.35, 0.15)
+    pool = {}
+    for r in sizes:  # one K = 8 frame per size; the first K slots are a K-slot buffer
+        f = synth.make_frame(r, r, 8, counts="all", seed=10 + r)
+        pool[r] = dict(g=torch.from_numpy(f.gbuf).pin_memory(), t=torch.from_numpy(f.tbuf).pin_memory(),
+                       c={K: torch.full((r, r), K, dtype=torch.uint8).pin_memory() for K in range(1, 9)},
+                       outs=[torch.empty((3, r, r)).pin_memory() for _ in range(16)])
+    results = []
+    srv = gl.glassnet_server_create(model.handle, n_streams=n_streams, max_scenes=32)
+    try:
+        ids = [gl.glassnet_server_add_scene(srv, synth.make_scene(200 + i)) for i in range(8)]
+        for rate in rates:
+            rng = np.random.default_rng([seed, rate])
+            res = rng.choice(sizes, size=n_requests, p=probs)
+            Ks = rng.integers(1, 9, size=n_requests)
+            arrive = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+            before = gl.glassnet_server_stats(srv)
+            ring = {r: [None] * 16 for r in sizes}
+            used = {r: 0 for r in sizes}
+            tickets = []
+            t0 = time.perf_counter()
+            for i in range(n_requests):
+                while time.perf_counter() - t0 < arrive[i]:
+                    pass
+                r, K = int(res[i]), int(Ks[i])
+                slot = used[r] % 16
+                used[r] += 1
+                if ring[r][slot] is not None:  # the output buffer's previous request
+                    gl.glassnet_server_wait(srv, ring[r][slot])
+                    ring[r][slot] = None
+                p = pool[r]
+                t = gl.glassnet_server_submit(srv, ids[i % 8], p["g"], p["t"], p["c"][K], K, r, r,
+                                              p["outs"][slot])
+                ring[r][slot] = t
+                tickets.append(t)
+            for r in sizes:
+                for t in ring[r]:
+                    if t is not None:
+                        gl.glassnet_server_wait(srv, t)
+            wall = time.perf_counter() - t0
+            st = gl.glassnet_server_stats(srv)
+            px = st["pixels"] - before["pixels"]
+            mean_px = float(np.mean(res.astype(np.float64) ** 2))
+            results.append({"rate_per_s": rate, "requests": n_requests,
+                            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                            "throughput_mpx_s": px / wall / 1e6,
+                            "demand_mpx_s": rate * mean_px / 1e6})
+            # latencies are cumulative in the server: restart it per rate
+            gl.glassnet_server_destroy(srv)
+            srv = gl.glassnet_server_create(model.handle, n_streams=n_streams, max_scenes=32)
+            ids = [gl.glassnet_server_add_scene(srv, synth.make_scene(200 + i)) for i in range(8)]
+        gl.glassnet_check(model.handle)
+    finally:
+        gl.glassnet_server_destroy(srv)
+    return {"workload": "Poisson arrivals; 256/512/1024 squared w.p. 0.5/0.35/0.15; K~U{1..8}, "
+                        "all slots valid; 8 scenes; host buffers in and out; "
+                        f"{n_streams} lanes", "rates": results}
 
 
 def batch_leg(model, dev, stream, steps=20):

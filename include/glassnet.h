@@ -247,6 +247,58 @@ int glassnet_graph_update(gn_graph* graph, const gn_frame* frames, int n);
 void glassnet_graph_free(gn_graph* graph);
 
 /*
+ * Serving loop.  A server owns `n_streams` lanes; each lane is a CUDA stream
+ * with a device arena for the largest request (max_h x max_w, max_K) and a
+ * CUDA graph per request shape (h, w, K) captured on first use.  Requests
+ * carry HOST buffers (page-locked for full copy bandwidth; they must stay
+ * valid until glassnet_server_wait returns for the request).  A dispatcher
+ * thread admits requests in arrival order once a lane is free and the bytes
+ * of all admitted requests stay within `budget_bytes`; on the lane's stream it
+ * copies the scene latent and the inputs to the device, replays the graph and
+ * copies RGB back.  Lanes run concurrently, so copies overlap kernels.  A
+ * completion thread records each request's latency (submission to result in
+ * host memory).  Scenes are encoded once (glassnet_server_add_scene) and kept
+ * resident; when `max_scenes` are resident the least recently used one is
+ * replaced (after its requests finish).  Each request's image equals
+ * glassnet_render_host of the same inputs alone, bit for bit.  The paper has
+ * no counterpart (its Sec. 5 times single frames); device errors of the
+ * kernels accumulate in the model's error word (glassnet_check).
+ *
+ * Functions may be called from any thread; glassnet_server_destroy waits for
+ * every submitted request, then joins the threads and frees the server.
+ * Errors: GN_EINVAL (bad config, request outside the maximum or the budget,
+ * unknown scene or ticket), GN_ENOMEM, GN_ECUDA (a request whose device work
+ * failed; glassnet_server_wait returns it).
+ */
+typedef struct gn_server gn_server;
+typedef struct gn_server_config {
+  int n_streams;        /* lanes, 1..16 */
+  int max_scenes;       /* resident scene latents */
+  size_t budget_bytes;  /* device bytes of admitted requests' buffers */
+  int max_h, max_w;     /* largest request */
+  int max_K;            /* largest layer-slot count, 0..8 */
+} gn_server_config;
+typedef struct gn_request {
+  int scene;                  /* id from glassnet_server_add_scene */
+  const float* gbuf;          /* host [14][h][w] */
+  const float* tbuf;          /* host [K][12][h][w] (NULL if K = 0) */
+  const uint8_t* layer_count; /* host [h][w] */
+  int K, h, w;
+  float* out;                 /* host [3][h][w] */
+} gn_request;
+typedef struct gn_server_stats {
+  uint64_t submitted, completed;
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* latency of completed requests */
+  double pixels;                           /* pixels of completed requests */
+} gn_server_stats;
+int glassnet_server_create(gn_model* model, const gn_server_config* config, gn_server** out);
+int glassnet_server_add_scene(gn_server* server, const float* scene, int* scene_id);
+int glassnet_server_submit(gn_server* server, const gn_request* request, uint64_t* ticket);
+int glassnet_server_wait(gn_server* server, uint64_t ticket, double* latency_ms);
+int glassnet_server_stats(gn_server* server, gn_server_stats* stats);
+void glassnet_server_destroy(gn_server* server);
+
+/*
  * Synchronises `stream`, then returns and clears the model's device error
  * bits: GN_EINVAL (a layer count above K), GN_ERANGE (a pixel's exact set-sum
  * reached 2^11 and lost exactness), GN_ETIMEOUT (a device wait gave up), or

@@ -51,6 +51,12 @@ _SIGNATURES = {
     "glassnet_render_fp32_static": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P]),
     "glassnet_calibrate_fp8": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P]),
     "glassnet_fp8_scales": (_I, [_P, _P]),
+    "glassnet_server_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
+    "glassnet_server_add_scene": (_I, [_P, _P, ctypes.POINTER(_I)]),
+    "glassnet_server_submit": (_I, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "glassnet_server_wait": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "glassnet_server_stats": (_I, [_P, _P]),
+    "glassnet_server_destroy": (None, [_P]),
     "glassnet_graph_create": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
     "glassnet_graph_launch": (_I, [_P, _P]),
     "glassnet_graph_update": (_I, [_P, _P, _I]),
@@ -239,6 +245,65 @@ def glassnet_graph_update(graph, frames):
 
 def glassnet_graph_free(graph):
     _lib().glassnet_graph_free(graph)
+
+
+class GnServerConfig(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int), ("max_scenes", ctypes.c_int),
+                ("budget_bytes", ctypes.c_size_t), ("max_h", ctypes.c_int), ("max_w", ctypes.c_int),
+                ("max_K", ctypes.c_int)]
+
+
+class GnRequest(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_int), ("gbuf", ctypes.c_void_p), ("tbuf", ctypes.c_void_p),
+                ("layer_count", ctypes.c_void_p), ("K", ctypes.c_int), ("h", ctypes.c_int),
+                ("w", ctypes.c_int), ("out", ctypes.c_void_p)]
+
+
+class GnServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("pixels", ctypes.c_double)]
+
+
+def glassnet_server_create(model, n_streams=4, max_scenes=32, budget_bytes=40 << 30, max_h=1024,
+                           max_w=1024, max_K=8) -> int:
+    cfg = GnServerConfig(n_streams, max_scenes, budget_bytes, max_h, max_w, max_K)
+    out = ctypes.c_void_p()
+    _check(_lib().glassnet_server_create(model, ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def glassnet_server_add_scene(server, scene) -> int:
+    s = np.ascontiguousarray(scene, dtype=np.float32)
+    sid = ctypes.c_int()
+    _check(_lib().glassnet_server_add_scene(server, s.ctypes.data, ctypes.byref(sid)))
+    return sid.value
+
+
+def glassnet_server_submit(server, scene_id, gbuf, tbuf, layer_count, K, h, w, out) -> int:
+    """Host tensors (page-locked for full bandwidth) that stay alive until the wait."""
+    req = GnRequest(scene_id, gbuf.data_ptr(), tbuf.data_ptr() if tbuf is not None and K > 0 else None,
+                    layer_count.data_ptr(), K, h, w, out.data_ptr())
+    t = ctypes.c_uint64()
+    _check(_lib().glassnet_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def glassnet_server_wait(server, ticket) -> float:
+    lat = ctypes.c_double()
+    _check(_lib().glassnet_server_wait(server, ticket, ctypes.byref(lat)))
+    return lat.value
+
+
+def glassnet_server_stats(server) -> dict:
+    st = GnServerStats()
+    _check(_lib().glassnet_server_stats(server, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in GnServerStats._fields_}
+
+
+def glassnet_server_destroy(server):
+    _lib().glassnet_server_destroy(server)
 
 
 def glassnet_render_fp32_static(model, latent, gbuf, tbuf, layer_count, K, h, w, out,

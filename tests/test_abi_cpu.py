@@ -112,6 +112,12 @@ def test_null_arguments_rejected(lib):
     assert lib.glassnet_graph_launch(None, None) == gl.GN_EINVAL
     assert lib.glassnet_graph_update(None, None, 1) == gl.GN_EINVAL
     lib.glassnet_graph_free(None)
+    assert lib.glassnet_server_create(None, None, ctypes.byref(out)) == gl.GN_EINVAL
+    t = ctypes.c_uint64()
+    assert lib.glassnet_server_submit(None, None, ctypes.byref(t)) == gl.GN_EINVAL
+    assert lib.glassnet_server_wait(None, 1, None) == gl.GN_EINVAL
+    assert lib.glassnet_server_stats(None, None) == gl.GN_EINVAL
+    lib.glassnet_server_destroy(None)
 
 
 def test_python_binding_raises_with_message(lib):

@@ -1,0 +1,105 @@
+"""Serving loop through the C ABI: requests with host buffers, mixed shape
+buckets and scenes, several lanes in flight.  Each request's image must equal
+glassnet_render_host of the same inputs alone, bit for bit, whatever the mix,
+the admission budget or the lane it ran on."""
+import numpy as np
+import pytest
+import torch
+
+from gen import synth
+from paper_2405_19056_gb300 import glassnet as gl
+
+pytestmark = pytest.mark.gpu
+
+
+def _pin(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+
+@pytest.fixture(scope="module")
+def model(cuda_lib):
+    return gl.Model(synth.make_weights(synth.DOUBLED_WIDTHS, seed=0), gl.GN_BF16_FUSED)
+
+
+SHAPES = [(64, 64), (128, 128), (96, 80), (33, 47)]
+
+
+def _requests(n, seed, n_scenes):
+    rng = np.random.default_rng([seed, 6])
+    reqs = []
+    for i in range(n):
+        h, w = SHAPES[int(rng.integers(len(SHAPES)))]
+        K = int(rng.integers(1, 9))
+        f = synth.make_frame(h, w, K, counts="uniform", seed=700 + seed * 100 + i)
+        reqs.append(dict(scene=i % n_scenes, h=h, w=w, K=K, g=_pin(f.gbuf), t=_pin(f.tbuf),
+                         c=_pin(f.counts), out=torch.full((3, h, w), float("nan")).pin_memory()))
+    return reqs
+
+
+def _alone(model, lat, r):
+    out = torch.full((3, r["h"], r["w"]), float("nan")).pin_memory()
+    gl.glassnet_render_host(model.handle, lat.handle, r["g"], r["t"], r["c"], r["K"], r["h"],
+                            r["w"], out)
+    return out.numpy().copy()
+
+
+def _serve(model, reqs, scene_ids, **cfg):
+    srv = gl.glassnet_server_create(model.handle, **cfg)
+    try:
+        ids = [gl.glassnet_server_add_scene(srv, synth.make_scene(s)) for s in scene_ids]
+        tickets = [gl.glassnet_server_submit(srv, ids[r["scene"]], r["g"], r["t"], r["c"], r["K"],
+                                             r["h"], r["w"], r["out"]) for r in reqs]
+        lat = [gl.glassnet_server_wait(srv, t) for t in tickets]
+        stats = gl.glassnet_server_stats(srv)
+    finally:
+        gl.glassnet_server_destroy(srv)
+    return lat, stats
+
+
+def test_mixed_requests_equal_alone(model):
+    scenes = [11, 12, 13]
+    reqs = _requests(24, seed=1, n_scenes=len(scenes))
+    lats, stats = _serve(model, reqs, scenes, n_streams=4, max_scenes=4, max_h=128, max_w=128,
+                         max_K=8)
+    model.check()
+    assert stats["submitted"] == 24 and stats["completed"] == 24
+    assert stats["pixels"] == sum(r["h"] * r["w"] for r in reqs)
+    assert 0 < stats["p50_ms"] <= stats["p99_ms"] <= stats["max_ms"]
+    assert all(l > 0 for l in lats)
+    latents = [model.encode(synth.make_scene(s)) for s in scenes]
+    for i, r in enumerate(reqs):
+        assert np.array_equal(r["out"].numpy(), _alone(model, latents[r["scene"]], r)), i
+
+
+def test_budget_of_one_request_serialises_admission(model):
+    reqs = _requests(10, seed=2, n_scenes=1)
+    one = 128 * 128 * (14 * 4 + 12 * 4 * 8 + 1 + 3 * 4) + 4 * 256  # the largest request, padded
+    lats, stats = _serve(model, reqs, [21], n_streams=4, max_scenes=1, max_h=128, max_w=128,
+                         max_K=8, budget_bytes=one)
+    assert stats["completed"] == 10
+    lat = model.encode(synth.make_scene(21))
+    for r in reqs:
+        assert np.array_equal(r["out"].numpy(), _alone(model, lat, r))
+
+
+def test_least_recently_used_scene_is_replaced(model):
+    srv = gl.glassnet_server_create(model.handle, n_streams=2, max_scenes=2, max_h=64, max_w=64,
+                                    max_K=4)
+    try:
+        a = gl.glassnet_server_add_scene(srv, synth.make_scene(31))
+        b = gl.glassnet_server_add_scene(srv, synth.make_scene(32))
+        c = gl.glassnet_server_add_scene(srv, synth.make_scene(33))  # replaces a
+        assert len({a, b, c}) == 3
+        f = synth.make_frame(64, 64, 4, counts="uniform", seed=9)
+        r = dict(h=64, w=64, K=4, g=_pin(f.gbuf), t=_pin(f.tbuf), c=_pin(f.counts),
+                 out=torch.empty((3, 64, 64)).pin_memory())
+        with pytest.raises(gl.GlassNetError) as ei:
+            gl.glassnet_server_submit(srv, a, r["g"], r["t"], r["c"], 4, 64, 64, r["out"])
+        assert ei.value.code == gl.GN_EINVAL
+        t = gl.glassnet_server_submit(srv, c, r["g"], r["t"], r["c"], 4, 64, 64, r["out"])
+        gl.glassnet_server_wait(srv, t)
+        assert np.array_equal(r["out"].numpy(), _alone(model, model.encode(synth.make_scene(33)), r))
+        with pytest.raises(gl.GlassNetError):  # larger than the server's maximum
+            gl.glassnet_server_submit(srv, c, r["g"], r["t"], r["c"], 8, 64, 64, r["out"])
+    finally:
+        gl.glassnet_server_destroy(srv)
