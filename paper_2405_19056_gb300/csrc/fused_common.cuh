@@ -9,11 +9,17 @@
 
 namespace gn {
 namespace fused {
-constexpr int kEpiWarps = 8;
-constexpr int kMmaWarp = 8;
-constexpr int kLoadWarp0 = 9;  // warps 9 and 10
+// Epilogue warps per TMEM lane quadrant (each serves H / kEW accumulator
+// columns of 32 pixel rows), then the MMA warp, then the two loader warps.
+#ifndef GN_FUSED_EW
+#define GN_FUSED_EW 2
+#endif
+constexpr int kEW = GN_FUSED_EW;
+constexpr int kEpiWarps = 4 * kEW;
+constexpr int kMmaWarp = 4 * kEW;
+constexpr int kLoadWarp0 = 4 * kEW + 1;
 constexpr int kLoadWarps = 2;
-constexpr int kThreadsF = 11 * 32;
+constexpr int kThreadsF = (4 * kEW + 3) * 32;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per device-side wait
 constexpr float kSumBase = 2048.0f;          // 2^11: quantum 2^-12 in [2^11, 2^12)
 constexpr float kSumLimit = 4096.0f;

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     fused_fp8_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   using L = FusedLayoutF8<H>;
   using T = TMapF8<H>;
-  constexpr int CH = H / 2;    // accumulator columns per epilogue thread
+  constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
   constexpr int CHQ = CH / 4;  // TMEM columns of CH e4m3 values
   constexpr int CHC = CH / 2;  // bf16 pairs of the running max
   static_assert(CH % 16 == 0, "accumulator columns per thread must be a multiple of 16");
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const uint32_t X = tl + T::buf(r3);
         const uint32_t Y = tl + T::buf(r3 == 2 ? 0 : r3 + 1);
         const uint32_t Z = tl + T::buf(r3 == 0 ? 2 : r3 - 1);
-#pragma unroll 1
+#pragma unroll
         for (int l = 0; l < 4; ++l) {
           if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
           ++n_dp;
