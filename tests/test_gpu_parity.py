@@ -208,17 +208,23 @@ def test_result_independent_of_tile_position(base):
     assert np.array_equal(np.roll(a, 37, axis=2), b)
 
 
-def test_count_above_K_reported(base):
+@pytest.mark.parametrize("hw,bad", [(8, 5), (64, 255)], ids=["8x8-count5", "64x64-count255"])
+def test_count_above_K_reported(base, hw, bad):
+    """A count above K sets GN_EINVAL; the pixel is still rendered (with K
+    layers), so every output is written."""
     m = base.model(gl.GN_BF16_FUSED)
     scene = synth.make_scene(8)
-    frame = synth.make_frame(8, 8, 2, counts="all", seed=8)
+    frame = synth.make_frame(hw, hw, 2, counts="all", seed=8)
     lat = m.encode(scene)
     cnt = frame.counts.copy()
-    cnt[3, 3] = 5
-    out = torch.empty((3, 8, 8), device=DEV)
+    cnt[3, 3] = bad
+    out = torch.full((3, hw, hw), float("nan"), device=DEV)
     m.render(lat, _dev(frame.gbuf), _dev(frame.tbuf), _dev(cnt), out)
     assert gl.glassnet_check_code(m.handle) == gl.GN_EINVAL
     assert gl.glassnet_check_code(m.handle) == gl.GN_OK  # cleared
+    got = out.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert np.array_equal(got, render(base, gl.GN_BF16_FUSED, scene, frame))
 
 
 def test_exact_sum_range_reported(cuda_lib):
