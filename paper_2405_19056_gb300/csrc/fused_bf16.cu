@@ -75,6 +75,12 @@ namespace gn {
 namespace {
 using namespace fused;
 
+// Per-pixel layers: the epilogue writes each layer's output A operand in two
+// halves of K, arriving on one barrier per half, so the next layer's MMAs
+// over the first half run while the second half is produced.
+constexpr int B_H = B_COUNT;  // + half: K half of the next per-pixel A operand written
+constexpr int B_COUNT_B = B_COUNT + 2;
+
 // TMEM column map (128 lanes x 4H columns of 32 bits): three accumulator
 // buffers of H columns, then U (H bf16 = H/2 columns) double buffered.  The
 // per-pixel layers of a tile use, with r = (first global slot of the next
@@ -260,7 +266,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   static_assert(CH % 16 == 0, "accumulator columns per thread must be a multiple of 16");
 
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[B_COUNT];
+  __shared__ __align__(8) uint64_t bars[B_COUNT_B];
   __shared__ uint32_t s_tmem;
   __shared__ LoaderShared s_ld;
   __shared__ volatile int s_abort;
@@ -282,6 +288,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       mbar_init(bar(B_AT_E + b), 1);
       mbar_init(bar(B_TILE + b), kLoadWarps);
       mbar_init(bar(B_SCHED + b), 1);
+      mbar_init(bar(B_H + b), kEpiWarps);
     }
     for (int b = 0; b < 3; ++b) {
       mbar_init(bar(B_D1 + b), 1);
@@ -355,6 +362,13 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       return true;
     };
     // the epilogue warps have written the next A operand in TMEM
+    uint32_t n_h[2] = {0, 0};
+    auto wait_h = [&](int h) -> bool {
+      if (!warp_wait(bar(B_H + h), n_h[h] & 1, &s_abort)) return false;
+      ++n_h[h];
+      tc_fence_after();
+      return true;
+    };
     auto wait_in = [&]() -> bool {
       if (!warp_wait(bar(B_IN + (n_in & 1)), (n_in >> 1) & 1, &s_abort)) return false;
       ++n_in;
@@ -400,31 +414,49 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         p2.next();
         if (k + 2 < ns && !phi1()) goto done;
       }
-      // Per-pixel layers rho, B1, B2, R1 into X, then R2 into Z + H/2.
+      // Per-pixel layers.  Accumulators alternate X / Y (a layer never
+      // overwrites the accumulator its input is being read from), A operands
+      // live in the U region (lo = first H/2 columns, hi = last H/2):
+      //   rho: X <- [max ; mean];  B1: Y <- [g ; r = lo];  B2: X <- y = hi;
+      //   R1: Y <- y2 = lo;  R2: Z <- q = hi.
+      // Each GEMM is issued in two K halves, each as soon as the epilogue
+      // half that produces it has arrived.
       const uint32_t X = tbase + T::buf(p1.b);
       const uint32_t Y = tbase + T::buf(p1.b == 2 ? 0 : p1.b + 1);
       const uint32_t Z = tbase + T::buf(p1.b == 0 ? 2 : p1.b - 1);
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        if (!wait_in()) goto done;
-        if (l == 1) {
-          if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
-          ++n_agf;
-          tc_fence_after();
-        }
-        if (l == 0) issue_gemm<H, 2 * H>(X, tbase + T::APOOL, dsc_rho, idH);
-        if (l == 1) {
-          mma_f16_ss_e(X, dsc_ag, dsc_b1, idH, 0u);
-          issue_gemm<H, H>(X, Y, dsc_b1r, idH, true);
-        }
-        if (l == 2) issue_gemm<H, H>(X, Y + H / 2, dsc_b2, idH);
-        if (l == 3) issue_gemm<H, H>(X, Z, dsc_r1, idH);
-        mma_commit_e(bar(B_DP));
-        if (l == 1) mma_commit_e(bar(B_AG_E));
-        __syncwarp();
-      }
-      if (!wait_in()) goto done;
-      issue_gemm<16, H>(Z + H / 2, Y + H / 2, dsc_r2, id16);
+      const uint32_t A_LO = tbase + T::APOOL, A_HI = tbase + T::APOOL + H / 2;
+      constexpr uint64_t kHalfK = static_cast<uint64_t>(H / 32) * ((2 * H * 16) >> 4);
+      if (!wait_h(0)) goto done;
+      issue_gemm<H, H>(X, A_LO, dsc_rho, idH);
+      if (!wait_h(1)) goto done;
+      issue_gemm<H, H>(X, A_HI, dsc_rho + 2 * kHalfK, idH, true);
+      mma_commit_e(bar(B_DP));
+      __syncwarp();
+      if (!wait_h(0)) goto done;
+      if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+      ++n_agf;
+      tc_fence_after();
+      mma_f16_ss_e(Y, dsc_ag, dsc_b1, idH, 0u);
+      issue_gemm<H, H / 2>(Y, A_LO, dsc_b1r, idH, true);
+      if (!wait_h(1)) goto done;
+      issue_gemm<H, H / 2>(Y, A_LO + H / 4, dsc_b1r + kHalfK, idH, true);
+      mma_commit_e(bar(B_DP));
+      mma_commit_e(bar(B_AG_E));
+      __syncwarp();
+      if (!wait_h(0)) goto done;
+      issue_gemm<H, H / 2>(X, A_HI, dsc_b2, idH);
+      if (!wait_h(1)) goto done;
+      issue_gemm<H, H / 2>(X, A_HI + H / 4, dsc_b2 + kHalfK, idH, true);
+      mma_commit_e(bar(B_DP));
+      __syncwarp();
+      if (!wait_h(0)) goto done;
+      issue_gemm<H, H / 2>(Y, A_LO, dsc_r1, idH);
+      if (!wait_h(1)) goto done;
+      issue_gemm<H, H / 2>(Y, A_LO + H / 4, dsc_r1 + kHalfK, idH, true);
+      mma_commit_e(bar(B_DP));
+      __syncwarp();
+      if (!wait_h(0) || !wait_h(1)) goto done;
+      issue_gemm<16, H>(Z, A_HI, dsc_r2, id16);
       mma_commit_e(bar(B_DR2));
       __syncwarp();
     }
@@ -433,12 +465,18 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     const int q = warp & 3, g = warp >> 2;
     const int row = q * 32 + lane;
     const uint32_t tl = tbase + (static_cast<uint32_t>(q * 32) << 16);
-    const float* b_rho = reinterpret_cast<const float*>(smem + L::bias_rho) + g * CH;
-    const float* b_b2 = reinterpret_cast<const float*>(smem + L::bias_b2) + g * CH;
-    const float* b_r1 = reinterpret_cast<const float*>(smem + L::bias_r1) + g * CH;
+    const float* b_rho = reinterpret_cast<const float*>(smem + L::bias_rho);
+    const float* b_b2 = reinterpret_cast<const float*>(smem + L::bias_b2);
+    const float* b_r1 = reinterpret_cast<const float*>(smem + L::bias_r1);
     const float* b_r2 = reinterpret_cast<const float*>(smem + L::bias_r2);
     uint32_t gs = 0;  // global index of the tile's first layer slot
     uint32_t n_in = 0, n_dp = 0, tb = 0;
+    auto arrive_h = [&](int h) {
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_H + h));
+    };
     auto arrive_in = [&]() {
       tmem_wait_st();
       tc_fence_before();
@@ -532,14 +570,23 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         if (!epi2(k)) goto done;
       }
 
-      // pool = [max ; mean] -> APOOL (bf16, 2H values = H columns).
+      // pool = [max ; mean] -> the U region (bf16, 2H values = H columns):
+      // the max half first (rho's first K half can start), then the mean.
+#pragma unroll
+      for (int hh = 0; hh < CHC / 8; ++hh) {
+        uint32_t pm[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pm[j] = mx[hh * 8 + j];
+        tmem_st8(tl + T::APOOL + g * CHC + hh * 8, pm);
+      }
+      arrive_h(0);
       {
         const float rcp = c > 0 ? __frcp_rn(static_cast<float>(c)) : 0.0f;
         const float off = kSumBase - static_cast<float>(c) * kHalfQuantum;
         bool over = false;
 #pragma unroll
         for (int hh = 0; hh < CHC / 8; ++hh) {
-          uint32_t pa[8], pm[8];
+          uint32_t pa[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int jj = hh * 8 + j;
@@ -547,65 +594,70 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             float a0, a1;
             fadd2_rn(a0, a1, sm[2 * jj], sm[2 * jj + 1], -off, -off);
             pa[j] = pack_bf16(a0 * rcp, a1 * rcp);
-            pm[j] = mx[jj];
           }
-          tmem_st8(tl + T::APOOL + g * CHC + hh * 8, pm);
           tmem_st8(tl + T::APOOL + H / 2 + g * CHC + hh * 8, pa);
         }
         if (over && c > 0) atomicOr(prm.err, kErrRange);
       }
-      arrive_in();
+      arrive_h(1);
 
-      // rho -> r (zero without layers) -> Y;  B1 -> y -> Y + H/2;
-      // B2 -> y2 -> Z;  R1 -> q -> Y + H/2.  Accumulator X.
+      // rho -> r (zero without layers) -> lo;  B1 -> y -> hi;  B2 -> y2 -> lo;
+      // R1 -> q -> hi.  Accumulators X, Y, X, Y.  Each layer in two passes of
+      // H/2 accumulator columns (this warp: H/4 of them), one arrival each.
       gs += ns;
       const uint32_t r3 = gs % 3u;
       const uint32_t X = tl + T::buf(r3);
       const uint32_t Y = tl + T::buf(r3 == 2 ? 0 : r3 + 1);
       const uint32_t Z = tl + T::buf(r3 == 0 ? 2 : r3 - 1);
+      const uint32_t A_LO = tl + T::APOOL, A_HI = tl + T::APOOL + H / 2;
+      constexpr int PC = H / 4;  // accumulator columns of this warp per pass
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
         ++n_dp;
         tc_fence_after();
         const float* bl = l == 0 ? b_rho : (l == 2 ? b_b2 : b_r1);
-        const uint32_t src = X + g * CH;
-        const uint32_t dst = (l == 0 ? Y : (l == 2 ? Z : Y + H / 2)) + g * CHC;
-        uint32_t ra[16], rb[16];
-        tmem_ld16_async(src, ra);
-        tmem_wait_ld_tied(ra);
+        const uint32_t acc = (l & 1) ? Y : X;
+        const uint32_t dst = (l & 1) ? A_HI : A_LO;
 #pragma unroll
-        for (int hh = 0; hh < CH / 16; ++hh) {
-          uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
-          uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
-          if (hh + 1 < CH / 16) tmem_ld16_async(src + (hh + 1) * 16, nxt);
-          uint32_t u[8];
-          if (l == 1) {
+        for (int h = 0; h < 2; ++h) {
+          const int c0 = h * (H / 2) + g * PC;  // first accumulator column of this pass
+          uint32_t ra[16], rb[16];
+          tmem_ld16_async(acc + c0, ra);
+          tmem_wait_ld_tied(ra);
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              u[i] = pack_bf16_relu(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
-          } else {
+          for (int hh = 0; hh < PC / 16; ++hh) {
+            uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
+            uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
+            if (hh + 1 < PC / 16) tmem_ld16_async(acc + c0 + (hh + 1) * 16, nxt);
+            uint32_t u[8];
+            if (l == 1) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              float v0, v1;
-              fadd2_rn(v0, v1, __uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]),
-                       bl[hh * 16 + 2 * i], bl[hh * 16 + 2 * i + 1]);
-              u[i] = (l == 0 && c == 0) ? 0u : pack_bf16_relu(v0, v1);
+              for (int i = 0; i < 8; ++i)
+                u[i] = pack_bf16_relu(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                float v0, v1;
+                fadd2_rn(v0, v1, __uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]),
+                         bl[c0 + hh * 16 + 2 * i], bl[c0 + hh * 16 + 2 * i + 1]);
+                u[i] = (l == 0 && c == 0) ? 0u : pack_bf16_relu(v0, v1);
+              }
             }
+            tmem_st8(dst + c0 / 2 + hh * 8, u);
+            if (hh + 1 < PC / 16) tmem_wait_ld_tied(nxt);
           }
-          tmem_st8(dst + hh * 8, u);
-          if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
+          arrive_h(h);
         }
-        arrive_in();
       }
       // R2 + sigmoid -> out (column group 0 stores).  Every warp waits for R2:
       // the next tile's phi1 for its third slot writes Z, and it is issued
-      // only after every warp's first arrival of that tile.
+      // only after every warp's first phi1 epilogue of that tile.
       if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
       if (g == 0) {
         tc_fence_after();
         uint32_t r[4];
-        tmem_ld4(Z + H / 2, r);
+        tmem_ld4(Z, r);
         if (ent != kPlanEmpty) {
           const FusedFrame& F = frame_of(prm, tile);
           const uint32_t pix = ent & kPlanPixelMask;
