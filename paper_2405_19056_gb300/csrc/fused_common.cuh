@@ -126,6 +126,7 @@ __device__ __forceinline__ const FusedFrame& frame_of(const FusedParams& prm, in
 struct LoaderShared {
   int ns[2][kLoadWarps];
   int tile[2];
+  uint8_t cnt[2][kTile];  // per tile parity: each row's layer count (0 for an empty row)
 };
 
 constexpr int kRowsPerLoadLane = kTile / (kLoadWarps * 32);  // 2

@@ -156,6 +156,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
       pix[i] = has[i] ? (e & kPlanPixelMask) : 0u;
       cnt[i] = has[i] ? static_cast<int>(e >> 28) : 0;
       cmax = max(cmax, cnt[i]);
+      ls.cnt[tb & 1][row0 + 32 * i] = static_cast<uint8_t>(cnt[i]);
     }
     const int wmax = __reduce_max_sync(0xffffffffu, cmax);
     if (lane == 0) ls.ns[tb & 1][li] = wmax;
@@ -420,9 +421,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
         const int tile = *reinterpret_cast<volatile int*>(&s_ld.tile[tb & 1]);
         if (tile >= prm.total_tiles) break;
-        const uint32_t ent = __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row);
         const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
-        const int c = ent != kPlanEmpty ? static_cast<int>(ent >> 28) : 0;
+        const int c = s_ld.cnt[tb & 1][row];
 
         uint32_t mx[CHC];
         float sm[CH];
@@ -563,6 +563,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           arrive_in();
         }
         // R2 + sigmoid -> out (column group 0 stores)
+        const uint32_t ent = g == 0 ? __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row)
+                                    : kPlanEmpty;
         if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
         if (g == 0) {
           tc_fence_after();
