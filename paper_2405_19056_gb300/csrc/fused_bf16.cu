@@ -64,7 +64,11 @@
 // cannot complete the phase of a slower one) or an accumulator has been read;
 // the loaders arrive when an operand is filled.  After the last slot the
 // per-pixel layers reuse the three buffers; the next tile's first two phi1
-// are issued right behind R2.  Every device-side wait gives up after 1 s,
+// are issued right behind R2.  The MMA and epilogue warps take the next
+// tile's slot count and frame (which the loaders publish in shared memory,
+// four tiles deep) while the per-pixel layers run, and the epilogue loads
+// each row's plan entry for the store before them, so little but the R2
+// epilogue separates two tiles.  Every device-side wait gives up after 1 s,
 // sets the timeout error bit and makes all warps leave through the common
 // exit.
 #include <cuda_bf16.h>
@@ -200,7 +204,14 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
       ls.cnt[tb & 1][row0 + 32 * i] = static_cast<uint8_t>(cnt[i]);
     }
     const int wmax = __reduce_max_sync(0xffffffffu, cmax);
-    if (lane == 0) ls.ns[tb & 1][li] = wmax;
+    if (lane == 0) {
+      ls.ns[tb & 1][li] = wmax;
+      if (li == 0) {
+        ls.out[tb & 3] = F.out;
+        ls.fold[tb & 3] = F.fold;
+        ls.P[tb & 3] = F.P;
+      }
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(bar(B_TILE + (tb & 1)));
     // the tile's slot count is the max over both loader warps
@@ -345,7 +356,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     // B1's weights for r start after its 16-wide G-buffer block
     const uint64_t dsc_b1r = dsc_b1 + static_cast<uint64_t>((2 * H * 16) >> 4);
     SlotPos p1, p2;  // next phi1 / phi2 buffer
-    uint32_t g1 = 0, n_in = 0, n_agf = 0, tb = 0;
+    uint32_t g1 = 0, n_in = 0, n_agf = 0;
+    const int total_tiles = prm.total_tiles;
     const float* cur_fold = nullptr;
     // phi1 for the next global layer slot, into its rotating buffer
     auto phi1 = [&]() -> bool {
@@ -376,33 +388,42 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       tc_fence_after();
       return true;
     };
-    if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
-    for (;; ++tb) {
-      if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
-      const int tile = *reinterpret_cast<volatile int*>(&s_ld.tile[tb & 1]);
-      if (tile >= prm.total_tiles) break;
-      const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
-      const FusedFrame& F = frame_of(prm, tile);
-      if (F.fold != cur_fold) {
-        // Per-scene folded biases -> the constant-one rows of phi1 and B1,
-        // once no MMA of the previous tile can still read them.
-        if (tb > 0 && !warp_wait(bar(B_DR2), (tb - 1) & 1, &s_abort)) goto done;
-        for (int i = lane; i < 2 * H; i += 32) {
-          const int n = i < H ? i : i - H;
-          const float cv = F.fold[i];
-          const float hi = bf16_value(cv);
-          const uint32_t packed = static_cast<uint32_t>(bf16_bits(hi)) |
-                                  (static_cast<uint32_t>(bf16_bits(cv - hi)) << 16);
-          const uint32_t off = i < H ? L::phi1 + ((H + n) * 8 + 4) * 2
-                                     : L::b1 + ((H + n) * 8 + 6) * 2;
-          *reinterpret_cast<uint32_t*>(smem + off) = packed;
-        }
-        fence_proxy_async_smem();
-        __syncwarp();
-        cur_fold = F.fold;
+    // Tile number t of this CTA as the loaders published it: global index
+    // (>= total_tiles ends the loop), slot count and the frame's biases.
+    auto take_tile = [&](uint32_t t, int& tile, int& ns, const float*& fold) -> bool {
+      if (!warp_wait(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
+      tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
+      ns = max(s_ld.ns[t & 1][0], s_ld.ns[t & 1][1]);
+      fold = tile < total_tiles ? s_ld.fold[t & 3] : nullptr;
+      return true;
+    };
+    // Per-scene folded biases -> the constant-one rows of phi1 and B1.  The
+    // caller makes sure that no MMA can still read the previous ones.
+    auto patch_fold = [&](const float* fold) {
+      for (int i = lane; i < 2 * H; i += 32) {
+        const int n = i < H ? i : i - H;
+        const float cv = fold[i];
+        const float hi = bf16_value(cv);
+        const uint32_t packed = static_cast<uint32_t>(bf16_bits(hi)) |
+                                (static_cast<uint32_t>(bf16_bits(cv - hi)) << 16);
+        const uint32_t off = i < H ? L::phi1 + ((H + n) * 8 + 4) * 2
+                                   : L::b1 + ((H + n) * 8 + 6) * 2;
+        *reinterpret_cast<uint32_t*>(smem + off) = packed;
       }
+      fence_proxy_async_smem();
+      __syncwarp();
+      cur_fold = fold;
+    };
+    int tile, ns;
+    const float* fold;
+    if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+    if (!take_tile(0, tile, ns, fold)) goto done;
+    if (tile < total_tiles) {
+      patch_fold(fold);
       for (int k = 0; k < ns && k < 2; ++k)
         if (!phi1()) goto done;
+    }
+    for (uint32_t tb = 0; tile < total_tiles; ++tb) {
       for (int k = 0; k < ns; ++k) {
         if (!wait_in()) goto done;  // U(k) written, its buffer read
         {
@@ -433,6 +454,11 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       issue_gemm<H, H>(X, A_HI, dsc_rho + 2 * kHalfK, idH, true);
       mma_commit_e(bar(B_DP));
       __syncwarp();
+      // the next tile, read while the per-pixel layers run (the loaders
+      // publish it once this tile's layer operands are written)
+      int next_tile, next_ns;
+      const float* next_fold;
+      if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
       if (!wait_h(0)) goto done;
       if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
       ++n_agf;
@@ -460,6 +486,18 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       issue_gemm<16, H>(Z, A_HI, dsc_r2, id16);
       mma_commit_e(bar(B_DR2));
       __syncwarp();
+      // the next tile's first two phi1 right behind R2 (they write X and Y)
+      tile = next_tile;
+      ns = next_ns;
+      if (tile < total_tiles) {
+        if (next_fold != cur_fold) {
+          // every MMA of this tile (B1 reads the old bias rows) has completed
+          if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
+          patch_fold(next_fold);
+        }
+        for (int k = 0; k < ns && k < 2; ++k)
+          if (!phi1()) goto done;
+      }
     }
   } else {
     // ------------------------------------------------------- epilogue warps
@@ -487,187 +525,198 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     };
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
     if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
-
-    for (;; ++tb) {
-      if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
-      const int tile = *reinterpret_cast<volatile int*>(&s_ld.tile[tb & 1]);
-      if (tile >= prm.total_tiles) break;
-      const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
-      const int c = s_ld.cnt[tb & 1][row];
-
-      uint32_t mx[CHC];  // running max, bf16 pairs
-      float sm[CH];      // fixed-point sums
-#pragma unroll
-      for (int j = 0; j < CHC; ++j) mx[j] = 0u;
-#pragma unroll
-      for (int j = 0; j < CH; ++j) sm[j] = kSumBase;
-
-      // phi1(k) accumulator -> U(k) = ReLU as bf16.  16-column TMEM loads
-      // are double buffered: block hh + 1 is in flight while hh is packed.
-      auto epi1 = [&](int k) -> bool {
-        const uint32_t gk = gs + k, b = gk % 3u;
-        if (!warp_wait(bar(B_D1 + b), (gk / 3u) & 1, &s_abort)) return false;
-        tc_fence_after();
-        const uint32_t src = tl + T::buf(b) + g * CH;
-        const uint32_t dst = tl + (k & 1 ? T::AU1 : T::AU0) + g * CHC;
-        uint32_t ra[16], rb[16];
-        tmem_ld16_async(src, ra);
-        tmem_wait_ld_tied(ra);
-#pragma unroll
-        for (int hh = 0; hh < CH / 16; ++hh) {
-          uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
-          uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
-          if (hh + 1 < CH / 16) tmem_ld16_async(src + (hh + 1) * 16, nxt);
-          uint32_t u[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            u[i] = pack_bf16_relu(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
-          tmem_st8(dst + hh * 8, u);
-          if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
-        }
-        arrive_in();
+    {
+      const int total_tiles = prm.total_tiles;
+      // Tile number t of this CTA as the loaders published it.
+      int tile, ns, c;
+      auto take_tile = [&](uint32_t t) -> bool {
+        if (!warp_wait(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
+        tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
+        ns = max(s_ld.ns[t & 1][0], s_ld.ns[t & 1][1]);
+        c = s_ld.cnt[t & 1][row];
         return true;
       };
-      // phi2(k) accumulator -> pool update for pixels with k < c.
-      auto epi2 = [&](int k) -> bool {
-        const uint32_t gk = gs + k, b = gk % 3u;
-        if (!warp_wait(bar(B_D2 + b), (gk / 3u) & 1, &s_abort)) return false;
-        tc_fence_after();
-        const uint32_t src = tl + T::buf(b) + g * CH;
-        uint32_t ra[16], rb[16];
-        tmem_ld16_async(src, ra);
-        tmem_wait_ld_tied(ra);
+      if (!take_tile(0)) goto done;
+      for (; tile < total_tiles; ++tb) {
+        uint32_t mx[CHC];  // running max, bf16 pairs
+        float sm[CH];      // fixed-point sums
 #pragma unroll
-        for (int hh = 0; hh < CH / 16; ++hh) {
-          uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
-          uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
-          if (hh + 1 < CH / 16) {
-            tmem_ld16_async(src + (hh + 1) * 16, nxt);
-          } else {
-            // every column of this buffer is in registers: release it
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar(B_BE + b));
-          }
-          if (k < c) {
+        for (int j = 0; j < CHC; ++j) mx[j] = 0u;
 #pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-              const int j = hh * 16 + i;
-              const uint32_t u =
-                  pack_bf16_relu(__uint_as_float(cur[i]), __uint_as_float(cur[i + 1]));
-              mx[j / 2] = bmax2(mx[j / 2], u);
-              add_bf16x2_rz(sm[j], sm[j + 1], u);
-            }
-          }
-          if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
-        }
-        return true;
-      };
+        for (int j = 0; j < CH; ++j) sm[j] = kSumBase;
 
-      if (ns > 0 && !epi1(0)) goto done;
-      for (int k = 0; k < ns; ++k) {
-        if (k + 1 < ns && !epi1(k + 1)) goto done;
-        if (!epi2(k)) goto done;
-      }
-
-      // pool = [max ; mean] -> the U region (bf16, 2H values = H columns):
-      // the max half first (rho's first K half can start), then the mean.
-#pragma unroll
-      for (int hh = 0; hh < CHC / 8; ++hh) {
-        uint32_t pm[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) pm[j] = mx[hh * 8 + j];
-        tmem_st8(tl + T::APOOL + g * CHC + hh * 8, pm);
-      }
-      arrive_h(0);
-      {
-        const float rcp = c > 0 ? __frcp_rn(static_cast<float>(c)) : 0.0f;
-        const float off = kSumBase - static_cast<float>(c) * kHalfQuantum;
-        bool over = false;
-#pragma unroll
-        for (int hh = 0; hh < CHC / 8; ++hh) {
-          uint32_t pa[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int jj = hh * 8 + j;
-            over |= !(fmaxf(sm[2 * jj], sm[2 * jj + 1]) < kSumLimit);
-            float a0, a1;
-            fadd2_rn(a0, a1, sm[2 * jj], sm[2 * jj + 1], -off, -off);
-            pa[j] = pack_bf16(a0 * rcp, a1 * rcp);
-          }
-          tmem_st8(tl + T::APOOL + H / 2 + g * CHC + hh * 8, pa);
-        }
-        if (over && c > 0) atomicOr(prm.err, kErrRange);
-      }
-      arrive_h(1);
-
-      // rho -> r (zero without layers) -> lo;  B1 -> y -> hi;  B2 -> y2 -> lo;
-      // R1 -> q -> hi.  Accumulators X, Y, X, Y.  Each layer in two passes of
-      // H/2 accumulator columns (this warp: H/4 of them), one arrival each.
-      gs += ns;
-      const uint32_t r3 = gs % 3u;
-      const uint32_t X = tl + T::buf(r3);
-      const uint32_t Y = tl + T::buf(r3 == 2 ? 0 : r3 + 1);
-      const uint32_t Z = tl + T::buf(r3 == 0 ? 2 : r3 - 1);
-      const uint32_t A_LO = tl + T::APOOL, A_HI = tl + T::APOOL + H / 2;
-      constexpr int PC = H / 4;  // accumulator columns of this warp per pass
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
-        ++n_dp;
-        tc_fence_after();
-        const float* bl = l == 0 ? b_rho : (l == 2 ? b_b2 : b_r1);
-        const uint32_t acc = (l & 1) ? Y : X;
-        const uint32_t dst = (l & 1) ? A_HI : A_LO;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c0 = h * (H / 2) + g * PC;  // first accumulator column of this pass
+        // phi1(k) accumulator -> U(k) = ReLU as bf16.  16-column TMEM loads
+        // are double buffered: block hh + 1 is in flight while hh is packed.
+        auto epi1 = [&](int k) -> bool {
+          const uint32_t gk = gs + k, b = gk % 3u;
+          if (!warp_wait(bar(B_D1 + b), (gk / 3u) & 1, &s_abort)) return false;
+          tc_fence_after();
+          const uint32_t src = tl + T::buf(b) + g * CH;
+          const uint32_t dst = tl + (k & 1 ? T::AU1 : T::AU0) + g * CHC;
           uint32_t ra[16], rb[16];
-          tmem_ld16_async(acc + c0, ra);
+          tmem_ld16_async(src, ra);
           tmem_wait_ld_tied(ra);
 #pragma unroll
-          for (int hh = 0; hh < PC / 16; ++hh) {
+          for (int hh = 0; hh < CH / 16; ++hh) {
             uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
             uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
-            if (hh + 1 < PC / 16) tmem_ld16_async(acc + c0 + (hh + 1) * 16, nxt);
+            if (hh + 1 < CH / 16) tmem_ld16_async(src + (hh + 1) * 16, nxt);
             uint32_t u[8];
-            if (l == 1) {
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
-                u[i] = pack_bf16_relu(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
+            for (int i = 0; i < 8; ++i)
+              u[i] = pack_bf16_relu(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
+            tmem_st8(dst + hh * 8, u);
+            if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
+          }
+          arrive_in();
+          return true;
+        };
+        // phi2(k) accumulator -> pool update for pixels with k < c.
+        auto epi2 = [&](int k) -> bool {
+          const uint32_t gk = gs + k, b = gk % 3u;
+          if (!warp_wait(bar(B_D2 + b), (gk / 3u) & 1, &s_abort)) return false;
+          tc_fence_after();
+          const uint32_t src = tl + T::buf(b) + g * CH;
+          uint32_t ra[16], rb[16];
+          tmem_ld16_async(src, ra);
+          tmem_wait_ld_tied(ra);
+#pragma unroll
+          for (int hh = 0; hh < CH / 16; ++hh) {
+            uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
+            uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
+            if (hh + 1 < CH / 16) {
+              tmem_ld16_async(src + (hh + 1) * 16, nxt);
             } else {
+              // every column of this buffer is in registers: release it
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(bar(B_BE + b));
+            }
+            if (k < c) {
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                float v0, v1;
-                fadd2_rn(v0, v1, __uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]),
-                         bl[c0 + hh * 16 + 2 * i], bl[c0 + hh * 16 + 2 * i + 1]);
-                u[i] = (l == 0 && c == 0) ? 0u : pack_bf16_relu(v0, v1);
+              for (int i = 0; i < 16; i += 2) {
+                const int j = hh * 16 + i;
+                const uint32_t u =
+                    pack_bf16_relu(__uint_as_float(cur[i]), __uint_as_float(cur[i + 1]));
+                mx[j / 2] = bmax2(mx[j / 2], u);
+                add_bf16x2_rz(sm[j], sm[j + 1], u);
               }
             }
-            tmem_st8(dst + c0 / 2 + hh * 8, u);
-            if (hh + 1 < PC / 16) tmem_wait_ld_tied(nxt);
+            if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
           }
-          arrive_h(h);
+          return true;
+        };
+
+        // epi1(k + 1) runs ahead of epi2(k); one call site each
+        for (int k = -1; k < ns; ++k) {
+          if (k + 1 < ns && !epi1(k + 1)) goto done;
+          if (k >= 0 && !epi2(k)) goto done;
         }
-      }
-      // R2 + sigmoid -> out (column group 0 stores).  Every warp waits for R2:
-      // the next tile's phi1 for its third slot writes Z, and it is issued
-      // only after every warp's first phi1 epilogue of that tile.
-      // the row's plan entry (pixel index) for the store, loaded while R2 runs
-      const uint32_t ent = g == 0 ? __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row)
-                                  : kPlanEmpty;
-      if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
-      if (g == 0) {
-        tc_fence_after();
-        uint32_t r[4];
-        tmem_ld4(Z, r);
-        if (ent != kPlanEmpty) {
-          const FusedFrame& F = frame_of(prm, tile);
-          const uint32_t pix = ent & kPlanPixelMask;
+
+        // pool = [max ; mean] -> the U region (bf16, 2H values = H columns):
+        // the max half first (rho's first K half can start), then the mean.
 #pragma unroll
-          for (int j = 0; j < kOut; ++j) {
-            const float y = __uint_as_float(r[j]) + b_r2[j];
-            F.out[static_cast<size_t>(j) * F.P + pix] = 1.0f / (1.0f + expf(-y));
+        for (int hh = 0; hh < CHC / 8; ++hh) {
+          uint32_t pm[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) pm[j] = mx[hh * 8 + j];
+          tmem_st8(tl + T::APOOL + g * CHC + hh * 8, pm);
+        }
+        arrive_h(0);
+        {
+          const float rcp = c > 0 ? __frcp_rn(static_cast<float>(c)) : 0.0f;
+          const float off = kSumBase - static_cast<float>(c) * kHalfQuantum;
+          bool over = false;
+#pragma unroll
+          for (int hh = 0; hh < CHC / 8; ++hh) {
+            uint32_t pa[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int jj = hh * 8 + j;
+              over |= !(fmaxf(sm[2 * jj], sm[2 * jj + 1]) < kSumLimit);
+              float a0, a1;
+              fadd2_rn(a0, a1, sm[2 * jj], sm[2 * jj + 1], -off, -off);
+              pa[j] = pack_bf16(a0 * rcp, a1 * rcp);
+            }
+            tmem_st8(tl + T::APOOL + H / 2 + g * CHC + hh * 8, pa);
+          }
+          if (over && c > 0) atomicOr(prm.err, kErrRange);
+        }
+        arrive_h(1);
+
+        // the row's plan entry (pixel index) for the store, loaded while the
+        // per-pixel layers run
+        const uint32_t ent =
+            g == 0 ? __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row) : kPlanEmpty;
+
+        // rho -> r (zero without layers) -> lo;  B1 -> y -> hi;  B2 -> y2 -> lo;
+        // R1 -> q -> hi.  Accumulators X, Y, X, Y.  Each layer in two passes of
+        // H/2 accumulator columns (this warp: H/4 of them), one arrival each.
+        gs += ns;
+        const uint32_t r3 = gs % 3u;
+        const uint32_t X = tl + T::buf(r3);
+        const uint32_t Y = tl + T::buf(r3 == 2 ? 0 : r3 + 1);
+        const uint32_t Z = tl + T::buf(r3 == 0 ? 2 : r3 - 1);
+        const uint32_t A_LO = tl + T::APOOL, A_HI = tl + T::APOOL + H / 2;
+        constexpr int PC = H / 4;  // accumulator columns of this warp per pass
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
+          ++n_dp;
+          tc_fence_after();
+          const float* bl = l == 0 ? b_rho : (l == 2 ? b_b2 : b_r1);
+          const uint32_t acc = (l & 1) ? Y : X;
+          const uint32_t dst = (l & 1) ? A_HI : A_LO;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c0 = h * (H / 2) + g * PC;  // first accumulator column of this pass
+            uint32_t ra[16], rb[16];
+            tmem_ld16_async(acc + c0, ra);
+            tmem_wait_ld_tied(ra);
+#pragma unroll
+            for (int hh = 0; hh < PC / 16; ++hh) {
+              uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
+              uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
+              if (hh + 1 < PC / 16) tmem_ld16_async(acc + c0 + (hh + 1) * 16, nxt);
+              uint32_t u[8];
+              if (l == 1) {  // B1's bias is folded into its GEMM
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                  u[i] = pack_bf16_relu(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
+              } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  float v0, v1;
+                  fadd2_rn(v0, v1, __uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]),
+                           bl[c0 + hh * 16 + 2 * i], bl[c0 + hh * 16 + 2 * i + 1]);
+                  u[i] = (l == 0 && c == 0) ? 0u : pack_bf16_relu(v0, v1);
+                }
+              }
+              tmem_st8(dst + c0 / 2 + hh * 8, u);
+              if (hh + 1 < PC / 16) tmem_wait_ld_tied(nxt);
+            }
+            arrive_h(h);
+          }
+        }
+        // R2 + sigmoid -> out (column group 0 stores).  Every warp waits for R2:
+        // the next tile's phi1 for its third slot writes Z, and it is issued
+        // only after every warp's first phi1 epilogue of that tile.  The next
+        // tile is taken first.
+        if (!take_tile(tb + 1)) goto done;
+        if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
+        if (g == 0) {
+          tc_fence_after();
+          uint32_t r[4];
+          tmem_ld4(Z, r);
+          if (ent != kPlanEmpty) {
+            float* const out = s_ld.out[tb & 3];
+            const size_t P = static_cast<size_t>(s_ld.P[tb & 3]);
+            const uint32_t pix = ent & kPlanPixelMask;
+#pragma unroll
+            for (int j = 0; j < kOut; ++j) {
+              const float y = __uint_as_float(r[j]) + b_r2[j];
+              out[j * P + pix] = 1.0f / (1.0f + expf(-y));
+            }
           }
         }
       }

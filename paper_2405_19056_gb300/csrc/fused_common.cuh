@@ -124,6 +124,12 @@ __device__ __forceinline__ const FusedFrame& frame_of(const FusedParams& prm, in
 // ---------------------------------------------------------------- loader
 // Slot count of the tile of each parity, per loader warp (max over its rows).
 struct LoaderShared {
+  // Frame of the tile of each index mod 4 (written by loader warp 0): output
+  // planes, folded per-scene biases and pixel count.  Four deep, so that the
+  // epilogue can still read them after the next tile has been published.
+  float* out[4];
+  const float* fold[4];
+  int P[4];
   int ns[2][kLoadWarps];
   int tile[2];
   uint8_t cnt[2][kTile];  // per tile parity: each row's layer count (0 for an empty row)
