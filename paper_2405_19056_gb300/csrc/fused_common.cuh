@@ -121,6 +121,22 @@ __device__ __forceinline__ const FusedFrame& frame_of(const FusedParams& prm, in
   return prm.f[fi];
 }
 
+// Schedule index (the value the dynamic tile counter handed out) -> tile.
+// Tiles go out in plan order, so the tiles of a window, which gather from the
+// same stretch of every plane, run at about the same time.  The last frame's
+// last windows are the end of the grid: there the partial window goes first,
+// then every window's largest tile, then every window's second tile and so
+// on, so that the CTAs that finish last finish on the smallest tiles.
+__device__ __forceinline__ int schedule_tile(const FusedParams& prm, uint32_t s) {
+  const int si = static_cast<int>(s);
+  if (si < prm.tail0 || si >= prm.total_tiles) return si;
+  int j = si - prm.tail0;
+  const int full = prm.tail_n * prm.win_tiles;
+  if (j < prm.tail_part) return prm.tail0 + full + j;
+  j -= prm.tail_part;
+  return prm.tail0 + (j % prm.tail_n) * prm.win_tiles + j / prm.tail_n;
+}
+
 // ---------------------------------------------------------------- loader
 // Slot count of the tile of each parity, per loader warp (max over its rows).
 struct LoaderShared {

@@ -129,7 +129,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
   for (uint32_t tb = 0;; ++tb) {
     int tile;
     if (li == 0) {
-      if (lane == 0) ls.tile[tb & 1] = static_cast<int>(atomicAdd(prm.next_tile, 1u));
+      if (lane == 0) ls.tile[tb & 1] = schedule_tile(prm, atomicAdd(prm.next_tile, 1u));
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_SCHED + (tb & 1)));
     } else if (!warp_wait(bar(B_SCHED + (tb & 1)), (tb >> 1) & 1, abort_flag)) {

@@ -156,6 +156,11 @@ struct FusedParams {
   uint32_t* err;
   uint32_t* plan;       // total_tiles * kTile entries (device)
   uint32_t* next_tile;  // dynamic tile counter (device), zeroed by the plan kernel
+  // Tail of the schedule (set by the launcher): the last frame's last
+  // tail_n full windows of win_tiles tiles start at tile tail0, its partial
+  // window (tail_part tiles) follows them.
+  int win_tiles;
+  int tail0, tail_n, tail_part;
 };
 
 // Launchers (return cudaGetLastError() of the launch).

@@ -11,6 +11,10 @@ using namespace fused;
 #define GN_WIN_TILES 4
 #endif
 constexpr int kWinTiles = GN_WIN_TILES;  // tiles per count-sorting window
+#ifndef GN_TAIL_WINDOWS
+#define GN_TAIL_WINDOWS 64
+#endif
+constexpr int kTailWindows = GN_TAIL_WINDOWS;  // windows scheduled rank-major at the end
 constexpr int kPlanWarps = 4;                         // windows per plan CTA
 constexpr int kPlanPer = kWinTiles * kTile / 32;        // pixels per lane
 static_assert(kPlanPer % 16 == 0 && kPlanPer <= 32, "a lane holds 16 or 32 pixels");
@@ -152,6 +156,14 @@ cudaError_t launch_plan(FusedParams& p, cudaStream_t s) {
     wins += (t + kWinTiles - 1) / kWinTiles;
   }
   p.total_windows = wins;
+  // schedule tail: the last frame's last full windows (see schedule_tile)
+  const FusedFrame& lf = p.f[p.nframes - 1];
+  const int tf = (lf.P + kTile - 1) / kTile;
+  const int wf = tf / kWinTiles;
+  p.win_tiles = kWinTiles;
+  p.tail_n = wf < kTailWindows ? wf : kTailWindows;
+  p.tail_part = tf % kWinTiles;
+  p.tail0 = lf.tile0 + (wf - p.tail_n) * kWinTiles;
   plan_kernel<<<(p.total_windows + kPlanWarps - 1) / kPlanWarps, kPlanWarps * 32, 0, s>>>(p);
   return cudaGetLastError();
 }
