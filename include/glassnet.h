@@ -169,6 +169,44 @@ int glassnet_render_host(gn_model* model, const gn_latent* latent, const float* 
                          const float* tbuf_host, const uint8_t* count_host, int K, int h, int w,
                          float* out_host, cudaStream_t stream);
 
+/*
+ * Streaming (incremental) rendering: the pooled set representation of Eq. 5
+ * built one transparency layer at a time (the paper's memory argument, Sec. 5
+ * and Fig. 9: the cost of a frame grows with the number of objects, the
+ * memory held need not).  A pool holds, per pixel, the running max and the
+ * exact fixed-point sum of phi over the layers accumulated so far and their
+ * number; the pooling is exact and order-independent, so accumulating a
+ * frame's layers in any order and resolving gives the same bits as
+ * glassnet_render of that frame (tested).
+ *
+ * Pool state: (H/2 + H) * 4 + 1 bytes per pixel in device memory (769 B at
+ * H = 128), plus a tile plan; owned by the pool object.
+ *
+ * glassnet_pool_create: a pool for h x w frames of this model (precision
+ *   GN_BF16_FUSED; GN_EUNSUPPORTED otherwise), empty (no layers).
+ * glassnet_pool_reset: empties the pool (stream-ordered).
+ * glassnet_accumulate_layer: phi of one transparency layer `layer` (device,
+ *   [12][h][w] f32, the channel layout of a tbuf slot) pooled into the pixels
+ *   it covers: `covered` (device, [h][w] u8, 0 or 1; NULL: every pixel).  At
+ *   most 8 layers per pool (Eq. 5's exact sum is bounded for K <= 8): a ninth
+ *   call returns GN_EINVAL.  Values other than 0 and 1 in `covered` set the
+ *   count error (GN_EINVAL at the next glassnet_check).
+ * glassnet_resolve: rho, B and R of the pooled state with the G-buffer `gbuf`
+ *   (device, [14][h][w] f32) -> `out` (device, [3][h][w] f32).  Pixels with no
+ *   layer take the opaque-only path (r = 0), as in glassnet_render.
+ * All three are asynchronous on `stream`; calls on one pool must be ordered
+ * (one stream); different pools may run concurrently.  Alignment rules are
+ * those of glassnet_render.
+ */
+typedef struct gn_pool gn_pool;
+int glassnet_pool_create(const gn_model* model, int h, int w, gn_pool** out);
+int glassnet_pool_reset(gn_pool* pool, cudaStream_t stream);
+int glassnet_accumulate_layer(const gn_model* model, const gn_latent* latent, gn_pool* pool,
+                              const float* layer, const uint8_t* covered, cudaStream_t stream);
+int glassnet_resolve(const gn_model* model, const gn_latent* latent, const gn_pool* pool,
+                     const float* gbuf, float* out, cudaStream_t stream);
+void glassnet_pool_free(gn_pool* pool);
+
 /* One frame of a batched launch. */
 typedef struct gn_frame {
   const gn_latent* latent;

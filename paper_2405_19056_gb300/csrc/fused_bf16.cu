@@ -156,11 +156,18 @@ __device__ __forceinline__ void store_slot(uint32_t base, int row0,
   }
 }
 
+// Launch modes: a whole frame (plan sorted by count, every layer slot, the
+// per-pixel layers), one streamed layer accumulated into a pool state in
+// device memory (one slot per tile, no per-pixel layers), or the per-pixel
+// layers of a pool state (no slots).  The arithmetic of each step is the same
+// code in all three, so a streamed frame resolves to the same bits.
+enum : int { kModeFrame = 0, kModeAccumulate = 1, kModeResolve = 2 };
+
 // Loader warps: per tile, read the plan entries of their rows and publish the
 // slot count, then fill the layer operands slot by slot (two buffers, released
 // by the phi1 MMAs that read them) and B1's G-buffer operand (released by B1
 // of the previous tile).
-template <int H>
+template <int H, int Mode>
 __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sbase,
                                             uint32_t bar_base, LoaderShared& ls,
                                             volatile int* abort_flag, int li, int lane) {
@@ -205,7 +212,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     }
     const int wmax = __reduce_max_sync(0xffffffffu, cmax);
     if (lane == 0) {
-      ls.ns[tb & 1][li] = wmax;
+      ls.ns[tb & 1][li] = Mode == kModeResolve ? 0 : wmax;  // resolve: no layer slots
       if (li == 0) {
         ls.out[tb & 3] = F.out;
         ls.fold[tb & 3] = F.fold;
@@ -219,8 +226,9 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     const int ns = max(ls.ns[tb & 1][0], ls.ns[tb & 1][1]);
 
     // G-buffer block [g0..g13, 1, 1] of the lane's rows, loads in flight now
-    float gv[kRowsPerLoadLane][kGC];
-    {
+    // (accumulate launches run no B1)
+    float gv[kRowsPerLoadLane][kGC] = {};
+    if constexpr (Mode != kModeAccumulate) {
       const uint32_t P = static_cast<uint32_t>(F.P);
 #pragma unroll
       for (int i = 0; i < kRowsPerLoadLane; ++i)
@@ -228,9 +236,14 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
         for (int ch = 0; ch < kGC; ++ch)
           gv[i][ch] = has[i] ? __ldg(F.gbuf + (static_cast<uint32_t>(ch) * P + pix[i])) : 0.0f;
     }
+    // The operand's release (B_AG_E) also paces the loaders: they are at most
+    // one tile ahead, as the two tile-publication barriers need.  Accumulate
+    // launches run no B1: there the MMA warp commits B_AG_E once per tile
+    // after phi2 and no operand is written.
     auto put_ag = [&]() -> bool {
       if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
+      if constexpr (Mode == kModeAccumulate) return true;
       const uint32_t one = pack_bf16(1.0f, 1.0f);
 #pragma unroll
       for (int i = 0; i < kRowsPerLoadLane; ++i) {
@@ -268,7 +281,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 }
 
 // ------------------------------------------------------------------ kernel
-template <int H>
+template <int H, int Mode>
 __global__ void __launch_bounds__(kThreadsF, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   using L = FusedLayout<H>;
@@ -327,7 +340,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     }
     fence_proxy_async_smem();
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
-    loader_loop<H>(prm, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
+    loader_loop<H, Mode>(prm, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA warp
     if (lane == 0) {
@@ -436,56 +449,64 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         p2.next();
         if (k + 2 < ns && !phi1()) goto done;
       }
-      // Per-pixel layers.  Accumulators alternate X / Y (a layer never
-      // overwrites the accumulator its input is being read from), A operands
-      // live in the U region (lo = first H/2 columns, hi = last H/2):
-      //   rho: X <- [max ; mean];  B1: Y <- [g ; r = lo];  B2: X <- y = hi;
-      //   R1: Y <- y2 = lo;  R2: Z <- q = hi.
-      // Each GEMM is issued in two K halves, each as soon as the epilogue
-      // half that produces it has arrived.
-      const uint32_t X = tbase + T::buf(p1.b);
-      const uint32_t Y = tbase + T::buf(p1.b == 2 ? 0 : p1.b + 1);
-      const uint32_t Z = tbase + T::buf(p1.b == 0 ? 2 : p1.b - 1);
-      const uint32_t A_LO = tbase + T::APOOL, A_HI = tbase + T::APOOL + H / 2;
-      constexpr uint64_t kHalfK = static_cast<uint64_t>(H / 32) * ((2 * H * 16) >> 4);
-      if (!wait_h(0)) goto done;
-      issue_gemm<H, H>(X, A_LO, dsc_rho, idH);
-      if (!wait_h(1)) goto done;
-      issue_gemm<H, H>(X, A_HI, dsc_rho + 2 * kHalfK, idH, true);
-      mma_commit_e(bar(B_DP));
-      __syncwarp();
-      // the next tile, read while the per-pixel layers run (the loaders
-      // publish it once this tile's layer operands are written)
       int next_tile, next_ns;
       const float* next_fold;
-      if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
-      if (!wait_h(0)) goto done;
-      if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
-      ++n_agf;
-      tc_fence_after();
-      mma_f16_ss_e(Y, dsc_ag, dsc_b1, idH, 0u);
-      issue_gemm<H, H / 2>(Y, A_LO, dsc_b1r, idH, true);
-      if (!wait_h(1)) goto done;
-      issue_gemm<H, H / 2>(Y, A_LO + H / 4, dsc_b1r + kHalfK, idH, true);
-      mma_commit_e(bar(B_DP));
-      mma_commit_e(bar(B_AG_E));
-      __syncwarp();
-      if (!wait_h(0)) goto done;
-      issue_gemm<H, H / 2>(X, A_HI, dsc_b2, idH);
-      if (!wait_h(1)) goto done;
-      issue_gemm<H, H / 2>(X, A_HI + H / 4, dsc_b2 + kHalfK, idH, true);
-      mma_commit_e(bar(B_DP));
-      __syncwarp();
-      if (!wait_h(0)) goto done;
-      issue_gemm<H, H / 2>(Y, A_LO, dsc_r1, idH);
-      if (!wait_h(1)) goto done;
-      issue_gemm<H, H / 2>(Y, A_LO + H / 4, dsc_r1 + kHalfK, idH, true);
-      mma_commit_e(bar(B_DP));
-      __syncwarp();
-      if (!wait_h(0) || !wait_h(1)) goto done;
-      issue_gemm<16, H>(Z, A_HI, dsc_r2, id16);
-      mma_commit_e(bar(B_DR2));
-      __syncwarp();
+      if constexpr (Mode == kModeAccumulate) {
+        // no per-pixel layers: the pool state goes back to device memory;
+        // B_AG_E paces the loaders (see loader_loop)
+        mma_commit_e(bar(B_AG_E));
+        __syncwarp();
+        if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
+      } else {
+        // Per-pixel layers.  Accumulators alternate X / Y (a layer never
+        // overwrites the accumulator its input is being read from), A operands
+        // live in the U region (lo = first H/2 columns, hi = last H/2):
+        //   rho: X <- [max ; mean];  B1: Y <- [g ; r = lo];  B2: X <- y = hi;
+        //   R1: Y <- y2 = lo;  R2: Z <- q = hi.
+        // Each GEMM is issued in two K halves, each as soon as the epilogue
+        // half that produces it has arrived.
+        const uint32_t X = tbase + T::buf(p1.b);
+        const uint32_t Y = tbase + T::buf(p1.b == 2 ? 0 : p1.b + 1);
+        const uint32_t Z = tbase + T::buf(p1.b == 0 ? 2 : p1.b - 1);
+        const uint32_t A_LO = tbase + T::APOOL, A_HI = tbase + T::APOOL + H / 2;
+        constexpr uint64_t kHalfK = static_cast<uint64_t>(H / 32) * ((2 * H * 16) >> 4);
+        if (!wait_h(0)) goto done;
+        issue_gemm<H, H>(X, A_LO, dsc_rho, idH);
+        if (!wait_h(1)) goto done;
+        issue_gemm<H, H>(X, A_HI, dsc_rho + 2 * kHalfK, idH, true);
+        mma_commit_e(bar(B_DP));
+        __syncwarp();
+        // the next tile, read while the per-pixel layers run (the loaders
+        // publish it once this tile's layer operands are written)
+        if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
+        if (!wait_h(0)) goto done;
+        if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        ++n_agf;
+        tc_fence_after();
+        mma_f16_ss_e(Y, dsc_ag, dsc_b1, idH, 0u);
+        issue_gemm<H, H / 2>(Y, A_LO, dsc_b1r, idH, true);
+        if (!wait_h(1)) goto done;
+        issue_gemm<H, H / 2>(Y, A_LO + H / 4, dsc_b1r + kHalfK, idH, true);
+        mma_commit_e(bar(B_DP));
+        mma_commit_e(bar(B_AG_E));
+        __syncwarp();
+        if (!wait_h(0)) goto done;
+        issue_gemm<H, H / 2>(X, A_HI, dsc_b2, idH);
+        if (!wait_h(1)) goto done;
+        issue_gemm<H, H / 2>(X, A_HI + H / 4, dsc_b2 + kHalfK, idH, true);
+        mma_commit_e(bar(B_DP));
+        __syncwarp();
+        if (!wait_h(0)) goto done;
+        issue_gemm<H, H / 2>(Y, A_LO, dsc_r1, idH);
+        if (!wait_h(1)) goto done;
+        issue_gemm<H, H / 2>(Y, A_LO + H / 4, dsc_r1 + kHalfK, idH, true);
+        mma_commit_e(bar(B_DP));
+        __syncwarp();
+        if (!wait_h(0) || !wait_h(1)) goto done;
+        issue_gemm<16, H>(Z, A_HI, dsc_r2, id16);
+        mma_commit_e(bar(B_DR2));
+        __syncwarp();
+      }
       // the next tile's first two phi1 right behind R2 (they write X and Y)
       tile = next_tile;
       ns = next_ns;
@@ -537,6 +558,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         return true;
       };
       if (!take_tile(0)) goto done;
+      const size_t Pst = static_cast<size_t>(prm.f[0].P);  // pool-state plane stride
       for (; tile < total_tiles; ++tb) {
         uint32_t mx[CHC];  // running max, bf16 pairs
         float sm[CH];      // fixed-point sums
@@ -544,6 +566,19 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         for (int j = 0; j < CHC; ++j) mx[j] = 0u;
 #pragma unroll
         for (int j = 0; j < CH; ++j) sm[j] = kSumBase;
+        // Streaming launches: a pixel that has layers starts from its pool
+        // state (planes of the pixel's channel pairs and channels).
+        uint32_t pix_st = 0;
+        if constexpr (Mode != kModeFrame) {
+          const uint32_t e = __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row);
+          pix_st = e & kPlanPixelMask;
+          if (e != kPlanEmpty && c > 0) {
+#pragma unroll
+            for (int j = 0; j < CHC; ++j) mx[j] = prm.pool_mx[(g * CHC + j) * Pst + pix_st];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) sm[j] = prm.pool_sum[(g * CH + j) * Pst + pix_st];
+          }
+        }
 
         // phi1(k) accumulator -> U(k) = ReLU as bf16.  16-column TMEM loads
         // are double buffered: block hh + 1 is in flight while hh is packed.
@@ -612,7 +647,18 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           if (k + 1 < ns && !epi1(k + 1)) goto done;
           if (k >= 0 && !epi2(k)) goto done;
         }
-
+        if constexpr (Mode == kModeAccumulate) {
+          // the covered pixels' state back to device memory, one more layer
+          if (c > 0) {
+#pragma unroll
+            for (int j = 0; j < CHC; ++j) prm.pool_mx[(g * CHC + j) * Pst + pix_st] = mx[j];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) prm.pool_sum[(g * CH + j) * Pst + pix_st] = sm[j];
+            if (g == 0) prm.pool_cnt[pix_st] = static_cast<uint8_t>(prm.pool_cnt[pix_st] + 1);
+          }
+          gs += ns;
+          if (!take_tile(tb + 1)) goto done;
+        } else {
         // pool = [max ; mean] -> the U region (bf16, 2H values = H columns):
         // the max half first (rho's first K half can start), then the mean.
 #pragma unroll
@@ -719,6 +765,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             }
           }
         }
+        }  // frame and resolve launches: the per-pixel layers
       }
     }
   }
@@ -732,21 +779,21 @@ done:
   }
 }
 
-template <int H>
+template <int H, int Mode>
 cudaError_t prepare_h() {
   static bool done = false;  // per process: the attribute holds for every later launch
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H>,
+  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, Mode>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FusedLayout<H>::smem_bytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <int H>
+template <int H, int Mode>
 cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
   constexpr int smem = FusedLayout<H>::smem_bytes;
-  cudaError_t e = prepare_h<H>();
+  cudaError_t e = prepare_h<H, Mode>();
   if (e != cudaSuccess) return e;
   // Programmatic dependent launch: the CTAs may start while the plan kernel
   // is still running; they wait on the grid dependency before the plan reads.
@@ -760,24 +807,44 @@ cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H>, p, static_cast<const uint8_t*>(wimg));
+  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H, Mode>, p,
+                            static_cast<const uint8_t*>(wimg));
+}
+
+template <int H>
+cudaError_t prepare_all() {
+  cudaError_t e = prepare_h<H, kModeFrame>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeAccumulate>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeResolve>();
+  return e;
+}
+
+template <int H>
+cudaError_t launch_mode(int mode, const void* wimg, const FusedParams& p, cudaStream_t s,
+                        int grid) {
+  switch (mode) {
+    case kModeAccumulate: return launch_h<H, kModeAccumulate>(wimg, p, s, grid);
+    case kModeResolve: return launch_h<H, kModeResolve>(wimg, p, s, grid);
+    default: return launch_h<H, kModeFrame>(wimg, p, s, grid);
+  }
 }
 
 }  // namespace
 
 cudaError_t prepare_fused_bf16(int H) {
   device_sm_count();
-  return H == 128 ? prepare_h<128>() : prepare_h<64>();
+  return H == 128 ? prepare_all<128>() : prepare_all<64>();
 }
 
 cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& params,
-                              cudaStream_t s) {
+                              cudaStream_t s, int mode) {
   if (params.total_tiles <= 0) return cudaSuccess;
   FusedParams p = params;
   cudaError_t e = launch_plan(p, s);
   if (e != cudaSuccess) return e;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
-  return H == 128 ? launch_h<128>(wimg, p, s, grid) : launch_h<64>(wimg, p, s, grid);
+  return H == 128 ? launch_mode<128>(mode, wimg, p, s, grid)
+                  : launch_mode<64>(mode, wimg, p, s, grid);
 }
 
 }  // namespace gn

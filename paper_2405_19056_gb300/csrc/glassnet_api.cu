@@ -635,6 +635,153 @@ void glassnet_free_latent(gn_latent* lat) {
   delete lat;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------- streaming
+struct gn_pool {
+  int h = 0, w = 0, H = 0;
+  void* dev = nullptr;  // sums [H][P] f32, max pairs [H/2][P] u32, counts [P] u8
+  float* sum = nullptr;
+  uint32_t* mx = nullptr;
+  uint8_t* cnt = nullptr;
+  void* plan = nullptr;  // tile plan of the pool's launches
+  int layers = 0;        // accumulate calls since the last reset
+};
+
+namespace {
+// Empty pool: running max 0 (the ReLU floor), sums at 2^11 (the fixed-point
+// base of the exact pooling), no layers.
+__global__ void pool_reset_kernel(float* sum, uint32_t* mx, uint8_t* cnt, size_t n_sum,
+                                  size_t n_mx, size_t n_cnt) {
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n_sum; i += stride) {
+    sum[i] = 2048.0f;
+    if (i < n_mx) mx[i] = 0u;
+    if (i < n_cnt) cnt[i] = 0u;
+  }
+}
+
+// One-frame fused parameters of a pool launch (pixel-order plan, the pool's
+// state and plan workspace).
+gn::FusedParams pool_params(const gn_model* m, const gn_latent* lat, const gn_pool* pool,
+                            const float* gbuf, const float* tbuf, const uint8_t* cnt, int K,
+                            float* out) {
+  gn::FusedParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nframes = 1;
+  p.err = m->err;
+  p.f[0] = gn::FusedFrame{gbuf, tbuf, cnt, out, lat->fold(), K, pool->h * pool->w, 0, 0};
+  number_tiles(p);
+  p.plan_identity = 1;
+  p.pool_sum = pool->sum;
+  p.pool_mx = pool->mx;
+  p.pool_cnt = pool->cnt;
+  gn::bind_plan(p, pool->plan);
+  return p;
+}
+
+int check_pool_call(const gn_model* m, const gn_latent* lat, const gn_pool* pool) {
+  if (!m) return fail(GN_EINVAL, "model is NULL");
+  if (!lat) return fail(GN_EINVAL, "latent is NULL");
+  if (!pool) return fail(GN_EINVAL, "pool is NULL");
+  if (m->precision != GN_BF16_FUSED)
+    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model");
+  if (lat->H != m->H || lat->Z != m->Z)
+    return fail(GN_EINVAL, "latent widths (%d, %d) do not match the model (%d, %d)", lat->H,
+                lat->Z, m->H, m->Z);
+  if (pool->H != m->H) return fail(GN_EINVAL, "pool of width %d, model of width %d", pool->H, m->H);
+  return GN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int glassnet_pool_create(const gn_model* m, int h, int w, gn_pool** out) {
+  if (!m || !out) return fail(GN_EINVAL, "model and out must be non-NULL");
+  *out = nullptr;
+  if (m->precision != GN_BF16_FUSED)
+    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model");
+  if (h < 1 || w < 1) return fail(GN_EINVAL, "frame %d x %d is empty", h, w);
+  const long long P = static_cast<long long>(h) * w;
+  if (P * gn::kTC >= (1ll << 31)) return fail(GN_EINVAL, "frame %d x %d too large", h, w);
+  cudaError_t e = gn::prepare_fused(m);
+  if (e != cudaSuccess) return cuda_fail(e, "fused kernel attributes");
+  gn_pool* pool = new gn_pool;
+  pool->h = h;
+  pool->w = w;
+  pool->H = m->H;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t b_sum = up(static_cast<size_t>(P) * m->H * 4), b_mx = up(static_cast<size_t>(P) * (m->H / 2) * 4);
+  const size_t b_cnt = up(static_cast<size_t>(P));
+  if (cudaMalloc(&pool->dev, b_sum + b_mx + b_cnt) != cudaSuccess) {
+    delete pool;
+    return fail(GN_ENOMEM, "cudaMalloc pool state (%zu bytes)", b_sum + b_mx + b_cnt);
+  }
+  uint8_t* base = static_cast<uint8_t*>(pool->dev);
+  pool->sum = reinterpret_cast<float*>(base);
+  pool->mx = reinterpret_cast<uint32_t*>(base + b_sum);
+  pool->cnt = base + b_sum + b_mx;
+  const long long tiles = (P + gn::kTile - 1) / gn::kTile;
+  if (cudaMalloc(&pool->plan, gn::fused_plan_bytes(tiles)) != cudaSuccess) {
+    cudaFree(pool->dev);
+    delete pool;
+    return fail(GN_ENOMEM, "cudaMalloc pool tile plan");
+  }
+  int rc = glassnet_pool_reset(pool, nullptr);
+  if (rc == GN_OK && (e = cudaStreamSynchronize(nullptr)) != cudaSuccess) rc = cuda_fail(e, "pool reset");
+  if (rc != GN_OK) {
+    glassnet_pool_free(pool);
+    return rc;
+  }
+  *out = pool;
+  return GN_OK;
+}
+
+int glassnet_pool_reset(gn_pool* pool, cudaStream_t s) {
+  if (!pool) return fail(GN_EINVAL, "pool is NULL");
+  const size_t P = static_cast<size_t>(pool->h) * pool->w;
+  pool_reset_kernel<<<std::min<size_t>((P * pool->H + 255) / 256, 4096), 256, 0, s>>>(
+      pool->sum, pool->mx, pool->cnt, P * pool->H, P * (pool->H / 2), P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "pool reset launch");
+  pool->layers = 0;
+  return GN_OK;
+}
+
+int glassnet_accumulate_layer(const gn_model* m, const gn_latent* lat, gn_pool* pool,
+                              const float* layer, const uint8_t* covered, cudaStream_t s) {
+  int rc = check_pool_call(m, lat, pool);
+  if (rc != GN_OK) return rc;
+  if (!layer) return fail(GN_EINVAL, "layer is NULL");
+  if (!aligned4(layer)) return fail(GN_EINVAL, "layer must be 4-byte aligned");
+  if (pool->layers >= gn::kMaxK)
+    return fail(GN_EINVAL, "the pool already holds %d layers (at most %d)", pool->layers, gn::kMaxK);
+  gn::FusedParams p = pool_params(m, lat, pool, nullptr, layer, covered, 1, nullptr);
+  cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s, 1);
+  if (e != cudaSuccess) return cuda_fail(e, "accumulate launch");
+  ++pool->layers;
+  return GN_OK;
+}
+
+int glassnet_resolve(const gn_model* m, const gn_latent* lat, const gn_pool* pool,
+                     const float* gbuf, float* out, cudaStream_t s) {
+  int rc = check_pool_call(m, lat, pool);
+  if (rc != GN_OK) return rc;
+  if (!gbuf || !out) return fail(GN_EINVAL, "gbuf and out must be non-NULL");
+  if (!aligned4(gbuf) || !aligned4(out)) return fail(GN_EINVAL, "gbuf and out must be 4-byte aligned");
+  gn::FusedParams p = pool_params(m, lat, pool, gbuf, nullptr, pool->cnt, gn::kMaxK, out);
+  cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s, 2);
+  if (e != cudaSuccess) return cuda_fail(e, "resolve launch");
+  return GN_OK;
+}
+
+void glassnet_pool_free(gn_pool* pool) {
+  if (!pool) return;
+  if (pool->dev) cudaFree(pool->dev);
+  if (pool->plan) cudaFree(pool->plan);
+  delete pool;
+}
+
 void glassnet_free_model(gn_model* m) {
   if (!m) return;
   if (m->w32) cudaFree(m->w32);

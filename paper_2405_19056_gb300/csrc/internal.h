@@ -161,13 +161,23 @@ struct FusedParams {
   // window (tail_part tiles) follows them.
   int win_tiles;
   int tail0, tail_n, tail_part;
+  // Streaming launches (accumulate / resolve): the plan keeps pixel order
+  // (identity), a frame's counts may be NULL (every pixel has K layers), and
+  // the pool state lives in device planes of P values each.
+  int plan_identity;
+  uint32_t* pool_mx;  // [H/2][P] running max, bf16 pairs
+  float* pool_sum;    // [H][P] fixed-point sums (start 2^11)
+  uint8_t* pool_cnt;  // [P] layers accumulated
 };
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_encode(const float* w32, const WeightIndex& wi, const float* scene_dev,
                           float* latent_dev, cudaStream_t s);
 // Plan kernel, then the fused kernel.
-cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& p, cudaStream_t s);
+// mode: 0 a whole frame, 1 accumulate one streamed layer into the pool state,
+// 2 resolve the pool state (see fused_bf16.cu).
+cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& p, cudaStream_t s,
+                              int mode = 0);
 // Kernel attributes the fused launch needs; call once outside stream capture.
 cudaError_t prepare_fused_bf16(int H);
 size_t fused_plan_bytes(long long tiles);

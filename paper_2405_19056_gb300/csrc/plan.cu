@@ -57,9 +57,13 @@ __global__ void __launch_bounds__(kPlanWarps * 32) plan_kernel(const __grid_cons
   const int p0 = lw * kWinTiles * kTile + lane * kPlanPer;            // lane's first pixel
   uint32_t* out = prm.plan + static_cast<size_t>(prm.f[fi].tile0 + lw * kWinTiles) * kTile;
 
-  // the lane's counts, one byte each (0 past the frame; presence is p < P)
+  // the lane's counts, one byte each (0 past the frame; presence is p < P;
+  // no count array: every pixel has K layers)
   uint32_t cw[kPlanPer / 4];
-  if ((reinterpret_cast<uintptr_t>(counts + p0) & 15u) == 0 && p0 + kPlanPer <= P) {
+  if (counts == nullptr) {
+#pragma unroll
+    for (int j = 0; j < kPlanPer / 4; ++j) cw[j] = static_cast<uint32_t>(K) * 0x01010101u;
+  } else if ((reinterpret_cast<uintptr_t>(counts + p0) & 15u) == 0 && p0 + kPlanPer <= P) {
 #pragma unroll
     for (int j = 0; j < kPlanPer / 16; ++j) {
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(counts + p0) + j);
@@ -94,6 +98,18 @@ __global__ void __launch_bounds__(kPlanWarps * 32) plan_kernel(const __grid_cons
     own.add(c, 1);
   }
   if (over) atomicOr(prm.err, kErrCount);
+  if (prm.plan_identity) {
+    // pixel order: row r of the window holds its r-th pixel
+#pragma unroll
+    for (int i = 0; i < kPlanPer; ++i) {
+      const int r = lane * kPlanPer + i;
+      if (r >= rows) continue;
+      const int c = static_cast<int>((cw[i / 4] >> (8 * (i % 4))) & 0xffu);
+      out[r] = p0 + i < P ? static_cast<uint32_t>(p0 + i) | (static_cast<uint32_t>(c) << 28)
+                          : kPlanEmpty;
+    }
+    return;
+  }
   // exclusive prefix of the packed counters over the lanes, and the totals
   Classes pre = own;
 #pragma unroll

@@ -57,6 +57,11 @@ _SIGNATURES = {
     "glassnet_server_wait": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "glassnet_server_stats": (_I, [_P, _P]),
     "glassnet_server_destroy": (None, [_P]),
+    "glassnet_pool_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
+    "glassnet_pool_reset": (_I, [_P, _P]),
+    "glassnet_accumulate_layer": (_I, [_P, _P, _P, _P, _P, _P]),
+    "glassnet_resolve": (_I, [_P, _P, _P, _P, _P, _P]),
+    "glassnet_pool_free": (None, [_P]),
     "glassnet_graph_create": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
     "glassnet_graph_launch": (_I, [_P, _P]),
     "glassnet_graph_update": (_I, [_P, _P, _I]),
@@ -233,6 +238,31 @@ def glassnet_graph_create(model, frames) -> int:
     out = ctypes.c_void_p()
     _check(_lib().glassnet_graph_create(model, _frame_array(frames), len(frames), ctypes.byref(out)))
     return out.value
+
+
+def glassnet_pool_create(model, h, w) -> int:
+    """Streaming pool for h x w frames (GN_BF16_FUSED models), empty."""
+    out = ctypes.c_void_p()
+    _check(_lib().glassnet_pool_create(model, h, w, ctypes.byref(out)))
+    return out.value
+
+
+def glassnet_pool_reset(pool, stream=None):
+    _check(_lib().glassnet_pool_reset(pool, _stream(stream)))
+
+
+def glassnet_accumulate_layer(model, latent, pool, layer, covered=None, stream=None):
+    """layer: device [12][h][w] f32; covered: device [h][w] u8 (0 / 1) or None (all)."""
+    _check(_lib().glassnet_accumulate_layer(model, latent, pool, _ptr(layer), _ptr(covered),
+                                            _stream(stream)))
+
+
+def glassnet_resolve(model, latent, pool, gbuf, out, stream=None):
+    _check(_lib().glassnet_resolve(model, latent, pool, _ptr(gbuf), _ptr(out), _stream(stream)))
+
+
+def glassnet_pool_free(pool):
+    _lib().glassnet_pool_free(pool)
 
 
 def glassnet_graph_launch(graph, stream=None):

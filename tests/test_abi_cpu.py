@@ -118,6 +118,11 @@ def test_null_arguments_rejected(lib):
     assert lib.glassnet_server_wait(None, 1, None) == gl.GN_EINVAL
     assert lib.glassnet_server_stats(None, None) == gl.GN_EINVAL
     lib.glassnet_server_destroy(None)
+    assert lib.glassnet_pool_create(None, 8, 8, ctypes.byref(out)) == gl.GN_EINVAL
+    assert lib.glassnet_pool_reset(None, None) == gl.GN_EINVAL
+    assert lib.glassnet_accumulate_layer(None, None, None, None, None, None) == gl.GN_EINVAL
+    assert lib.glassnet_resolve(None, None, None, None, None, None) == gl.GN_EINVAL
+    lib.glassnet_pool_free(None)
 
 
 def test_python_binding_raises_with_message(lib):
