@@ -327,6 +327,7 @@ def run_fused(args, world, rank, local):
         result["fp32_plain"]["speedup_of_bf16_fused"] = value / world / result["fp32_plain"]["value"]
         result["e2e"] = e2e_leg(model, lat, scene, frames, args, stream, world)
         result["batch_16_frames"] = batch_leg(model, dev, stream)
+        result["streaming"] = streaming_leg(model, lat, dframes, stream)
         result["fp8"] = fp8_leg(weights, scene, dframes, flops, stream, dev)
         result["serving"] = (serving_leg(model, (50, 200, 800), 2000) if args.serving_full
                              else serving_leg(model, (200, 800), 300))
@@ -472,6 +473,62 @@ def serving_leg(model, rates, n_requests, n_streams=4, seed=0):
     return {"workload": "Poisson arrivals; 256/512/1024 squared w.p. 0.5/0.35/0.15; K~U{1..8}, "
                         "all slots valid; 8 scenes; host buffers in and out; "
                         f"{n_streams} lanes", "rates": results}
+
+
+def streaming_leg(model, lat, dframes, stream, steps=20):
+    """The workload's frames streamed one layer at a time: pool reset, the 8
+    layers accumulated (layer k covers the pixels whose count exceeds k), one
+    resolve (glassnet_pool_* / _accumulate_layer / _resolve).  The accumulate
+    launches are bound by the pool state's device-memory traffic: per covered
+    (pixel, layer) the layer's 48 bytes are read and the 768 bytes of state
+    (running max pairs and sums) read and written, plus the count byte."""
+    import torch
+    from paper_2405_19056_gb300 import glassnet as gl
+    if model.precision != gl.GN_BF16_FUSED:
+        return None
+    _, hbm_gbs, hbm_src = measured_peaks()
+    pool = gl.glassnet_pool_create(model.handle, H_IMG, W_IMG)
+    covs = []
+    for d in dframes:
+        covs.append([(d["counts"] > k).to(torch.uint8) for k in range(K_SLOTS)])
+    covered = [int(sum(int(c.sum()) for c in cv)) for cv in covs]
+    try:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        acc_ms, res_ms, tot_ms = 0.0, 0.0, 0.0
+        for it in range(steps + 3):
+            i = it % N_ROTATE
+            d = dframes[i]
+            ev[0].record(stream)
+            gl.glassnet_pool_reset(pool, stream)
+            for k in range(K_SLOTS):
+                gl.glassnet_accumulate_layer(model.handle, lat.handle, pool, d["tbuf"][k],
+                                             covs[i][k], stream)
+            ev[1].record(stream)
+            gl.glassnet_resolve(model.handle, lat.handle, pool, d["gbuf"], d["out"], stream)
+            ev[2].record(stream)
+            stream.synchronize()
+            if it >= 3:
+                acc_ms += ev[0].elapsed_time(ev[1])
+                res_ms += ev[1].elapsed_time(ev[2])
+                tot_ms += ev[0].elapsed_time(ev[2])
+        model.check(stream)
+    finally:
+        gl.glassnet_pool_free(pool)
+    acc_ms /= steps
+    res_ms /= steps
+    tot_ms /= steps
+    P = H_IMG * W_IMG
+    cov_mean = sum(covered) / len(covered)
+    acc_bytes = P * K_SLOTS * (1 + 8) + cov_mean * (48 + 2 * 768 + 2)  # masks, plans, layers, state
+    gbs = acc_bytes / (acc_ms * 1e-3) / 1e9
+    return {"value": P / (tot_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_frame": tot_ms,
+            "accumulate_ms_per_frame": acc_ms, "resolve_ms": res_ms, "steps": steps,
+            "covered_pixel_layers": cov_mean,
+            "roofline_accumulate": {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs,
+                                    "unit": "GB/s", "frac": gbs / hbm_gbs,
+                                    "bytes_per_frame": acc_bytes,
+                                    "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json)"},
+            "api": "glassnet_pool_reset + 8 x glassnet_accumulate_layer + glassnet_resolve"}
 
 
 def batch_leg(model, dev, stream, steps=20):

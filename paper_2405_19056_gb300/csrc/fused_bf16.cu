@@ -453,7 +453,13 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       const float* next_fold;
       if constexpr (Mode == kModeAccumulate) {
         // no per-pixel layers: the pool state goes back to device memory;
-        // B_AG_E paces the loaders (see loader_loop)
+        // B_AG_E paces the loaders (see loader_loop), once every epilogue
+        // warp has taken this tile (a tile without covered pixels involves
+        // no epilogue work, and the loaders must not get two tiles ahead of
+        // the epilogue either)
+        // (two alternating barriers: the epilogue cannot take tile tb + 2
+        // before this commit, so neither runs two phases ahead)
+        if (!warp_wait(bar(B_H + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
         mma_commit_e(bar(B_AG_E));
         __syncwarp();
         if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
@@ -569,6 +575,9 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         // Streaming launches: a pixel that has layers starts from its pool
         // state (planes of the pixel's channel pairs and channels).
         uint32_t pix_st = 0;
+        if constexpr (Mode == kModeAccumulate) {
+          if (lane == 0) mbar_arrive(bar(B_H + (tb & 1)));  // this tile is taken (paces the loaders)
+        }
         if constexpr (Mode != kModeFrame) {
           const uint32_t e = __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row);
           pix_st = e & kPlanPixelMask;
