@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         if constexpr (Mode != kModeFrame) {
           const uint32_t e = __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row);
           pix_st = e & kPlanPixelMask;
-          if (e != kPlanEmpty && c > 0) {
+          if (e != kPlanEmpty && c > 0 && !prm.pool_fresh) {
 #pragma unroll
             for (int j = 0; j < CHC; ++j) mx[j] = prm.pool_mx[(g * CHC + j) * Pst + pix_st];
 #pragma unroll

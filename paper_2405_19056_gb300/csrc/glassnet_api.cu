@@ -757,6 +757,7 @@ int glassnet_accumulate_layer(const gn_model* m, const gn_latent* lat, gn_pool* 
   if (pool->layers >= gn::kMaxK)
     return fail(GN_EINVAL, "the pool already holds %d layers (at most %d)", pool->layers, gn::kMaxK);
   gn::FusedParams p = pool_params(m, lat, pool, nullptr, layer, covered, 1, nullptr);
+  p.pool_fresh = pool->layers == 0;  // after a reset the state need not be read
   cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s, 1);
   if (e != cudaSuccess) return cuda_fail(e, "accumulate launch");
   ++pool->layers;

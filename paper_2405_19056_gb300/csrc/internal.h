@@ -168,6 +168,7 @@ struct FusedParams {
   uint32_t* pool_mx;  // [H/2][P] running max, bf16 pairs
   float* pool_sum;    // [H][P] fixed-point sums (start 2^11)
   uint8_t* pool_cnt;  // [P] layers accumulated
+  int pool_fresh;     // the pool is empty: its state is the start value, not read
 };
 
 // Launchers (return cudaGetLastError() of the launch).
