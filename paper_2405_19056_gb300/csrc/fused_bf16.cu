@@ -224,6 +224,20 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     // the tile's slot count is the max over both loader warps
     if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
     const int ns = max(ls.ns[tb & 1][0], ls.ns[tb & 1][1]);
+    if (Mode == kModeResolve || (Mode == kModeAccumulate && ns > 0 && !prm.pool_fresh)) {
+      // Streaming launches: the pool state of this warp's rows (row0 + 32 i:
+      // 32 consecutive pixels, one 128-byte line in each of the tile's H/2 + H
+      // planes) into L2 ahead of the epilogue's loads, for the lines that
+      // hold a pixel whose state is read.
+      const uint32_t* blk =
+          prm.pool_st + static_cast<size_t>(tile - F.tile0) * ((H / 2 + H) * kTile) + li * 64;
+#pragma unroll
+      for (int i = 0; i < kRowsPerLoadLane; ++i) {
+        if (!__any_sync(0xffffffffu, has[i] && cnt[i] > 0)) continue;
+        for (int pl = lane; pl < H / 2 + H; pl += 32)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + pl * kTile + 32 * i));
+      }
+    }
 
     // G-buffer block [g0..g13, 1, 1] of the lane's rows, loads in flight now
     // (accumulate launches run no B1)
@@ -564,7 +578,6 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         return true;
       };
       if (!take_tile(0)) goto done;
-      const size_t Pst = static_cast<size_t>(prm.f[0].P);  // pool-state plane stride
       for (; tile < total_tiles; ++tb) {
         uint32_t mx[CHC];  // running max, bf16 pairs
         float sm[CH];      // fixed-point sums
@@ -574,18 +587,18 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         for (int j = 0; j < CH; ++j) sm[j] = kSumBase;
         // Streaming launches: a pixel that has layers starts from its pool
         // state (planes of the pixel's channel pairs and channels).
-        uint32_t pix_st = 0;
+        uint32_t* st = nullptr;  // this row's word in plane 0 of the tile's state block
         if constexpr (Mode == kModeAccumulate) {
           if (lane == 0) mbar_arrive(bar(B_H + (tb & 1)));  // this tile is taken (paces the loaders)
         }
         if constexpr (Mode != kModeFrame) {
-          const uint32_t e = __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row);
-          pix_st = e & kPlanPixelMask;
-          if (e != kPlanEmpty && c > 0 && !prm.pool_fresh) {
+          // pixel order: row `row` of the tile is its pixel
+          st = prm.pool_st + static_cast<size_t>(tile - prm.f[0].tile0) * ((H / 2 + H) * kTile) + row;
+          if (c > 0 && !prm.pool_fresh) {
 #pragma unroll
-            for (int j = 0; j < CHC; ++j) mx[j] = prm.pool_mx[(g * CHC + j) * Pst + pix_st];
+            for (int j = 0; j < CHC; ++j) mx[j] = st[(g * CHC + j) * kTile];
 #pragma unroll
-            for (int j = 0; j < CH; ++j) sm[j] = prm.pool_sum[(g * CH + j) * Pst + pix_st];
+            for (int j = 0; j < CH; ++j) sm[j] = __uint_as_float(st[(H / 2 + g * CH + j) * kTile]);
           }
         }
 
@@ -660,10 +673,13 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           // the covered pixels' state back to device memory, one more layer
           if (c > 0) {
 #pragma unroll
-            for (int j = 0; j < CHC; ++j) prm.pool_mx[(g * CHC + j) * Pst + pix_st] = mx[j];
+            for (int j = 0; j < CHC; ++j) st[(g * CHC + j) * kTile] = mx[j];
 #pragma unroll
-            for (int j = 0; j < CH; ++j) prm.pool_sum[(g * CH + j) * Pst + pix_st] = sm[j];
-            if (g == 0) prm.pool_cnt[pix_st] = static_cast<uint8_t>(prm.pool_cnt[pix_st] + 1);
+            for (int j = 0; j < CH; ++j) st[(H / 2 + g * CH + j) * kTile] = __float_as_uint(sm[j]);
+            if (g == 0) {
+              const size_t pix = static_cast<size_t>(tile - prm.f[0].tile0) * kTile + row;
+              prm.pool_cnt[pix] = static_cast<uint8_t>(prm.pool_cnt[pix] + 1);
+            }
           }
           gs += ns;
           if (!take_tile(tb + 1)) goto done;

@@ -640,9 +640,9 @@ void glassnet_free_latent(gn_latent* lat) {
 // ------------------------------------------------------------- streaming
 struct gn_pool {
   int h = 0, w = 0, H = 0;
-  void* dev = nullptr;  // sums [H][P] f32, max pairs [H/2][P] u32, counts [P] u8
-  float* sum = nullptr;
-  uint32_t* mx = nullptr;
+  void* dev = nullptr;  // state blocks (tile-major, see FusedParams), then counts [P] u8
+  uint32_t* st = nullptr;
+  size_t st_words = 0;
   uint8_t* cnt = nullptr;
   void* plan = nullptr;  // tile plan of the pool's launches
   int layers = 0;        // accumulate calls since the last reset
@@ -650,13 +650,15 @@ struct gn_pool {
 
 namespace {
 // Empty pool: running max 0 (the ReLU floor), sums at 2^11 (the fixed-point
-// base of the exact pooling), no layers.
-__global__ void pool_reset_kernel(float* sum, uint32_t* mx, uint8_t* cnt, size_t n_sum,
-                                  size_t n_mx, size_t n_cnt) {
+// base of the exact pooling), no layers.  Word w of the state lies in plane
+// (w / 128) mod (H/2 + H) of its tile's block: the first H/2 planes hold the
+// max pairs, the others the sums.
+__global__ void pool_reset_kernel(uint32_t* st, size_t n_st, int planes, int mx_planes,
+                                  uint8_t* cnt, size_t n_cnt) {
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
-  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n_sum; i += stride) {
-    sum[i] = 2048.0f;
-    if (i < n_mx) mx[i] = 0u;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n_st; i += stride) {
+    const int pl = static_cast<int>((i / gn::kTile) % static_cast<size_t>(planes));
+    st[i] = pl < mx_planes ? 0u : 0x45000000u;  // 2048.0f
     if (i < n_cnt) cnt[i] = 0u;
   }
 }
@@ -673,8 +675,7 @@ gn::FusedParams pool_params(const gn_model* m, const gn_latent* lat, const gn_po
   p.f[0] = gn::FusedFrame{gbuf, tbuf, cnt, out, lat->fold(), K, pool->h * pool->w, 0, 0};
   number_tiles(p);
   p.plan_identity = 1;
-  p.pool_sum = pool->sum;
-  p.pool_mx = pool->mx;
+  p.pool_st = pool->st;
   p.pool_cnt = pool->cnt;
   gn::bind_plan(p, pool->plan);
   return p;
@@ -711,17 +712,16 @@ int glassnet_pool_create(const gn_model* m, int h, int w, gn_pool** out) {
   pool->w = w;
   pool->H = m->H;
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-  const size_t b_sum = up(static_cast<size_t>(P) * m->H * 4), b_mx = up(static_cast<size_t>(P) * (m->H / 2) * 4);
-  const size_t b_cnt = up(static_cast<size_t>(P));
-  if (cudaMalloc(&pool->dev, b_sum + b_mx + b_cnt) != cudaSuccess) {
+  const long long tiles = (P + gn::kTile - 1) / gn::kTile;
+  pool->st_words = static_cast<size_t>(tiles) * (m->H / 2 + m->H) * gn::kTile;
+  const size_t b_st = up(pool->st_words * 4), b_cnt = up(static_cast<size_t>(P));
+  if (cudaMalloc(&pool->dev, b_st + b_cnt) != cudaSuccess) {
     delete pool;
-    return fail(GN_ENOMEM, "cudaMalloc pool state (%zu bytes)", b_sum + b_mx + b_cnt);
+    return fail(GN_ENOMEM, "cudaMalloc pool state (%zu bytes)", b_st + b_cnt);
   }
   uint8_t* base = static_cast<uint8_t*>(pool->dev);
-  pool->sum = reinterpret_cast<float*>(base);
-  pool->mx = reinterpret_cast<uint32_t*>(base + b_sum);
-  pool->cnt = base + b_sum + b_mx;
-  const long long tiles = (P + gn::kTile - 1) / gn::kTile;
+  pool->st = reinterpret_cast<uint32_t*>(base);
+  pool->cnt = base + b_st;
   if (cudaMalloc(&pool->plan, gn::fused_plan_bytes(tiles)) != cudaSuccess) {
     cudaFree(pool->dev);
     delete pool;
@@ -740,8 +740,8 @@ int glassnet_pool_create(const gn_model* m, int h, int w, gn_pool** out) {
 int glassnet_pool_reset(gn_pool* pool, cudaStream_t s) {
   if (!pool) return fail(GN_EINVAL, "pool is NULL");
   const size_t P = static_cast<size_t>(pool->h) * pool->w;
-  pool_reset_kernel<<<std::min<size_t>((P * pool->H + 255) / 256, 4096), 256, 0, s>>>(
-      pool->sum, pool->mx, pool->cnt, P * pool->H, P * (pool->H / 2), P);
+  pool_reset_kernel<<<std::min<size_t>((pool->st_words + 255) / 256, 4096), 256, 0, s>>>(
+      pool->st, pool->st_words, pool->H / 2 + pool->H, pool->H / 2, pool->cnt, P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "pool reset launch");
   pool->layers = 0;

@@ -165,8 +165,11 @@ struct FusedParams {
   // (identity), a frame's counts may be NULL (every pixel has K layers), and
   // the pool state lives in device planes of P values each.
   int plan_identity;
-  uint32_t* pool_mx;  // [H/2][P] running max, bf16 pairs
-  float* pool_sum;    // [H][P] fixed-point sums (start 2^11)
+  // Pool state, tile-major: per 128-pixel tile of the frame a block of
+  // H/2 + H planes of 128 words (running max as bf16 pairs, then the
+  // fixed-point sums as f32 bits, start 2^11), so a tile's state is one
+  // contiguous block and a warp's access to a plane is coalesced.
+  uint32_t* pool_st;
   uint8_t* pool_cnt;  // [P] layers accumulated
   int pool_fresh;     // the pool is empty: its state is the start value, not read
 };
