@@ -18,7 +18,8 @@ Readings where the paper is silent (each is listed with its reason in the
 design notes): ReLU after every linear layer except the last one of R, which
 is a sigmoid; the mean divides by the number of valid layers; an empty layer
 set gives r = 0; input concat orders are [b ; sigma] and [g ; r ; sigma];
-pool order is [max ; mean].
+pool order is [max ; mean].  The paper's own form of Eq. 5 is also given
+(``pooling="sum"``): tau = sum_k h(b_k, sigma) enters B directly, no rho.
 
 Every function below is pinned by ``tests/test_oracle_pins.py`` (hand-worked
 closed forms, brute force, invariants and library routines).
@@ -87,6 +88,20 @@ def set_pool(V) -> np.ndarray | None:
     return np.concatenate([mx, s / c])
 
 
+def set_sum(V) -> np.ndarray:
+    """Eq. 5's symmetric function as the paper writes it: tau = sum_k v_k over
+    the set V [c][H], each channel's values summed in ascending order (a
+    canonical order, so the result is exactly independent of the order of the
+    layers).  The empty set sums to the zero vector.
+    """
+    V = _f64(V)
+    s = np.zeros(V.shape[1])
+    srt = np.sort(V, axis=0)
+    for k in range(V.shape[0]):
+        s = s + srt[k]
+    return s
+
+
 def post_pool_rho(weights, pool) -> np.ndarray:
     """Post-pooling network rho: r = ReLU(W_rho pool + b_rho)."""
     return relu(linear(pool, *weights["rho"]))
@@ -120,6 +135,17 @@ def render_pixel(weights, sigma, g, layers) -> np.ndarray:
     return render_R(weights, y)
 
 
+def render_pixel_sum(weights, sigma, g, layers) -> np.ndarray:
+    """One pixel in the paper's form of Eq. 5: tau = sum_k h(b_k, sigma) enters
+    B directly as [g ; tau ; sigma] (no rho; rho's weights are not used)."""
+    layers = _f64(layers).reshape(-1, np.shape(weights["phi1"][0])[1] - np.shape(sigma)[-1])
+    H = np.shape(weights["phi2"][0])[0]
+    V = np.stack([per_layer_h(weights, layers[k], sigma) for k in range(layers.shape[0])]) \
+        if layers.shape[0] else np.zeros((0, H))
+    y = final_blend_B(weights, g, set_sum(V), sigma)
+    return render_R(weights, y)
+
+
 def render_opaque_only(weights, sigma, gbuf_rows) -> np.ndarray:
     """Opaque-only path: B and R with the rho input removed.
 
@@ -138,14 +164,18 @@ def render_opaque_only(weights, sigma, gbuf_rows) -> np.ndarray:
     return render_R(weights, y)
 
 
-def render_frame(weights, scene, gbuf, tbuf, counts, chunk: int = 16384) -> np.ndarray:
+def render_frame(weights, scene, gbuf, tbuf, counts, chunk: int = 16384,
+                 pooling: str = "max_mean") -> np.ndarray:
     """Whole frame, vectorised over pixels; returns rgb float64 [3][h][w].
 
     ``gbuf`` [n_g][h][w], ``tbuf`` [K][n_t][h][w], ``counts`` [h][w].  Slots
     ``k >= counts`` are never read into the result.  Pixels are processed in
     chunks only to bound memory; every pixel's arithmetic is the same as
-    ``render_pixel``.
+    ``render_pixel`` (``pooling="max_mean"``) or ``render_pixel_sum``
+    (``pooling="sum"``, the paper's Eq. 5 form).
     """
+    if pooling not in ("max_mean", "sum"):
+        raise ValueError(f"pooling must be 'max_mean' or 'sum', got {pooling!r}")
     sigma = scene_encoder(weights, scene)
     n_g, h, w = np.shape(gbuf)
     K, n_t = np.shape(tbuf)[0], np.shape(tbuf)[1]
@@ -172,11 +202,14 @@ def render_frame(weights, scene, gbuf, tbuf, counts, chunk: int = 16384) -> np.n
         s = np.zeros((n, H))
         for k in range(K):
             s = s + np.where((k < c)[:, None], srt[k], 0.0)
-        has = c > 0
-        r = np.zeros((n, H))
-        if np.any(has):
-            pool = np.concatenate([mx[has], s[has] / c[has][:, None]], axis=1)
-            r[has] = post_pool_rho(weights, pool)
+        if pooling == "sum":
+            r = s  # tau: the sum over the valid layers, 0 without any
+        else:
+            has = c > 0
+            r = np.zeros((n, H))
+            if np.any(has):
+                pool = np.concatenate([mx[has], s[has] / c[has][:, None]], axis=1)
+                r[has] = post_pool_rho(weights, pool)
         y = final_blend_B(weights, _f64(G[:, p0:p1]).T, r, sigma)
         out[:, p0:p1] = render_R(weights, y).T
     return out.reshape(3, h, w)

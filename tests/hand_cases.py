@@ -56,3 +56,13 @@ LOGITS_ONE_LAYER = np.array([5.0, 2.0, -6.0])
 LOGITS_TWO_LAYERS = np.array([-2.0, 5.0, -2.0])
 LOGITS_NO_LAYER = np.array([2.0, 1.0, -2.0])
 POOL_TWO_LAYERS = np.array([5.0, 2.0, 5.0, 1.0])
+
+# Sum pooling (the paper's Eq. 5 form, tau = sum_k v_k straight into B, no rho):
+#   one layer  tau = [5, 0]:  B1 [1 + 5 + 1, 0 + 1] = [7, 1];  B2 [14 - 1, 7 - 1] = [13, 6]
+#              R1 [13, -13 + 6 + 3] -> [13, 0];  R2 [13, 0, -13 + 1]
+#   two layers tau = [10, 2]: B1 [12, 3];  B2 [24 - 3, 12 - 1] = [21, 11]
+#              R1 [21, -21 + 11 + 3] -> [21, 0];  R2 [21, 0, -21 + 1]
+#   no layer   tau = [0, 0]:  the opaque-only logits above
+TAU_TWO_LAYERS = np.array([10.0, 2.0])
+LOGITS_SUM_ONE_LAYER = np.array([13.0, 0.0, -12.0])
+LOGITS_SUM_TWO_LAYERS = np.array([21.0, 0.0, -20.0])

@@ -320,6 +320,133 @@ def test_mean_over_slots_instead_of_valid_layers_is_caught():
     np.testing.assert_array_equal(right, hc.POOL_TWO_LAYERS)
 
 
+# ------------------------------------------------------ sum pooling (Eq. 5 form)
+
+def test_hand_set_sum_two_layers():
+    V = np.stack([O.per_layer_h(hc.W, hc.LAYER_A, hc.SIGMA),
+                  O.per_layer_h(hc.W, hc.LAYER_B, hc.SIGMA)])
+    np.testing.assert_array_equal(O.set_sum(V), hc.TAU_TWO_LAYERS)
+    np.testing.assert_array_equal(O.set_sum(np.zeros((0, 2))), np.zeros(2))
+
+
+@pytest.mark.parametrize("layers,logits", [
+    ([hc.LAYER_A], hc.LOGITS_SUM_ONE_LAYER),
+    ([hc.LAYER_A, hc.LAYER_B], hc.LOGITS_SUM_TWO_LAYERS),
+    ([hc.LAYER_B, hc.LAYER_A], hc.LOGITS_SUM_TWO_LAYERS),
+    ([], hc.LOGITS_NO_LAYER),
+])
+def test_hand_render_pixel_sum(layers, logits):
+    sigma = O.scene_encoder(hc.W, hc.SCENE)
+    L = np.array(layers, np.float32).reshape(len(layers), 2)
+    np.testing.assert_allclose(O.render_pixel_sum(hc.W, sigma, hc.G, L), expit(logits),
+                               rtol=1e-15, atol=0)
+
+
+def test_hand_render_frame_sum_matches_closed_forms():
+    counts = np.array([[1, 2], [0, 2]], np.uint8)
+    gbuf = np.broadcast_to(hc.G[:, None, None], (2, 2, 2)).copy()
+    tbuf = np.full((3, 2, 2, 2), np.nan, np.float32)
+    tbuf[0, :, 0, 0] = hc.LAYER_A
+    tbuf[0, :, 0, 1] = hc.LAYER_A
+    tbuf[1, :, 0, 1] = hc.LAYER_B
+    tbuf[0, :, 1, 1] = hc.LAYER_B
+    tbuf[1, :, 1, 1] = hc.LAYER_A
+    rgb = O.render_frame(hc.W, hc.SCENE, gbuf, tbuf, counts, pooling="sum")
+    np.testing.assert_allclose(rgb[:, 0, 0], expit(hc.LOGITS_SUM_ONE_LAYER), rtol=1e-15)
+    np.testing.assert_allclose(rgb[:, 0, 1], expit(hc.LOGITS_SUM_TWO_LAYERS), rtol=1e-15)
+    np.testing.assert_allclose(rgb[:, 1, 0], expit(hc.LOGITS_NO_LAYER), rtol=1e-15)
+    np.testing.assert_allclose(rgb[:, 1, 1], expit(hc.LOGITS_SUM_TWO_LAYERS), rtol=1e-15)
+
+
+def test_sum_pooling_is_not_duplication_invariant():
+    """Unlike [max ; mean], the sum of {a, a, b, b} is twice that of {a, b}."""
+    rng = np.random.default_rng(11)
+    a, b = rng.random(4), rng.random(4)
+    np.testing.assert_allclose(O.set_sum(np.stack([a, a, b, b])), 2 * O.set_sum(np.stack([a, b])),
+                               rtol=1e-15)
+    p1, p2 = O.set_pool(np.stack([a, b])), O.set_pool(np.stack([a, a, b, b]))
+    np.testing.assert_array_equal(p1, p2)
+
+
+def test_sum_pooling_permutation_invariant_and_empty_is_opaque_only():
+    w = synth.make_weights(synth.Widths(hidden=8, latent=6), seed=3, bias="uniform")
+    sigma = O.scene_encoder(w, synth.make_scene(2))
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal(14)
+    L = rng.standard_normal((4, 12))
+    ref = O.render_pixel_sum(w, sigma, g, L)
+    for perm in itertools.permutations(range(4)):
+        np.testing.assert_array_equal(O.render_pixel_sum(w, sigma, g, L[list(perm)]), ref)
+    np.testing.assert_allclose(O.render_pixel_sum(w, sigma, g, np.zeros((0, 12))),
+                               O.render_opaque_only(w, sigma, g[None, :])[0], rtol=1e-14)
+
+
+def test_sum_frame_matches_per_pixel_definition():
+    w = synth.make_weights(synth.Widths(hidden=8, latent=6), seed=4, bias="uniform")
+    scene = synth.make_scene(1)
+    f = synth.make_frame(5, 3, 4, counts="uniform", seed=6)
+    rgb = O.render_frame(w, scene, f.gbuf, f.tbuf, f.counts, pooling="sum")
+    sigma = O.scene_encoder(w, scene)
+    for y in range(5):
+        for x in range(3):
+            c = int(f.counts[y, x])
+            exp = O.render_pixel_sum(w, sigma, f.gbuf[:, y, x], f.tbuf[:c, :, y, x])
+            np.testing.assert_allclose(rgb[:, y, x], exp, rtol=1e-13, atol=1e-15)
+
+
+def _sum_pins_pass(mod):
+    """The sum-pooling hand pins, per pixel and through the frame path."""
+    try:
+        sigma = mod.scene_encoder(hc.W, hc.SCENE)
+        for layers, logits in [([hc.LAYER_A], hc.LOGITS_SUM_ONE_LAYER),
+                               ([hc.LAYER_A, hc.LAYER_B], hc.LOGITS_SUM_TWO_LAYERS),
+                               ([], hc.LOGITS_NO_LAYER)]:
+            L = np.array(layers, np.float32).reshape(len(layers), 2)
+            if not np.allclose(mod.render_pixel_sum(hc.W, sigma, hc.G, L), expit(logits),
+                               rtol=1e-12, atol=0):
+                return False
+        tbuf = np.full((3, 2, 1, 1), np.nan, np.float32)
+        tbuf[0, :, 0, 0] = hc.LAYER_A
+        tbuf[1, :, 0, 0] = hc.LAYER_B
+        rgb = mod.render_frame(hc.W, hc.SCENE, hc.G.reshape(2, 1, 1), tbuf,
+                               np.array([[2]], np.uint8), pooling="sum")
+        return bool(np.allclose(rgb[:, 0, 0], expit(hc.LOGITS_SUM_TWO_LAYERS), rtol=1e-12, atol=0))
+    except Exception:
+        return False
+
+
+SUM_MUTATIONS = {
+    "sum drops the last layer": ("set_sum", lambda V: _ORIG_SUM(np.asarray(V)[:-1])
+                                 if len(V) else _ORIG_SUM(V)),
+    "sum is the mean": ("set_sum", lambda V: _ORIG_SUM(V) / max(len(V), 1)),
+    "sum is the max": ("set_sum", lambda V: np.max(V, axis=0) if len(V) else _ORIG_SUM(V)),
+    "tau through rho": ("final_blend_B", lambda w, g, r, s: _ORIG["final_blend_B"](
+        w, g, O.relu(O.linear(np.concatenate([r, r], -1), *w["rho"])) if np.shape(r)[-1] ==
+        np.shape(w["rho"][0])[0] else r, s)),
+    "B input [tau; g; sigma]": ("final_blend_B", lambda w, g, r, s: _ORIG["final_blend_B"](w, r, g, s)),
+}
+_ORIG_SUM = O.set_sum
+
+
+def test_unmutated_oracle_passes_sum_pins():
+    assert _sum_pins_pass(O)
+
+
+@pytest.mark.parametrize("label", sorted(SUM_MUTATIONS))
+def test_planted_sum_mistake_is_caught(monkeypatch, label):
+    name, fn = SUM_MUTATIONS[label]
+    monkeypatch.setattr(O, name, fn)
+    assert not _sum_pins_pass(O), label
+
+
+def test_mean_instead_of_sum_is_caught():
+    """A tau that divides by the count (the mean) fails the two-layer hand pin."""
+    sigma = O.scene_encoder(hc.W, hc.SCENE)
+    V = np.stack([O.per_layer_h(hc.W, hc.LAYER_A, sigma), O.per_layer_h(hc.W, hc.LAYER_B, sigma)])
+    wrong = O.render_R(hc.W, O.final_blend_B(hc.W, hc.G, O.set_sum(V) / 2, sigma))
+    assert not np.allclose(wrong, expit(hc.LOGITS_SUM_TWO_LAYERS), rtol=1e-12)
+
+
 def test_oracle_package_exports():
     for n in oracle.__all__ if hasattr(oracle, "__all__") else []:
         assert hasattr(oracle, n)
