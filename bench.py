@@ -152,13 +152,26 @@ def barrier(world):
 
 
 def allreduce_max(world, x: float) -> float:
+    """Max of ``x`` over all ranks (the slowest rank's time is the job's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_frame_seeds(rank: int, n: int) -> list[int]:
+    """Seeds of the ``n`` frames a replica renders: disjoint across ranks, so
+    every rank works on frames of its own (weak scaling, no exchange)."""
+    return [100 * rank + i for i in range(n)]
+
+
+def job_mpx_per_s(world: int, pixels_per_step: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: all ranks' pixels over the slowest rank's time."""
+    return world * pixels_per_step * steps / (max_ms * 1e-3) / 1e6
 
 
 # --------------------------------------------------------------- reference arm
@@ -240,8 +253,8 @@ def run_fused(args, world, rank, local):
     scene = synth.make_scene(0)
     stream = torch.cuda.Stream(device=dev)
 
-    frames = [synth.make_frame(H_IMG, W_IMG, K_SLOTS, counts="poisson3", seed=100 * rank + i)
-              for i in range(N_ROTATE)]
+    frames = [synth.make_frame(H_IMG, W_IMG, K_SLOTS, counts="poisson3", seed=sd)
+              for sd in rank_frame_seeds(rank, N_ROTATE)]
     dframes = []
     for f in frames:
         dframes.append(dict(gbuf=torch.from_numpy(f.gbuf).to(dev),
@@ -289,7 +302,7 @@ def run_fused(args, world, rank, local):
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = starts[0].elapsed_time(ends[-1])
     total_ms = allreduce_max(world, total_ms)
-    value = world * P * args.steps / (total_ms * 1e-3) / 1e6
+    value = job_mpx_per_s(world, P, args.steps, total_ms)
     step_flops = sum(flops[i % N_ROTATE] for i in range(args.steps)) / args.steps
     avg_kernel_ms = statistics.mean(per)
     peak_tf, _, peak_src = measured_peaks()
