@@ -52,14 +52,15 @@ def parse():
     return ap.parse_args()
 
 
-def algorithmic_flops(H: int, counts: np.ndarray) -> float:
+def algorithmic_flops(H: int, counts: np.ndarray, pooling: str = "max_mean") -> float:
     """FLOPs of the folded network on the valid layers only.
 
     Per valid (pixel, layer): phi1 12*H (latent folded) + phi2 H*H MACs.
-    Per pixel: rho 2H*H + B1 (14+H)*H (latent folded) + B2 H*H + R1 H*H + R2 3H.
+    Per pixel: rho 2H*H + B1 (14+H)*H (latent folded) + B2 H*H + R1 H*H + R2 3H;
+    the sum form of Eq. 5 has no rho.
     """
     per_layer = 12 * H + H * H
-    per_pixel = 2 * H * H + (14 + H) * H + H * H + H * H + 3 * H
+    per_pixel = (0 if pooling == "sum" else 2 * H * H) + (14 + H) * H + H * H + H * H + 3 * H
     return 2.0 * (per_layer * float(counts.sum()) + per_pixel * counts.size)
 
 
@@ -342,6 +343,7 @@ def run_fused(args, world, rank, local):
         result["batch_16_frames"] = batch_leg(model, dev, stream)
         result["streaming"] = streaming_leg(model, lat, dframes, stream)
         result["fp8"] = fp8_leg(weights, scene, dframes, flops, stream, dev)
+        result["sum_pooling"] = sum_pooling_leg(weights, scene, dframes, frames, stream)
         result["serving"] = (serving_leg(model, (50, 200, 800), 2000) if args.serving_full
                              else serving_leg(model, (200, 800), 300))
     clocks = clk.summary()
@@ -416,6 +418,43 @@ def fp8_leg(weights, scene, dframes, flops, stream, dev, steps=200):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": 2 * peak_bf16,
                          "unit": "TFLOP/s", "frac": achieved / (2 * peak_bf16),
                          "peak_source": "measured bf16 burst x 2 (nominal fp8/bf16 ratio)"}}
+
+
+def sum_pooling_leg(weights, scene, dframes, frames, stream, steps=200):
+    """The same workload with the paper's sum form of Eq. 5 (tau = sum of the
+    layers' phi outputs straight into B, no rho), BF16 fused."""
+    import torch
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    ms_model = gl.Model(weights, gl.GN_BF16_FUSED, gl.GN_POOL_SUM)
+    lat = ms_model.encode(scene, stream)
+    flops = [algorithmic_flops(weights["phi2"][0].shape[0], f.counts, "sum") for f in frames]
+
+    def step(i):
+        d = dframes[i % N_ROTATE]
+        gl.glassnet_render(ms_model.handle, lat.handle, d["gbuf"], d["tbuf"], d["counts"], K_SLOTS,
+                           H_IMG, W_IMG, d["out"], stream)
+
+    for i in range(5):
+        step(i)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        step(i)
+    e1.record(stream)
+    stream.synchronize()
+    gl.glassnet_check(ms_model.handle, stream)
+    ms = e0.elapsed_time(e1) / steps
+    peak_bf16, _, _ = measured_peaks()
+    step_flops = sum(flops[i % N_ROTATE] for i in range(steps)) / steps
+    achieved = step_flops / (ms * 1e-3) / 1e12
+    return {"value": H_IMG * W_IMG / (ms * 1e-3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms,
+            "steps": steps, "dtype": "bf16 operands, fp32 accumulate", "pooling": "sum (Eq. 5)",
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16,
+                         "unit": "TFLOP/s", "frac": achieved / peak_bf16,
+                         "peak_source": "measured bf16 burst"}}
 
 
 def serving_leg(model, rates, n_requests, n_streams=4, seed=0):

@@ -67,6 +67,16 @@ typedef enum gn_precision {
   GN_FP8_FUSED = 2   /* fused kernel with E4M3 operands and FP32 scales */
 } gn_precision;
 
+/* Symmetric function of Eq. 5 that pools a pixel's per-layer phi outputs.
+ * GN_POOL_MAX_MEAN: pool = [max ; mean] over the valid layers, then
+ *   r = ReLU(W_rho pool + b_rho) (r = 0 without layers) enters B.
+ * GN_POOL_SUM: the paper's own form, tau = sum of the phi outputs (the zero
+ *   vector without layers) enters B directly; rho is not used. */
+typedef enum gn_pooling {
+  GN_POOL_MAX_MEAN = 0,
+  GN_POOL_SUM = 1
+} gn_pooling;
+
 typedef struct gn_model gn_model;   /* device weights of one network */
 typedef struct gn_latent gn_latent; /* one encoded scene: sigma and folded biases */
 
@@ -106,6 +116,24 @@ typedef struct gn_blob_header {
  * (64, 128) or (128, 256)), GN_ENOMEM, GN_ECUDA.  Synchronous.
  */
 int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_model** out);
+
+/*
+ * As glassnet_load_weights, with the pooling of Eq. 5 (gn_pooling).
+ * glassnet_load_weights is this call with GN_POOL_MAX_MEAN.  A GN_POOL_SUM
+ * network has no rho: its blob keeps the rho tensor and bias slots (any
+ * values; zeros for a network trained in that form), which are never read.
+ * GN_POOL_SUM is built for GN_FP32_PLAIN and GN_BF16_FUSED (every render,
+ * batch, graph, server and streaming call of those precisions); with
+ * GN_FP8_FUSED it returns GN_EUNSUPPORTED.  The sum uses the same exact
+ * fixed-point accumulator as the mean (range [0, 2^11) per pixel-channel,
+ * GN_ERANGE beyond it), so the BF16 result is bit-identical under any order
+ * of a pixel's layers.  Errors: those of glassnet_load_weights, GN_EINVAL
+ * (unknown pooling), GN_EUNSUPPORTED.
+ */
+int glassnet_load_weights_ex(const void* blob, size_t nbytes, int precision, int pooling,
+                             gn_model** out);
+/* The model's gn_pooling.  Errors: GN_EINVAL (NULL argument). */
+int glassnet_model_pooling(const gn_model* model, int* pooling);
 
 /* Widths and precision of a loaded model (any pointer may be NULL). */
 int glassnet_model_info(const gn_model* model, int* hidden, int* latent, int* precision);
@@ -192,7 +220,8 @@ int glassnet_render_host(gn_model* model, const gn_latent* latent, const float* 
  *   call returns GN_EINVAL.  Values other than 0 and 1 in `covered` set the
  *   count error (GN_EINVAL at the next glassnet_check).
  * glassnet_resolve: rho, B and R of the pooled state with the G-buffer `gbuf`
- *   (device, [14][h][w] f32) -> `out` (device, [3][h][w] f32).  Pixels with no
+ *   (device, [14][h][w] f32) -> `out` (device, [3][h][w] f32); for a
+ *   GN_POOL_SUM model the pooled sum enters B directly.  Pixels with no
  *   layer take the opaque-only path (r = 0), as in glassnet_render.
  * All three are asynchronous on `stream`; calls on one pool must be ordered
  * (one stream); different pools may run concurrently.  Alignment rules are

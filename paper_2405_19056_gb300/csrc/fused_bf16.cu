@@ -295,9 +295,14 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 }
 
 // ------------------------------------------------------------------ kernel
-template <int H, int Mode>
+// Sum: the paper's own form of Eq. 5, tau = sum of the valid layers' phi
+// outputs entering B1 directly (no rho).  tau is the same fixed-point sum as
+// the mean's, tau = s - 2^11 + c 2^-13 (0 without layers), so it is
+// bit-identical under any order of the layers; the max is not kept.
+template <int H, int Mode, bool Sum>
 __global__ void __launch_bounds__(kThreadsF, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
+  static_assert(!Sum || Mode != kModeAccumulate, "accumulation does not depend on the pooling");
   using L = FusedLayout<H>;
   using T = TMap<H>;
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
@@ -483,6 +488,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         // live in the U region (lo = first H/2 columns, hi = last H/2):
         //   rho: X <- [max ; mean];  B1: Y <- [g ; r = lo];  B2: X <- y = hi;
         //   R1: Y <- y2 = lo;  R2: Z <- q = hi.
+        // The sum form has no rho: B1 reads tau from lo.
         // Each GEMM is issued in two K halves, each as soon as the epilogue
         // half that produces it has arrived.
         const uint32_t X = tbase + T::buf(p1.b);
@@ -490,12 +496,14 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const uint32_t Z = tbase + T::buf(p1.b == 0 ? 2 : p1.b - 1);
         const uint32_t A_LO = tbase + T::APOOL, A_HI = tbase + T::APOOL + H / 2;
         constexpr uint64_t kHalfK = static_cast<uint64_t>(H / 32) * ((2 * H * 16) >> 4);
-        if (!wait_h(0)) goto done;
-        issue_gemm<H, H>(X, A_LO, dsc_rho, idH);
-        if (!wait_h(1)) goto done;
-        issue_gemm<H, H>(X, A_HI, dsc_rho + 2 * kHalfK, idH, true);
-        mma_commit_e(bar(B_DP));
-        __syncwarp();
+        if constexpr (!Sum) {
+          if (!wait_h(0)) goto done;
+          issue_gemm<H, H>(X, A_LO, dsc_rho, idH);
+          if (!wait_h(1)) goto done;
+          issue_gemm<H, H>(X, A_HI, dsc_rho + 2 * kHalfK, idH, true);
+          mma_commit_e(bar(B_DP));
+          __syncwarp();
+        }
         // the next tile, read while the per-pixel layers run (the loaders
         // publish it once this tile's layer operands are written)
         if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
@@ -596,7 +604,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           st = prm.pool_st + static_cast<size_t>(tile - prm.f[0].tile0) * ((H / 2 + H) * kTile) + row;
           if (c > 0 && !prm.pool_fresh) {
 #pragma unroll
-            for (int j = 0; j < CHC; ++j) mx[j] = st[(g * CHC + j) * kTile];
+            for (int j = 0; j < CHC; ++j) mx[j] = Sum ? 0u : st[(g * CHC + j) * kTile];
 #pragma unroll
             for (int j = 0; j < CH; ++j) sm[j] = __uint_as_float(st[(H / 2 + g * CH + j) * kTile]);
           }
@@ -655,7 +663,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
                 const int j = hh * 16 + i;
                 const uint32_t u =
                     pack_bf16_relu(__uint_as_float(cur[i]), __uint_as_float(cur[i + 1]));
-                mx[j / 2] = bmax2(mx[j / 2], u);
+                if constexpr (!Sum) mx[j / 2] = bmax2(mx[j / 2], u);
                 add_bf16x2_rz(sm[j], sm[j + 1], u);
               }
             }
@@ -683,6 +691,33 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           }
           gs += ns;
           if (!take_tile(tb + 1)) goto done;
+        } else {
+        if constexpr (Sum) {
+        // tau -> lo (bf16, H values = H/2 columns), B1's K half by K half.
+        // This warp's channels lie in one half (all of them for kEW = 1): it
+        // arrives on the other half's barrier without writing.
+        const bool first_half = g * CH < H / 2;
+        if (!first_half) arrive_h(0);
+        {
+          const float off = kSumBase - static_cast<float>(c) * kHalfQuantum;
+          bool over = false;
+#pragma unroll
+          for (int hh = 0; hh < CHC / 8; ++hh) {
+            uint32_t pa[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int jj = hh * 8 + j;
+              over |= !(fmaxf(sm[2 * jj], sm[2 * jj + 1]) < kSumLimit);
+              float a0, a1;
+              fadd2_rn(a0, a1, sm[2 * jj], sm[2 * jj + 1], -off, -off);
+              pa[j] = pack_bf16(a0, a1);
+            }
+            tmem_st8(tl + T::APOOL + g * CHC + hh * 8, pa);
+          }
+          if (over && c > 0) atomicOr(prm.err, kErrRange);
+        }
+        if (first_half) arrive_h(0);
+        arrive_h(1);
         } else {
         // pool = [max ; mean] -> the U region (bf16, 2H values = H columns):
         // the max half first (rho's first K half can start), then the mean.
@@ -714,6 +749,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           if (over && c > 0) atomicOr(prm.err, kErrRange);
         }
         arrive_h(1);
+        }  // max + mean
 
         // the row's plan entry (pixel index) for the store, loaded while the
         // per-pixel layers run
@@ -731,7 +767,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const uint32_t A_LO = tl + T::APOOL, A_HI = tl + T::APOOL + H / 2;
         constexpr int PC = H / 4;  // accumulator columns of this warp per pass
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
+        for (int l = Sum ? 1 : 0; l < 4; ++l) {
           if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
           ++n_dp;
           tc_fence_after();
@@ -804,21 +840,21 @@ done:
   }
 }
 
-template <int H, int Mode>
+template <int H, int Mode, bool Sum>
 cudaError_t prepare_h() {
   static bool done = false;  // per process: the attribute holds for every later launch
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, Mode>,
+  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, Mode, Sum>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FusedLayout<H>::smem_bytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <int H, int Mode>
+template <int H, int Mode, bool Sum>
 cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
   constexpr int smem = FusedLayout<H>::smem_bytes;
-  cudaError_t e = prepare_h<H, Mode>();
+  cudaError_t e = prepare_h<H, Mode, Sum>();
   if (e != cudaSuccess) return e;
   // Programmatic dependent launch: the CTAs may start while the plan kernel
   // is still running; they wait on the grid dependency before the plan reads.
@@ -832,26 +868,30 @@ cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H, Mode>, p,
+  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H, Mode, Sum>, p,
                             static_cast<const uint8_t*>(wimg));
 }
 
 template <int H>
 cudaError_t prepare_all() {
-  cudaError_t e = prepare_h<H, kModeFrame>();
-  if (e == cudaSuccess) e = prepare_h<H, kModeAccumulate>();
-  if (e == cudaSuccess) e = prepare_h<H, kModeResolve>();
+  cudaError_t e = prepare_h<H, kModeFrame, false>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeAccumulate, false>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeResolve, false>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeFrame, true>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeResolve, true>();
   return e;
 }
 
 template <int H>
 cudaError_t launch_mode(int mode, const void* wimg, const FusedParams& p, cudaStream_t s,
                         int grid) {
-  switch (mode) {
-    case kModeAccumulate: return launch_h<H, kModeAccumulate>(wimg, p, s, grid);
-    case kModeResolve: return launch_h<H, kModeResolve>(wimg, p, s, grid);
-    default: return launch_h<H, kModeFrame>(wimg, p, s, grid);
-  }
+  // accumulation is the same for both poolings (the state holds max and sum)
+  if (mode == kModeAccumulate) return launch_h<H, kModeAccumulate, false>(wimg, p, s, grid);
+  if (p.pool_sum)
+    return mode == kModeResolve ? launch_h<H, kModeResolve, true>(wimg, p, s, grid)
+                                : launch_h<H, kModeFrame, true>(wimg, p, s, grid);
+  return mode == kModeResolve ? launch_h<H, kModeResolve, false>(wimg, p, s, grid)
+                              : launch_h<H, kModeFrame, false>(wimg, p, s, grid);
 }
 
 }  // namespace

@@ -221,10 +221,19 @@ extern "C" {
 const char* glassnet_last_error(void) { return g_last_error.c_str(); }
 
 int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_model** out) {
+  return glassnet_load_weights_ex(blob, nbytes, precision, GN_POOL_MAX_MEAN, out);
+}
+
+int glassnet_load_weights_ex(const void* blob, size_t nbytes, int precision, int pooling,
+                             gn_model** out) {
   if (!blob || !out) return fail(GN_EINVAL, "blob and out must be non-NULL");
   *out = nullptr;
   if (precision != GN_FP32_PLAIN && precision != GN_BF16_FUSED && precision != GN_FP8_FUSED)
     return fail(GN_EINVAL, "unknown precision %d", precision);
+  if (pooling != GN_POOL_MAX_MEAN && pooling != GN_POOL_SUM)
+    return fail(GN_EINVAL, "unknown pooling %d", pooling);
+  if (pooling == GN_POOL_SUM && precision == GN_FP8_FUSED)
+    return fail(GN_EUNSUPPORTED, "sum pooling is built for GN_FP32_PLAIN and GN_BF16_FUSED");
   if (nbytes < sizeof(gn_blob_header))
     return fail(GN_EFORMAT, "blob of %zu bytes is shorter than its header", nbytes);
   gn_blob_header hd;
@@ -259,6 +268,7 @@ int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_mod
   m->H = wi.H;
   m->Z = wi.Z;
   m->precision = precision;
+  m->pooling = pooling;
   m->wi = wi;
   cudaGetDevice(&m->device);
   cudaError_t e;
@@ -308,6 +318,12 @@ int glassnet_model_info(const gn_model* m, int* hidden, int* latent, int* precis
   if (hidden) *hidden = m->H;
   if (latent) *latent = m->Z;
   if (precision) *precision = m->precision;
+  return GN_OK;
+}
+
+int glassnet_model_pooling(const gn_model* m, int* pooling) {
+  if (!m || !pooling) return fail(GN_EINVAL, "model and pooling must be non-NULL");
+  *pooling = m->pooling;
   return GN_OK;
 }
 
@@ -435,8 +451,13 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
 }
 
 cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s) {
-  return m->precision == GN_FP8_FUSED ? launch_fused_fp8(m->H, m->fused, p, s)
-                                      : launch_fused_bf16(m->H, m->fused, p, s);
+  if (m->precision == GN_FP8_FUSED) return launch_fused_fp8(m->H, m->fused, p, s);
+  if (m->pooling == GN_POOL_SUM) {
+    FusedParams q = p;
+    q.pool_sum = 1;
+    return launch_fused_bf16(m->H, m->fused, q, s);
+  }
+  return launch_fused_bf16(m->H, m->fused, p, s);
 }
 
 cudaError_t prepare_fused(const gn_model* m) {
@@ -465,7 +486,8 @@ int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbu
       return fail(GN_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, need);
     if (reinterpret_cast<uintptr_t>(ws) & 255u)
       return fail(GN_EINVAL, "workspace must be 256-byte aligned");
-    e = gn::launch_plain_fp32(m->w32, m->wi, lat->d, gbuf, tbuf, cnt, K, P, out, ws, m->err, s);
+    e = gn::launch_plain_fp32(m->w32, m->wi, lat->d, gbuf, tbuf, cnt, K, P, out, ws, m->err, s,
+                              m->pooling == GN_POOL_SUM);
     if (e != cudaSuccess) return cuda_fail(e, "FP32 plain launch");
     return GN_OK;
   }
@@ -675,6 +697,7 @@ gn::FusedParams pool_params(const gn_model* m, const gn_latent* lat, const gn_po
   p.f[0] = gn::FusedFrame{gbuf, tbuf, cnt, out, lat->fold(), K, pool->h * pool->w, 0, 0};
   number_tiles(p);
   p.plan_identity = 1;
+  p.pool_sum = m->pooling == GN_POOL_SUM;
   p.pool_st = pool->st;
   p.pool_cnt = pool->cnt;
   gn::bind_plan(p, pool->plan);

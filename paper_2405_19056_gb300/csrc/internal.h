@@ -172,6 +172,9 @@ struct FusedParams {
   uint32_t* pool_st;
   uint8_t* pool_cnt;  // [P] layers accumulated
   int pool_fresh;     // the pool is empty: its state is the start value, not read
+  // Pooling of Eq. 5: 0 = [max ; mean] then rho, 1 = the sum tau fed to B1
+  // directly (frame and resolve launches; accumulation is the same for both).
+  int pool_sum;
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -189,9 +192,12 @@ size_t fused_plan_bytes(long long tiles);
 // tile-plan kernel that the fused kernels read.
 cudaError_t launch_plan(FusedParams& p, cudaStream_t s);
 size_t plain_workspace_bytes(int H, int K, int P);
+// pool_sum: Eq. 5's sum form (tau = sum of the valid layers' phi outputs, no
+// rho) instead of [max ; mean] then rho.
 cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const float* latent,
                               const float* gbuf, const float* tbuf, const uint8_t* counts, int K,
-                              int P, float* out, void* ws, uint32_t* err, cudaStream_t s);
+                              int P, float* out, void* ws, uint32_t* err, cudaStream_t s,
+                              int pool_sum = 0);
 int device_sm_count();
 // FP8 fused path (fused_fp8.cu): plan kernel, then the fused E4M3 kernel.
 cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& p, cudaStream_t s);
@@ -207,6 +213,7 @@ cudaError_t launch_fp8_act_amax(const void* ws, const float* gbuf, const float* 
 
 struct gn_model {
   int H = 0, Z = 0, precision = 0, device = 0;
+  int pooling = GN_POOL_MAX_MEAN;  // gn_pooling
   gn::WeightIndex wi;
   float* w32 = nullptr;     // concat-form f32 weights (device)
   void* fused = nullptr;    // packed operand image (device)

@@ -8,6 +8,7 @@
 //   V = ReLU(W_phi2 U + b)
 //   pool_p = [max_k V ; (sum_k V) / c_p]   FP32 sum in slot order
 //   R = ReLU(W_rho pool + b), R = 0 when c_p = 0
+//   (sum form of Eq. 5: R = sum_k V over the valid layers, no rho)
 //   Y = ReLU(W_B2 ReLU(W_B1 [g ; R ; sigma] + b) + b)
 //   out = sigmoid(W_R2 ReLU(W_R1 Y + b) + b)
 #include "internal.h"
@@ -132,9 +133,10 @@ __global__ void __launch_bounds__(256) linear_kernel(In in, const float* __restr
   }
 }
 
-// pool[p] = [max_k V ; (sum_k V) / c_p] over k < c_p (zeros when c_p = 0).
+// pool[p] = [max_k V ; (sum_k V) / c_p] over k < c_p (zeros when c_p = 0), or
+// with `tau` set, R[p] = sum_k V (Eq. 5's sum form, zero when c_p = 0).
 __global__ void pool_kernel(const float* __restrict__ V, const uint8_t* __restrict__ counts,
-                            float* pool, int P, int K, int H, uint32_t* err) {
+                            float* pool, float* tau, int P, int K, int H, uint32_t* err) {
   const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<size_t>(P) * H) return;
   const int p = static_cast<int>(i / H), n = static_cast<int>(i % H);
@@ -148,6 +150,10 @@ __global__ void pool_kernel(const float* __restrict__ V, const uint8_t* __restri
     const float v = V[(static_cast<size_t>(k) * P + p) * H + n];
     mx = fmaxf(mx, v);
     s += v;
+  }
+  if (tau) {
+    tau[static_cast<size_t>(p) * H + n] = s;
+    return;
   }
   pool[static_cast<size_t>(p) * 2 * H + n] = mx;
   pool[static_cast<size_t>(p) * 2 * H + H + n] = c > 0 ? s / static_cast<float>(c) : 0.0f;
@@ -205,7 +211,8 @@ size_t plain_workspace_bytes(int H, int K, int P) {
 
 cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const float* latent,
                               const float* gbuf, const float* tbuf, const uint8_t* counts, int K,
-                              int P, float* out, void* ws, uint32_t* err, cudaStream_t s) {
+                              int P, float* out, void* ws, uint32_t* err, cudaStream_t s,
+                              int pool_sum) {
   const int H = wi.H, Z = wi.Z;
   const size_t rows = static_cast<size_t>(K) * P;
   float* U = static_cast<float*>(ws);
@@ -227,10 +234,11 @@ cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const flo
                                   static_cast<int>(rows), H, H, s);
     if (e != cudaSuccess) return e;
     const size_t n = static_cast<size_t>(P) * H;
-    pool_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(V, counts, pool, P, K, H,
-                                                                       err);
+    pool_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+        V, counts, pool, pool_sum ? R : nullptr, P, K, H, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = run_linear<RhoIn, false>(RhoIn{pool, counts, 2 * H}, W(LRHO), B(LRHO), R, P, H, 2 * H, s);
+    if (!pool_sum)
+      e = run_linear<RhoIn, false>(RhoIn{pool, counts, 2 * H}, W(LRHO), B(LRHO), R, P, H, 2 * H, s);
   } else {
     e = cudaMemsetAsync(R, 0, static_cast<size_t>(P) * H * sizeof(float), s);
   }

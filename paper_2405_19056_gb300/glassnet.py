@@ -27,6 +27,8 @@ GN_ERANGE = -7
 GN_FP32_PLAIN = 0
 GN_BF16_FUSED = 1
 GN_FP8_FUSED = 2
+GN_POOL_MAX_MEAN = 0
+GN_POOL_SUM = 1
 
 BLOB_MAGIC = 0x544E4C47
 BLOB_VERSION = 1
@@ -39,6 +41,8 @@ _I = ctypes.c_int
 _SIGNATURES = {
     "glassnet_load_weights": (_I, [_P, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     "glassnet_model_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "glassnet_load_weights_ex": (_I, [_P, ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
+    "glassnet_model_pooling": (_I, [_P, ctypes.POINTER(_I)]),
     "glassnet_encode_scene": (_I, [_P, _P, ctypes.POINTER(_P), _P]),
     "glassnet_encode_scene_device": (_I, [_P, _P, _P, _P]),
     "glassnet_latent_read": (_I, [_P, _P, _P, _P, _P]),
@@ -154,10 +158,23 @@ def glassnet_load_weights(blob: bytes, precision: int) -> int:
     return out.value
 
 
+def glassnet_load_weights_ex(blob: bytes, precision: int, pooling: int) -> int:
+    out = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(_lib().glassnet_load_weights_ex(buf, len(blob), precision, pooling, ctypes.byref(out)))
+    return out.value
+
+
 def glassnet_model_info(model: int):
     h, z, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(_lib().glassnet_model_info(model, ctypes.byref(h), ctypes.byref(z), ctypes.byref(p)))
     return h.value, z.value, p.value
+
+
+def glassnet_model_pooling(model: int) -> int:
+    v = ctypes.c_int()
+    _check(_lib().glassnet_model_pooling(model, ctypes.byref(v)))
+    return v.value
 
 
 def glassnet_encode_scene(model: int, scene, stream=None) -> int:
@@ -370,10 +387,12 @@ def glassnet_last_error() -> str:
 class Model:
     """Owns a gn_model handle."""
 
-    def __init__(self, weights_or_blob, precision: int = GN_BF16_FUSED):
+    def __init__(self, weights_or_blob, precision: int = GN_BF16_FUSED,
+                 pooling: int = GN_POOL_MAX_MEAN):
         blob = weights_or_blob if isinstance(weights_or_blob, (bytes, bytearray)) else pack_blob(weights_or_blob)
-        self.handle = glassnet_load_weights(bytes(blob), precision)
+        self.handle = glassnet_load_weights_ex(bytes(blob), precision, pooling)
         self.hidden, self.latent_width, self.precision = glassnet_model_info(self.handle)
+        self.pooling = glassnet_model_pooling(self.handle)
 
     def encode(self, scene, stream=None) -> "Latent":
         return Latent(glassnet_encode_scene(self.handle, scene, stream))

@@ -96,6 +96,21 @@ def test_unknown_precision_rejected(lib):
     assert rc == gl.GN_EINVAL
 
 
+def test_pooling_arguments_checked_before_any_device_work(lib):
+    """Unknown pooling -> EINVAL; the sum form with FP8 -> EUNSUPPORTED; both
+    rejected on the host, before the blob reaches the device."""
+    blob = _blob()
+    out = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    assert lib.glassnet_load_weights_ex(buf, len(blob), gl.GN_BF16_FUSED, 2, ctypes.byref(out)) == gl.GN_EINVAL
+    assert lib.glassnet_load_weights_ex(buf, len(blob), gl.GN_FP8_FUSED, gl.GN_POOL_SUM,
+                                        ctypes.byref(out)) == gl.GN_EUNSUPPORTED
+    assert "sum pooling" in gl.glassnet_last_error()
+    assert not out.value
+    assert lib.glassnet_load_weights_ex(None, 10, 1, 1, ctypes.byref(out)) == gl.GN_EINVAL
+    assert lib.glassnet_model_pooling(None, None) == gl.GN_EINVAL
+
+
 def test_null_arguments_rejected(lib):
     out = ctypes.c_void_p()
     assert lib.glassnet_load_weights(None, 10, 1, ctypes.byref(out)) == gl.GN_EINVAL
