@@ -34,6 +34,17 @@ METRIC = "Mpixel/s at 512x512 K=8 (BF16 fused)"
 UNIT = "Mpixel/s"
 WORKLOAD = "512x512 frame, K=8 slots, counts min(Poisson(3),8), H=128 Z=256"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "fused_bf16_512x512_K8.traffic.json")
+PROFILE_TRAFFIC_SUM = os.path.join(ROOT, "profiles", "fused_bf16_sum_512x512_K8.traffic.json")
+
+
+def profiled_traffic(path: str):
+    """DRAM bytes per launch from an ncu capture, if it was taken of the
+    kernel sources as they are now (else None: the counters are stale)."""
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        prof = json.load(f)
+    return prof.get("dram_bytes_per_launch") if prof.get("kernel_sha256") == kernel_digest() else None
 
 
 def parse():
@@ -49,6 +60,9 @@ def parse():
                          "(default: 200 and 800 req/s, 300 requests each)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8"],
                     help="precision of the timed fused leg (fp8: calibrated on a seed-1 frame)")
+    ap.add_argument("--pooling", default="max_mean", choices=["max_mean", "sum"],
+                    help="pooling of Eq. 5 in the timed BF16 leg: [max ; mean] then rho, or the "
+                         "paper's sum form (tau straight into B)")
     return ap.parse_args()
 
 
@@ -250,7 +264,11 @@ def run_fused(args, world, rank, local):
     gl.load_library()
     weights = synth.make_weights(synth.DOUBLED_WIDTHS, seed=0)
     fp8 = args.precision == "fp8"
-    model = gl.Model(weights, gl.GN_FP8_FUSED if fp8 else gl.GN_BF16_FUSED)
+    pool_sum = args.pooling == "sum"
+    if fp8 and pool_sum:
+        raise SystemExit("the sum pooling form is built for BF16 only")
+    model = gl.Model(weights, gl.GN_FP8_FUSED if fp8 else gl.GN_BF16_FUSED,
+                     gl.GN_POOL_SUM if pool_sum else gl.GN_POOL_MAX_MEAN)
     scene = synth.make_scene(0)
     stream = torch.cuda.Stream(device=dev)
 
@@ -262,7 +280,7 @@ def run_fused(args, world, rank, local):
                             tbuf=torch.from_numpy(f.tbuf).to(dev),
                             counts=torch.from_numpy(f.counts).to(dev),
                             out=torch.empty((3, H_IMG, W_IMG), device=dev)))
-    flops = [algorithmic_flops(128, f.counts) for f in frames]
+    flops = [algorithmic_flops(128, f.counts, args.pooling) for f in frames]
     P = H_IMG * W_IMG
 
     with torch.cuda.stream(stream):
@@ -310,14 +328,12 @@ def run_fused(args, world, rank, local):
     if fp8:
         peak_tf *= 2
     achieved_tf = step_flops / (avg_kernel_ms * 1e-3) / 1e12
-    traffic = None
-    if os.path.exists(PROFILE_TRAFFIC):
-        with open(PROFILE_TRAFFIC) as f:
-            prof = json.load(f)
-        if not fp8 and prof.get("kernel_sha256") == kernel_digest():
-            traffic = prof.get("dram_bytes_per_launch")
+    traffic = None if fp8 else profiled_traffic(PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC)
+    metric = METRIC.replace("BF16", "FP8") if fp8 else METRIC
+    if pool_sum:
+        metric = metric.replace("BF16 fused", "BF16 fused, sum pooling")
     result = {
-        "metric": METRIC.replace("BF16", "FP8") if fp8 else METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if fp8 else "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_rotated": N_ROTATE,
@@ -329,7 +345,8 @@ def run_fused(args, world, rank, local):
         "gpu_launches": 2 * args.steps,  # per step: tile-plan kernel + fused kernel
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
-                     "kernel": "fused_fp8_kernel<128>" if fp8 else "fused_bf16_kernel<128>",
+                     "kernel": "fused_fp8_kernel<128>" if fp8 else
+                               f"fused_bf16_kernel<128, frame, sum={int(pool_sum)}>",
                      "duration": "CUDA events around the render call (plan kernel + fused kernel)",
                      "flops_per_launch": step_flops,
                      "peak_source": (f"{peak_src} bf16 burst (MEASURED_PEAKS.json) x 2 (nominal "
@@ -454,6 +471,8 @@ def sum_pooling_leg(weights, scene, dframes, frames, stream, steps=200):
             "steps": steps, "dtype": "bf16 operands, fp32 accumulate", "pooling": "sum (Eq. 5)",
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16,
                          "unit": "TFLOP/s", "frac": achieved / peak_bf16,
+                         "traffic": profiled_traffic(PROFILE_TRAFFIC_SUM),
+                         "kernel": "fused_bf16_kernel<128, frame, sum=1>",
                          "peak_source": "measured bf16 burst"}}
 
 
