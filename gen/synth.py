@@ -40,14 +40,19 @@ OUT_CHANNELS = 3
 
 @dataclass(frozen=True)
 class Widths:
-    """Hidden width H and latent width Z of the per-pixel network."""
+    """Hidden width H and latent width Z of the per-pixel network, and the
+    frequency count L of the inputs' positional encoding (0: none), which
+    widens every input block of n channels to n (1 + 2L)."""
 
     hidden: int
     latent: int
+    pe_freqs: int = 0
 
 
 BASE_WIDTHS = Widths(hidden=64, latent=128)
 DOUBLED_WIDTHS = Widths(hidden=128, latent=256)
+# Base widths with every input positionally encoded at 4 frequencies.
+BASE_PE_WIDTHS = Widths(hidden=64, latent=128, pe_freqs=4)
 
 # Linear layers in draw order: name, and (out, in) as a function of (H, Z).
 WEIGHT_ORDER = ("F1", "F2", "phi1", "phi2", "rho", "B1", "B2", "R1", "R2")
@@ -56,13 +61,14 @@ WEIGHT_ORDER = ("F1", "F2", "phi1", "phi2", "rho", "B1", "B2", "R1", "R2")
 def weight_shapes(widths: Widths) -> dict[str, tuple[int, int]]:
     """(out, in) of every linear layer, concat form (no folding)."""
     H, Z = widths.hidden, widths.latent
+    e = 1 + 2 * widths.pe_freqs
     return {
-        "F1": (Z, SCENE_DIM),
+        "F1": (Z, SCENE_DIM * e),
         "F2": (Z, Z),
-        "phi1": (H, TBUF_CHANNELS + Z),
+        "phi1": (H, TBUF_CHANNELS * e + Z),
         "phi2": (H, H),
         "rho": (H, 2 * H),
-        "B1": (H, GBUF_CHANNELS + H + Z),
+        "B1": (H, GBUF_CHANNELS * e + H + Z),
         "B2": (H, H),
         "R1": (H, H),
         "R2": (OUT_CHANNELS, H),
@@ -75,7 +81,8 @@ def make_weights(widths: Widths, seed: int = 0, bias: str = "zero") -> dict:
     Draw order: one ``default_rng(seed)``; every W in ``WEIGHT_ORDER`` as a
     standard normal scaled by its std; then, if ``bias == "uniform"``, every b
     in the same order from U[-0.1, 0.1].  ``bias == "zero"`` gives zero biases.
-    Values are drawn in float64 and stored as float32.
+    Values are drawn in float64 and stored as float32.  With positional
+    encoding the dict also holds ``"pe_freqs": L``.
     """
     if bias not in ("zero", "uniform"):
         raise ValueError(f"bias must be 'zero' or 'uniform', got {bias!r}")
@@ -93,7 +100,10 @@ def make_weights(widths: Widths, seed: int = 0, bias: str = "zero") -> dict:
         else:
             b = np.zeros(fo)
         out[name][1] = b.astype(np.float32)
-    return {k: (v[0], v[1]) for k, v in out.items()}
+    res = {k: (v[0], v[1]) for k, v in out.items()}
+    if widths.pe_freqs:
+        res["pe_freqs"] = widths.pe_freqs
+    return res
 
 
 def make_scene(seed: int = 0) -> np.ndarray:

@@ -8,13 +8,17 @@ from .glassnet_oracle import (  # noqa: F401
     linear,
     relu,
     sigmoid,
+    pe_freqs,
+    positional_encoding,
     scene_encoder,
     per_layer_h,
     set_pool,
+    set_sum,
     post_pool_rho,
     final_blend_B,
     render_R,
     render_pixel,
+    render_pixel_sum,
     render_frame,
     render_opaque_only,
     alpha_blend,

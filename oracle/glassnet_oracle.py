@@ -21,6 +21,14 @@ set gives r = 0; input concat orders are [b ; sigma] and [g ; r ; sigma];
 pool order is [max ; mean].  The paper's own form of Eq. 5 is also given
 (``pooling="sum"``): tau = sum_k h(b_k, sigma) enters B directly, no rho.
 
+Positional encoding (Sec. 3.4: all inputs are encoded with the method of
+Mildenhall et al.; the frequency count is not given): a weight set with
+``weights["pe_freqs"] = L > 0`` feeds every network input x -- the scene
+vector s, each layer b_k and the G-buffer g -- as
+gamma_L(x) = [x ; sin(2^0 pi x) ; cos(2^0 pi x) ; ... ; sin(2^(L-1) pi x) ;
+cos(2^(L-1) pi x)], each block over all channels of x.  L = 0 (or no key)
+is the network above unchanged.
+
 Every function below is pinned by ``tests/test_oracle_pins.py`` (hand-worked
 closed forms, brute force, invariants and library routines).
 """
@@ -49,9 +57,29 @@ def sigmoid(x) -> np.ndarray:
         return 1.0 / (1.0 + np.exp(-x))
 
 
+def pe_freqs(weights) -> int:
+    """Frequency count L of the weight set's positional encoding (0: none)."""
+    return int(weights.get("pe_freqs", 0))
+
+
+def positional_encoding(x, L: int) -> np.ndarray:
+    """gamma_L(x) on the last axis (Sec. 3.4, after Mildenhall et al.):
+    x itself, then for f = 0 .. L-1 the blocks sin(2^f pi x) and cos(2^f pi x).
+    Width n (1 + 2L) for n channels; L = 0 returns x.
+    """
+    x = _f64(x)
+    parts = [x]
+    for f in range(L):
+        a = (np.pi * 2.0 ** f) * x
+        parts.append(np.sin(a))
+        parts.append(np.cos(a))
+    return np.concatenate(parts, axis=-1)
+
+
 def scene_encoder(weights, s) -> np.ndarray:
-    """Scene encoder F (Sec. 3.4): sigma = ReLU(F2 ReLU(F1 s + b1) + b2)."""
-    h1 = relu(linear(s, *weights["F1"]))
+    """Scene encoder F (Sec. 3.4): sigma = ReLU(F2 ReLU(F1 s + b1) + b2),
+    on the encoded scene vector gamma_L(s)."""
+    h1 = relu(linear(positional_encoding(s, pe_freqs(weights)), *weights["F1"]))
     return relu(linear(h1, *weights["F2"]))
 
 
@@ -59,9 +87,10 @@ def per_layer_h(weights, b_k, sigma) -> np.ndarray:
     """Shared per-layer network h(b_i, sigma) of Eq. 5.
 
     ``b_k`` is [..., n_t] (one transparency layer per row); sigma is
-    broadcast to every row and appended after the layer's channels.
+    broadcast to every row and appended after the layer's encoded channels
+    gamma_L(b_k).
     """
-    b_k = _f64(b_k)
+    b_k = positional_encoding(b_k, pe_freqs(weights))
     sig = np.broadcast_to(_f64(sigma), b_k.shape[:-1] + (np.shape(sigma)[-1],))
     x = np.concatenate([b_k, sig], axis=-1)
     u = relu(linear(x, *weights["phi1"]))
@@ -108,8 +137,8 @@ def post_pool_rho(weights, pool) -> np.ndarray:
 
 
 def final_blend_B(weights, g, r, sigma) -> np.ndarray:
-    """Final blending network B (Sec. 3.4) on [g ; r ; sigma]."""
-    g, r = _f64(g), _f64(r)
+    """Final blending network B (Sec. 3.4) on [gamma_L(g) ; r ; sigma]."""
+    g, r = positional_encoding(g, pe_freqs(weights)), _f64(r)
     sig = np.broadcast_to(_f64(sigma), g.shape[:-1] + (np.shape(sigma)[-1],))
     x = np.concatenate([g, r, sig], axis=-1)
     y = relu(linear(x, *weights["B1"]))
@@ -122,9 +151,15 @@ def render_R(weights, y) -> np.ndarray:
     return sigmoid(linear(q, *weights["R2"]))
 
 
+def _layer_width(weights, sigma) -> int:
+    """Channels n_t of a raw transparency layer: phi1 reads n_t (1 + 2L) + Z."""
+    enc = np.shape(weights["phi1"][0])[1] - np.shape(sigma)[-1]
+    return enc // (1 + 2 * pe_freqs(weights))
+
+
 def render_pixel(weights, sigma, g, layers) -> np.ndarray:
     """One pixel: ``g`` [n_g] opaque G-buffer, ``layers`` [c][n_t] valid layers."""
-    layers = _f64(layers).reshape(-1, np.shape(weights["phi1"][0])[1] - np.shape(sigma)[-1])
+    layers = _f64(layers).reshape(-1, _layer_width(weights, sigma))
     H = np.shape(weights["phi2"][0])[0]
     if layers.shape[0] == 0:
         r = np.zeros(H)
@@ -138,7 +173,7 @@ def render_pixel(weights, sigma, g, layers) -> np.ndarray:
 def render_pixel_sum(weights, sigma, g, layers) -> np.ndarray:
     """One pixel in the paper's form of Eq. 5: tau = sum_k h(b_k, sigma) enters
     B directly as [g ; tau ; sigma] (no rho; rho's weights are not used)."""
-    layers = _f64(layers).reshape(-1, np.shape(weights["phi1"][0])[1] - np.shape(sigma)[-1])
+    layers = _f64(layers).reshape(-1, _layer_width(weights, sigma))
     H = np.shape(weights["phi2"][0])[0]
     V = np.stack([per_layer_h(weights, layers[k], sigma) for k in range(layers.shape[0])]) \
         if layers.shape[0] else np.zeros((0, H))
@@ -154,10 +189,11 @@ def render_opaque_only(weights, sigma, gbuf_rows) -> np.ndarray:
     """
     W1, b1 = weights["B1"]
     W1 = _f64(W1)
-    n_g = np.shape(gbuf_rows)[-1]
+    G = positional_encoding(gbuf_rows, pe_freqs(weights))
+    n_g = G.shape[-1]
     Z = np.shape(sigma)[-1]
     keep = np.r_[0:n_g, W1.shape[1] - Z:W1.shape[1]]
-    x = np.concatenate([_f64(gbuf_rows),
+    x = np.concatenate([G,
                         np.broadcast_to(_f64(sigma), np.shape(gbuf_rows)[:-1] + (Z,))], axis=-1)
     y = relu(x @ W1[:, keep].T + _f64(b1))
     y = relu(linear(y, *weights["B2"]))

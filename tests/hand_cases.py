@@ -66,3 +66,48 @@ POOL_TWO_LAYERS = np.array([5.0, 2.0, 5.0, 1.0])
 TAU_TWO_LAYERS = np.array([10.0, 2.0])
 LOGITS_SUM_ONE_LAYER = np.array([13.0, 0.0, -12.0])
 LOGITS_SUM_TWO_LAYERS = np.array([21.0, 0.0, -20.0])
+
+# Positional encoding with L = 1: every input x of n channels enters as
+# [x ; sin(pi x) ; cos(pi x)] (3n columns, blocks in that order).  Inputs are
+# multiples of 1/2, so every sine and cosine is 0 or +-1 (to within 2^-52).
+#   scene s = [1/2, 1]  -> [0.5, 1, 1, 0, 0, -1]
+#   F1 rows [2, 0, 1, 0, 0, 0] and [0, 1, 0, 0, 0, -1], bias [0, 1]:
+#     [1 + 1, 1 + 1 + 1] = [2, 3];  F2 [[1, -1], [0, 1]] + [2, -1]: sigma = [1, 2]
+#   layer A = [1/2, 0]  -> [0.5, 0, 1, 0, 0, 1]
+#   layer B = [1, 1/2]  -> [1, 0.5, 0, 1, -1, 0]
+#   phi1 on [gamma(t) ; z0 ; z1], rows [2, 0, 3, 0, 0, 0, 1, 0], [0, 2, 0, 1, 0, -1, 0, 1]:
+#     A: [1 + 3 + 1, -1 + 2] = [5, 1];  B: [2 + 0 + 1, 1 + 1 + 2] = [3, 4]
+#   phi2 (as W): A [5 + 1 + 1, -5 + 2] -> v_A = [7, 0];  B [3 + 4 + 1, -3 + 8] -> v_B = [8, 5]
+#   rho (as W): one layer pool [7, 0, 7, 0] -> [7, 8]
+#               two layers max [8, 5], mean [7.5, 2.5] -> [8 - 2.5, 5 + 7.5 + 1] = [5.5, 13.5]
+#   g = [1/2, -1] -> [0.5, -1, 1, 0, 0, -1]
+#   B1 on [gamma(g) ; r ; z], rows [2, 0, 1, 0, 0, 0, 1, 0, 0, 1], [0, 1, 0, 0, 0, -2, 0, 1, 1, 0]:
+#     row 0 = 1 + 1 + r0 + 2 = 4 + r0, row 1 = -1 + 2 + r1 + 1 = 2 + r1
+#     one layer [11, 10];  two layers [9.5, 15.5];  no layer [4, 2]
+#   B2 [[1, -1], [0, 1]]: [1, 10];  [-6 -> 0, 15.5];  [2, 2]
+#   R1 [[1, 0], [-1, 1]] + [0, 1]: [1, 10];  [0, 16.5];  [2, 1]
+#   R2 (as W): [-9, 10, 0];  [-16.5, 16.5, 1];  [1, 1, -1]
+#   sum pooling: tau one layer [7, 0] -> B1 [11, 2] -> B2 [9, 2] -> R1 [9, 0] -> R2 [9, 0, -8]
+#                tau two layers [15, 5] -> B1 [19, 7] -> B2 [12, 7] -> R1 [12, 0] -> R2 [12, 0, -11]
+W_PE = dict(W)
+W_PE.update({
+    "F1": (np.array([[2, 0, 1, 0, 0, 0], [0, 1, 0, 0, 0, -1]], np.float32), np.array([0, 1], np.float32)),
+    "F2": (np.array([[1, -1], [0, 1]], np.float32), np.array([2, -1], np.float32)),
+    "phi1": (np.array([[2, 0, 3, 0, 0, 0, 1, 0], [0, 2, 0, 1, 0, -1, 0, 1]], np.float32),
+             np.array([0, 0], np.float32)),
+    "B1": (np.array([[2, 0, 1, 0, 0, 0, 1, 0, 0, 1], [0, 1, 0, 0, 0, -2, 0, 1, 1, 0]], np.float32),
+           np.array([0, 0], np.float32)),
+    "B2": (np.array([[1, -1], [0, 1]], np.float32), np.array([0, 0], np.float32)),
+    "R1": (np.array([[1, 0], [-1, 1]], np.float32), np.array([0, 1], np.float32)),
+    "pe_freqs": 1,
+})
+SCENE_PE = np.array([0.5, 1.0], np.float32)
+SIGMA_PE = np.array([1.0, 2.0])
+G_PE = np.array([0.5, -1.0], np.float32)
+LAYER_PA = np.array([0.5, 0.0], np.float32)
+LAYER_PB = np.array([1.0, 0.5], np.float32)
+LOGITS_PE_ONE_LAYER = np.array([-9.0, 10.0, 0.0])
+LOGITS_PE_TWO_LAYERS = np.array([-16.5, 16.5, 1.0])
+LOGITS_PE_NO_LAYER = np.array([1.0, 1.0, -1.0])
+LOGITS_PE_SUM_ONE_LAYER = np.array([9.0, 0.0, -8.0])
+LOGITS_PE_SUM_TWO_LAYERS = np.array([12.0, 0.0, -11.0])

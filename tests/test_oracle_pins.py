@@ -439,6 +439,159 @@ def test_planted_sum_mistake_is_caught(monkeypatch, label):
     assert not _sum_pins_pass(O), label
 
 
+# ------------------------------------------ positional encoding (Sec. 3.4)
+
+def test_pe_of_zero_frequencies_is_the_input():
+    x = np.random.default_rng(0).standard_normal((5, 3))
+    np.testing.assert_array_equal(O.positional_encoding(x, 0), x)
+
+
+def test_pe_known_values_and_block_layout():
+    """Blocks [x ; sin(pi x) ; cos(pi x) ; sin(2 pi x) ; cos(2 pi x) ; ...],
+    each over all channels; values at x = 0, 1/6, 1/2 fixed by trigonometry."""
+    x = np.array([0.0, 1 / 6, 0.5])
+    e = O.positional_encoding(x, 3)
+    assert e.shape == (3 * 7,)
+    r3 = np.sqrt(3) / 2
+    want = np.array([0, 1 / 6, 0.5,        # x
+                     0, 0.5, 1,            # sin(pi x)
+                     1, r3, 0,             # cos(pi x)
+                     0, r3, 0,             # sin(2 pi x)
+                     1, 0.5, -1,           # cos(2 pi x)
+                     0, r3, 0,             # sin(4 pi x) = sin(2 pi / 3)
+                     1, -0.5, 1])          # cos(4 pi x)
+    np.testing.assert_allclose(e, want, atol=1e-15)
+
+
+def test_pe_blocks_obey_pythagoras_and_double_angle():
+    x = np.random.default_rng(1).uniform(-3, 3, 7)
+    e = O.positional_encoding(x, 5).reshape(11, 7)
+    sn, cs = e[1::2], e[2::2]
+    np.testing.assert_allclose(sn ** 2 + cs ** 2, 1.0, atol=1e-14)
+    np.testing.assert_allclose(sn[1:], 2 * sn[:-1] * cs[:-1], atol=1e-12)
+    np.testing.assert_allclose(cs[1:], 1 - 2 * sn[:-1] ** 2, atol=1e-12)
+
+
+@pytest.mark.parametrize("layers,logits,sum_logits", [
+    ([hc.LAYER_PA], hc.LOGITS_PE_ONE_LAYER, hc.LOGITS_PE_SUM_ONE_LAYER),
+    ([hc.LAYER_PA, hc.LAYER_PB], hc.LOGITS_PE_TWO_LAYERS, hc.LOGITS_PE_SUM_TWO_LAYERS),
+    ([hc.LAYER_PB, hc.LAYER_PA], hc.LOGITS_PE_TWO_LAYERS, hc.LOGITS_PE_SUM_TWO_LAYERS),
+    ([], hc.LOGITS_PE_NO_LAYER, hc.LOGITS_PE_NO_LAYER),
+])
+def test_hand_pe_network(layers, logits, sum_logits):
+    sigma = O.scene_encoder(hc.W_PE, hc.SCENE_PE)
+    np.testing.assert_allclose(sigma, hc.SIGMA_PE, atol=1e-14)
+    L = np.array(layers, np.float32).reshape(len(layers), 2)
+    np.testing.assert_allclose(O.render_pixel(hc.W_PE, sigma, hc.G_PE, L), expit(logits), rtol=1e-12)
+    np.testing.assert_allclose(O.render_pixel_sum(hc.W_PE, sigma, hc.G_PE, L), expit(sum_logits),
+                               rtol=1e-12)
+
+
+def test_hand_pe_frame_and_opaque_only():
+    counts = np.array([[1, 2], [0, 2]], np.uint8)
+    gbuf = np.broadcast_to(hc.G_PE[:, None, None], (2, 2, 2)).copy()
+    tbuf = np.full((2, 2, 2, 2), np.nan, np.float32)
+    tbuf[0, :, 0, 0] = hc.LAYER_PA
+    tbuf[0, :, 0, 1] = hc.LAYER_PA
+    tbuf[1, :, 0, 1] = hc.LAYER_PB
+    tbuf[0, :, 1, 1] = hc.LAYER_PB
+    tbuf[1, :, 1, 1] = hc.LAYER_PA
+    for pooling, one, two in [("max_mean", hc.LOGITS_PE_ONE_LAYER, hc.LOGITS_PE_TWO_LAYERS),
+                              ("sum", hc.LOGITS_PE_SUM_ONE_LAYER, hc.LOGITS_PE_SUM_TWO_LAYERS)]:
+        rgb = O.render_frame(hc.W_PE, hc.SCENE_PE, gbuf, tbuf, counts, pooling=pooling)
+        np.testing.assert_allclose(rgb[:, 0, 0], expit(one), rtol=1e-12)
+        np.testing.assert_allclose(rgb[:, 0, 1], expit(two), rtol=1e-12)
+        np.testing.assert_allclose(rgb[:, 1, 0], expit(hc.LOGITS_PE_NO_LAYER), rtol=1e-12)
+        np.testing.assert_allclose(rgb[:, 1, 1], expit(two), rtol=1e-12)
+    sigma = O.scene_encoder(hc.W_PE, hc.SCENE_PE)
+    np.testing.assert_allclose(O.render_opaque_only(hc.W_PE, sigma, hc.G_PE[None, :])[0],
+                               expit(hc.LOGITS_PE_NO_LAYER), rtol=1e-12)
+
+
+def test_pe_network_with_zero_encoding_columns_is_the_plain_network():
+    """Embed a plain weight set into L = 2 shapes with zeros in every sin / cos
+    column: the raw block comes first in each input, so the outputs agree."""
+    L = 2
+    plain = synth.make_weights(synth.Widths(hidden=8, latent=6), seed=7, bias="uniform")
+    pe = dict(plain)
+    for name, n_raw in (("F1", synth.SCENE_DIM), ("phi1", 12), ("B1", 14)):
+        W, b = plain[name]
+        Wz = np.zeros((W.shape[0], W.shape[1] + 2 * L * n_raw), np.float32)
+        Wz[:, :n_raw] = W[:, :n_raw]
+        Wz[:, n_raw * (1 + 2 * L):] = W[:, n_raw:]
+        pe[name] = (Wz, b)
+    pe["pe_freqs"] = L
+    scene = synth.make_scene(3)
+    f = synth.make_frame(4, 5, 3, counts="uniform", seed=8)
+    for pooling in ("max_mean", "sum"):
+        np.testing.assert_allclose(O.render_frame(pe, scene, f.gbuf, f.tbuf, f.counts, pooling=pooling),
+                                   O.render_frame(plain, scene, f.gbuf, f.tbuf, f.counts, pooling=pooling),
+                                   rtol=1e-13, atol=1e-15)
+
+
+def test_pe_frame_matches_per_pixel_definition():
+    w = synth.make_weights(synth.Widths(hidden=8, latent=6, pe_freqs=3), seed=4, bias="uniform")
+    scene = synth.make_scene(1)
+    f = synth.make_frame(4, 3, 4, counts="uniform", seed=6)
+    rgb = O.render_frame(w, scene, f.gbuf, f.tbuf, f.counts)
+    sigma = O.scene_encoder(w, scene)
+    for y in range(4):
+        for x in range(3):
+            c = int(f.counts[y, x])
+            exp = O.render_pixel(w, sigma, f.gbuf[:, y, x], f.tbuf[:c, :, y, x])
+            np.testing.assert_allclose(rgb[:, y, x], exp, rtol=1e-13, atol=1e-15)
+
+
+def _pe_pins_pass(mod):
+    try:
+        sigma = mod.scene_encoder(hc.W_PE, hc.SCENE_PE)
+        for layers, logits in [([hc.LAYER_PA], hc.LOGITS_PE_ONE_LAYER),
+                               ([hc.LAYER_PA, hc.LAYER_PB], hc.LOGITS_PE_TWO_LAYERS),
+                               ([], hc.LOGITS_PE_NO_LAYER)]:
+            L = np.array(layers, np.float32).reshape(len(layers), 2)
+            if not np.allclose(mod.render_pixel(hc.W_PE, sigma, hc.G_PE, L), expit(logits),
+                               rtol=1e-12, atol=0):
+                return False
+        return True
+    except Exception:
+        return False
+
+
+def _pe_interleaved(x, L):
+    x = np.float64(x)
+    cols = []
+    for c in range(x.shape[-1]):
+        cols.append(x[..., c:c + 1])
+        for f in range(L):
+            cols += [np.sin(np.pi * 2.0 ** f * x[..., c:c + 1]), np.cos(np.pi * 2.0 ** f * x[..., c:c + 1])]
+    return np.concatenate(cols, axis=-1)
+
+
+PE_MUTATIONS = {
+    "sin and cos swapped": lambda x, L: (lambda e: np.concatenate(
+        [e[..., :x.shape[-1]]] + [e[..., (2 * f + 2 - j) * x.shape[-1]:(2 * f + 3 - j) * x.shape[-1]]
+                                  for f in range(L) for j in (0, 1)], axis=-1))(_ORIG_PE(x, L)),
+    "no pi": lambda x, L: np.concatenate([np.float64(x)] + [fn(2.0 ** f * np.float64(x)) for f in range(L)
+                                                            for fn in (np.sin, np.cos)], axis=-1),
+    "frequencies from 2^1": lambda x, L: np.concatenate(
+        [np.float64(x)] + [fn(np.pi * 2.0 ** (f + 1) * np.float64(x)) for f in range(L)
+                           for fn in (np.sin, np.cos)], axis=-1),
+    "interleaved per channel": _pe_interleaved,
+    "raw input dropped": lambda x, L: _ORIG_PE(x, L)[..., x.shape[-1]:] if L else _ORIG_PE(x, L),
+}
+_ORIG_PE = O.positional_encoding
+
+
+def test_unmutated_oracle_passes_pe_pins():
+    assert _pe_pins_pass(O)
+
+
+@pytest.mark.parametrize("label", sorted(PE_MUTATIONS))
+def test_planted_pe_mistake_is_caught(monkeypatch, label):
+    monkeypatch.setattr(O, "positional_encoding", PE_MUTATIONS[label])
+    assert not _pe_pins_pass(O), label
+
+
 def test_mean_instead_of_sum_is_caught():
     """A tau that divides by the count (the mean) fails the two-layer hand pin."""
     sigma = O.scene_encoder(hc.W, hc.SCENE)
