@@ -66,15 +66,16 @@ def parse():
     return ap.parse_args()
 
 
-def algorithmic_flops(H: int, counts: np.ndarray, pooling: str = "max_mean") -> float:
+def algorithmic_flops(H: int, counts: np.ndarray, pooling: str = "max_mean", pe: int = 0) -> float:
     """FLOPs of the folded network on the valid layers only.
 
-    Per valid (pixel, layer): phi1 12*H (latent folded) + phi2 H*H MACs.
-    Per pixel: rho 2H*H + B1 (14+H)*H (latent folded) + B2 H*H + R1 H*H + R2 3H;
-    the sum form of Eq. 5 has no rho.
+    Per valid (pixel, layer): phi1 12e*H (latent folded) + phi2 H*H MACs.
+    Per pixel: rho 2H*H + B1 (14e+H)*H (latent folded) + B2 H*H + R1 H*H + R2 3H;
+    the sum form of Eq. 5 has no rho; e = 1 + 2 pe encoded bands per input.
     """
-    per_layer = 12 * H + H * H
-    per_pixel = (0 if pooling == "sum" else 2 * H * H) + (14 + H) * H + H * H + H * H + 3 * H
+    e = 1 + 2 * pe
+    per_layer = 12 * e * H + H * H
+    per_pixel = (0 if pooling == "sum" else 2 * H * H) + (14 * e + H) * H + H * H + H * H + 3 * H
     return 2.0 * (per_layer * float(counts.sum()) + per_pixel * counts.size)
 
 
@@ -361,6 +362,7 @@ def run_fused(args, world, rank, local):
         result["streaming"] = streaming_leg(model, lat, dframes, stream)
         result["fp8"] = fp8_leg(weights, scene, dframes, flops, stream, dev)
         result["sum_pooling"] = sum_pooling_leg(weights, scene, dframes, frames, stream)
+        result["positional_encoding"] = pe_leg(scene, dframes, frames, stream)
         result["serving"] = (serving_leg(model, (50, 200, 800), 2000) if args.serving_full
                              else serving_leg(model, (200, 800), 300))
     clocks = clk.summary()
@@ -474,6 +476,59 @@ def sum_pooling_leg(weights, scene, dframes, frames, stream, steps=200):
                          "traffic": profiled_traffic(PROFILE_TRAFFIC_SUM),
                          "kernel": "fused_bf16_kernel<128, frame, sum=1>",
                          "peak_source": "measured bf16 burst"}}
+
+
+def _time_renders(m, lat, dframes, stream, steps):
+    import torch
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    def step(i):
+        d = dframes[i % N_ROTATE]
+        gl.glassnet_render(m.handle, lat.handle, d["gbuf"], d["tbuf"], d["counts"], K_SLOTS,
+                           H_IMG, W_IMG, d["out"], stream)
+
+    for i in range(5):
+        step(i)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        step(i)
+    e1.record(stream)
+    stream.synchronize()
+    gl.glassnet_check(m.handle, stream)
+    return e0.elapsed_time(e1) / steps
+
+
+def pe_leg(scene, dframes, frames, stream, L=4, steps=200):
+    """The same frames through the base widths (H=64, Z=128) with every input
+    positionally encoded at L frequencies (Sec. 3.4), BF16 fused; the same
+    widths without encoding are timed beside it."""
+    from gen import synth
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    peak_bf16, _, _ = measured_peaks()
+    out = {"widths": f"H=64 Z=128, pe_freqs={L}", "pooling": "max_mean"}
+    for key, pe in (("pe", L), ("no_pe", 0)):
+        w = synth.make_weights(synth.Widths(64, 128, pe), seed=0)
+        m = gl.Model(w, gl.GN_BF16_FUSED)
+        lat = m.encode(scene, stream)
+        ms = _time_renders(m, lat, dframes, stream, steps)
+        flops = sum(algorithmic_flops(64, frames[i % N_ROTATE].counts, "max_mean", pe)
+                    for i in range(steps)) / steps
+        achieved = flops / (ms * 1e-3) / 1e12
+        leg = {"value": H_IMG * W_IMG / (ms * 1e-3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms,
+               "steps": steps, "gflop_per_step": flops / 1e9,
+               "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16,
+                            "unit": "TFLOP/s", "frac": achieved / peak_bf16,
+                            "kernel": f"fused_bf16_kernel<64, frame, sum=0, pe={int(pe > 0)}>",
+                            "peak_source": "measured bf16 burst"}}
+        if key == "pe":
+            out.update(leg)
+        else:
+            out["no_pe"] = leg
+    return out
 
 
 def serving_leg(model, rates, n_requests, n_streams=4, seed=0):

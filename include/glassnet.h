@@ -117,23 +117,47 @@ typedef struct gn_blob_header {
  */
 int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_model** out);
 
+/* Form of the network a blob is loaded as. */
+typedef struct gn_model_config {
+  int precision; /* gn_precision */
+  int pooling;   /* gn_pooling */
+  /* Positional encoding of the inputs (Sec. 3.4, after Mildenhall et al.):
+   * L = pe_freqs frequency bands, 0 = inputs as given.  Every input of n
+   * channels -- the scene vector, each transparency layer and the G-buffer --
+   * enters its first linear layer as the n (1 + 2L) values
+   *   [x ; sin(2^0 pi x) ; cos(2^0 pi x) ; ... ; sin(2^(L-1) pi x) ; cos(2^(L-1) pi x)]
+   * (blocks of n, in that order), so F1, phi1 and B1 are wider:
+   *   F1 [Z][32 e]   phi1 [H][12 e + Z]   B1 [H][14 e + H + Z],  e = 1 + 2L. */
+  int pe_freqs;
+} gn_model_config;
+
 /*
- * As glassnet_load_weights, with the pooling of Eq. 5 (gn_pooling).
- * glassnet_load_weights is this call with GN_POOL_MAX_MEAN.  A GN_POOL_SUM
- * network has no rho: its blob keeps the rho tensor and bias slots (any
- * values; zeros for a network trained in that form), which are never read.
- * GN_POOL_SUM is built for GN_FP32_PLAIN and GN_BF16_FUSED (every render,
- * batch, graph, server and streaming call of those precisions); with
- * GN_FP8_FUSED it returns GN_EUNSUPPORTED.  The sum uses the same exact
- * fixed-point accumulator as the mean (range [0, 2^11) per pixel-channel,
- * GN_ERANGE beyond it), so the BF16 result is bit-identical under any order
- * of a pixel's layers.  Errors: those of glassnet_load_weights, GN_EINVAL
- * (unknown pooling), GN_EUNSUPPORTED.
+ * As glassnet_load_weights, for the form in `config`;
+ * glassnet_load_weights is this call with {precision, GN_POOL_MAX_MEAN, 0}.
+ * The blob's payload must hold the widths of that form (the header's H and Z
+ * with pe_freqs), else GN_EFORMAT.
+ * Pooling: a GN_POOL_SUM network has no rho; its blob keeps the rho tensor
+ *   and bias slots (any values; zeros for a network trained in that form),
+ *   which are never read.  The sum uses the same exact fixed-point
+ *   accumulator as the mean (range [0, 2^11) per pixel-channel, GN_ERANGE
+ *   beyond it), so the BF16 result is bit-identical under any order of a
+ *   pixel's layers.
+ * Positional encoding: pe_freqs 0..10 for GN_FP32_PLAIN; 0..4 at H = 64 for
+ *   GN_BF16_FUSED (the encoded operands fill the fused kernel's shared
+ *   memory; H = 128 with pe_freqs > 0 is GN_EUNSUPPORTED).  The fused kernel
+ *   computes sin(pi x) and cos(pi x) of each input channel with exact
+ *   argument reduction and the higher bands by the double-angle identities
+ *   in FP32, then rounds every band to BF16.
+ * GN_POOL_SUM and pe_freqs > 0 serve every render, batch, graph, server and
+ * streaming call of GN_FP32_PLAIN / GN_BF16_FUSED models; with GN_FP8_FUSED
+ * they return GN_EUNSUPPORTED.
+ * Errors: those of glassnet_load_weights, GN_EINVAL (NULL config, unknown
+ * pooling, pe_freqs outside 0..10), GN_EUNSUPPORTED.
  */
-int glassnet_load_weights_ex(const void* blob, size_t nbytes, int precision, int pooling,
+int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_config* config,
                              gn_model** out);
-/* The model's gn_pooling.  Errors: GN_EINVAL (NULL argument). */
-int glassnet_model_pooling(const gn_model* model, int* pooling);
+/* The form a model was loaded as.  Errors: GN_EINVAL (NULL argument). */
+int glassnet_model_config(const gn_model* model, gn_model_config* config);
 
 /* Widths and precision of a loaded model (any pointer may be NULL). */
 int glassnet_model_info(const gn_model* model, int* hidden, int* latent, int* precision);

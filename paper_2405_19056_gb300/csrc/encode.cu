@@ -1,20 +1,22 @@
 // Scene encoder F and the per-scene folded biases (once per scene).
 //
-// F (Sec. 3.4): sigma = ReLU(W_F2 ReLU(W_F1 s + b_F1) + b_F2), s = 32 floats.
+// F (Sec. 3.4): sigma = ReLU(W_F2 ReLU(W_F1 s' + b_F1) + b_F2), s = 32 floats,
+// s' = s or, with positional encoding, its 32 (1 + 2L) encoded values.
 // The latent enters phi1 and B1 only through a matrix-vector product that is
 // the same for every pixel, so it is folded into two bias vectors:
-//   c_phi = W_phi1[:, 12:] sigma + b_phi1        (H)
-//   c_B   = W_B1[:, 14+H:] sigma + b_B1          (H)
-// which is exact algebra of the concat form W [x ; sigma] + b.
+//   c_phi = W_phi1[:, 12 e:] sigma + b_phi1      (H)
+//   c_B   = W_B1[:, 14 e + H:] sigma + b_B1      (H)
+// (e = 1 + 2L bands) which is exact algebra of the concat form W [x ; sigma] + b.
 #include "internal.h"
 
 namespace gn {
 
-void WeightIndex::build(int H_, int Z_) {
+void WeightIndex::build(int H_, int Z_, int L_) {
   H = H_;
   Z = Z_;
+  L = L_;
   const int o[kLayers] = {Z, Z, H, H, H, H, H, H, kOut};
-  const int i[kLayers] = {kScene, Z, kTC + Z, H, 2 * H, kGC + H + Z, H, H, H};
+  const int i[kLayers] = {sc_enc(), Z, tc_enc() + Z, H, 2 * H, gc_enc() + H + Z, H, H, H};
   size_t at = 0;
   for (int l = 0; l < kLayers; ++l) {
     out[l] = o[l];
@@ -31,22 +33,23 @@ struct EncodeArgs {
   const float *Wf1, *bf1, *Wf2, *bf2, *Wp, *bp, *Wb, *bb;
   const float* scene;
   float* latent;
-  int H, Z;
+  int H, Z, L;
 };
 
 // One CTA of 256 threads; every dot product is a sequential FP32 sum in
 // index order.
 __global__ void __launch_bounds__(256) encode_kernel(EncodeArgs a) {
-  __shared__ float s_in[kScene];
+  __shared__ float s_in[kScene * (1 + 2 * kMaxPeFreqs)];
   __shared__ float s_h1[256];
   __shared__ float s_z[256];
   const int t = threadIdx.x;
-  if (t < kScene) s_in[t] = a.scene[t];
+  const int n_in = kScene * (1 + 2 * a.L);  // band b of channel c at b * 32 + c
+  for (int i = t; i < n_in; i += blockDim.x) s_in[i] = pe_band_value(a.scene[i % kScene], i / kScene);
   __syncthreads();
   if (t < a.Z) {
     float acc = a.bf1[t];
-    const float* row = a.Wf1 + static_cast<size_t>(t) * kScene;
-    for (int i = 0; i < kScene; ++i) acc = fmaf(row[i], s_in[i], acc);
+    const float* row = a.Wf1 + static_cast<size_t>(t) * n_in;
+    for (int i = 0; i < n_in; ++i) acc = fmaf(row[i], s_in[i], acc);
     s_h1[t] = fmaxf(acc, 0.0f);
   }
   __syncthreads();
@@ -60,13 +63,15 @@ __global__ void __launch_bounds__(256) encode_kernel(EncodeArgs a) {
   __syncthreads();
   if (t < a.H) {
     float acc = a.bp[t];
-    const float* row = a.Wp + static_cast<size_t>(t) * (kTC + a.Z) + kTC;
+    const int tce = kTC * (1 + 2 * a.L);
+    const float* row = a.Wp + static_cast<size_t>(t) * (tce + a.Z) + tce;
     for (int i = 0; i < a.Z; ++i) acc = fmaf(row[i], s_z[i], acc);
     a.latent[a.Z + t] = acc;
   } else if (t < 2 * a.H) {
     const int n = t - a.H;
     float acc = a.bb[n];
-    const float* row = a.Wb + static_cast<size_t>(n) * (kGC + a.H + a.Z) + kGC + a.H;
+    const int gce = kGC * (1 + 2 * a.L);
+    const float* row = a.Wb + static_cast<size_t>(n) * (gce + a.H + a.Z) + gce + a.H;
     for (int i = 0; i < a.Z; ++i) acc = fmaf(row[i], s_z[i], acc);
     a.latent[a.Z + a.H + n] = acc;
   }
@@ -87,6 +92,7 @@ cudaError_t launch_encode(const float* w32, const WeightIndex& wi, const float* 
   a.latent = latent_dev;
   a.H = wi.H;
   a.Z = wi.Z;
+  a.L = wi.L;
   encode_kernel<<<1, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

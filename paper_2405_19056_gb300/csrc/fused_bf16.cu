@@ -156,6 +156,69 @@ __device__ __forceinline__ void store_slot(uint32_t base, int row0,
   }
 }
 
+// Positional encoding (Sec. 3.4): each input channel x enters as the bands
+// [x ; sin(2^0 pi x) ; cos(2^0 pi x) ; ... ; cos(2^(L-1) pi x)].  The first
+// sine / cosine comes from sincospif (exact argument reduction), every next
+// band from the double-angle identities sin 2a = 2 sin a cos a and
+// cos 2a = 1 - 2 sin^2 a in FP32: each doubling at most quadruples the error,
+// so band f is within about 4^f FP32 ulps of the exact value, far below the
+// BF16 rounding of the operand.
+template <int N>
+__device__ __forceinline__ void pe_first(const float (&x)[N], float (&sn)[N], float (&cs)[N]) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) sincospif(x[j], &sn[j], &cs[j]);
+}
+template <int N>
+__device__ __forceinline__ void pe_double(float (&sn)[N], float (&cs)[N]) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const float a = sn[j];
+    sn[j] = 2.0f * a * cs[j];
+    cs[j] = fmaf(-2.0f * a, a, 1.0f);
+  }
+}
+
+// One 16-byte chunk (8 K values, one core-matrix column of one row) holding
+// N <= 8 values and zeros.
+template <int N>
+__device__ __forceinline__ void sts_chunk(uint32_t a, const float (&v)[N]) {
+  uint32_t q[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) q[j] = 2 * j < N ? pack_bf16(v[2 * j], v[2 * j + 1 < N ? 2 * j + 1 : 2 * j]) : 0u;
+  if constexpr (N % 2 == 1) q[N / 2] = pack_bf16(v[N - 1], 0.0f);
+  sts128(a, q[0], q[1], q[2], q[3]);
+}
+// Bands 1 .. 2 nf of N consecutive channels whose band-0 chunk is at `a`:
+// band t is 16 K columns (4096 bytes of a [K/8][128][8] operand) further on.
+template <int N>
+__device__ __forceinline__ void pe_chunks(uint32_t a, const float (&v)[N], int nf) {
+  float sn[N], cs[N];
+  pe_first(v, sn, cs);
+  for (int f = 0; f < nf; ++f) {
+    if (f > 0) pe_double(sn, cs);
+    sts_chunk(a + static_cast<uint32_t>(2 * f + 1) * 4096u, sn);
+    sts_chunk(a + static_cast<uint32_t>(2 * f + 2) * 4096u, cs);
+  }
+}
+
+// Encoded layer operand: band 0 as store_slot writes it (channels 0-7, then
+// 8-11 and the constant-one pair), then the nf frequencies' sine and cosine
+// bands, one core-matrix column of channels at a time.
+__device__ __forceinline__ void store_slot_pe(uint32_t base, int row0,
+                                              const float (&x)[kRowsPerLoadLane][kTC], int nf) {
+  const uint32_t one = pack_bf16(1.0f, 1.0f);
+#pragma unroll
+  for (int i = 0; i < kRowsPerLoadLane; ++i) {
+    const uint32_t r = base + static_cast<uint32_t>(row0 + 32 * i) * 16u;
+    const float lo[8] = {x[i][0], x[i][1], x[i][2], x[i][3], x[i][4], x[i][5], x[i][6], x[i][7]};
+    const float hi[4] = {x[i][8], x[i][9], x[i][10], x[i][11]};
+    sts_chunk(r, lo);
+    sts128(r + 2048u, pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), one, 0u);
+    pe_chunks(r, lo, nf);
+    pe_chunks(r + 2048u, hi, nf);
+  }
+}
+
 // Launch modes: a whole frame (plan sorted by count, every layer slot, the
 // per-pixel layers), one streamed layer accumulated into a pool state in
 // device memory (one slot per tile, no per-pixel layers), or the per-pixel
@@ -167,11 +230,12 @@ enum : int { kModeFrame = 0, kModeAccumulate = 1, kModeResolve = 2 };
 // slot count, then fill the layer operands slot by slot (two buffers, released
 // by the phi1 MMAs that read them) and B1's G-buffer operand (released by B1
 // of the previous tile).
-template <int H, int Mode>
+template <int H, int Mode, bool PE>
 __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sbase,
                                             uint32_t bar_base, LoaderShared& ls,
                                             volatile int* abort_flag, int li, int lane) {
-  using L = FusedLayout<H>;
+  using L = FusedLayout<H, PE>;
+  const int nf = PE ? prm.pe_freqs : 0;  // positional-encoding frequencies
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
   const int row0 = li * 64 + lane;
   uint32_t lc = 0, n_ag = 0;
@@ -266,6 +330,13 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
                pack_bf16(gv[i][4], gv[i][5]), pack_bf16(gv[i][6], gv[i][7]));
         sts128(r + 2048u, pack_bf16(gv[i][8], gv[i][9]), pack_bf16(gv[i][10], gv[i][11]),
                pack_bf16(gv[i][12], gv[i][13]), one);
+        if constexpr (PE) {
+          const float lo[8] = {gv[i][0], gv[i][1], gv[i][2], gv[i][3],
+                               gv[i][4], gv[i][5], gv[i][6], gv[i][7]};
+          const float hi[6] = {gv[i][8], gv[i][9], gv[i][10], gv[i][11], gv[i][12], gv[i][13]};
+          pe_chunks(r, lo, nf);
+          pe_chunks(r + 2048u, hi, nf);
+        }
       }
       fence_proxy_async_smem();
       __syncwarp();
@@ -281,7 +352,10 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
       if (k + 1 < ns) load_slot(F, k + 1, pix, cnt, y);
       const int b = lc & 1;
       if (!warp_wait(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
-      store_slot(sbase + (b ? L::at1 : L::at0), row0, x);
+      if constexpr (PE)
+        store_slot_pe(sbase + (b ? L::at1 : L::at0), row0, x, nf);
+      else
+        store_slot(sbase + (b ? L::at1 : L::at0), row0, x);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_AT_F + b));
@@ -299,11 +373,13 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 // outputs entering B1 directly (no rho).  tau is the same fixed-point sum as
 // the mean's, tau = s - 2^11 + c 2^-13 (0 without layers), so it is
 // bit-identical under any order of the layers; the max is not kept.
-template <int H, int Mode, bool Sum>
+// PE: the inputs are positionally encoded (H = 64 layout, 1 + 2 pe_freqs
+// bands of 16 K columns in phi1's and B1's first operands).
+template <int H, int Mode, bool Sum, bool PE>
 __global__ void __launch_bounds__(kThreadsF, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   static_assert(!Sum || Mode != kModeAccumulate, "accumulation does not depend on the pooling");
-  using L = FusedLayout<H>;
+  using L = FusedLayout<H, PE>;
   using T = TMap<H>;
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
   constexpr int CHC = CH / 2;  // TMEM columns of CH bf16 values
@@ -359,7 +435,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     }
     fence_proxy_async_smem();
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
-    loader_loop<H, Mode>(prm, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
+    loader_loop<H, Mode, PE>(prm, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA warp
     if (lane == 0) {
@@ -385,8 +461,20 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     const uint64_t dsc_at1 = make_sdesc(sbase + L::at1, 128 * 16, 128);
     const uint64_t dsc_one = make_sdesc(sbase + L::aone, 128 * 16, 128);
     const uint64_t dsc_ag = make_sdesc(sbase + L::ag, 128 * 16, 128);
-    // B1's weights for r start after its 16-wide G-buffer block
-    const uint64_t dsc_b1r = dsc_b1 + static_cast<uint64_t>((2 * H * 16) >> 4);
+    // bands of phi1's and B1's first operands (16 K columns each); B1's
+    // weights for r start after the last G-buffer band.  A K step of 16 is
+    // 4096 bytes of an A operand and 2 H 16 bytes of a weight operand.
+    const int nb = PE ? 1 + 2 * prm.pe_freqs : 1;
+    const uint64_t dsc_b1r = dsc_b1 + static_cast<uint64_t>(nb) * ((2 * H * 16) >> 4);
+    auto mma_bands = [&](uint32_t d, uint64_t a0, uint64_t b0) {
+      if constexpr (PE) {
+        for (int t = 0; t < nb; ++t)
+          mma_f16_ss_e(d, a0 + static_cast<uint64_t>(t) * 256u,
+                       b0 + static_cast<uint64_t>(t) * ((2 * H * 16) >> 4), idH, t > 0 ? 1u : 0u);
+      } else {
+        mma_f16_ss_e(d, a0, b0, idH, 0u);
+      }
+    };
     SlotPos p1, p2;  // next phi1 / phi2 buffer
     uint32_t g1 = 0, n_in = 0, n_agf = 0;
     const int total_tiles = prm.total_tiles;
@@ -398,7 +486,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       const int a = g1 & 1;
       if (!warp_wait(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
       tc_fence_after();
-      mma_f16_ss_e(tbase + T::buf(p1.b), a ? dsc_at1 : dsc_at0, dsc_phi1, idH, 0u);
+      mma_bands(tbase + T::buf(p1.b), a ? dsc_at1 : dsc_at0, dsc_phi1);
       mma_commit_e(bar(B_D1 + p1.b));
       mma_commit_e(bar(B_AT_E + a));
       __syncwarp();
@@ -511,7 +599,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
         ++n_agf;
         tc_fence_after();
-        mma_f16_ss_e(Y, dsc_ag, dsc_b1, idH, 0u);
+        mma_bands(Y, dsc_ag, dsc_b1);
         issue_gemm<H, H / 2>(Y, A_LO, dsc_b1r, idH, true);
         if (!wait_h(1)) goto done;
         issue_gemm<H, H / 2>(Y, A_LO + H / 4, dsc_b1r + kHalfK, idH, true);
@@ -840,21 +928,21 @@ done:
   }
 }
 
-template <int H, int Mode, bool Sum>
+template <int H, int Mode, bool Sum, bool PE>
 cudaError_t prepare_h() {
   static bool done = false;  // per process: the attribute holds for every later launch
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, Mode, Sum>,
+  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, Mode, Sum, PE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       FusedLayout<H>::smem_bytes);
+                                       FusedLayout<H, PE>::smem_bytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <int H, int Mode, bool Sum>
+template <int H, int Mode, bool Sum, bool PE>
 cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
-  constexpr int smem = FusedLayout<H>::smem_bytes;
-  cudaError_t e = prepare_h<H, Mode, Sum>();
+  constexpr int smem = FusedLayout<H, PE>::smem_bytes;
+  cudaError_t e = prepare_h<H, Mode, Sum, PE>();
   if (e != cudaSuccess) return e;
   // Programmatic dependent launch: the CTAs may start while the plan kernel
   // is still running; they wait on the grid dependency before the plan reads.
@@ -868,37 +956,39 @@ cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H, Mode, Sum>, p,
+  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H, Mode, Sum, PE>, p,
                             static_cast<const uint8_t*>(wimg));
 }
 
-template <int H>
+template <int H, bool PE>
 cudaError_t prepare_all() {
-  cudaError_t e = prepare_h<H, kModeFrame, false>();
-  if (e == cudaSuccess) e = prepare_h<H, kModeAccumulate, false>();
-  if (e == cudaSuccess) e = prepare_h<H, kModeResolve, false>();
-  if (e == cudaSuccess) e = prepare_h<H, kModeFrame, true>();
-  if (e == cudaSuccess) e = prepare_h<H, kModeResolve, true>();
+  cudaError_t e = prepare_h<H, kModeFrame, false, PE>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeAccumulate, false, PE>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeResolve, false, PE>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeFrame, true, PE>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeResolve, true, PE>();
   return e;
 }
 
-template <int H>
+template <int H, bool PE>
 cudaError_t launch_mode(int mode, const void* wimg, const FusedParams& p, cudaStream_t s,
                         int grid) {
   // accumulation is the same for both poolings (the state holds max and sum)
-  if (mode == kModeAccumulate) return launch_h<H, kModeAccumulate, false>(wimg, p, s, grid);
+  if (mode == kModeAccumulate) return launch_h<H, kModeAccumulate, false, PE>(wimg, p, s, grid);
   if (p.pool_sum)
-    return mode == kModeResolve ? launch_h<H, kModeResolve, true>(wimg, p, s, grid)
-                                : launch_h<H, kModeFrame, true>(wimg, p, s, grid);
-  return mode == kModeResolve ? launch_h<H, kModeResolve, false>(wimg, p, s, grid)
-                              : launch_h<H, kModeFrame, false>(wimg, p, s, grid);
+    return mode == kModeResolve ? launch_h<H, kModeResolve, true, PE>(wimg, p, s, grid)
+                                : launch_h<H, kModeFrame, true, PE>(wimg, p, s, grid);
+  return mode == kModeResolve ? launch_h<H, kModeResolve, false, PE>(wimg, p, s, grid)
+                              : launch_h<H, kModeFrame, false, PE>(wimg, p, s, grid);
 }
 
 }  // namespace
 
 cudaError_t prepare_fused_bf16(int H) {
   device_sm_count();
-  return H == 128 ? prepare_all<128>() : prepare_all<64>();
+  if (H == 128) return prepare_all<128, false>();
+  cudaError_t e = prepare_all<64, false>();
+  return e == cudaSuccess ? prepare_all<64, true>() : e;
 }
 
 cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& params,
@@ -908,8 +998,13 @@ cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& params
   cudaError_t e = launch_plan(p, s);
   if (e != cudaSuccess) return e;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
-  return H == 128 ? launch_mode<128>(mode, wimg, p, s, grid)
-                  : launch_mode<64>(mode, wimg, p, s, grid);
+  if (p.pe_freqs > 0) {
+    // the encoded operands exist for H = 64 only (the loader refuses others)
+    if (H != 64 || p.pe_freqs > kMaxPeFreqsFused) return cudaErrorInvalidValue;
+    return launch_mode<64, true>(mode, wimg, p, s, grid);
+  }
+  return H == 128 ? launch_mode<128, false>(mode, wimg, p, s, grid)
+                  : launch_mode<64, false>(mode, wimg, p, s, grid);
 }
 
 }  // namespace gn

@@ -55,9 +55,13 @@ inline size_t core_idx(int N, int n, int k) {
   return (static_cast<size_t>(k / 8) * N + n) * 8 + (k % 8);
 }
 
-template <int H>
+// With positional encoding, band t of phi1's input (12 encoded values) and of
+// B1's G-buffer block (14) go to K columns 16 t .. (FusedLayout); r follows
+// the last band.
+template <int H, bool PE>
 std::vector<uint8_t> pack_fused_bf16(const float* w, const gn::WeightIndex& wi) {
-  using L = gn::FusedLayout<H>;
+  using L = gn::FusedLayout<H, PE>;
+  const int nb = wi.bands();
   std::vector<uint8_t> img(L::bytes, 0);
   auto put = [&](uint32_t off, int N, int n, int k, float v) {
     uint16_t b = bf16_rne(v);
@@ -65,11 +69,13 @@ std::vector<uint8_t> pack_fused_bf16(const float* w, const gn::WeightIndex& wi) 
   };
   auto W = [&](int l, int n, int j) { return w[wi.w[l] + static_cast<size_t>(n) * wi.in[l] + j]; };
   for (int n = 0; n < H; ++n) {
-    for (int k = 0; k < gn::kTC; ++k) put(L::phi1, H, n, k, W(gn::LPHI1, n, k));
+    for (int t = 0; t < nb; ++t)
+      for (int k = 0; k < gn::kTC; ++k) put(L::phi1, H, n, 16 * t + k, W(gn::LPHI1, n, t * gn::kTC + k));
     for (int k = 0; k < H; ++k) put(L::phi2, H, n, k, W(gn::LPHI2, n, k));
     for (int k = 0; k < 2 * H; ++k) put(L::rho, H, n, k, W(gn::LRHO, n, k));
-    for (int k = 0; k < gn::kGC; ++k) put(L::b1, H, n, k, W(gn::LB1, n, k));
-    for (int k = 0; k < H; ++k) put(L::b1, H, n, 16 + k, W(gn::LB1, n, gn::kGC + k));
+    for (int t = 0; t < nb; ++t)
+      for (int k = 0; k < gn::kGC; ++k) put(L::b1, H, n, 16 * t + k, W(gn::LB1, n, t * gn::kGC + k));
+    for (int k = 0; k < H; ++k) put(L::b1, H, n, 16 * nb + k, W(gn::LB1, n, wi.gc_enc() + k));
     for (int k = 0; k < H; ++k) put(L::b2, H, n, k, W(gn::LB2, n, k));
     for (int k = 0; k < H; ++k) put(L::r1, H, n, k, W(gn::LR1, n, k));
   }
@@ -221,19 +227,24 @@ extern "C" {
 const char* glassnet_last_error(void) { return g_last_error.c_str(); }
 
 int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_model** out) {
-  return glassnet_load_weights_ex(blob, nbytes, precision, GN_POOL_MAX_MEAN, out);
+  const gn_model_config cfg = {precision, GN_POOL_MAX_MEAN, 0};
+  return glassnet_load_weights_ex(blob, nbytes, &cfg, out);
 }
 
-int glassnet_load_weights_ex(const void* blob, size_t nbytes, int precision, int pooling,
+int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_config* cfg,
                              gn_model** out) {
-  if (!blob || !out) return fail(GN_EINVAL, "blob and out must be non-NULL");
+  if (!blob || !cfg || !out) return fail(GN_EINVAL, "blob, config and out must be non-NULL");
   *out = nullptr;
+  const int precision = cfg->precision, pooling = cfg->pooling, pe = cfg->pe_freqs;
   if (precision != GN_FP32_PLAIN && precision != GN_BF16_FUSED && precision != GN_FP8_FUSED)
     return fail(GN_EINVAL, "unknown precision %d", precision);
   if (pooling != GN_POOL_MAX_MEAN && pooling != GN_POOL_SUM)
     return fail(GN_EINVAL, "unknown pooling %d", pooling);
-  if (pooling == GN_POOL_SUM && precision == GN_FP8_FUSED)
-    return fail(GN_EUNSUPPORTED, "sum pooling is built for GN_FP32_PLAIN and GN_BF16_FUSED");
+  if (pe < 0 || pe > gn::kMaxPeFreqs)
+    return fail(GN_EINVAL, "pe_freqs %d outside 0..%d", pe, gn::kMaxPeFreqs);
+  if (precision == GN_FP8_FUSED && (pooling == GN_POOL_SUM || pe > 0))
+    return fail(GN_EUNSUPPORTED,
+                "sum pooling and positional encoding are built for GN_FP32_PLAIN and GN_BF16_FUSED");
   if (nbytes < sizeof(gn_blob_header))
     return fail(GN_EFORMAT, "blob of %zu bytes is shorter than its header", nbytes);
   gn_blob_header hd;
@@ -246,10 +257,11 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, int precision, int
                 hd.scene_dim, hd.tbuf_channels, hd.gbuf_channels, hd.out_channels);
   if (hd.hidden > 4096 || hd.latent > 4096) return fail(GN_EFORMAT, "implausible widths");
   gn::WeightIndex wi;
-  wi.build(static_cast<int>(hd.hidden), static_cast<int>(hd.latent));
+  wi.build(static_cast<int>(hd.hidden), static_cast<int>(hd.latent), pe);
   if (hd.payload_floats != wi.total)
-    return fail(GN_EFORMAT, "payload holds %llu floats, widths (%u, %u) need %zu",
-                static_cast<unsigned long long>(hd.payload_floats), hd.hidden, hd.latent, wi.total);
+    return fail(GN_EFORMAT, "payload holds %llu floats, widths (%u, %u) with pe_freqs %d need %zu",
+                static_cast<unsigned long long>(hd.payload_floats), hd.hidden, hd.latent, pe,
+                wi.total);
   if (nbytes != sizeof(gn_blob_header) + wi.total * sizeof(float))
     return fail(GN_EFORMAT, "blob size %zu != %zu", nbytes,
                 sizeof(gn_blob_header) + wi.total * sizeof(float));
@@ -260,6 +272,11 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, int precision, int
   if (!ok_widths)
     return fail(GN_EUNSUPPORTED, "widths (H, Z) = (%u, %u); this build has (64, 128), (128, 256)",
                 hd.hidden, hd.latent);
+  if (precision == GN_BF16_FUSED && pe > 0 && (hd.hidden != 64 || pe > gn::kMaxPeFreqsFused))
+    return fail(GN_EUNSUPPORTED,
+                "positional encoding in the fused BF16 kernel is built for H = 64 and pe_freqs "
+                "1..%d (its operands fill the shared memory); H = %u, pe_freqs = %d",
+                gn::kMaxPeFreqsFused, hd.hidden, pe);
 
   std::vector<float> w(wi.total);
   std::memcpy(w.data(), payload, wi.total * sizeof(float));
@@ -296,8 +313,9 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, int precision, int
     std::memcpy(m->host_w, w.data(), wi.total * sizeof(float));
   }
   if (precision == GN_BF16_FUSED) {
-    std::vector<uint8_t> img =
-        wi.H == 128 ? pack_fused_bf16<128>(w.data(), wi) : pack_fused_bf16<64>(w.data(), wi);
+    std::vector<uint8_t> img = wi.H == 128 ? pack_fused_bf16<128, false>(w.data(), wi)
+                               : wi.L > 0  ? pack_fused_bf16<64, true>(w.data(), wi)
+                                           : pack_fused_bf16<64, false>(w.data(), wi);
     m->fused_bytes = img.size();
     if ((e = cudaMalloc(&m->fused, img.size())) != cudaSuccess) {
       glassnet_free_model(m);
@@ -321,9 +339,11 @@ int glassnet_model_info(const gn_model* m, int* hidden, int* latent, int* precis
   return GN_OK;
 }
 
-int glassnet_model_pooling(const gn_model* m, int* pooling) {
-  if (!m || !pooling) return fail(GN_EINVAL, "model and pooling must be non-NULL");
-  *pooling = m->pooling;
+int glassnet_model_config(const gn_model* m, gn_model_config* cfg) {
+  if (!m || !cfg) return fail(GN_EINVAL, "model and config must be non-NULL");
+  cfg->precision = m->precision;
+  cfg->pooling = m->pooling;
+  cfg->pe_freqs = m->wi.L;
   return GN_OK;
 }
 
@@ -452,9 +472,10 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
 
 cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s) {
   if (m->precision == GN_FP8_FUSED) return launch_fused_fp8(m->H, m->fused, p, s);
-  if (m->pooling == GN_POOL_SUM) {
+  if (m->pooling == GN_POOL_SUM || m->wi.L > 0) {
     FusedParams q = p;
-    q.pool_sum = 1;
+    q.pool_sum = m->pooling == GN_POOL_SUM;
+    q.pe_freqs = m->wi.L;
     return launch_fused_bf16(m->H, m->fused, q, s);
   }
   return launch_fused_bf16(m->H, m->fused, p, s);
@@ -698,6 +719,7 @@ gn::FusedParams pool_params(const gn_model* m, const gn_latent* lat, const gn_po
   number_tiles(p);
   p.plan_identity = 1;
   p.pool_sum = m->pooling == GN_POOL_SUM;
+  p.pe_freqs = m->wi.L;
   p.pool_st = pool->st;
   p.pool_cnt = pool->cnt;
   gn::bind_plan(p, pool->plan);

@@ -32,14 +32,35 @@ constexpr uint32_t kErrTimeout = 4u;  // a device wait gave up
 // Linear layers in blob order.
 enum Layer { LF1 = 0, LF2, LPHI1, LPHI2, LRHO, LB1, LB2, LR1, LR2, kLayers };
 
+// Positional encoding of the inputs (Sec. 3.4): an input of n channels
+// enters as n (1 + 2L) values, the blocks [x ; sin(2^0 pi x) ; cos(2^0 pi x) ;
+// ... ; sin(2^(L-1) pi x) ; cos(2^(L-1) pi x)].  Band t of an input is block t.
+constexpr int kMaxPeFreqs = 10;       // any precision's limit
+constexpr int kMaxPeFreqsFused = 4;   // the fused BF16 kernel at H = 64
+
 // Offsets (in floats) of each W and b inside the concat-form f32 weights.
 struct WeightIndex {
-  int H = 0, Z = 0;
+  int H = 0, Z = 0, L = 0;  // L: positional-encoding frequencies (0: none)
   size_t w[kLayers] = {}, b[kLayers] = {};
   int out[kLayers] = {}, in[kLayers] = {};
   size_t total = 0;
-  void build(int H_, int Z_);
+  int bands() const { return 1 + 2 * L; }
+  int tc_enc() const { return kTC * bands(); }     // encoded layer channels (phi1's first block)
+  int gc_enc() const { return kGC * bands(); }     // encoded G-buffer channels (B1's first block)
+  int sc_enc() const { return kScene * bands(); }  // encoded scene vector (F1's input)
+  void build(int H_, int Z_, int L_ = 0);
 };
+
+#ifdef __CUDACC__
+// Band t of the encoding of x: x (t = 0), sin(2^f pi x) (t = 2f + 1) or
+// cos(2^f pi x) (t = 2f + 2).  The scaling by 2^f is exact; sinpif / cospif
+// reduce the argument exactly.
+__device__ __forceinline__ float pe_band_value(float x, int t) {
+  if (t == 0) return x;
+  const float y = ldexpf(x, (t - 1) >> 1);
+  return (t & 1) ? sinpif(y) : cospif(y);
+}
+#endif
 
 // Packed operand image of the fused kernels: B operands (weights, [N][K]) in
 // the K-major no-swizzle core-matrix layout [K/8][N][8] bf16, then the f32
@@ -53,10 +74,20 @@ struct WeightIndex {
 //                   split into a high and a low BF16 part, k >= 2 zero; the
 //                   GEMM multiplies it by a constant [1, 1, 0, ...] A column
 //   bias f32: phi2[H], rho[H], B2[H], R1[H], R2[16]
-template <int H>
+//
+// With positional encoding (PE, H = 64 only) every band of phi1's input and
+// of B1's G-buffer block takes 16 K columns (12 or 14 values, then zeros),
+// for up to kMaxPeFreqsFused frequencies: band 0 keeps the layout above
+// (constant-one columns at k = 12, 13 of phi1 and k = 14, 15 of B1), band t
+// sits at k = 16 t, and B1's r block starts after the last band.  The
+// operands are sized for the largest L; a model with fewer frequencies uses
+// the first 1 + 2L bands.
+template <int H, bool PE = false>
 struct FusedLayout {
-  static constexpr int KT = 16;
-  static constexpr int KB1 = 16 + H;
+  static constexpr int kBands = PE ? 1 + 2 * kMaxPeFreqsFused : 1;
+  static constexpr int KT = 16 * kBands;
+  static constexpr int KG = 16 * kBands;
+  static constexpr int KB1 = KG + H;
   static constexpr int NR2 = 16;
   static constexpr uint32_t phi1 = 0;
   static constexpr uint32_t phi2 = phi1 + KT * H * 2;
@@ -73,15 +104,16 @@ struct FusedLayout {
   static constexpr uint32_t bias_r1 = bias + 3 * H * 4;
   static constexpr uint32_t bias_r2 = bias + 4 * H * 4;
   static constexpr uint32_t bytes = bias + (4 * H + 16) * 4;
-  // Shared memory beyond the weights, each a [2][128][8] bf16 A operand
-  // (K = 16 for 128 rows): two layer operands of phi1, the constant
-  // [1, 1, 0, ...] operand that multiplies phi2b, and the G-buffer block
-  // [g0..g13, 1, 1] of B1.
+  // Shared memory beyond the weights, each a [K/8][128][8] bf16 A operand
+  // for 128 rows: two layer operands of phi1 (K = KT), the constant
+  // [1, 1, 0, ...] operand that multiplies phi2b (K = 16), and the G-buffer
+  // block [g0..g13, 1, 1] of B1 (K = KG).
   static constexpr uint32_t at0 = (bytes + 127) / 128 * 128;
-  static constexpr uint32_t at1 = at0 + 4096;
-  static constexpr uint32_t aone = at1 + 4096;
+  static constexpr uint32_t at1 = at0 + KT * 256;
+  static constexpr uint32_t aone = at1 + KT * 256;
   static constexpr uint32_t ag = aone + 4096;
-  static constexpr uint32_t smem_bytes = ag + 4096;
+  static constexpr uint32_t smem_bytes = ag + KG * 256;
+  static_assert(smem_bytes <= 232448, "operands exceed the 227 KB of shared memory per CTA");
 };
 
 // Packed operand image of the FP8 fused kernel (E4M3 operands, FP32
@@ -175,6 +207,9 @@ struct FusedParams {
   // Pooling of Eq. 5: 0 = [max ; mean] then rho, 1 = the sum tau fed to B1
   // directly (frame and resolve launches; accumulation is the same for both).
   int pool_sum;
+  // Positional-encoding frequencies of the inputs (0: none; the PE kernel
+  // variant serves 1 .. kMaxPeFreqsFused).
+  int pe_freqs;
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -213,7 +248,7 @@ cudaError_t launch_fp8_act_amax(const void* ws, const float* gbuf, const float* 
 
 struct gn_model {
   int H = 0, Z = 0, precision = 0, device = 0;
-  int pooling = GN_POOL_MAX_MEAN;  // gn_pooling
+  int pooling = GN_POOL_MAX_MEAN;  // gn_pooling (the frequency count is wi.L)
   gn::WeightIndex wi;
   float* w32 = nullptr;     // concat-form f32 weights (device)
   void* fused = nullptr;    // packed operand image (device)

@@ -3,7 +3,8 @@
 // FMA on CUDA cores (no tensor cores, no TF32, no folding).  It is the
 // same-GPU baseline for the fused kernels.
 //
-// Layers (Sec. 3.3-3.4, Eq. 5):
+// Layers (Sec. 3.3-3.4, Eq. 5), inputs b_k and g positionally encoded when
+// the weights have L > 0 frequencies (bands computed as the GEMM reads them):
 //   U = ReLU(W_phi1 [b_k ; sigma] + b)    rows (k, p) with k < c_p
 //   V = ReLU(W_phi2 U + b)
 //   pool_p = [max_k V ; (sum_k V) / c_p]   FP32 sum in slot order
@@ -20,15 +21,17 @@ constexpr int BM = 64, BN = 64, BK = 16;
 
 // Input row assemblers: x(r, j) is element j of input row r; valid(r) tells
 // whether row r is computed (invalid rows are written as 0 and never read).
-struct PhiIn {
+struct PhiIn {  // [gamma_L(b_k) (12 (1 + 2L)) ; sigma (Z)]
   const float* tbuf;
   const float* sigma;
   const uint8_t* counts;
-  int P;
+  int P, L;
   __device__ bool valid(int r) const { return (r / P) < counts[r % P]; }
   __device__ float x(int r, int j) const {
     const int k = r / P, p = r % P;
-    return j < kTC ? tbuf[(static_cast<size_t>(k) * kTC + j) * P + p] : sigma[j - kTC];
+    const int tce = kTC * (1 + 2 * L);
+    if (j >= tce) return sigma[j - tce];
+    return pe_band_value(tbuf[(static_cast<size_t>(k) * kTC + j % kTC) * P + p], j / kTC);
   }
 };
 struct RowsIn {  // row-major [M][Kx]; validity from the layer counts (rows (k, p))
@@ -45,16 +48,17 @@ struct RhoIn {  // pool rows; a pixel without valid layers gets r = 0
   __device__ bool valid(int r) const { return counts[r] > 0; }
   __device__ float x(int r, int j) const { return pool[static_cast<size_t>(r) * Kx + j]; }
 };
-struct BIn {  // [g (14) ; r (H) ; sigma (Z)]
+struct BIn {  // [gamma_L(g) (14 (1 + 2L)) ; r (H) ; sigma (Z)]
   const float* gbuf;
   const float* R;
   const float* sigma;
-  int P, H;
+  int P, H, L;
   __device__ bool valid(int) const { return true; }
   __device__ float x(int r, int j) const {
-    if (j < kGC) return gbuf[static_cast<size_t>(j) * P + r];
-    if (j < kGC + H) return R[static_cast<size_t>(r) * H + (j - kGC)];
-    return sigma[j - kGC - H];
+    const int gce = kGC * (1 + 2 * L);
+    if (j < gce) return pe_band_value(gbuf[static_cast<size_t>(j % kGC) * P + r], j / kGC);
+    if (j < gce + H) return R[static_cast<size_t>(r) * H + (j - gce)];
+    return sigma[j - gce - H];
   }
 };
 
@@ -227,8 +231,8 @@ cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const flo
   auto B = [&](int l) { return w32 + wi.b[l]; };
   cudaError_t e = cudaSuccess;
   if (K > 0) {
-    e = run_linear<PhiIn, false>(PhiIn{tbuf, sigma, counts, P}, W(LPHI1), B(LPHI1), U,
-                                 static_cast<int>(rows), H, kTC + Z, s);
+    e = run_linear<PhiIn, false>(PhiIn{tbuf, sigma, counts, P, wi.L}, W(LPHI1), B(LPHI1), U,
+                                 static_cast<int>(rows), H, wi.tc_enc() + Z, s);
     if (e != cudaSuccess) return e;
     e = run_linear<RowsIn, false>(RowsIn{U, counts, P, H}, W(LPHI2), B(LPHI2), V,
                                   static_cast<int>(rows), H, H, s);
@@ -243,7 +247,8 @@ cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const flo
     e = cudaMemsetAsync(R, 0, static_cast<size_t>(P) * H * sizeof(float), s);
   }
   if (e != cudaSuccess) return e;
-  e = run_linear<BIn, false>(BIn{gbuf, R, sigma, P, H}, W(LB1), B(LB1), Y1, P, H, kGC + H + Z, s);
+  e = run_linear<BIn, false>(BIn{gbuf, R, sigma, P, H, wi.L}, W(LB1), B(LB1), Y1, P, H,
+                             wi.gc_enc() + H + Z, s);
   if (e != cudaSuccess) return e;
   e = run_linear<RowsIn, false>(RowsIn{Y1, nullptr, P, H}, W(LB2), B(LB2), Y2, P, H, H, s);
   if (e != cudaSuccess) return e;

@@ -41,8 +41,8 @@ _I = ctypes.c_int
 _SIGNATURES = {
     "glassnet_load_weights": (_I, [_P, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     "glassnet_model_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
-    "glassnet_load_weights_ex": (_I, [_P, ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
-    "glassnet_model_pooling": (_I, [_P, ctypes.POINTER(_I)]),
+    "glassnet_load_weights_ex": (_I, [_P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "glassnet_model_config": (_I, [_P, _P]),
     "glassnet_encode_scene": (_I, [_P, _P, ctypes.POINTER(_P), _P]),
     "glassnet_encode_scene_device": (_I, [_P, _P, _P, _P]),
     "glassnet_latent_read": (_I, [_P, _P, _P, _P, _P]),
@@ -158,10 +158,16 @@ def glassnet_load_weights(blob: bytes, precision: int) -> int:
     return out.value
 
 
-def glassnet_load_weights_ex(blob: bytes, precision: int, pooling: int) -> int:
+class ModelConfig(ctypes.Structure):
+    """gn_model_config."""
+    _fields_ = [("precision", ctypes.c_int), ("pooling", ctypes.c_int), ("pe_freqs", ctypes.c_int)]
+
+
+def glassnet_load_weights_ex(blob: bytes, precision: int, pooling: int = 0, pe_freqs: int = 0) -> int:
     out = ctypes.c_void_p()
     buf = ctypes.create_string_buffer(blob, len(blob))
-    _check(_lib().glassnet_load_weights_ex(buf, len(blob), precision, pooling, ctypes.byref(out)))
+    cfg = ModelConfig(precision, pooling, pe_freqs)
+    _check(_lib().glassnet_load_weights_ex(buf, len(blob), ctypes.byref(cfg), ctypes.byref(out)))
     return out.value
 
 
@@ -171,10 +177,10 @@ def glassnet_model_info(model: int):
     return h.value, z.value, p.value
 
 
-def glassnet_model_pooling(model: int) -> int:
-    v = ctypes.c_int()
-    _check(_lib().glassnet_model_pooling(model, ctypes.byref(v)))
-    return v.value
+def glassnet_model_config(model: int) -> ModelConfig:
+    cfg = ModelConfig()
+    _check(_lib().glassnet_model_config(model, ctypes.byref(cfg)))
+    return cfg
 
 
 def glassnet_encode_scene(model: int, scene, stream=None) -> int:
@@ -388,11 +394,16 @@ class Model:
     """Owns a gn_model handle."""
 
     def __init__(self, weights_or_blob, precision: int = GN_BF16_FUSED,
-                 pooling: int = GN_POOL_MAX_MEAN):
+                 pooling: int = GN_POOL_MAX_MEAN, pe_freqs=None):
+        """``pe_freqs`` defaults to the weight dict's ``"pe_freqs"`` (0 for a blob)."""
+        if pe_freqs is None:
+            pe_freqs = 0 if isinstance(weights_or_blob, (bytes, bytearray)) else \
+                int(weights_or_blob.get("pe_freqs", 0))
         blob = weights_or_blob if isinstance(weights_or_blob, (bytes, bytearray)) else pack_blob(weights_or_blob)
-        self.handle = glassnet_load_weights_ex(bytes(blob), precision, pooling)
+        self.handle = glassnet_load_weights_ex(bytes(blob), precision, pooling, pe_freqs)
         self.hidden, self.latent_width, self.precision = glassnet_model_info(self.handle)
-        self.pooling = glassnet_model_pooling(self.handle)
+        cfg = glassnet_model_config(self.handle)
+        self.pooling, self.pe_freqs = cfg.pooling, cfg.pe_freqs
 
     def encode(self, scene, stream=None) -> "Latent":
         return Latent(glassnet_encode_scene(self.handle, scene, stream))

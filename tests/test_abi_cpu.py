@@ -102,13 +102,36 @@ def test_pooling_arguments_checked_before_any_device_work(lib):
     blob = _blob()
     out = ctypes.c_void_p()
     buf = ctypes.create_string_buffer(blob, len(blob))
-    assert lib.glassnet_load_weights_ex(buf, len(blob), gl.GN_BF16_FUSED, 2, ctypes.byref(out)) == gl.GN_EINVAL
-    assert lib.glassnet_load_weights_ex(buf, len(blob), gl.GN_FP8_FUSED, gl.GN_POOL_SUM,
-                                        ctypes.byref(out)) == gl.GN_EUNSUPPORTED
+
+    def load(precision, pooling, pe):
+        cfg = gl.ModelConfig(precision, pooling, pe)
+        return lib.glassnet_load_weights_ex(buf, len(blob), ctypes.byref(cfg), ctypes.byref(out))
+
+    assert load(gl.GN_BF16_FUSED, 2, 0) == gl.GN_EINVAL
+    assert load(gl.GN_BF16_FUSED, 0, -1) == gl.GN_EINVAL
+    assert load(gl.GN_BF16_FUSED, 0, 11) == gl.GN_EINVAL
+    assert load(gl.GN_FP8_FUSED, gl.GN_POOL_SUM, 0) == gl.GN_EUNSUPPORTED
     assert "sum pooling" in gl.glassnet_last_error()
+    assert load(gl.GN_FP8_FUSED, 0, 2) == gl.GN_EUNSUPPORTED
+    # a plain (L = 0) blob read as L = 1 has the wrong payload size
+    assert load(gl.GN_BF16_FUSED, 0, 1) == gl.GN_EFORMAT
+    assert "pe_freqs 1" in gl.glassnet_last_error()
     assert not out.value
-    assert lib.glassnet_load_weights_ex(None, 10, 1, 1, ctypes.byref(out)) == gl.GN_EINVAL
-    assert lib.glassnet_model_pooling(None, None) == gl.GN_EINVAL
+    assert lib.glassnet_load_weights_ex(None, 10, None, ctypes.byref(out)) == gl.GN_EINVAL
+    assert lib.glassnet_model_config(None, None) == gl.GN_EINVAL
+
+
+def test_positional_encoding_limits_checked_on_the_host(lib):
+    """The fused kernel's PE variant exists for H = 64, L <= 4 only: larger
+    forms are refused before the blob reaches the device."""
+    out = ctypes.c_void_p()
+    for widths, pe, code in [(synth.Widths(hidden=128, latent=256, pe_freqs=1), 1, gl.GN_EUNSUPPORTED),
+                             (synth.Widths(hidden=64, latent=128, pe_freqs=5), 5, gl.GN_EUNSUPPORTED)]:
+        blob = gl.pack_blob(synth.make_weights(widths, seed=0))
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        cfg = gl.ModelConfig(gl.GN_BF16_FUSED, 0, pe)
+        assert lib.glassnet_load_weights_ex(buf, len(blob), ctypes.byref(cfg), ctypes.byref(out)) == code
+        assert "H = 64" in gl.glassnet_last_error()
 
 
 def test_null_arguments_rejected(lib):
