@@ -157,16 +157,27 @@ __device__ __forceinline__ void store_slot(uint32_t base, int row0,
 }
 
 // Positional encoding (Sec. 3.4): each input channel x enters as the bands
-// [x ; sin(2^0 pi x) ; cos(2^0 pi x) ; ... ; cos(2^(L-1) pi x)].  The first
-// sine / cosine comes from sincospif (exact argument reduction), every next
-// band from the double-angle identities sin 2a = 2 sin a cos a and
-// cos 2a = 1 - 2 sin^2 a in FP32: each doubling at most quadruples the error,
-// so band f is within about 4^f FP32 ulps of the exact value, far below the
-// BF16 rounding of the operand.
+// [x ; sin(2^0 pi x) ; cos(2^0 pi x) ; ... ; cos(2^(L-1) pi x)].
+// First band: x = n + r with n = rint(x) and r = x - n exact, |r| <= 1/2, so
+// sin(pi x) = (-1)^n sin(pi r) and cos(pi x) = (-1)^n cos(pi r) with
+// |pi r| <= pi/2, where the hardware sine and cosine (__sinf, __cosf) are
+// accurate to about 2^-21 absolute.  Every next band follows from the
+// double-angle identities sin 2a = 2 sin a cos a and cos 2a = 1 - 2 sin^2 a
+// in FP32; each doubling at most quadruples the error, so band f is within
+// about 4^f 2^-21 of the exact value (3e-5 at f = 3), far below the BF16
+// rounding (2^-9 relative) of the operand it feeds.
+__device__ __forceinline__ void sincospi_reduced(float x, float& sn, float& cs) {
+  const float n = rintf(x);
+  const float a = (x - n) * 3.14159265358979f;
+  const float h = 0.5f * n;
+  const float sign = rintf(h) == h ? 1.0f : -1.0f;  // (-1)^n, also for |n| >= 2^24 (even)
+  sn = sign * __sinf(a);
+  cs = sign * __cosf(a);
+}
 template <int N>
 __device__ __forceinline__ void pe_first(const float (&x)[N], float (&sn)[N], float (&cs)[N]) {
 #pragma unroll
-  for (int j = 0; j < N; ++j) sincospif(x[j], &sn[j], &cs[j]);
+  for (int j = 0; j < N; ++j) sincospi_reduced(x[j], sn[j], cs[j]);
 }
 template <int N>
 __device__ __forceinline__ void pe_double(float (&sn)[N], float (&cs)[N]) {
@@ -305,15 +316,18 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 
     // G-buffer block [g0..g13, 1, 1] of the lane's rows, loads in flight now
     // (accumulate launches run no B1)
+    // (with positional encoding they are loaded where they are used: the
+    // encoding's temporaries leave no registers to hold them over the slots)
     float gv[kRowsPerLoadLane][kGC] = {};
-    if constexpr (Mode != kModeAccumulate) {
+    auto load_g = [&]() {
       const uint32_t P = static_cast<uint32_t>(F.P);
 #pragma unroll
       for (int i = 0; i < kRowsPerLoadLane; ++i)
 #pragma unroll
         for (int ch = 0; ch < kGC; ++ch)
           gv[i][ch] = has[i] ? __ldg(F.gbuf + (static_cast<uint32_t>(ch) * P + pix[i])) : 0.0f;
-    }
+    };
+    if constexpr (Mode != kModeAccumulate && !PE) load_g();
     // The operand's release (B_AG_E) also paces the loaders: they are at most
     // one tile ahead, as the two tile-publication barriers need.  Accumulate
     // launches run no B1: there the MMA warp commits B_AG_E once per tile
@@ -322,6 +336,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
       if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
       if constexpr (Mode == kModeAccumulate) return true;
+      if constexpr (PE) load_g();
       const uint32_t one = pack_bf16(1.0f, 1.0f);
 #pragma unroll
       for (int i = 0; i < kRowsPerLoadLane; ++i) {
