@@ -35,6 +35,7 @@ UNIT = "Mpixel/s"
 WORKLOAD = "512x512 frame, K=8 slots, counts min(Poisson(3),8), H=128 Z=256"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "fused_bf16_512x512_K8.traffic.json")
 PROFILE_TRAFFIC_SUM = os.path.join(ROOT, "profiles", "fused_bf16_sum_512x512_K8.traffic.json")
+PROFILE_TRAFFIC_PE = os.path.join(ROOT, "profiles", "fused_bf16_pe4_512x512_K8.traffic.json")
 
 
 def profiled_traffic(path: str):
@@ -63,6 +64,9 @@ def parse():
     ap.add_argument("--pooling", default="max_mean", choices=["max_mean", "sum"],
                     help="pooling of Eq. 5 in the timed BF16 leg: [max ; mean] then rho, or the "
                          "paper's sum form (tau straight into B)")
+    ap.add_argument("--pe-freqs", type=int, default=0,
+                    help="time the base widths (H=64 Z=128) with every input positionally "
+                         "encoded at this many frequencies (BF16, 1..4) instead of the doubled widths")
     return ap.parse_args()
 
 
@@ -263,11 +267,13 @@ def run_fused(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     gl.load_library()
-    weights = synth.make_weights(synth.DOUBLED_WIDTHS, seed=0)
+    pe = args.pe_freqs
+    widths = synth.Widths(64, 128, pe) if pe else synth.DOUBLED_WIDTHS
+    weights = synth.make_weights(widths, seed=0)
     fp8 = args.precision == "fp8"
     pool_sum = args.pooling == "sum"
-    if fp8 and pool_sum:
-        raise SystemExit("the sum pooling form is built for BF16 only")
+    if fp8 and (pool_sum or pe):
+        raise SystemExit("the sum pooling form and positional encoding are built for BF16 only")
     model = gl.Model(weights, gl.GN_FP8_FUSED if fp8 else gl.GN_BF16_FUSED,
                      gl.GN_POOL_SUM if pool_sum else gl.GN_POOL_MAX_MEAN)
     scene = synth.make_scene(0)
@@ -281,7 +287,7 @@ def run_fused(args, world, rank, local):
                             tbuf=torch.from_numpy(f.tbuf).to(dev),
                             counts=torch.from_numpy(f.counts).to(dev),
                             out=torch.empty((3, H_IMG, W_IMG), device=dev)))
-    flops = [algorithmic_flops(128, f.counts, args.pooling) for f in frames]
+    flops = [algorithmic_flops(widths.hidden, f.counts, args.pooling, pe) for f in frames]
     P = H_IMG * W_IMG
 
     with torch.cuda.stream(stream):
@@ -329,15 +335,21 @@ def run_fused(args, world, rank, local):
     if fp8:
         peak_tf *= 2
     achieved_tf = step_flops / (avg_kernel_ms * 1e-3) / 1e12
-    traffic = None if fp8 else profiled_traffic(PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC)
+    # the captures cover L = 4 (encoded) and the two poolings of the doubled widths
+    traffic = None if fp8 or (pe and (pe != 4 or pool_sum)) else profiled_traffic(
+        PROFILE_TRAFFIC_PE if pe else PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC)
     metric = METRIC.replace("BF16", "FP8") if fp8 else METRIC
     if pool_sum:
         metric = metric.replace("BF16 fused", "BF16 fused, sum pooling")
+    if pe:
+        metric = metric.replace("BF16 fused", f"BF16 fused, H=64, inputs encoded at L={pe}")
     result = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if fp8 else "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames_rotated": N_ROTATE,
+        "config": {"workload": WORKLOAD if not pe else
+                   WORKLOAD.replace("H=128 Z=256", f"H=64 Z=128, positional encoding L={pe}"),
+                   "frames_rotated": N_ROTATE,
                    "l2": "inputs rotate over 3 frames of 115 MB (> 129 MB L2 in total)",
                    "parallelism": f"replicas{world}", "weights": "Xavier-normal seed 0, zero bias"},
         "fps": world * args.steps / (total_ms * 1e-3),
@@ -347,7 +359,8 @@ def run_fused(args, world, rank, local):
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
                      "kernel": "fused_fp8_kernel<128>" if fp8 else
-                               f"fused_bf16_kernel<128, frame, sum={int(pool_sum)}>",
+                               f"fused_bf16_kernel<{widths.hidden}, frame, sum={int(pool_sum)}, "
+                               f"pe={int(pe > 0)}>",
                      "duration": "CUDA events around the render call (plan kernel + fused kernel)",
                      "flops_per_launch": step_flops,
                      "peak_source": (f"{peak_src} bf16 burst (MEASURED_PEAKS.json) x 2 (nominal "

@@ -49,7 +49,9 @@
 //    every tcgen05.mma from lane 0.
 //  - warps 9-10 (loaders, 64 pixel rows each): read each tile's plan entries,
 //    gather its G-buffer and layers, convert them to BF16 and write the
-//    shared-memory A operands, running up to two layer slots ahead.
+//    shared-memory A operands, running up to two layer slots ahead.  With
+//    positional encoding there are four loader warps (9-12, 32 rows each)
+//    that also compute the encoded bands (13 warps).
 //
 // Layer-slot pipeline.  Three TMEM accumulator buffers rotate over the global
 // sequence of layer slots: phi1(k) writes buffer k mod 3, the epilogue turns
@@ -128,13 +130,12 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, uint32_t a_tmem, uin
 
 // Layer k of the lane's rows: 12 channels each, zeros where the slot is not
 // valid.  Element offsets fit in 32 bits: the host requires 12 K h w < 2^31.
-__device__ __forceinline__ void load_slot(const FusedFrame& F, int k,
-                                          const uint32_t (&pix)[kRowsPerLoadLane],
-                                          const int (&cnt)[kRowsPerLoadLane],
-                                          float (&x)[kRowsPerLoadLane][kTC]) {
+template <int RPL>
+__device__ __forceinline__ void load_slot(const FusedFrame& F, int k, const uint32_t (&pix)[RPL],
+                                          const int (&cnt)[RPL], float (&x)[RPL][kTC]) {
   const uint32_t P = static_cast<uint32_t>(F.P);
 #pragma unroll
-  for (int i = 0; i < kRowsPerLoadLane; ++i) {
+  for (int i = 0; i < RPL; ++i) {
     const bool v = k < cnt[i];
     const uint32_t o = static_cast<uint32_t>(k) * kTC * P + pix[i];
 #pragma unroll
@@ -144,11 +145,11 @@ __device__ __forceinline__ void load_slot(const FusedFrame& F, int k,
 
 // Writes rows row0 + 32 i of a [2][128][8] bf16 operand: K entries 0..11 from
 // x, then the constant-one columns [1, 1, 0, 0].
-__device__ __forceinline__ void store_slot(uint32_t base, int row0,
-                                           const float (&x)[kRowsPerLoadLane][kTC]) {
+template <int RPL>
+__device__ __forceinline__ void store_slot(uint32_t base, int row0, const float (&x)[RPL][kTC]) {
   const uint32_t one = pack_bf16(1.0f, 1.0f);
 #pragma unroll
-  for (int i = 0; i < kRowsPerLoadLane; ++i) {
+  for (int i = 0; i < RPL; ++i) {
     const uint32_t r = base + static_cast<uint32_t>(row0 + 32 * i) * 16u;
     sts128(r, pack_bf16(x[i][0], x[i][1]), pack_bf16(x[i][2], x[i][3]), pack_bf16(x[i][4], x[i][5]),
            pack_bf16(x[i][6], x[i][7]));
@@ -214,15 +215,23 @@ __device__ __forceinline__ void pe_chunks(uint32_t a, const float (&v)[N], int n
 
 // Encoded layer operand: band 0 as store_slot writes it (channels 0-7, then
 // 8-11 and the constant-one pair), then the nf frequencies' sine and cosine
-// bands, one core-matrix column of channels at a time.
-__device__ __forceinline__ void store_slot_pe(uint32_t base, int row0,
-                                              const float (&x)[kRowsPerLoadLane][kTC], int nf) {
+// bands, one core-matrix column of channels at a time.  With one row per
+// lane the encoding's code stays small enough that the loaders do not evict
+// the epilogue's loops from the instruction cache (the same code unrolled
+// over two rows per lane measured 40 % slower), and four loader warps, one
+// per SM sub-partition, share the encoding work.
+template <int RPL>
+__device__ __forceinline__ void store_slot_pe(uint32_t base, int row0, const float (&x)[RPL][kTC],
+                                              int nf) {
+  static_assert(RPL == 1, "one row per loader lane with positional encoding");
   const uint32_t one = pack_bf16(1.0f, 1.0f);
+  {
+    const uint32_t r = base + static_cast<uint32_t>(row0) * 16u;
+    float lo[8], hi[4];
 #pragma unroll
-  for (int i = 0; i < kRowsPerLoadLane; ++i) {
-    const uint32_t r = base + static_cast<uint32_t>(row0 + 32 * i) * 16u;
-    const float lo[8] = {x[i][0], x[i][1], x[i][2], x[i][3], x[i][4], x[i][5], x[i][6], x[i][7]};
-    const float hi[4] = {x[i][8], x[i][9], x[i][10], x[i][11]};
+    for (int j = 0; j < 8; ++j) lo[j] = x[0][j];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hi[j] = x[0][8 + j];
     sts_chunk(r, lo);
     sts128(r + 2048u, pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), one, 0u);
     pe_chunks(r, lo, nf);
@@ -237,6 +246,16 @@ __device__ __forceinline__ void store_slot_pe(uint32_t base, int row0,
 // code in all three, so a streamed frame resolves to the same bits.
 enum : int { kModeFrame = 0, kModeAccumulate = 1, kModeResolve = 2 };
 
+// Warp counts: 2 loader warps (2 rows per lane), or 4 (1 row per lane) when
+// the loaders also encode the inputs.
+template <bool PE>
+struct Roles {
+  static constexpr int LW = PE ? 4 : kLoadWarps;
+  static constexpr int RPL = kTile / (LW * 32);
+  static constexpr int kThreads = (4 * kEW + 1 + LW) * 32;
+  static_assert(LW <= kMaxLoadWarps && RPL * LW * 32 == kTile, "loader rows must cover the tile");
+};
+
 // Loader warps: per tile, read the plan entries of their rows and publish the
 // slot count, then fill the layer operands slot by slot (two buffers, released
 // by the phi1 MMAs that read them) and B1's G-buffer operand (released by B1
@@ -246,9 +265,10 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
                                             uint32_t bar_base, LoaderShared& ls,
                                             volatile int* abort_flag, int li, int lane) {
   using L = FusedLayout<H, PE>;
+  constexpr int RPL = Roles<PE>::RPL, LW = Roles<PE>::LW;
   const int nf = PE ? prm.pe_freqs : 0;  // positional-encoding frequencies
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
-  const int row0 = li * 64 + lane;
+  const int row0 = li * (32 * RPL) + lane;
   uint32_t lc = 0, n_ag = 0;
   for (uint32_t tb = 0;; ++tb) {
     // Dynamic schedule: loader warp 0 takes the next tile from the global
@@ -272,12 +292,12 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     }
     const FusedFrame& F = frame_of(prm, tile);
     const uint32_t* ent = prm.plan + static_cast<size_t>(tile) * kTile;
-    uint32_t pix[kRowsPerLoadLane];
-    int cnt[kRowsPerLoadLane];
-    bool has[kRowsPerLoadLane];
+    uint32_t pix[RPL];
+    int cnt[RPL];
+    bool has[RPL];
     int cmax = 0;
 #pragma unroll
-    for (int i = 0; i < kRowsPerLoadLane; ++i) {
+    for (int i = 0; i < RPL; ++i) {
       const uint32_t e = __ldg(ent + row0 + 32 * i);
       has[i] = e != kPlanEmpty;
       pix[i] = has[i] ? (e & kPlanPixelMask) : 0u;
@@ -298,16 +318,18 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     if (lane == 0) mbar_arrive(bar(B_TILE + (tb & 1)));
     // the tile's slot count is the max over both loader warps
     if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
-    const int ns = max(ls.ns[tb & 1][0], ls.ns[tb & 1][1]);
+    int ns = 0;
+#pragma unroll
+    for (int w = 0; w < LW; ++w) ns = max(ns, ls.ns[tb & 1][w]);
     if (Mode == kModeResolve || (Mode == kModeAccumulate && ns > 0 && !prm.pool_fresh)) {
       // Streaming launches: the pool state of this warp's rows (row0 + 32 i:
       // 32 consecutive pixels, one 128-byte line in each of the tile's H/2 + H
       // planes) into L2 ahead of the epilogue's loads, for the lines that
       // hold a pixel whose state is read.
       const uint32_t* blk =
-          prm.pool_st + static_cast<size_t>(tile - F.tile0) * ((H / 2 + H) * kTile) + li * 64;
+          prm.pool_st + static_cast<size_t>(tile - F.tile0) * ((H / 2 + H) * kTile) + li * (32 * RPL);
 #pragma unroll
-      for (int i = 0; i < kRowsPerLoadLane; ++i) {
+      for (int i = 0; i < RPL; ++i) {
         if (!__any_sync(0xffffffffu, has[i] && cnt[i] > 0)) continue;
         for (int pl = lane; pl < H / 2 + H; pl += 32)
           asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + pl * kTile + 32 * i));
@@ -316,18 +338,16 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 
     // G-buffer block [g0..g13, 1, 1] of the lane's rows, loads in flight now
     // (accumulate launches run no B1)
-    // (with positional encoding they are loaded where they are used: the
-    // encoding's temporaries leave no registers to hold them over the slots)
-    float gv[kRowsPerLoadLane][kGC] = {};
+    float gv[RPL][kGC] = {};
     auto load_g = [&]() {
       const uint32_t P = static_cast<uint32_t>(F.P);
 #pragma unroll
-      for (int i = 0; i < kRowsPerLoadLane; ++i)
+      for (int i = 0; i < RPL; ++i)
 #pragma unroll
         for (int ch = 0; ch < kGC; ++ch)
           gv[i][ch] = has[i] ? __ldg(F.gbuf + (static_cast<uint32_t>(ch) * P + pix[i])) : 0.0f;
     };
-    if constexpr (Mode != kModeAccumulate && !PE) load_g();
+    if constexpr (Mode != kModeAccumulate) load_g();
     // The operand's release (B_AG_E) also paces the loaders: they are at most
     // one tile ahead, as the two tile-publication barriers need.  Accumulate
     // launches run no B1: there the MMA warp commits B_AG_E once per tile
@@ -336,19 +356,18 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
       if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
       if constexpr (Mode == kModeAccumulate) return true;
-      if constexpr (PE) load_g();
       const uint32_t one = pack_bf16(1.0f, 1.0f);
 #pragma unroll
-      for (int i = 0; i < kRowsPerLoadLane; ++i) {
+      for (int i = 0; i < RPL; ++i) {
         const uint32_t r = sbase + L::ag + static_cast<uint32_t>(row0 + 32 * i) * 16u;
-        sts128(r, pack_bf16(gv[i][0], gv[i][1]), pack_bf16(gv[i][2], gv[i][3]),
-               pack_bf16(gv[i][4], gv[i][5]), pack_bf16(gv[i][6], gv[i][7]));
-        sts128(r + 2048u, pack_bf16(gv[i][8], gv[i][9]), pack_bf16(gv[i][10], gv[i][11]),
-               pack_bf16(gv[i][12], gv[i][13]), one);
+        const float (&g)[kGC] = gv[i];
+        sts128(r, pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
+               pack_bf16(g[6], g[7]));
+        sts128(r + 2048u, pack_bf16(g[8], g[9]), pack_bf16(g[10], g[11]), pack_bf16(g[12], g[13]),
+               one);
         if constexpr (PE) {
-          const float lo[8] = {gv[i][0], gv[i][1], gv[i][2], gv[i][3],
-                               gv[i][4], gv[i][5], gv[i][6], gv[i][7]};
-          const float hi[6] = {gv[i][8], gv[i][9], gv[i][10], gv[i][11], gv[i][12], gv[i][13]};
+          const float lo[8] = {g[0], g[1], g[2], g[3], g[4], g[5], g[6], g[7]};
+          const float hi[6] = {g[8], g[9], g[10], g[11], g[12], g[13]};
           pe_chunks(r, lo, nf);
           pe_chunks(r + 2048u, hi, nf);
         }
@@ -359,7 +378,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
       return true;
     };
 
-    float x[kRowsPerLoadLane][kTC], y[kRowsPerLoadLane][kTC];
+    float x[RPL][kTC], y[RPL][kTC];
     if (ns > 0) load_slot(F, 0, pix, cnt, x);
     const int ag_after = min(ns, 2) - 1;  // B1's operand after the first slots
     if (ag_after < 0 && !put_ag()) return;
@@ -376,7 +395,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
       if (lane == 0) mbar_arrive(bar(B_AT_F + b));
       if (k == ag_after && !put_ag()) return;
 #pragma unroll
-      for (int i = 0; i < kRowsPerLoadLane; ++i)
+      for (int i = 0; i < RPL; ++i)
 #pragma unroll
         for (int ch = 0; ch < kTC; ++ch) x[i][ch] = y[i][ch];
     }
@@ -391,7 +410,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 // PE: the inputs are positionally encoded (H = 64 layout, 1 + 2 pe_freqs
 // bands of 16 K columns in phi1's and B1's first operands).
 template <int H, int Mode, bool Sum, bool PE>
-__global__ void __launch_bounds__(kThreadsF, 1)
+__global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   static_assert(!Sum || Mode != kModeAccumulate, "accumulation does not depend on the pooling");
   using L = FusedLayout<H, PE>;
@@ -415,13 +434,13 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     mbar_init(bar(B_W), 1);
     mbar_init(bar(B_DP), 1);
     mbar_init(bar(B_DR2), 1);
-    mbar_init(bar(B_AG_F), kLoadWarps);
+    mbar_init(bar(B_AG_F), Roles<PE>::LW);
     mbar_init(bar(B_AG_E), 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(bar(B_IN + b), kEpiWarps);
-      mbar_init(bar(B_AT_F + b), kLoadWarps);
+      mbar_init(bar(B_AT_F + b), Roles<PE>::LW);
       mbar_init(bar(B_AT_E + b), 1);
-      mbar_init(bar(B_TILE + b), kLoadWarps);
+      mbar_init(bar(B_TILE + b), Roles<PE>::LW);
       mbar_init(bar(B_SCHED + b), 1);
       mbar_init(bar(B_H + b), kEpiWarps);
     }
@@ -444,7 +463,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 
   if (warp >= kLoadWarp0) {
     // the constant [1, 1, 0, ...] operand that multiplies phi2's bias rows
-    for (int r = (warp - kLoadWarp0) * 32 + lane; r < kTile; r += kLoadWarps * 32) {
+    for (int r = (warp - kLoadWarp0) * 32 + lane; r < kTile; r += Roles<PE>::LW * 32) {
       sts128(sbase + L::aone + r * 16u, pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
       sts128(sbase + L::aone + 2048u + r * 16u, 0u, 0u, 0u, 0u);
     }
@@ -528,7 +547,9 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     auto take_tile = [&](uint32_t t, int& tile, int& ns, const float*& fold) -> bool {
       if (!warp_wait(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
       tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
-      ns = max(s_ld.ns[t & 1][0], s_ld.ns[t & 1][1]);
+      ns = 0;
+#pragma unroll
+      for (int w = 0; w < Roles<PE>::LW; ++w) ns = max(ns, s_ld.ns[t & 1][w]);
       fold = tile < total_tiles ? s_ld.fold[t & 3] : nullptr;
       return true;
     };
@@ -684,7 +705,9 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       auto take_tile = [&](uint32_t t) -> bool {
         if (!warp_wait(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
         tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
-        ns = max(s_ld.ns[t & 1][0], s_ld.ns[t & 1][1]);
+        ns = 0;
+#pragma unroll
+      for (int w = 0; w < Roles<PE>::LW; ++w) ns = max(ns, s_ld.ns[t & 1][w]);
         c = s_ld.cnt[t & 1][row];
         return true;
       };
@@ -963,7 +986,7 @@ cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int
   // is still running; they wait on the grid dependency before the plan reads.
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreadsF);
+  cfg.blockDim = dim3(Roles<PE>::kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

@@ -18,7 +18,8 @@ constexpr int kEW = GN_FUSED_EW;
 constexpr int kEpiWarps = 4 * kEW;
 constexpr int kMmaWarp = 4 * kEW;
 constexpr int kLoadWarp0 = 4 * kEW + 1;
-constexpr int kLoadWarps = 2;
+constexpr int kLoadWarps = 2;      // loader warps of the FP8 kernel and the plain BF16 one
+constexpr int kMaxLoadWarps = 4;   // the BF16 kernel with positional encoding
 constexpr int kThreadsF = (4 * kEW + 3) * 32;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per device-side wait
 constexpr float kSumBase = 2048.0f;          // 2^11: quantum 2^-12 in [2^11, 2^12)
@@ -146,7 +147,7 @@ struct LoaderShared {
   float* out[4];
   const float* fold[4];
   int P[4];
-  int ns[2][kLoadWarps];
+  int ns[2][kMaxLoadWarps];
   int tile[2];
   uint8_t cnt[2][kTile];  // per tile parity: each row's layer count (0 for an empty row)
 };
