@@ -884,14 +884,15 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
 
         // rho -> r (zero without layers) -> lo;  B1 -> y -> hi;  B2 -> y2 -> lo;
         // R1 -> q -> hi.  Accumulators X, Y, X, Y.  Each layer in two passes of
-        // H/2 accumulator columns (this warp: H/4 of them), one arrival each.
+        // H/2 accumulator columns (this warp: H/(2 kEW) of them), one arrival each.
         gs += ns;
         const uint32_t r3 = gs % 3u;
         const uint32_t X = tl + T::buf(r3);
         const uint32_t Y = tl + T::buf(r3 == 2 ? 0 : r3 + 1);
         const uint32_t Z = tl + T::buf(r3 == 0 ? 2 : r3 - 1);
         const uint32_t A_LO = tl + T::APOOL, A_HI = tl + T::APOOL + H / 2;
-        constexpr int PC = H / 4;  // accumulator columns of this warp per pass
+        constexpr int PC = H / (2 * kEW);  // accumulator columns of this warp per pass
+        static_assert(PC % 16 == 0, "per-pixel passes load 16 accumulator columns at a time");
 #pragma unroll
         for (int l = Sum ? 1 : 0; l < 4; ++l) {
           if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
