@@ -17,6 +17,8 @@ from .glassnet_oracle import (  # noqa: F401
     post_pool_rho,
     final_blend_B,
     render_R,
+    render_R_frame,
+    r_kernel,
     render_pixel,
     render_pixel_sum,
     render_frame,

@@ -29,6 +29,14 @@ gamma_L(x) = [x ; sin(2^0 pi x) ; cos(2^0 pi x) ; ... ; sin(2^(L-1) pi x) ;
 cos(2^(L-1) pi x)], each block over all channels of x.  L = 0 (or no key)
 is the network above unchanged.
 
+Spatial R (Sec. 3.4: larger kernels in R before 1x1 kernels at its end): a
+weight set with ``weights["r_kernel"] = 3`` makes R's first layer a 3x3
+convolution over the frame's neural buffer y (the output of B, H channels per
+pixel): q(p) = ReLU(b + sum over (dy, dx) in {-1, 0, 1}^2 of
+W[:, :, dy + 1, dx + 1] y(p + (dy, dx))), cross-correlation with zero padding
+outside the frame; R1's weight is stored as [H][H * 9], the [out][in][3][3]
+kernel flattened.  R2 stays 1x1.  Only the frame path evaluates it.
+
 Every function below is pinned by ``tests/test_oracle_pins.py`` (hand-worked
 closed forms, brute force, invariants and library routines).
 """
@@ -145,6 +153,32 @@ def final_blend_B(weights, g, r, sigma) -> np.ndarray:
     return relu(linear(y, *weights["B2"]))
 
 
+def r_kernel(weights) -> int:
+    """Kernel size of R's first layer: 1 (per pixel) or 3 (over the frame)."""
+    return int(weights.get("r_kernel", 1))
+
+
+def render_R_frame(weights, Y) -> np.ndarray:
+    """R over a whole frame's neural buffer ``Y`` [h][w][H]; returns rgb [3][h][w].
+
+    R1 with a 3x3 kernel: each of the 9 taps (dy, dx) multiplies the buffer
+    shifted by (dy, dx), zero outside the frame; with a 1x1 kernel R is
+    ``render_R`` pixel by pixel.
+    """
+    Y = _f64(Y)
+    h, w, H = Y.shape
+    if r_kernel(weights) == 1:
+        return render_R(weights, Y).transpose(2, 0, 1)
+    W, b = _f64(weights["R1"][0]).reshape(-1, H, 3, 3), _f64(weights["R1"][1])
+    Yp = np.pad(Y, ((1, 1), (1, 1), (0, 0)))
+    acc = np.broadcast_to(b, (h, w, W.shape[0])).copy()
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            acc = acc + Yp[1 + dy:1 + dy + h, 1 + dx:1 + dx + w, :] @ W[:, :, dy + 1, dx + 1].T
+    q = relu(acc)
+    return sigmoid(linear(q, *weights["R2"])).transpose(2, 0, 1)
+
+
 def render_R(weights, y) -> np.ndarray:
     """Rendering network R (Sec. 3.4): rgb = sigmoid(R2 ReLU(R1 y + b) + b)."""
     q = relu(linear(y, *weights["R1"]))
@@ -157,8 +191,14 @@ def _layer_width(weights, sigma) -> int:
     return enc // (1 + 2 * pe_freqs(weights))
 
 
+def _per_pixel_R(weights) -> None:
+    if r_kernel(weights) != 1:
+        raise ValueError("a 3x3 R reads neighbouring pixels: use render_frame")
+
+
 def render_pixel(weights, sigma, g, layers) -> np.ndarray:
     """One pixel: ``g`` [n_g] opaque G-buffer, ``layers`` [c][n_t] valid layers."""
+    _per_pixel_R(weights)
     layers = _f64(layers).reshape(-1, _layer_width(weights, sigma))
     H = np.shape(weights["phi2"][0])[0]
     if layers.shape[0] == 0:
@@ -173,6 +213,7 @@ def render_pixel(weights, sigma, g, layers) -> np.ndarray:
 def render_pixel_sum(weights, sigma, g, layers) -> np.ndarray:
     """One pixel in the paper's form of Eq. 5: tau = sum_k h(b_k, sigma) enters
     B directly as [g ; tau ; sigma] (no rho; rho's weights are not used)."""
+    _per_pixel_R(weights)
     layers = _f64(layers).reshape(-1, _layer_width(weights, sigma))
     H = np.shape(weights["phi2"][0])[0]
     V = np.stack([per_layer_h(weights, layers[k], sigma) for k in range(layers.shape[0])]) \
@@ -187,6 +228,7 @@ def render_opaque_only(weights, sigma, gbuf_rows) -> np.ndarray:
     Written independently of ``render_pixel``: B1's columns that multiply r
     are dropped instead of multiplying a zero vector.  ``gbuf_rows`` is [P][n_g].
     """
+    _per_pixel_R(weights)
     W1, b1 = weights["B1"]
     W1 = _f64(W1)
     G = positional_encoding(gbuf_rows, pe_freqs(weights))
@@ -208,7 +250,8 @@ def render_frame(weights, scene, gbuf, tbuf, counts, chunk: int = 16384,
     ``k >= counts`` are never read into the result.  Pixels are processed in
     chunks only to bound memory; every pixel's arithmetic is the same as
     ``render_pixel`` (``pooling="max_mean"``) or ``render_pixel_sum``
-    (``pooling="sum"``, the paper's Eq. 5 form).
+    (``pooling="sum"``, the paper's Eq. 5 form), up to the neural buffer y;
+    R then runs on the whole frame's y (``render_R_frame``).
     """
     if pooling not in ("max_mean", "sum"):
         raise ValueError(f"pooling must be 'max_mean' or 'sum', got {pooling!r}")
@@ -220,7 +263,7 @@ def render_frame(weights, scene, gbuf, tbuf, counts, chunk: int = 16384,
     T = np.asarray(tbuf).reshape(K, n_t, P)
     C = np.asarray(counts).reshape(P).astype(np.int64)
     H = np.shape(weights["phi2"][0])[0]
-    out = np.empty((3, P))
+    Y = np.empty((P, H))
     for p0 in range(0, P, chunk):
         p1 = min(P, p0 + chunk)
         n = p1 - p0
@@ -246,9 +289,8 @@ def render_frame(weights, scene, gbuf, tbuf, counts, chunk: int = 16384,
             if np.any(has):
                 pool = np.concatenate([mx[has], s[has] / c[has][:, None]], axis=1)
                 r[has] = post_pool_rho(weights, pool)
-        y = final_blend_B(weights, _f64(G[:, p0:p1]).T, r, sigma)
-        out[:, p0:p1] = render_R(weights, y).T
-    return out.reshape(3, h, w)
+        Y[p0:p1] = final_blend_B(weights, _f64(G[:, p0:p1]).T, r, sigma)
+    return render_R_frame(weights, Y.reshape(h, w, H))
 
 
 def alpha_blend(colors, alphas) -> np.ndarray:

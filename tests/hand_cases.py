@@ -111,3 +111,24 @@ LOGITS_PE_TWO_LAYERS = np.array([-16.5, 16.5, 1.0])
 LOGITS_PE_NO_LAYER = np.array([1.0, 1.0, -1.0])
 LOGITS_PE_SUM_ONE_LAYER = np.array([9.0, 0.0, -8.0])
 LOGITS_PE_SUM_TWO_LAYERS = np.array([12.0, 0.0, -11.0])
+
+# Spatial R: R1 as a 3x3 kernel over the neural buffer y (B's output) of a
+# 2x2 frame, the network W otherwise.  Pixels: (0,0) layer A -> y = [7, 6];
+# (0,1) layers A, B -> [3, 5]; (1,0) no layer -> [3, 1]; (1,1) B, A -> [3, 5].
+# Kernel [out][in][ky][kx] (tap (dy, dx) at [dy + 1][dx + 1]):
+#   out 0 = in 0 at the centre + in 1 of the right neighbour
+#   out 1 = in 0 of the neighbour below - in 1 at the centre, bias 3
+#   (0,0): [7 + 5, 3 - 6 + 3] = [12, 0]     (0,1): [3 + 0, 3 - 5 + 3] = [3, 1]
+#   (1,0): [3 + 5, 0 - 1 + 3] = [8, 2]      (1,1): [3 + 0, 0 - 5 + 3] -> [3, 0]
+#   R2 (as W): [12, 0, -11];  [2, 1, -2];  [6, 2, -7];  [3, 0, -2]
+_K3 = np.zeros((2, 2, 3, 3), np.float32)
+_K3[0, 0, 1, 1] = 1
+_K3[0, 1, 1, 2] = 1
+_K3[1, 0, 2, 1] = 1
+_K3[1, 1, 1, 1] = -1
+W_R3 = dict(W)
+W_R3["R1"] = (_K3.reshape(2, 18), np.array([0, 3], np.float32))
+W_R3["r_kernel"] = 3
+LOGITS_R3 = np.array([[[12.0, 2.0], [6.0, 3.0]],
+                      [[0.0, 1.0], [2.0, 0.0]],
+                      [[-11.0, -2.0], [-7.0, -2.0]]])  # [3][h][w]

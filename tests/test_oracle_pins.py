@@ -592,6 +592,140 @@ def test_planted_pe_mistake_is_caught(monkeypatch, label):
     assert not _pe_pins_pass(O), label
 
 
+# -------------------------------------------- spatial R (3x3 first layer)
+
+def _r3_frame():
+    counts = np.array([[1, 2], [0, 2]], np.uint8)
+    gbuf = np.broadcast_to(hc.G[:, None, None], (2, 2, 2)).copy()
+    tbuf = np.full((2, 2, 2, 2), np.nan, np.float32)
+    tbuf[0, :, 0, 0] = hc.LAYER_A
+    tbuf[0, :, 0, 1] = hc.LAYER_A
+    tbuf[1, :, 0, 1] = hc.LAYER_B
+    tbuf[0, :, 1, 1] = hc.LAYER_B
+    tbuf[1, :, 1, 1] = hc.LAYER_A
+    return gbuf, tbuf, counts
+
+
+def test_hand_r3_frame():
+    gbuf, tbuf, counts = _r3_frame()
+    rgb = O.render_frame(hc.W_R3, hc.SCENE, gbuf, tbuf, counts)
+    np.testing.assert_allclose(rgb, expit(hc.LOGITS_R3), rtol=1e-13)
+
+
+def test_r3_per_pixel_paths_refuse():
+    with pytest.raises(ValueError):
+        O.render_pixel(hc.W_R3, hc.SIGMA, hc.G, np.zeros((0, 2)))
+
+
+def _r3_weights(seed=7, H=8, Z=6, center_only=False):
+    w = synth.make_weights(synth.Widths(hidden=H, latent=Z), seed=seed, bias="uniform")
+    rng = np.random.default_rng(seed + 100)
+    if center_only:
+        K = np.zeros((H, H, 3, 3), np.float32)
+        K[:, :, 1, 1] = w["R1"][0]
+    else:
+        K = (rng.standard_normal((H, H, 3, 3)) * 0.3).astype(np.float32)
+    w3 = dict(w)
+    w3["R1"] = (K.reshape(H, H * 9), w["R1"][1])
+    w3["r_kernel"] = 3
+    return w, w3, K
+
+
+def test_r3_with_centre_tap_only_is_the_1x1_network():
+    w, w3, _ = _r3_weights(center_only=True)
+    scene = synth.make_scene(2)
+    f = synth.make_frame(5, 7, 3, counts="uniform", seed=3)
+    np.testing.assert_allclose(O.render_frame(w3, scene, f.gbuf, f.tbuf, f.counts),
+                               O.render_frame(w, scene, f.gbuf, f.tbuf, f.counts), rtol=1e-13, atol=1e-15)
+
+
+def test_r3_matches_torch_conv2d_cross_correlation():
+    """torch's conv2d (cross-correlation, zero padding 1), FP64 on the CPU."""
+    torch = pytest.importorskip("torch")
+    _, w3, K = _r3_weights()
+    rng = np.random.default_rng(4)
+    Y = rng.random((6, 9, 8))
+    b = np.float64(w3["R1"][1])
+    ref = torch.nn.functional.conv2d(torch.from_numpy(Y.transpose(2, 0, 1)[None]),
+                                     torch.from_numpy(np.float64(K)), torch.from_numpy(b), padding=1)
+    q = np.maximum(ref[0].numpy().transpose(1, 2, 0), 0)
+    W2, b2 = (np.float64(a) for a in w3["R2"])
+    exp = (1 / (1 + np.exp(-(q @ W2.T + b2)))).transpose(2, 0, 1)
+    np.testing.assert_allclose(O.render_R_frame(w3, Y), exp, rtol=1e-12, atol=1e-15)
+
+
+def test_r3_brute_force_loops():
+    _, w3, K = _r3_weights(seed=9, H=4)
+    rng = np.random.default_rng(5)
+    h, wd, H = 3, 4, 4
+    Y = rng.standard_normal((h, wd, H))
+    b = np.float64(w3["R1"][1])
+    W2, b2 = (np.float64(a) for a in w3["R2"])
+    out = np.zeros((3, h, wd))
+    for y in range(h):
+        for x in range(wd):
+            q = [float(b[o]) for o in range(H)]
+            for o in range(H):
+                for i in range(H):
+                    for ky in range(3):
+                        for kx in range(3):
+                            yy, xx = y + ky - 1, x + kx - 1
+                            if 0 <= yy < h and 0 <= xx < wd:
+                                q[o] += float(K[o, i, ky, kx]) * Y[yy, xx, i]
+            q = [max(v, 0.0) for v in q]
+            for c in range(3):
+                z = float(b2[c]) + sum(float(W2[c, i]) * q[i] for i in range(H))
+                out[c, y, x] = 1 / (1 + math.exp(-z))
+    np.testing.assert_allclose(O.render_R_frame(w3, Y), out, rtol=1e-12)
+
+
+def _r3_pins_pass(mod):
+    try:
+        gbuf, tbuf, counts = _r3_frame()
+        rgb = mod.render_frame(hc.W_R3, hc.SCENE, gbuf, tbuf, counts)
+        return bool(np.allclose(rgb, expit(hc.LOGITS_R3), rtol=1e-12, atol=0))
+    except Exception:
+        return False
+
+
+def _r3_variant(kind):
+    def f(weights, Y):
+        Y = np.float64(Y)
+        h, wd, H = Y.shape
+        if O.r_kernel(weights) == 1:
+            return O.render_R(weights, Y).transpose(2, 0, 1)
+        flat = np.float64(weights["R1"][0])
+        W = flat.reshape(-1, 9, H).transpose(0, 2, 1).reshape(-1, H, 3, 3) if kind == "tap_major" \
+            else flat.reshape(-1, H, 3, 3)
+        if kind == "flipped":
+            W = W[:, :, ::-1, ::-1]
+        if kind == "transposed":
+            W = W.transpose(0, 1, 3, 2)
+        Yp = np.pad(Y, ((1, 1), (1, 1), (0, 0)), mode="edge" if kind == "edge" else "constant")
+        acc = np.broadcast_to(np.float64(weights["R1"][1]), (h, wd, W.shape[0])).copy()
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                acc = acc + Yp[1 + dy:1 + dy + h, 1 + dx:1 + dx + wd, :] @ W[:, :, dy + 1, dx + 1].T
+        return O.sigmoid(O.linear(O.relu(acc), *weights["R2"])).transpose(2, 0, 1)
+    return f
+
+
+R3_MUTATIONS = ["flipped", "edge", "transposed", "tap_major"]
+
+
+def test_unmutated_oracle_passes_r3_pins():
+    assert _r3_pins_pass(O)
+    # the reference re-implementation used for the mutations agrees when unmutated
+    Y = np.random.default_rng(1).random((3, 4, 2))
+    np.testing.assert_allclose(_r3_variant("none")(hc.W_R3, Y), O.render_R_frame(hc.W_R3, Y), rtol=1e-14)
+
+
+@pytest.mark.parametrize("kind", R3_MUTATIONS)
+def test_planted_r3_mistake_is_caught(monkeypatch, kind):
+    monkeypatch.setattr(O, "render_R_frame", _r3_variant(kind))
+    assert not _r3_pins_pass(O), kind
+
+
 def test_mean_instead_of_sum_is_caught():
     """A tau that divides by the count (the mean) fails the two-layer hand pin."""
     sigma = O.scene_encoder(hc.W, hc.SCENE)
