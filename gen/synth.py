@@ -40,13 +40,15 @@ OUT_CHANNELS = 3
 
 @dataclass(frozen=True)
 class Widths:
-    """Hidden width H and latent width Z of the per-pixel network, and the
+    """Hidden width H and latent width Z of the per-pixel network, the
     frequency count L of the inputs' positional encoding (0: none), which
-    widens every input block of n channels to n (1 + 2L)."""
+    widens every input block of n channels to n (1 + 2L), and the kernel size
+    of R's first layer (1, or 3 over the frame: R1 is then [H][9 H])."""
 
     hidden: int
     latent: int
     pe_freqs: int = 0
+    r_kernel: int = 1
 
 
 BASE_WIDTHS = Widths(hidden=64, latent=128)
@@ -70,7 +72,7 @@ def weight_shapes(widths: Widths) -> dict[str, tuple[int, int]]:
         "rho": (H, 2 * H),
         "B1": (H, GBUF_CHANNELS * e + H + Z),
         "B2": (H, H),
-        "R1": (H, H),
+        "R1": (H, H * widths.r_kernel ** 2),
         "R2": (OUT_CHANNELS, H),
     }
 
@@ -82,7 +84,8 @@ def make_weights(widths: Widths, seed: int = 0, bias: str = "zero") -> dict:
     standard normal scaled by its std; then, if ``bias == "uniform"``, every b
     in the same order from U[-0.1, 0.1].  ``bias == "zero"`` gives zero biases.
     Values are drawn in float64 and stored as float32.  With positional
-    encoding the dict also holds ``"pe_freqs": L``.
+    encoding the dict also holds ``"pe_freqs": L``, with a 3x3 R
+    ``"r_kernel": 3``.
     """
     if bias not in ("zero", "uniform"):
         raise ValueError(f"bias must be 'zero' or 'uniform', got {bias!r}")
@@ -103,6 +106,8 @@ def make_weights(widths: Widths, seed: int = 0, bias: str = "zero") -> dict:
     res = {k: (v[0], v[1]) for k, v in out.items()}
     if widths.pe_freqs:
         res["pe_freqs"] = widths.pe_freqs
+    if widths.r_kernel != 1:
+        res["r_kernel"] = widths.r_kernel
     return res
 
 

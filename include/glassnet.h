@@ -129,11 +129,18 @@ typedef struct gn_model_config {
    * (blocks of n, in that order), so F1, phi1 and B1 are wider:
    *   F1 [Z][32 e]   phi1 [H][12 e + Z]   B1 [H][14 e + H + Z],  e = 1 + 2L. */
   int pe_freqs;
+  /* Kernel size of R's first layer (Sec. 3.4: larger kernels ahead of the
+   * 1x1 end of R): 1 (or 0) = per pixel; 3 = a 3x3 kernel over the frame's
+   * neural buffer y (B's output), q(p) = ReLU(b + sum over (dy, dx) in
+   * {-1,0,1}^2 of W[:, :, dy+1, dx+1] y(p + (dy, dx))), y = 0 outside the
+   * frame.  R1 is then stored as [H][9 H], the [out][in][3][3] kernel
+   * flattened (column k 9 + (dy+1) 3 + dx+1).  R2 stays 1x1. */
+  int r_kernel;
 } gn_model_config;
 
 /*
  * As glassnet_load_weights, for the form in `config`;
- * glassnet_load_weights is this call with {precision, GN_POOL_MAX_MEAN, 0}.
+ * glassnet_load_weights is this call with {precision, GN_POOL_MAX_MEAN, 0, 1}.
  * The blob's payload must hold the widths of that form (the header's H and Z
  * with pe_freqs), else GN_EFORMAT.
  * Pooling: a GN_POOL_SUM network has no rho; its blob keeps the rho tensor
@@ -151,8 +158,15 @@ typedef struct gn_model_config {
  * GN_POOL_SUM and pe_freqs > 0 serve every render, batch, graph, server and
  * streaming call of GN_FP32_PLAIN / GN_BF16_FUSED models; with GN_FP8_FUSED
  * they return GN_EUNSUPPORTED.
+ * r_kernel = 3 serves glassnet_render, glassnet_render_ws and
+ *   glassnet_render_host of GN_FP32_PLAIN and GN_BF16_FUSED models (any
+ *   pooling; with pe_freqs as above): the fused kernel writes the neural
+ *   buffer (BF16, H 2 bytes per pixel, in the render's workspace, so
+ *   glassnet_workspace_bytes grows by about h w H 2 bytes), then a tcgen05
+ *   kernel runs the 3x3 layer, R2 and the sigmoid.  Batched, graph, server
+ *   and streaming calls and GN_FP8_FUSED return GN_EUNSUPPORTED.
  * Errors: those of glassnet_load_weights, GN_EINVAL (NULL config, unknown
- * pooling, pe_freqs outside 0..10), GN_EUNSUPPORTED.
+ * pooling, pe_freqs outside 0..10, r_kernel not 0, 1 or 3), GN_EUNSUPPORTED.
  */
 int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_config* config,
                              gn_model** out);

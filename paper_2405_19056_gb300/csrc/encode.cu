@@ -11,12 +11,13 @@
 
 namespace gn {
 
-void WeightIndex::build(int H_, int Z_, int L_) {
+void WeightIndex::build(int H_, int Z_, int L_, int RK_) {
   H = H_;
   Z = Z_;
   L = L_;
+  RK = RK_;
   const int o[kLayers] = {Z, Z, H, H, H, H, H, H, kOut};
-  const int i[kLayers] = {sc_enc(), Z, tc_enc() + Z, H, 2 * H, gc_enc() + H + Z, H, H, H};
+  const int i[kLayers] = {sc_enc(), Z, tc_enc() + Z, H, 2 * H, gc_enc() + H + Z, H, H * RK * RK, H};
   size_t at = 0;
   for (int l = 0; l < kLayers; ++l) {
     out[l] = o[l];

@@ -409,10 +409,14 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 // bit-identical under any order of the layers; the max is not kept.
 // PE: the inputs are positionally encoded (H = 64 layout, 1 + 2 pe_freqs
 // bands of 16 K columns in phi1's and B1's first operands).
-template <int H, int Mode, bool Sum, bool PE>
+// R3: R's first layer is a 3x3 kernel over the frame (conv_r3.cu): the tile
+// ends after B2 and writes the neural buffer y (BF16, layout
+// [y][H/8][x][8] per frame) to device memory instead of running R.
+template <int H, int Mode, bool Sum, bool PE, bool R3>
 __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   static_assert(!Sum || Mode != kModeAccumulate, "accumulation does not depend on the pooling");
+  static_assert(!R3 || Mode == kModeFrame, "the 3x3 R runs on whole frames");
   using L = FusedLayout<H, PE>;
   using T = TMap<H>;
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
@@ -648,6 +652,13 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
         issue_gemm<H, H / 2>(X, A_HI + H / 4, dsc_b2 + kHalfK, idH, true);
         mma_commit_e(bar(B_DP));
         __syncwarp();
+        if constexpr (R3) {
+          // y goes to device memory: the epilogue's B2 passes arrive as they
+          // would for R1 (X is read before the next tile's phi1 writes it)
+          if (!wait_h(0) || !wait_h(1)) goto done;
+          mma_commit_e(bar(B_DR2));
+          __syncwarp();
+        } else {
         if (!wait_h(0)) goto done;
         issue_gemm<H, H / 2>(Y, A_LO, dsc_r1, idH);
         if (!wait_h(1)) goto done;
@@ -658,6 +669,7 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
         issue_gemm<16, H>(Z, A_HI, dsc_r2, id16);
         mma_commit_e(bar(B_DR2));
         __syncwarp();
+        }  // R1, R2
       }
       // the next tile's first two phi1 right behind R2 (they write X and Y)
       tile = next_tile;
@@ -879,8 +891,22 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
 
         // the row's plan entry (pixel index) for the store, loaded while the
         // per-pixel layers run
-        const uint32_t ent =
-            g == 0 ? __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row) : kPlanEmpty;
+        const uint32_t ent = (g == 0 || R3)
+                                 ? __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row)
+                                 : kPlanEmpty;
+        // 3x3 R: this row's pixel in the neural buffer (chunk c of 8 channels
+        // at phi_px + c w)
+        uint4* phi_px = nullptr;
+        uint32_t fw = 0;
+        if constexpr (R3) {
+          fw = static_cast<uint32_t>(prm.f[0].w);
+          if (ent != kPlanEmpty) {
+            const uint32_t pix = ent & kPlanPixelMask;
+            const uint32_t py = pix / fw;
+            phi_px = reinterpret_cast<uint4*>(prm.f[0].phi) + static_cast<size_t>(py) * (H / 8) * fw +
+                     (pix - py * fw);
+          }
+        }
 
         // rho -> r (zero without layers) -> lo;  B1 -> y -> hi;  B2 -> y2 -> lo;
         // R1 -> q -> hi.  Accumulators X, Y, X, Y.  Each layer in two passes of
@@ -894,7 +920,7 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
         constexpr int PC = H / (2 * kEW);  // accumulator columns of this warp per pass
         static_assert(PC % 16 == 0, "per-pixel passes load 16 accumulator columns at a time");
 #pragma unroll
-        for (int l = Sum ? 1 : 0; l < 4; ++l) {
+        for (int l = Sum ? 1 : 0; l < (R3 ? 3 : 4); ++l) {
           if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
           ++n_dp;
           tc_fence_after();
@@ -926,7 +952,15 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
                   u[i] = (l == 0 && c == 0) ? 0u : pack_bf16_relu(v0, v1);
                 }
               }
-              tmem_st8(dst + c0 / 2 + hh * 8, u);
+              if (R3 && l == 2) {  // y -> the neural buffer
+                if (phi_px) {
+                  const size_t c8 = static_cast<size_t>(c0 + hh * 16) / 8;
+                  phi_px[c8 * fw] = make_uint4(u[0], u[1], u[2], u[3]);
+                  phi_px[(c8 + 1) * fw] = make_uint4(u[4], u[5], u[6], u[7]);
+                }
+              } else {
+                tmem_st8(dst + c0 / 2 + hh * 8, u);
+              }
               if (hh + 1 < PC / 16) tmem_wait_ld_tied(nxt);
             }
             arrive_h(h);
@@ -938,7 +972,7 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
         // tile is taken first.
         if (!take_tile(tb + 1)) goto done;
         if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
-        if (g == 0) {
+        if (!R3 && g == 0) {
           tc_fence_after();
           uint32_t r[4];
           tmem_ld4(Z, r);
@@ -967,21 +1001,21 @@ done:
   }
 }
 
-template <int H, int Mode, bool Sum, bool PE>
+template <int H, int Mode, bool Sum, bool PE, bool R3 = false>
 cudaError_t prepare_h() {
   static bool done = false;  // per process: the attribute holds for every later launch
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, Mode, Sum, PE>,
+  cudaError_t e = cudaFuncSetAttribute(fused_bf16_kernel<H, Mode, Sum, PE, R3>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FusedLayout<H, PE>::smem_bytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <int H, int Mode, bool Sum, bool PE>
+template <int H, int Mode, bool Sum, bool PE, bool R3 = false>
 cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
   constexpr int smem = FusedLayout<H, PE>::smem_bytes;
-  cudaError_t e = prepare_h<H, Mode, Sum, PE>();
+  cudaError_t e = prepare_h<H, Mode, Sum, PE, R3>();
   if (e != cudaSuccess) return e;
   // Programmatic dependent launch: the CTAs may start while the plan kernel
   // is still running; they wait on the grid dependency before the plan reads.
@@ -995,7 +1029,7 @@ cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H, Mode, Sum, PE>, p,
+  return cudaLaunchKernelEx(&cfg, fused_bf16_kernel<H, Mode, Sum, PE, R3>, p,
                             static_cast<const uint8_t*>(wimg));
 }
 
@@ -1006,6 +1040,8 @@ cudaError_t prepare_all() {
   if (e == cudaSuccess) e = prepare_h<H, kModeResolve, false, PE>();
   if (e == cudaSuccess) e = prepare_h<H, kModeFrame, true, PE>();
   if (e == cudaSuccess) e = prepare_h<H, kModeResolve, true, PE>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeFrame, false, PE, true>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeFrame, true, PE, true>();
   return e;
 }
 
@@ -1014,6 +1050,11 @@ cudaError_t launch_mode(int mode, const void* wimg, const FusedParams& p, cudaSt
                         int grid) {
   // accumulation is the same for both poolings (the state holds max and sum)
   if (mode == kModeAccumulate) return launch_h<H, kModeAccumulate, false, PE>(wimg, p, s, grid);
+  if (p.f[0].phi) {  // the neural buffer out, for the 3x3 R (whole frames only)
+    if (mode != kModeFrame || p.nframes != 1) return cudaErrorInvalidValue;
+    return p.pool_sum ? launch_h<H, kModeFrame, true, PE, true>(wimg, p, s, grid)
+                      : launch_h<H, kModeFrame, false, PE, true>(wimg, p, s, grid);
+  }
   if (p.pool_sum)
     return mode == kModeResolve ? launch_h<H, kModeResolve, true, PE>(wimg, p, s, grid)
                                 : launch_h<H, kModeFrame, true, PE>(wimg, p, s, grid);

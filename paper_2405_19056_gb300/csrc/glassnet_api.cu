@@ -101,6 +101,31 @@ std::vector<uint8_t> pack_fused_bf16(const float* w, const gn::WeightIndex& wi) 
   return img;
 }
 
+// Image of the 3x3 R kernel (conv_r3.cu): per tap t = (dy + 1) 3 + dx + 1
+// the [H/8][H][8] BF16 B operand of W_R1[:, :, dy + 1, dx + 1] (the blob
+// stores R1 as [H][H 9], column k 9 + t), then R2 as [H/8][16][8] BF16, then
+// b_R1 [H] and b_R2 [16] in FP32.
+std::vector<uint8_t> pack_conv_r3(const float* w, const gn::WeightIndex& wi) {
+  const int H = wi.H;
+  std::vector<uint8_t> img(gn::conv_r3_image_bytes(H), 0);
+  const size_t tap_bytes = static_cast<size_t>(H) * H * 2;
+  auto put = [&](size_t off, int N, int n, int k, float v) {
+    uint16_t b = bf16_rne(v);
+    std::memcpy(img.data() + off + core_idx(N, n, k) * 2, &b, 2);
+  };
+  const float* W1 = w + wi.w[gn::LR1];
+  for (int t = 0; t < 9; ++t)
+    for (int n = 0; n < H; ++n)
+      for (int k = 0; k < H; ++k) put(t * tap_bytes, H, n, k, W1[static_cast<size_t>(n) * 9 * H + k * 9 + t]);
+  const size_t r2 = 9 * tap_bytes;
+  for (int n = 0; n < gn::kOut; ++n)
+    for (int k = 0; k < H; ++k) put(r2, 16, n, k, w[wi.w[gn::LR2] + static_cast<size_t>(n) * H + k]);
+  float* bias = reinterpret_cast<float*>(img.data() + r2 + static_cast<size_t>(H) * 16 * 2);
+  for (int n = 0; n < H; ++n) bias[n] = w[wi.b[gn::LR1] + n];
+  for (int n = 0; n < gn::kOut; ++n) bias[H + n] = w[wi.b[gn::LR2] + n];
+  return img;
+}
+
 // Round-to-nearest-even float -> E4M3 code (1 sign, 4 exponent bits with bias
 // 7, 3 mantissa bits; largest finite 448, no infinities), saturating to
 // +-448 (the satfinite rule).  NaN -> 0x7f.
@@ -227,7 +252,7 @@ extern "C" {
 const char* glassnet_last_error(void) { return g_last_error.c_str(); }
 
 int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_model** out) {
-  const gn_model_config cfg = {precision, GN_POOL_MAX_MEAN, 0};
+  const gn_model_config cfg = {precision, GN_POOL_MAX_MEAN, 0, 1};
   return glassnet_load_weights_ex(blob, nbytes, &cfg, out);
 }
 
@@ -236,6 +261,10 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_con
   if (!blob || !cfg || !out) return fail(GN_EINVAL, "blob, config and out must be non-NULL");
   *out = nullptr;
   const int precision = cfg->precision, pooling = cfg->pooling, pe = cfg->pe_freqs;
+  const int rk = cfg->r_kernel == 0 ? 1 : cfg->r_kernel;
+  if (rk != 1 && rk != 3) return fail(GN_EINVAL, "r_kernel %d is neither 1 nor 3", cfg->r_kernel);
+  if (precision == GN_FP8_FUSED && rk == 3)
+    return fail(GN_EUNSUPPORTED, "a 3x3 R is built for GN_FP32_PLAIN and GN_BF16_FUSED");
   if (precision != GN_FP32_PLAIN && precision != GN_BF16_FUSED && precision != GN_FP8_FUSED)
     return fail(GN_EINVAL, "unknown precision %d", precision);
   if (pooling != GN_POOL_MAX_MEAN && pooling != GN_POOL_SUM)
@@ -257,10 +286,11 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_con
                 hd.scene_dim, hd.tbuf_channels, hd.gbuf_channels, hd.out_channels);
   if (hd.hidden > 4096 || hd.latent > 4096) return fail(GN_EFORMAT, "implausible widths");
   gn::WeightIndex wi;
-  wi.build(static_cast<int>(hd.hidden), static_cast<int>(hd.latent), pe);
+  wi.build(static_cast<int>(hd.hidden), static_cast<int>(hd.latent), pe, rk);
   if (hd.payload_floats != wi.total)
-    return fail(GN_EFORMAT, "payload holds %llu floats, widths (%u, %u) with pe_freqs %d need %zu",
-                static_cast<unsigned long long>(hd.payload_floats), hd.hidden, hd.latent, pe,
+    return fail(GN_EFORMAT,
+                "payload holds %llu floats, widths (%u, %u) with pe_freqs %d, r_kernel %d need %zu",
+                static_cast<unsigned long long>(hd.payload_floats), hd.hidden, hd.latent, pe, rk,
                 wi.total);
   if (nbytes != sizeof(gn_blob_header) + wi.total * sizeof(float))
     return fail(GN_EFORMAT, "blob size %zu != %zu", nbytes,
@@ -326,6 +356,18 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_con
       glassnet_free_model(m);
       return cuda_fail(e, "upload packed weights");
     }
+    if (rk == 3) {
+      std::vector<uint8_t> cimg = pack_conv_r3(w.data(), wi);
+      if ((e = cudaMalloc(&m->conv, cimg.size())) != cudaSuccess) {
+        glassnet_free_model(m);
+        return fail(GN_ENOMEM, "cudaMalloc 3x3 R weights: %s", cudaGetErrorString(e));
+      }
+      if ((e = cudaMemcpy(m->conv, cimg.data(), cimg.size(), cudaMemcpyHostToDevice)) !=
+          cudaSuccess) {
+        glassnet_free_model(m);
+        return cuda_fail(e, "upload 3x3 R weights");
+      }
+    }
   }
   *out = m;
   return GN_OK;
@@ -344,6 +386,7 @@ int glassnet_model_config(const gn_model* m, gn_model_config* cfg) {
   cfg->precision = m->precision;
   cfg->pooling = m->pooling;
   cfg->pe_freqs = m->wi.L;
+  cfg->r_kernel = m->wi.RK;
   return GN_OK;
 }
 
@@ -401,12 +444,21 @@ int glassnet_latent_read(const gn_latent* lat, float* sigma, float* c_phi, float
   return GN_OK;
 }
 
+namespace {
+// The BF16 neural buffer of a 3x3 R render: [h][H/8][w][8], 256-byte rounded.
+size_t phi_bytes(const gn_model* m, int h, int w) {
+  return (static_cast<size_t>(h) * w * m->H * 2 + 255) / 256 * 256;
+}
+}  // namespace
+
 int glassnet_workspace_bytes(const gn_model* m, int K, int h, int w, size_t* bytes) {
   if (!m || !bytes) return fail(GN_EINVAL, "model and bytes must be non-NULL");
   if (K < 0 || K > gn::kMaxK || h < 1 || w < 1) return fail(GN_EINVAL, "bad frame size");
   const long long tiles = (static_cast<long long>(h) * w + gn::kTile - 1) / gn::kTile;
   *bytes = m->precision == GN_FP32_PLAIN ? gn::plain_workspace_bytes(m->H, K, h * w)
                                          : gn::fused_plan_bytes(tiles);
+  if (m->precision != GN_FP32_PLAIN && m->wi.RK == 3)  // plan, then the neural buffer
+    *bytes = (*bytes + 255) / 256 * 256 + phi_bytes(m, h, w);
   return GN_OK;
 }
 
@@ -447,6 +499,8 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
   if (n < 1 || n > kMaxBatch) return fail(GN_EINVAL, "batch of %d frames outside 1..%d", n, kMaxBatch);
   if (m->precision == GN_FP32_PLAIN)
     return fail(GN_EUNSUPPORTED, "batched launch needs a fused precision");
+  if (m->wi.RK == 3)
+    return fail(GN_EUNSUPPORTED, "a 3x3 R renders one frame per call (glassnet_render)");
   if (m->precision == GN_FP8_FUSED && !m->fp8_ready)
     return fail(GN_EINVAL, "FP8 model is not calibrated (glassnet_calibrate_fp8)");
   FusedParams& p = *out;
@@ -482,7 +536,9 @@ cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s
 }
 
 cudaError_t prepare_fused(const gn_model* m) {
-  return m->precision == GN_FP8_FUSED ? prepare_fused_fp8(m->H) : prepare_fused_bf16(m->H);
+  if (m->precision == GN_FP8_FUSED) return prepare_fused_fp8(m->H);
+  cudaError_t e = prepare_fused_bf16(m->H);
+  return e == cudaSuccess && m->wi.RK == 3 ? prepare_conv_r3(m->H) : e;
 }
 
 void bind_plan(FusedParams& p, void* ws) {
@@ -508,7 +564,7 @@ int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbu
     if (reinterpret_cast<uintptr_t>(ws) & 255u)
       return fail(GN_EINVAL, "workspace must be 256-byte aligned");
     e = gn::launch_plain_fp32(m->w32, m->wi, lat->d, gbuf, tbuf, cnt, K, P, out, ws, m->err, s,
-                              m->pooling == GN_POOL_SUM);
+                              m->pooling == GN_POOL_SUM, w);
     if (e != cudaSuccess) return cuda_fail(e, "FP32 plain launch");
     return GN_OK;
   }
@@ -520,14 +576,25 @@ int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbu
   p.err = m->err;
   p.f[0] = gn::FusedFrame{gbuf, tbuf, cnt, out, lat->fold(), K, P, 0, 0};
   number_tiles(p);
-  const size_t need = gn::fused_plan_bytes(p.total_tiles);
+  size_t need = 0;
+  glassnet_workspace_bytes(m, K, h, w, &need);
   if (!ws || ws_bytes < need)
     return fail(GN_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, need);
   if (reinterpret_cast<uintptr_t>(ws) & 255u)
     return fail(GN_EINVAL, "workspace must be 256-byte aligned");
   gn::bind_plan(p, ws);
+  uint16_t* phi = nullptr;
+  if (m->wi.RK == 3) {  // the fused kernel stops at the neural buffer, the 3x3 R follows
+    phi = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(ws) + need - phi_bytes(m, h, w));
+    p.f[0].phi = phi;
+    p.f[0].w = w;
+  }
   e = gn::launch_fused(m, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+  if (phi) {
+    e = gn::launch_conv_r3(m->H, m->conv, phi, out, h, w, m->err, s);
+    if (e != cudaSuccess) return cuda_fail(e, "3x3 R launch");
+  }
   return GN_OK;
 }
 
@@ -620,7 +687,8 @@ int glassnet_calibrate_fp8(gn_model* m, const gn_latent* lat, const float* gbuf,
   float* out = static_cast<float*>(tmp);
   uint32_t* amax = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(tmp) + out_bytes);
   uint32_t bits[gn::kFp8Acts] = {};
-  e = gn::launch_plain_fp32(m->w32, m->wi, lat->d, gbuf, tbuf, cnt, K, P, out, m->ws, m->err, s);
+  e = gn::launch_plain_fp32(m->w32, m->wi, lat->d, gbuf, tbuf, cnt, K, P, out, m->ws, m->err, s,
+                            0, w);
   if (e == cudaSuccess)
     e = gn::launch_fp8_act_amax(m->ws, gbuf, tbuf, cnt, m->H, K, P, amax, s);
   if (e == cudaSuccess)
@@ -730,8 +798,8 @@ int check_pool_call(const gn_model* m, const gn_latent* lat, const gn_pool* pool
   if (!m) return fail(GN_EINVAL, "model is NULL");
   if (!lat) return fail(GN_EINVAL, "latent is NULL");
   if (!pool) return fail(GN_EINVAL, "pool is NULL");
-  if (m->precision != GN_BF16_FUSED)
-    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model");
+  if (m->precision != GN_BF16_FUSED || m->wi.RK == 3)
+    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model with a 1x1 R");
   if (lat->H != m->H || lat->Z != m->Z)
     return fail(GN_EINVAL, "latent widths (%d, %d) do not match the model (%d, %d)", lat->H,
                 lat->Z, m->H, m->Z);
@@ -745,8 +813,8 @@ extern "C" {
 int glassnet_pool_create(const gn_model* m, int h, int w, gn_pool** out) {
   if (!m || !out) return fail(GN_EINVAL, "model and out must be non-NULL");
   *out = nullptr;
-  if (m->precision != GN_BF16_FUSED)
-    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model");
+  if (m->precision != GN_BF16_FUSED || m->wi.RK == 3)
+    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model with a 1x1 R");
   if (h < 1 || w < 1) return fail(GN_EINVAL, "frame %d x %d is empty", h, w);
   const long long P = static_cast<long long>(h) * w;
   if (P * gn::kTC >= (1ll << 31)) return fail(GN_EINVAL, "frame %d x %d too large", h, w);
@@ -834,6 +902,7 @@ void glassnet_free_model(gn_model* m) {
   if (m->fused) cudaFree(m->fused);
   if (m->err) cudaFree(m->err);
   if (m->ws) cudaFree(m->ws);
+  if (m->conv) cudaFree(m->conv);
   if (m->stage) cudaFree(m->stage);
   if (m->plan) cudaFree(m->plan);
   std::free(m->host_w);

@@ -41,6 +41,7 @@ constexpr int kMaxPeFreqsFused = 4;   // the fused BF16 kernel at H = 64
 // Offsets (in floats) of each W and b inside the concat-form f32 weights.
 struct WeightIndex {
   int H = 0, Z = 0, L = 0;  // L: positional-encoding frequencies (0: none)
+  int RK = 1;               // kernel size of R's first layer (1, or 3 over the frame)
   size_t w[kLayers] = {}, b[kLayers] = {};
   int out[kLayers] = {}, in[kLayers] = {};
   size_t total = 0;
@@ -48,7 +49,7 @@ struct WeightIndex {
   int tc_enc() const { return kTC * bands(); }     // encoded layer channels (phi1's first block)
   int gc_enc() const { return kGC * bands(); }     // encoded G-buffer channels (B1's first block)
   int sc_enc() const { return kScene * bands(); }  // encoded scene vector (F1's input)
-  void build(int H_, int Z_, int L_ = 0);
+  void build(int H_, int Z_, int L_ = 0, int RK_ = 1);
 };
 
 #ifdef __CUDACC__
@@ -176,6 +177,10 @@ struct FusedFrame {
   int P;      // pixels
   int tile0;  // first global tile index of this frame
   int win0;   // first global plan window of this frame (set by the launcher)
+  // 3x3 R only (single-frame launches): the neural buffer the fused kernel
+  // writes, BF16 [h][H/8][w][8], and the frame width.
+  uint16_t* phi;
+  int w;
 };
 
 constexpr int kMaxBatch = 64;
@@ -229,11 +234,20 @@ cudaError_t launch_plan(FusedParams& p, cudaStream_t s);
 size_t plain_workspace_bytes(int H, int K, int P);
 // pool_sum: Eq. 5's sum form (tau = sum of the valid layers' phi outputs, no
 // rho) instead of [max ; mean] then rho.
+// w: frame width (the 3x3 R1 reads neighbouring pixels; P = h w).
 cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const float* latent,
                               const float* gbuf, const float* tbuf, const uint8_t* counts, int K,
                               int P, float* out, void* ws, uint32_t* err, cudaStream_t s,
-                              int pool_sum = 0);
+                              int pool_sum, int w);
 int device_sm_count();
+// 3x3 R (conv_r3.cu): R1 as a 3x3 kernel over the neural buffer phi
+// (BF16 [h][H/8][w][8]) the fused kernel wrote, then R2 and the sigmoid.
+// The image holds the 9 taps' [H/8][H][8] BF16 weights (tap = (dy + 1) 3 +
+// dx + 1), R2 as [H/8][16][8] BF16, then b_R1 [H] and b_R2 [16] FP32.
+size_t conv_r3_image_bytes(int H);
+cudaError_t prepare_conv_r3(int H);
+cudaError_t launch_conv_r3(int H, const void* img, const uint16_t* phi, float* out, int h, int w,
+                           uint32_t* err, cudaStream_t s);
 // FP8 fused path (fused_fp8.cu): plan kernel, then the fused E4M3 kernel.
 cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& p, cudaStream_t s);
 cudaError_t prepare_fused_fp8(int H);
@@ -253,6 +267,7 @@ struct gn_model {
   float* w32 = nullptr;     // concat-form f32 weights (device)
   void* fused = nullptr;    // packed operand image (device)
   size_t fused_bytes = 0;
+  void* conv = nullptr;     // 3x3 R image of the BF16 path (device)
   uint32_t* err = nullptr;  // sticky error word (device)
   void* ws = nullptr;       // FP32 plain workspace (device), grown on demand
   size_t ws_bytes = 0;

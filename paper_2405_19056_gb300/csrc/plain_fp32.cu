@@ -12,6 +12,7 @@
 //   (sum form of Eq. 5: R = sum_k V over the valid layers, no rho)
 //   Y = ReLU(W_B2 ReLU(W_B1 [g ; R ; sigma] + b) + b)
 //   out = sigmoid(W_R2 ReLU(W_R1 Y + b) + b)
+//   (with a 3x3 R1, W_R1 reads the 3x3 neighbourhood of Y, zero outside the frame)
 #include "internal.h"
 
 namespace gn {
@@ -40,6 +41,17 @@ struct RowsIn {  // row-major [M][Kx]; validity from the layer counts (rows (k, 
   int P, Kx;
   __device__ bool valid(int r) const { return counts == nullptr || (r / P) < counts[r % P]; }
   __device__ float x(int r, int j) const { return X[static_cast<size_t>(r) * Kx + j]; }
+};
+struct ConvIn {  // R1 with a 3x3 kernel: j = k * 9 + (dy + 1) * 3 + (dx + 1), zero outside the frame
+  const float* Y;  // [P][H] neural buffer, pixel p = y w + x
+  int h, w, H;
+  __device__ bool valid(int) const { return true; }
+  __device__ float x(int r, int j) const {
+    const int k = j / 9, t = j % 9;
+    const int yy = r / w + t / 3 - 1, xx = r % w + t % 3 - 1;
+    if (yy < 0 || yy >= h || xx < 0 || xx >= w) return 0.0f;
+    return Y[static_cast<size_t>(yy * w + xx) * H + k];
+  }
 };
 struct RhoIn {  // pool rows; a pixel without valid layers gets r = 0
   const float* pool;
@@ -216,7 +228,7 @@ size_t plain_workspace_bytes(int H, int K, int P) {
 cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const float* latent,
                               const float* gbuf, const float* tbuf, const uint8_t* counts, int K,
                               int P, float* out, void* ws, uint32_t* err, cudaStream_t s,
-                              int pool_sum) {
+                              int pool_sum, int w) {
   const int H = wi.H, Z = wi.Z;
   const size_t rows = static_cast<size_t>(K) * P;
   float* U = static_cast<float*>(ws);
@@ -252,7 +264,10 @@ cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const flo
   if (e != cudaSuccess) return e;
   e = run_linear<RowsIn, false>(RowsIn{Y1, nullptr, P, H}, W(LB2), B(LB2), Y2, P, H, H, s);
   if (e != cudaSuccess) return e;
-  e = run_linear<RowsIn, false>(RowsIn{Y2, nullptr, P, H}, W(LR1), B(LR1), Q, P, H, H, s);
+  if (wi.RK == 3)
+    e = run_linear<ConvIn, false>(ConvIn{Y2, P / w, w, H}, W(LR1), B(LR1), Q, P, H, 9 * H, s);
+  else
+    e = run_linear<RowsIn, false>(RowsIn{Y2, nullptr, P, H}, W(LR1), B(LR1), Q, P, H, H, s);
   if (e != cudaSuccess) return e;
   return run_linear<RowsIn, true>(RowsIn{Q, nullptr, P, H}, W(LR2), B(LR2), out, P, kOut, H, s);
 }

@@ -160,13 +160,15 @@ def glassnet_load_weights(blob: bytes, precision: int) -> int:
 
 class ModelConfig(ctypes.Structure):
     """gn_model_config."""
-    _fields_ = [("precision", ctypes.c_int), ("pooling", ctypes.c_int), ("pe_freqs", ctypes.c_int)]
+    _fields_ = [("precision", ctypes.c_int), ("pooling", ctypes.c_int), ("pe_freqs", ctypes.c_int),
+                ("r_kernel", ctypes.c_int)]
 
 
-def glassnet_load_weights_ex(blob: bytes, precision: int, pooling: int = 0, pe_freqs: int = 0) -> int:
+def glassnet_load_weights_ex(blob: bytes, precision: int, pooling: int = 0, pe_freqs: int = 0,
+                             r_kernel: int = 1) -> int:
     out = ctypes.c_void_p()
     buf = ctypes.create_string_buffer(blob, len(blob))
-    cfg = ModelConfig(precision, pooling, pe_freqs)
+    cfg = ModelConfig(precision, pooling, pe_freqs, r_kernel)
     _check(_lib().glassnet_load_weights_ex(buf, len(blob), ctypes.byref(cfg), ctypes.byref(out)))
     return out.value
 
@@ -394,16 +396,19 @@ class Model:
     """Owns a gn_model handle."""
 
     def __init__(self, weights_or_blob, precision: int = GN_BF16_FUSED,
-                 pooling: int = GN_POOL_MAX_MEAN, pe_freqs=None):
-        """``pe_freqs`` defaults to the weight dict's ``"pe_freqs"`` (0 for a blob)."""
+                 pooling: int = GN_POOL_MAX_MEAN, pe_freqs=None, r_kernel=None):
+        """``pe_freqs`` and ``r_kernel`` default to the weight dict's keys of
+        those names (0 and 1 for a blob)."""
+        is_blob = isinstance(weights_or_blob, (bytes, bytearray))
         if pe_freqs is None:
-            pe_freqs = 0 if isinstance(weights_or_blob, (bytes, bytearray)) else \
-                int(weights_or_blob.get("pe_freqs", 0))
-        blob = weights_or_blob if isinstance(weights_or_blob, (bytes, bytearray)) else pack_blob(weights_or_blob)
-        self.handle = glassnet_load_weights_ex(bytes(blob), precision, pooling, pe_freqs)
+            pe_freqs = 0 if is_blob else int(weights_or_blob.get("pe_freqs", 0))
+        if r_kernel is None:
+            r_kernel = 1 if is_blob else int(weights_or_blob.get("r_kernel", 1))
+        blob = weights_or_blob if is_blob else pack_blob(weights_or_blob)
+        self.handle = glassnet_load_weights_ex(bytes(blob), precision, pooling, pe_freqs, r_kernel)
         self.hidden, self.latent_width, self.precision = glassnet_model_info(self.handle)
         cfg = glassnet_model_config(self.handle)
-        self.pooling, self.pe_freqs = cfg.pooling, cfg.pe_freqs
+        self.pooling, self.pe_freqs, self.r_kernel = cfg.pooling, cfg.pe_freqs, cfg.r_kernel
 
     def encode(self, scene, stream=None) -> "Latent":
         return Latent(glassnet_encode_scene(self.handle, scene, stream))
