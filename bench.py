@@ -64,22 +64,28 @@ def parse():
     ap.add_argument("--pooling", default="max_mean", choices=["max_mean", "sum"],
                     help="pooling of Eq. 5 in the timed BF16 leg: [max ; mean] then rho, or the "
                          "paper's sum form (tau straight into B)")
+    ap.add_argument("--r-kernel", type=int, default=1, choices=[1, 3],
+                    help="R's first layer: 1x1, or a 3x3 kernel over the frame (fused kernel to "
+                         "the neural buffer, then the tcgen05 3x3 kernel)")
     ap.add_argument("--pe-freqs", type=int, default=0,
                     help="time the base widths (H=64 Z=128) with every input positionally "
                          "encoded at this many frequencies (BF16, 1..4) instead of the doubled widths")
     return ap.parse_args()
 
 
-def algorithmic_flops(H: int, counts: np.ndarray, pooling: str = "max_mean", pe: int = 0) -> float:
+def algorithmic_flops(H: int, counts: np.ndarray, pooling: str = "max_mean", pe: int = 0,
+                      r_kernel: int = 1) -> float:
     """FLOPs of the folded network on the valid layers only.
 
     Per valid (pixel, layer): phi1 12e*H (latent folded) + phi2 H*H MACs.
-    Per pixel: rho 2H*H + B1 (14e+H)*H (latent folded) + B2 H*H + R1 H*H + R2 3H;
-    the sum form of Eq. 5 has no rho; e = 1 + 2 pe encoded bands per input.
+    Per pixel: rho 2H*H + B1 (14e+H)*H (latent folded) + B2 H*H + R1 k^2 H*H + R2 3H;
+    the sum form of Eq. 5 has no rho; e = 1 + 2 pe encoded bands per input;
+    k = R1's kernel size.
     """
     e = 1 + 2 * pe
     per_layer = 12 * e * H + H * H
-    per_pixel = (0 if pooling == "sum" else 2 * H * H) + (14 * e + H) * H + H * H + H * H + 3 * H
+    per_pixel = ((0 if pooling == "sum" else 2 * H * H) + (14 * e + H) * H + H * H
+                 + r_kernel ** 2 * H * H + 3 * H)
     return 2.0 * (per_layer * float(counts.sum()) + per_pixel * counts.size)
 
 
@@ -268,12 +274,13 @@ def run_fused(args, world, rank, local):
     dev = torch.device("cuda", local)
     gl.load_library()
     pe = args.pe_freqs
-    widths = synth.Widths(64, 128, pe) if pe else synth.DOUBLED_WIDTHS
+    rk = args.r_kernel
+    widths = synth.Widths(64, 128, pe, rk) if pe else synth.Widths(128, 256, 0, rk)
     weights = synth.make_weights(widths, seed=0)
     fp8 = args.precision == "fp8"
     pool_sum = args.pooling == "sum"
-    if fp8 and (pool_sum or pe):
-        raise SystemExit("the sum pooling form and positional encoding are built for BF16 only")
+    if fp8 and (pool_sum or pe or rk == 3):
+        raise SystemExit("sum pooling, positional encoding and the 3x3 R are built for BF16 only")
     model = gl.Model(weights, gl.GN_FP8_FUSED if fp8 else gl.GN_BF16_FUSED,
                      gl.GN_POOL_SUM if pool_sum else gl.GN_POOL_MAX_MEAN)
     scene = synth.make_scene(0)
@@ -287,7 +294,7 @@ def run_fused(args, world, rank, local):
                             tbuf=torch.from_numpy(f.tbuf).to(dev),
                             counts=torch.from_numpy(f.counts).to(dev),
                             out=torch.empty((3, H_IMG, W_IMG), device=dev)))
-    flops = [algorithmic_flops(widths.hidden, f.counts, args.pooling, pe) for f in frames]
+    flops = [algorithmic_flops(widths.hidden, f.counts, args.pooling, pe, rk) for f in frames]
     P = H_IMG * W_IMG
 
     with torch.cuda.stream(stream):
@@ -336,13 +343,15 @@ def run_fused(args, world, rank, local):
         peak_tf *= 2
     achieved_tf = step_flops / (avg_kernel_ms * 1e-3) / 1e12
     # the captures cover L = 4 (encoded) and the two poolings of the doubled widths
-    traffic = None if fp8 or (pe and (pe != 4 or pool_sum)) else profiled_traffic(
+    traffic = None if fp8 or rk == 3 or (pe and (pe != 4 or pool_sum)) else profiled_traffic(
         PROFILE_TRAFFIC_PE if pe else PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC)
     metric = METRIC.replace("BF16", "FP8") if fp8 else METRIC
     if pool_sum:
         metric = metric.replace("BF16 fused", "BF16 fused, sum pooling")
     if pe:
         metric = metric.replace("BF16 fused", f"BF16 fused, H=64, inputs encoded at L={pe}")
+    if rk == 3:
+        metric = metric.replace("BF16 fused", "BF16 fused, 3x3 R")
     result = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -355,12 +364,13 @@ def run_fused(args, world, rank, local):
         "fps": world * args.steps / (total_ms * 1e-3),
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "encode_scene_ms": encode_ms,
-        "gpu_launches": 2 * args.steps,  # per step: tile-plan kernel + fused kernel
+        # per step: tile-plan kernel + fused kernel (+ the 3x3 R kernel)
+        "gpu_launches": (3 if rk == 3 else 2) * args.steps,
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
                      "kernel": "fused_fp8_kernel<128>" if fp8 else
                                f"fused_bf16_kernel<{widths.hidden}, frame, sum={int(pool_sum)}, "
-                               f"pe={int(pe > 0)}>",
+                               f"pe={int(pe > 0)}>" + (" + conv_r3_kernel" if rk == 3 else ""),
                      "duration": "CUDA events around the render call (plan kernel + fused kernel)",
                      "flops_per_launch": step_flops,
                      "peak_source": (f"{peak_src} bf16 burst (MEASURED_PEAKS.json) x 2 (nominal "
@@ -376,6 +386,7 @@ def run_fused(args, world, rank, local):
         result["fp8"] = fp8_leg(weights, scene, dframes, flops, stream, dev)
         result["sum_pooling"] = sum_pooling_leg(weights, scene, dframes, frames, stream)
         result["positional_encoding"] = pe_leg(scene, dframes, frames, stream)
+        result["spatial_r3"] = r3_leg(scene, dframes, frames, stream)
         result["serving"] = (serving_leg(model, (50, 200, 800), 2000) if args.serving_full
                              else serving_leg(model, (200, 800), 300))
     clocks = clk.summary()
@@ -512,6 +523,31 @@ def _time_renders(m, lat, dframes, stream, steps):
     stream.synchronize()
     gl.glassnet_check(m.handle, stream)
     return e0.elapsed_time(e1) / steps
+
+
+def r3_leg(scene, dframes, frames, stream, steps=200):
+    """The same frames through the doubled widths with R's first layer a 3x3
+    kernel over the frame (Sec. 3.4): the fused kernel writes the neural
+    buffer, the tcgen05 3x3 kernel reads it."""
+    from gen import synth
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    peak_bf16, _, _ = measured_peaks()
+    w = synth.make_weights(synth.Widths(128, 256, 0, 3), seed=0)
+    m = gl.Model(w, gl.GN_BF16_FUSED)
+    lat = m.encode(scene, stream)
+    ms = _time_renders(m, lat, dframes, stream, steps)
+    flops = sum(algorithmic_flops(128, frames[i % N_ROTATE].counts, "max_mean", 0, 3)
+                for i in range(steps)) / steps
+    conv = 2.0 * (9 * 128 * 128 + 3 * 128) * H_IMG * W_IMG
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"value": H_IMG * W_IMG / (ms * 1e-3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms,
+            "steps": steps, "gflop_per_step": flops / 1e9, "gflop_3x3_R_per_step": conv / 1e9,
+            "widths": "H=128 Z=256, R1 3x3", "launches_per_step": 3,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16,
+                         "unit": "TFLOP/s", "frac": achieved / peak_bf16,
+                         "kernel": "plan + fused_bf16_kernel<128, frame, r3> + conv_r3_kernel<128>",
+                         "peak_source": "measured bf16 burst"}}
 
 
 def pe_leg(scene, dframes, frames, stream, L=4, steps=200):
