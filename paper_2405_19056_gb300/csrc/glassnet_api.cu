@@ -103,8 +103,9 @@ std::vector<uint8_t> pack_fused_bf16(const float* w, const gn::WeightIndex& wi) 
 
 // Image of the 3x3 R kernel (conv_r3.cu): per tap t = (dy + 1) 3 + dx + 1
 // the [H/8][H][8] BF16 B operand of W_R1[:, :, dy + 1, dx + 1] (the blob
-// stores R1 as [H][H 9], column k 9 + t), then R2 as [H/8][16][8] BF16, then
-// b_R1 [H] and b_R2 [16] in FP32.
+// stores R1 as [H][H 9], column k 9 + t), then in FP32 b_R1 [H], W_R2 [3][H]
+// (rounded to BF16, the precision of every other weight operand) and b_R2
+// [4] (3 used).
 std::vector<uint8_t> pack_conv_r3(const float* w, const gn::WeightIndex& wi) {
   const int H = wi.H;
   std::vector<uint8_t> img(gn::conv_r3_image_bytes(H), 0);
@@ -117,12 +118,14 @@ std::vector<uint8_t> pack_conv_r3(const float* w, const gn::WeightIndex& wi) {
   for (int t = 0; t < 9; ++t)
     for (int n = 0; n < H; ++n)
       for (int k = 0; k < H; ++k) put(t * tap_bytes, H, n, k, W1[static_cast<size_t>(n) * 9 * H + k * 9 + t]);
-  const size_t r2 = 9 * tap_bytes;
+  float* tail = reinterpret_cast<float*>(img.data() + 9 * tap_bytes);
+  for (int n = 0; n < H; ++n) tail[n] = w[wi.b[gn::LR1] + n];
   for (int n = 0; n < gn::kOut; ++n)
-    for (int k = 0; k < H; ++k) put(r2, 16, n, k, w[wi.w[gn::LR2] + static_cast<size_t>(n) * H + k]);
-  float* bias = reinterpret_cast<float*>(img.data() + r2 + static_cast<size_t>(H) * 16 * 2);
-  for (int n = 0; n < H; ++n) bias[n] = w[wi.b[gn::LR1] + n];
-  for (int n = 0; n < gn::kOut; ++n) bias[H + n] = w[wi.b[gn::LR2] + n];
+    for (int k = 0; k < H; ++k) {
+      const uint32_t u = static_cast<uint32_t>(bf16_rne(w[wi.w[gn::LR2] + static_cast<size_t>(n) * H + k])) << 16;
+      std::memcpy(&tail[H + n * H + k], &u, 4);
+    }
+  for (int n = 0; n < gn::kOut; ++n) tail[4 * H + n] = w[wi.b[gn::LR2] + n];
   return img;
 }
 

@@ -100,10 +100,12 @@ def test_bf16_fused_r3_vs_oracle(cuda_lib, case):
     assert np.abs(got - render(mp, scene, f)).max() <= BF16_MAX
 
 
-def test_centre_tap_only_equals_the_1x1_model_bit_for_bit(cuda_lib):
+def test_centre_tap_only_equals_the_1x1_model(cuda_lib):
     """With only the centre tap set, the 3x3 R is the 1x1 R: zero taps add
-    exact zeros and the centre tap's MMAs, the bias, ReLU, R2 and sigmoid run
-    in the same order, so the frames agree bit for bit."""
+    exact zeros and the centre tap's MMAs, the bias, ReLU and BF16 rounding of
+    q run as in the fused kernel; R2 (128 terms) then sums in FP32 on the CUDA
+    cores instead of the tensor core, so the frames agree to FP32 rounding of
+    that sum (2e-6 in RGB), far inside any tap or halo mistake."""
     w1 = synth.make_weights(synth.DOUBLED_WIDTHS, seed=4, bias="uniform")
     H = 128
     K3 = np.zeros((H, H, 3, 3), np.float32)
@@ -115,7 +117,7 @@ def test_centre_tap_only_equals_the_1x1_model_bit_for_bit(cuda_lib):
     f = synth.make_frame(77, 300, 8, counts="poisson3", seed=5)
     a = render(gl.Model(w1, gl.GN_BF16_FUSED), scene, f)
     b = render(gl.Model(w3, gl.GN_BF16_FUSED), scene, f)
-    assert np.array_equal(a, b), np.abs(a - b).max()
+    assert np.abs(a - b).max() <= 2e-6, np.abs(a - b).max()
 
 
 def test_r3_bit_identical_under_permutations(cuda_lib):
