@@ -181,3 +181,23 @@ def test_python_binding_raises_with_message(lib):
     with pytest.raises(gl.GlassNetError) as ei:
         gl.glassnet_load_weights(b"short", gl.GN_BF16_FUSED)
     assert ei.value.code == gl.GN_EFORMAT
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: a library that is not there is an error, not a
+    silent substitute."""
+    with pytest.raises(gl.GlassNetError) as ei:
+        gl.load_library(path=str(tmp_path / "libglassnet_absent.so"))
+    assert "not found" in str(ei.value)
+
+
+def test_product_package_never_imports_the_oracle():
+    """The oracle is test infrastructure: nothing in the product package
+    imports it or any numpy / torch math path that could stand in for the
+    CUDA library."""
+    import pathlib
+    pkg = pathlib.Path(gl.__file__).parent
+    for f in pkg.rglob("*.py"):
+        text = f.read_text()
+        assert "import oracle" not in text and "from oracle" not in text, f
+        assert "glassnet_oracle" not in text, f
