@@ -322,17 +322,17 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 #pragma unroll
     for (int w = 0; w < LW; ++w) ns = max(ns, ls.ns[tb & 1][w]);
     if (Mode == kModeResolve || (Mode == kModeAccumulate && ns > 0 && !prm.pool_fresh)) {
-      // Streaming launches: the pool state of each of the lane's rows whose
-      // state is read (its pixel's (H/2 + H) words, whole 128-byte lines)
-      // into L2 ahead of the epilogue's loads.
-      constexpr int kLines = (H / 2 + H) * 4 / 128;
+      // Streaming launches: the pool state of this warp's rows (row0 + 32 i:
+      // 32 consecutive pixels, one 128-byte line in each of the tile's H/2 + H
+      // planes) into L2 ahead of the epilogue's loads, for the lines that
+      // hold a pixel whose state is read.
+      const uint32_t* blk =
+          prm.pool_st + static_cast<size_t>(tile - F.tile0) * ((H / 2 + H) * kTile) + li * (32 * RPL);
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
-        if (!(has[i] && cnt[i] > 0)) continue;
-        const uint32_t* px = prm.pool_st + (static_cast<size_t>(tile - F.tile0) * kTile + row0 + 32 * i) *
-                                               (H / 2 + H);
-#pragma unroll
-        for (int l = 0; l < kLines; ++l) asm volatile("prefetch.global.L2 [%0];" ::"l"(px + l * 32));
+        if (!__any_sync(0xffffffffu, has[i] && cnt[i] > 0)) continue;
+        for (int pl = lane; pl < H / 2 + H; pl += 32)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + pl * kTile + 32 * i));
       }
     }
 
@@ -732,38 +732,19 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
 #pragma unroll
         for (int j = 0; j < CH; ++j) sm[j] = kSumBase;
         // Streaming launches: a pixel that has layers starts from its pool
-        // state: the pixel's H/2 max pairs, then its H fixed-point sums
-        // (this warp's CHC and CH of them, read as 16-byte vectors).
-        uint4* st_mx = nullptr;
-        uint4* st_sm = nullptr;
+        // state (planes of the pixel's channel pairs and channels).
+        uint32_t* st = nullptr;  // this row's word in plane 0 of the tile's state block
         if constexpr (Mode == kModeAccumulate) {
           if (lane == 0) mbar_arrive(bar(B_H + (tb & 1)));  // this tile is taken (paces the loaders)
         }
         if constexpr (Mode != kModeFrame) {
           // pixel order: row `row` of the tile is its pixel
-          uint32_t* px = prm.pool_st +
-                         (static_cast<size_t>(tile - prm.f[0].tile0) * kTile + row) * (H / 2 + H);
-          st_mx = reinterpret_cast<uint4*>(px + g * CHC);
-          st_sm = reinterpret_cast<uint4*>(px + H / 2 + g * CH);
+          st = prm.pool_st + static_cast<size_t>(tile - prm.f[0].tile0) * ((H / 2 + H) * kTile) + row;
           if (c > 0 && !prm.pool_fresh) {
-            if constexpr (!Sum) {
 #pragma unroll
-              for (int j = 0; j < CHC / 4; ++j) {
-                const uint4 v = st_mx[j];
-                mx[4 * j] = v.x;
-                mx[4 * j + 1] = v.y;
-                mx[4 * j + 2] = v.z;
-                mx[4 * j + 3] = v.w;
-              }
-            }
+            for (int j = 0; j < CHC; ++j) mx[j] = Sum ? 0u : st[(g * CHC + j) * kTile];
 #pragma unroll
-            for (int j = 0; j < CH / 4; ++j) {
-              const uint4 v = st_sm[j];
-              sm[4 * j] = __uint_as_float(v.x);
-              sm[4 * j + 1] = __uint_as_float(v.y);
-              sm[4 * j + 2] = __uint_as_float(v.z);
-              sm[4 * j + 3] = __uint_as_float(v.w);
-            }
+            for (int j = 0; j < CH; ++j) sm[j] = __uint_as_float(st[(H / 2 + g * CH + j) * kTile]);
           }
         }
 
@@ -838,12 +819,9 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
           // the covered pixels' state back to device memory, one more layer
           if (c > 0) {
 #pragma unroll
-            for (int j = 0; j < CHC / 4; ++j)
-              st_mx[j] = make_uint4(mx[4 * j], mx[4 * j + 1], mx[4 * j + 2], mx[4 * j + 3]);
+            for (int j = 0; j < CHC; ++j) st[(g * CHC + j) * kTile] = mx[j];
 #pragma unroll
-            for (int j = 0; j < CH / 4; ++j)
-              st_sm[j] = make_uint4(__float_as_uint(sm[4 * j]), __float_as_uint(sm[4 * j + 1]),
-                                    __float_as_uint(sm[4 * j + 2]), __float_as_uint(sm[4 * j + 3]));
+            for (int j = 0; j < CH; ++j) st[(H / 2 + g * CH + j) * kTile] = __float_as_uint(sm[j]);
             if (g == 0) {
               const size_t pix = static_cast<size_t>(tile - prm.f[0].tile0) * kTile + row;
               prm.pool_cnt[pix] = static_cast<uint8_t>(prm.pool_cnt[pix] + 1);

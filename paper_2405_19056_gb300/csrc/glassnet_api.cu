@@ -764,15 +764,15 @@ struct gn_pool {
 
 namespace {
 // Empty pool: running max 0 (the ReLU floor), sums at 2^11 (the fixed-point
-// base of the exact pooling), no layers.  Each pixel's state is `words`
-// consecutive words: the first mx_words hold the max pairs, the others the
-// sums.
-__global__ void pool_reset_kernel(uint32_t* st, size_t n_st, int words, int mx_words,
+// base of the exact pooling), no layers.  Word w of the state lies in plane
+// (w / 128) mod (H/2 + H) of its tile's block: the first H/2 planes hold the
+// max pairs, the others the sums.
+__global__ void pool_reset_kernel(uint32_t* st, size_t n_st, int planes, int mx_planes,
                                   uint8_t* cnt, size_t n_cnt) {
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n_st; i += stride) {
-    const int wd = static_cast<int>(i % static_cast<size_t>(words));
-    st[i] = wd < mx_words ? 0u : 0x45000000u;  // 2048.0f
+    const int pl = static_cast<int>((i / gn::kTile) % static_cast<size_t>(planes));
+    st[i] = pl < mx_planes ? 0u : 0x45000000u;  // 2048.0f
     if (i < n_cnt) cnt[i] = 0u;
   }
 }

@@ -202,10 +202,10 @@ struct FusedParams {
   // (identity), a frame's counts may be NULL (every pixel has K layers), and
   // the pool state lives in device planes of P values each.
   int plan_identity;
-  // Pool state, pixel-major: per pixel (frame index, padded to whole tiles)
-  // H/2 + H consecutive words, the running max as bf16 pairs, then the
-  // fixed-point sums as f32 bits (start 2^11).  A pixel's state is whole
-  // 128-byte lines, so a launch moves only the state of the pixels it covers.
+  // Pool state, tile-major: per 128-pixel tile of the frame a block of
+  // H/2 + H planes of 128 words (running max as bf16 pairs, then the
+  // fixed-point sums as f32 bits, start 2^11), so a tile's state is one
+  // contiguous block and a warp's access to a plane is coalesced.
   uint32_t* pool_st;
   uint8_t* pool_cnt;  // [P] layers accumulated
   int pool_fresh;     // the pool is empty: its state is the start value, not read
