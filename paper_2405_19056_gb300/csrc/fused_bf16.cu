@@ -322,28 +322,17 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 #pragma unroll
     for (int w = 0; w < LW; ++w) ns = max(ns, ls.ns[tb & 1][w]);
     if (Mode == kModeResolve || (Mode == kModeAccumulate && ns > 0 && !prm.pool_fresh)) {
-      // Streaming launches: the pool state of this warp's rows into L2 ahead
-      // of the epilogue's loads.  A 32-pixel block of a state tile is one
-      // 128-byte line in each of its H/2 + H planes; the rows' pixels ascend
-      // (pixel order, or the covered pixels of a window in pixel order), so
-      // each block that holds a pixel whose state is read starts where a
-      // lane's block differs from the previous lane's, and the warp
-      // prefetches its planes once.
+      // Streaming launches: the pool state of this warp's rows (row0 + 32 i:
+      // 32 consecutive pixels, one 128-byte line in each of the tile's H/2 + H
+      // planes) into L2 ahead of the epilogue's loads, for the lines that
+      // hold a pixel whose state is read.
+      const uint32_t* blk =
+          prm.pool_st + static_cast<size_t>(tile - F.tile0) * ((H / 2 + H) * kTile) + li * (32 * RPL);
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
-        const bool need = has[i] && cnt[i] > 0;
-        const uint32_t key = need ? pix[i] >> 5 : 0xffffffffu;
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-        uint32_t heads = __ballot_sync(0xffffffffu, need && (lane == 0 || prev != key));
-        while (heads) {
-          const int src = __ffs(heads) - 1;
-          heads &= heads - 1u;
-          const uint32_t kb = __shfl_sync(0xffffffffu, key, src);
-          const uint32_t* blk = prm.pool_st + static_cast<size_t>(kb >> 2) * ((H / 2 + H) * kTile) +
-                                (kb & 3u) * 32u;
-          for (int pl = lane; pl < H / 2 + H; pl += 32)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + pl * kTile));
-        }
+        if (!__any_sync(0xffffffffu, has[i] && cnt[i] > 0)) continue;
+        for (int pl = lane; pl < H / 2 + H; pl += 32)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + pl * kTile + 32 * i));
       }
     }
 
@@ -748,14 +737,9 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
         if constexpr (Mode == kModeAccumulate) {
           if (lane == 0) mbar_arrive(bar(B_H + (tb & 1)));  // this tile is taken (paces the loaders)
         }
-        uint32_t st_pix = 0;  // this row's pixel (streaming launches)
         if constexpr (Mode != kModeFrame) {
-          // the row's pixel from its plan entry (resolve: pixel order;
-          // accumulate: each window's covered pixels first, in pixel order);
-          // its state word in plane 0 of its tile's block
-          const uint32_t e = __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row);
-          st_pix = e == kPlanEmpty ? 0u : (e & kPlanPixelMask);  // an empty row has no layers (c = 0)
-          st = prm.pool_st + static_cast<size_t>(st_pix >> 7) * ((H / 2 + H) * kTile) + (st_pix & 127u);
+          // pixel order: row `row` of the tile is its pixel
+          st = prm.pool_st + static_cast<size_t>(tile - prm.f[0].tile0) * ((H / 2 + H) * kTile) + row;
           if (c > 0 && !prm.pool_fresh) {
 #pragma unroll
             for (int j = 0; j < CHC; ++j) mx[j] = Sum ? 0u : st[(g * CHC + j) * kTile];
@@ -838,7 +822,10 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
             for (int j = 0; j < CHC; ++j) st[(g * CHC + j) * kTile] = mx[j];
 #pragma unroll
             for (int j = 0; j < CH; ++j) st[(H / 2 + g * CH + j) * kTile] = __float_as_uint(sm[j]);
-            if (g == 0) prm.pool_cnt[st_pix] = static_cast<uint8_t>(prm.pool_cnt[st_pix] + 1);
+            if (g == 0) {
+              const size_t pix = static_cast<size_t>(tile - prm.f[0].tile0) * kTile + row;
+              prm.pool_cnt[pix] = static_cast<uint8_t>(prm.pool_cnt[pix] + 1);
+            }
           }
           gs += ns;
           if (!take_tile(tb + 1)) goto done;

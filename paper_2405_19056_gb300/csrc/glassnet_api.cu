@@ -777,8 +777,8 @@ __global__ void pool_reset_kernel(uint32_t* st, size_t n_st, int planes, int mx_
   }
 }
 
-// One-frame fused parameters of a pool launch (the pool's state and plan
-// workspace; a pixel-order plan unless the caller sorts it).
+// One-frame fused parameters of a pool launch (pixel-order plan, the pool's
+// state and plan workspace).
 gn::FusedParams pool_params(const gn_model* m, const gn_latent* lat, const gn_pool* pool,
                             const float* gbuf, const float* tbuf, const uint8_t* cnt, int K,
                             float* out) {
@@ -874,10 +874,6 @@ int glassnet_accumulate_layer(const gn_model* m, const gn_latent* lat, gn_pool* 
     return fail(GN_EINVAL, "the pool already holds %d layers (at most %d)", pool->layers, gn::kMaxK);
   gn::FusedParams p = pool_params(m, lat, pool, nullptr, layer, covered, 1, nullptr);
   p.pool_fresh = pool->layers == 0;  // after a reset the state need not be read
-  // the coverage mask as counts 0 / 1: the count-sorting plan puts each
-  // window's covered pixels first, in pixel order, so tiles of uncovered
-  // pixels have no slot and a sparse layer runs few tiles
-  p.plan_identity = 0;
   cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s, 1);
   if (e != cudaSuccess) return cuda_fail(e, "accumulate launch");
   ++pool->layers;

@@ -198,10 +198,9 @@ struct FusedParams {
   // window (tail_part tiles) follows them.
   int win_tiles;
   int tail0, tail_n, tail_part;
-  // Streaming launches (accumulate / resolve): the resolve plan keeps pixel
-  // order (identity), the accumulate plan sorts each window by coverage; a
-  // frame's counts may be NULL (every pixel has K layers); each row finds
-  // its pool state through its plan entry's pixel.
+  // Streaming launches (accumulate / resolve): the plan keeps pixel order
+  // (identity), a frame's counts may be NULL (every pixel has K layers), and
+  // the pool state lives in device planes of P values each.
   int plan_identity;
   // Pool state, tile-major: per 128-pixel tile of the frame a block of
   // H/2 + H planes of 128 words (running max as bf16 pairs, then the
