@@ -324,15 +324,13 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     if (Mode == kModeResolve || (Mode == kModeAccumulate && ns > 0 && !prm.pool_fresh)) {
       // Streaming launches: the pool state of this warp's rows (row0 + 32 i:
       // 32 consecutive pixels, one 128-byte line in each of the tile's H/2 + H
-      // planes) into L2 ahead of the epilogue's loads, for the blocks in
-      // which at least 8 of the 32 pixels have their state read.
+      // planes) into L2 ahead of the epilogue's loads, for the lines that
+      // hold a pixel whose state is read.
       const uint32_t* blk =
           prm.pool_st + static_cast<size_t>(tile - F.tile0) * ((H / 2 + H) * kTile) + li * (32 * RPL);
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
-        // a block with few such pixels is left to the epilogue's loads, which
-        // fetch only the 32-byte sectors they touch
-        if (__popc(__ballot_sync(0xffffffffu, has[i] && cnt[i] > 0)) < 8) continue;
+        if (!__any_sync(0xffffffffu, has[i] && cnt[i] > 0)) continue;
         for (int pl = lane; pl < H / 2 + H; pl += 32)
           asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + pl * kTile + 32 * i));
       }
