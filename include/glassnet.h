@@ -155,9 +155,11 @@ typedef struct gn_model_config {
  *   computes sin(pi x) and cos(pi x) of each input channel with exact
  *   argument reduction and the higher bands by the double-angle identities
  *   in FP32, then rounds every band to BF16.
- * GN_POOL_SUM and pe_freqs > 0 serve every render, batch, graph, server and
- * streaming call of GN_FP32_PLAIN / GN_BF16_FUSED models; with GN_FP8_FUSED
- * they return GN_EUNSUPPORTED.
+ * GN_POOL_SUM serves every precision (for GN_FP8_FUSED the sum enters B1 as
+ * codes of B1's input scale, calibrated on the FP32 path's sum form).
+ * pe_freqs > 0 serves every render, batch, graph, server and streaming call
+ * of GN_FP32_PLAIN / GN_BF16_FUSED models; with GN_FP8_FUSED it returns
+ * GN_EUNSUPPORTED.
  * r_kernel = 3 serves glassnet_render, glassnet_render_ws and
  *   glassnet_render_host of GN_FP32_PLAIN and GN_BF16_FUSED models (any
  *   pooling; with pe_freqs as above): the fused kernel writes the neural

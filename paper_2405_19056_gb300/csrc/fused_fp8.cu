@@ -216,7 +216,11 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
 }
 
 // ------------------------------------------------------------------ kernel
-template <int H>
+// Sum: the paper's sum form of Eq. 5.  tau = s - 2^11 + c 2^-13 (the exact
+// fixed-point sum) goes straight to B1's r operand as codes of tau / s_g,
+// where rho's output would go; rho's GEMM and its epilogue pass are skipped
+// and the max is not kept.
+template <int H, bool Sum>
 __global__ void __launch_bounds__(kThreadsF, 1)
     fused_fp8_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   using L = FusedLayoutF8<H>;
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       const uint32_t Y = tbase + T::buf(p1.b == 2 ? 0 : p1.b + 1);
       const uint32_t Z = tbase + T::buf(p1.b == 0 ? 2 : p1.b - 1);
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
+      for (int l = Sum ? 1 : 0; l < 4; ++l) {
         if (!wait_in()) goto done;
         if (l == 1) {
           if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
                 ffma2(v0, v1, __uint_as_float(cur[i]), __uint_as_float(cur[i + 1]), s_phi2[j],
                       s_phi2[j + 1], b_phi2[j], b_phi2[j + 1]);
                 const uint32_t u = pack_bf16_relu(v0, v1);
-                mx[j / 2] = bmax2(mx[j / 2], u);
+                if constexpr (!Sum) mx[j / 2] = bmax2(mx[j / 2], u);
                 add_bf16x2_rz(sm[j], sm[j + 1], u);
               }
             }
@@ -497,6 +501,34 @@ __global__ void __launch_bounds__(kThreadsF, 1)
           if (!epi2(k)) goto done;
         }
 
+        if constexpr (Sum) {
+          // tau -> the r operand of B1 (buffer Y, see below) as codes of
+          // tau / s_g
+          const uint32_t Yr = tl + T::buf((gs + ns) % 3u == 2 ? 0 : (gs + ns) % 3u + 1);
+          const float inv_s_g = cst[L::INV_S_G];
+          const float off = kSumBase - static_cast<float>(c) * kHalfQuantum;
+          bool over = false;
+#pragma unroll
+          for (int hh = 0; hh < CH / 16; ++hh) {
+            uint32_t u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              float a[4];
+#pragma unroll
+              for (int t = 0; t < 4; t += 2) {
+                const int e = hh * 16 + 4 * j + t;
+                over |= !(fmaxf(sm[e], sm[e + 1]) < kSumLimit);
+                float d0, d1;
+                fadd2_rn(d0, d1, sm[e], sm[e + 1], -off, -off);
+                a[t] = d0 * inv_s_g;
+                a[t + 1] = d1 * inv_s_g;
+              }
+              u[j] = pack_u16x2(pack_e4m3_relu(a[0], a[1]), pack_e4m3_relu(a[2], a[3]));
+            }
+            tmem_st4(Yr + g * CHQ + hh * 4, u);
+          }
+          if (over && c > 0) atomicOr(prm.err, kErrRange);
+        } else
         // pool = [max ; mean] -> APOOL as codes of pool / s_pool
         {
           const float rcp = c > 0 ? __frcp_rn(static_cast<float>(c)) : 0.0f;
@@ -538,7 +570,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const uint32_t Y = tl + T::buf(r3 == 2 ? 0 : r3 + 1);
         const uint32_t Z = tl + T::buf(r3 == 0 ? 2 : r3 - 1);
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
+        for (int l = Sum ? 1 : 0; l < 4; ++l) {
           if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
           ++n_dp;
           tc_fence_after();
@@ -593,20 +625,20 @@ done:
   }
 }
 
-template <int H>
+template <int H, bool Sum>
 cudaError_t prepare_f8() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_fp8_kernel<H>,
+  cudaError_t e = cudaFuncSetAttribute(fused_fp8_kernel<H, Sum>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FusedLayoutF8<H>::smem_bytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <int H>
+template <int H, bool Sum>
 cudaError_t launch_f8(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
-  cudaError_t e = prepare_f8<H>();
+  cudaError_t e = prepare_f8<H, Sum>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -618,14 +650,16 @@ cudaError_t launch_f8(const void* wimg, const FusedParams& p, cudaStream_t s, in
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_fp8_kernel<H>, p, static_cast<const uint8_t*>(wimg));
+  return cudaLaunchKernelEx(&cfg, fused_fp8_kernel<H, Sum>, p, static_cast<const uint8_t*>(wimg));
 }
 
 }  // namespace
 
 cudaError_t prepare_fused_fp8(int H) {
   device_sm_count();
-  return H == 128 ? prepare_f8<128>() : prepare_f8<64>();
+  cudaError_t e = H == 128 ? prepare_f8<128, false>() : prepare_f8<64, false>();
+  if (e == cudaSuccess) e = H == 128 ? prepare_f8<128, true>() : prepare_f8<64, true>();
+  return e;
 }
 
 cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& params, cudaStream_t s) {
@@ -634,7 +668,9 @@ cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& params,
   cudaError_t e = launch_plan(p, s);
   if (e != cudaSuccess) return e;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
-  return H == 128 ? launch_f8<128>(wimg, p, s, grid) : launch_f8<64>(wimg, p, s, grid);
+  if (p.pool_sum)
+    return H == 128 ? launch_f8<128, true>(wimg, p, s, grid) : launch_f8<64, true>(wimg, p, s, grid);
+  return H == 128 ? launch_f8<128, false>(wimg, p, s, grid) : launch_f8<64, false>(wimg, p, s, grid);
 }
 
 }  // namespace gn

@@ -274,9 +274,9 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_con
     return fail(GN_EINVAL, "unknown pooling %d", pooling);
   if (pe < 0 || pe > gn::kMaxPeFreqs)
     return fail(GN_EINVAL, "pe_freqs %d outside 0..%d", pe, gn::kMaxPeFreqs);
-  if (precision == GN_FP8_FUSED && (pooling == GN_POOL_SUM || pe > 0))
+  if (precision == GN_FP8_FUSED && pe > 0)
     return fail(GN_EUNSUPPORTED,
-                "sum pooling and positional encoding are built for GN_FP32_PLAIN and GN_BF16_FUSED");
+                "positional encoding is built for GN_FP32_PLAIN and GN_BF16_FUSED");
   if (nbytes < sizeof(gn_blob_header))
     return fail(GN_EFORMAT, "blob of %zu bytes is shorter than its header", nbytes);
   gn_blob_header hd;
@@ -528,7 +528,12 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
 }
 
 cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s) {
-  if (m->precision == GN_FP8_FUSED) return launch_fused_fp8(m->H, m->fused, p, s);
+  if (m->precision == GN_FP8_FUSED) {
+    if (m->pooling != GN_POOL_SUM) return launch_fused_fp8(m->H, m->fused, p, s);
+    FusedParams q = p;
+    q.pool_sum = 1;
+    return launch_fused_fp8(m->H, m->fused, q, s);
+  }
   if (m->pooling == GN_POOL_SUM || m->wi.L > 0) {
     FusedParams q = p;
     q.pool_sum = m->pooling == GN_POOL_SUM;
@@ -691,7 +696,7 @@ int glassnet_calibrate_fp8(gn_model* m, const gn_latent* lat, const float* gbuf,
   uint32_t* amax = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(tmp) + out_bytes);
   uint32_t bits[gn::kFp8Acts] = {};
   e = gn::launch_plain_fp32(m->w32, m->wi, lat->d, gbuf, tbuf, cnt, K, P, out, m->ws, m->err, s,
-                            0, w);
+                            m->pooling == GN_POOL_SUM, w);
   if (e == cudaSuccess)
     e = gn::launch_fp8_act_amax(m->ws, gbuf, tbuf, cnt, m->H, K, P, amax, s);
   if (e == cudaSuccess)

@@ -30,9 +30,9 @@ CAL = dict(h=128, w=128, K=8, counts="poisson3", seed=1)
 
 
 class Fp8Net:
-    def __init__(self, widths, seed=0, bias="zero"):
+    def __init__(self, widths, seed=0, bias="zero", pooling=gl.GN_POOL_MAX_MEAN):
         self.w = synth.make_weights(widths, seed=seed, bias=bias)
-        self.model = gl.Model(self.w, gl.GN_FP8_FUSED)
+        self.model = gl.Model(self.w, gl.GN_FP8_FUSED, pooling)
         self.cal = synth.make_frame(CAL["h"], CAL["w"], CAL["K"], counts=CAL["counts"],
                                     seed=CAL["seed"])
         lat = self.model.encode(synth.make_scene(0))
@@ -178,3 +178,30 @@ def test_fp8_full_512_K8_poisson_sampled(doubled8):
                        counts=frame.counts[ys, xs][None, :].copy())
     e2 = np.abs(got[:, ys, xs] - _ref(doubled8, samp)[:, 0, :])
     assert e2.max() <= FP8_MAX and e2.mean() <= FP8_MEAN, (e2.max(), e2.mean())
+
+
+# ------------------------------------------------ sum pooling (Eq. 5 form)
+
+@pytest.fixture(scope="module")
+def doubled8_sum(cuda_lib):
+    return Fp8Net(synth.DOUBLED_WIDTHS, seed=0, bias="uniform", pooling=gl.GN_POOL_SUM)
+
+
+@pytest.mark.parametrize("case", [(96, 80, 8, "poisson3", 2), (64, 64, 4, "uniform", 3), (33, 47, 8, "all", 4)],
+                         ids=lambda c: f"{c[0]}x{c[1]}-K{c[2]}-{c[3]}")
+def test_fp8_sum_pooling_vs_oracle(doubled8_sum, case):
+    """The sum form calibrates on the FP32 plain path's sum form (tau is the
+    r input of B1 and shares its scale) and meets the FP8 tolerance."""
+    h, w, K, counts, seed = case
+    f = synth.make_frame(h, w, K, counts=counts, seed=seed)
+    got = doubled8_sum.render(f)
+    exp = oracle.render_frame(doubled8_sum.w, synth.make_scene(0), f.gbuf, f.tbuf, f.counts, pooling="sum")
+    err = np.abs(got - exp)
+    assert err.max() <= FP8_MAX and err.mean() <= FP8_MEAN, (err.max(), err.mean())
+
+
+def test_fp8_sum_pooling_bit_identical_under_permutations(doubled8_sum):
+    f = synth.make_frame(128, 96, 8, counts="uniform", seed=9)
+    base = doubled8_sum.render(f)
+    for s in range(1, 5):
+        assert np.array_equal(doubled8_sum.render(synth.permute_layers(f, seed=s)), base), s
