@@ -20,7 +20,7 @@
 // 128-column strip, so a pass reads 4 rows of which it loads 2 new ones, the
 // first while the previous pass runs and the second (needed only by the
 // taps with dy = +1) once that pass has released its oldest row.  Weights
-// stream from L2 through a ring of 7 stages of a quarter tap (K = 32) each.
+// stream from L2 through a ring of 3 stages of half a tap (K = 64) each.
 //
 // Warps: 0-3 epilogue (TMEM lane quadrant = warp), 4 MMA, 5 weight loads,
 // 6 row loads.  The epilogue turns each accumulator into q = BF16(ReLU(D +
@@ -43,10 +43,10 @@ struct ConvLayout {
   static constexpr uint32_t kChunkBytes = kCols * 16;     // one 8-channel chunk of a halo row
   static constexpr uint32_t kRowBytes = (H / 8) * kChunkBytes;
   static constexpr int kSlots = 5;
-  static constexpr int kStageChunks = 4;                  // K = 32 per weight stage
+  static constexpr int kStageChunks = 8;                  // K = 64 per weight stage
   static constexpr uint32_t kStageBytes = kStageChunks * H * 16;
   static constexpr int kStagesPerTap = (H / 8) / kStageChunks;
-  static constexpr int kStages = 7;
+  static constexpr int kStages = 3;
   static constexpr uint32_t kTapBytes = H * H * 2;        // [H/8][H][8] bf16
   static constexpr uint32_t kTailBytes = (H + 3 * H + 4) * 4;  // b_R1 [H], W_R2 [3][H], b_R2 [4]
   // shared memory
@@ -72,7 +72,7 @@ struct ConvParams {
   int h, w, hp, passes;  // hp = passes per strip = ceil(h / 2)
 };
 
-constexpr int kSlotsC = 5, kStagesC = 7;
+constexpr int kSlotsC = 5, kStagesC = 3;
 enum : int {
   C_TAIL = 0,                     // biases and R2 copied
   C_FULL = 1,                     // + slot: halo row loaded
