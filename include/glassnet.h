@@ -203,11 +203,14 @@ int glassnet_latent_read(const gn_latent* latent, float* sigma_dev, float* c_phi
  * Renders one frame: the per-pixel network over every pixel (Sec. 3.2-3.4).
  * K is the number of layer slots in tbuf (0..8); K = 0 renders the
  * opaque-only path (r = 0) and tbuf may be NULL.  h, w >= 1, 12*max(K,1)*h*w < 2^31.
- * Precision is the model's.  GN_BF16_FUSED: one kernel launch, output
- * bit-identical under any permutation of each pixel's valid layers.
- * GN_FP32_PLAIN: one kernel per layer with intermediates in a workspace the
- * model owns and grows on demand (a growing call synchronises the device);
- * concurrent FP32 renders of one model on different streams must use
+ * Precision is the model's.  GN_BF16_FUSED / GN_FP8_FUSED: the tile-plan
+ * kernel and one fused kernel (and the 3x3 R kernel for r_kernel = 3),
+ * output bit-identical under any permutation of each pixel's valid layers.
+ * GN_FP32_PLAIN: one kernel per layer.  The workspace (FP32 intermediates,
+ * or the fused tile plan with its tile counter and, for r_kernel = 3, the
+ * neural buffer) is owned by the model and grows on demand (a growing call
+ * synchronises the device), so renders of one model must be ordered on one
+ * stream; concurrent renders of one model on different streams must use
  * glassnet_render_ws with separate workspaces.
  * Errors: GN_EINVAL (bad sizes, NULL pointers, misalignment, latent of another
  * width), GN_ENOMEM, GN_ECUDA.
