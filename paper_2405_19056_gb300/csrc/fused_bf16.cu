@@ -411,7 +411,8 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 // bands of 16 K columns in phi1's and B1's first operands).
 // R3: R's first layer is a 3x3 kernel over the frame (conv_r3.cu): the tile
 // ends after B2 and writes the neural buffer y (BF16, layout
-// [y][H/8][x][8] per frame) to device memory instead of running R.
+// [y][H/8][x][8], one buffer per frame of the launch) to device memory
+// instead of running R.
 template <int H, int Mode, bool Sum, bool PE, bool R3>
 __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
@@ -899,11 +900,12 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
         uint4* phi_px = nullptr;
         uint32_t fw = 0;
         if constexpr (R3) {
-          fw = static_cast<uint32_t>(prm.f[0].w);
+          const FusedFrame& Fr = frame_of(prm, tile);
+          fw = static_cast<uint32_t>(Fr.w);
           if (ent != kPlanEmpty) {
             const uint32_t pix = ent & kPlanPixelMask;
             const uint32_t py = pix / fw;
-            phi_px = reinterpret_cast<uint4*>(prm.f[0].phi) + static_cast<size_t>(py) * (H / 8) * fw +
+            phi_px = reinterpret_cast<uint4*>(Fr.phi) + static_cast<size_t>(py) * (H / 8) * fw +
                      (pix - py * fw);
           }
         }
@@ -1051,7 +1053,7 @@ cudaError_t launch_mode(int mode, const void* wimg, const FusedParams& p, cudaSt
   // accumulation is the same for both poolings (the state holds max and sum)
   if (mode == kModeAccumulate) return launch_h<H, kModeAccumulate, false, PE>(wimg, p, s, grid);
   if (p.f[0].phi) {  // the neural buffer out, for the 3x3 R (whole frames only)
-    if (mode != kModeFrame || p.nframes != 1) return cudaErrorInvalidValue;
+    if (mode != kModeFrame) return cudaErrorInvalidValue;
     return p.pool_sum ? launch_h<H, kModeFrame, true, PE, true>(wimg, p, s, grid)
                       : launch_h<H, kModeFrame, false, PE, true>(wimg, p, s, grid);
   }

@@ -18,6 +18,11 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// The BF16 neural buffer of a 3x3 R render: [h][H/8][w][8], 256-byte rounded.
+size_t phi_bytes(const gn_model* m, int h, int w) {
+  return (static_cast<size_t>(h) * w * m->H * 2 + 255) / 256 * 256;
+}
+
 int fail(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -447,13 +452,6 @@ int glassnet_latent_read(const gn_latent* lat, float* sigma, float* c_phi, float
   return GN_OK;
 }
 
-namespace {
-// The BF16 neural buffer of a 3x3 R render: [h][H/8][w][8], 256-byte rounded.
-size_t phi_bytes(const gn_model* m, int h, int w) {
-  return (static_cast<size_t>(h) * w * m->H * 2 + 255) / 256 * 256;
-}
-}  // namespace
-
 int glassnet_workspace_bytes(const gn_model* m, int K, int h, int w, size_t* bytes) {
   if (!m || !bytes) return fail(GN_EINVAL, "model and bytes must be non-NULL");
   if (K < 0 || K > gn::kMaxK || h < 1 || w < 1) return fail(GN_EINVAL, "bad frame size");
@@ -502,8 +500,6 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
   if (n < 1 || n > kMaxBatch) return fail(GN_EINVAL, "batch of %d frames outside 1..%d", n, kMaxBatch);
   if (m->precision == GN_FP32_PLAIN)
     return fail(GN_EUNSUPPORTED, "batched launch needs a fused precision");
-  if (m->wi.RK == 3)
-    return fail(GN_EUNSUPPORTED, "a 3x3 R renders one frame per call (glassnet_render)");
   if (m->precision == GN_FP8_FUSED && !m->fp8_ready)
     return fail(GN_EINVAL, "FP8 model is not calibrated (glassnet_calibrate_fp8)");
   FusedParams& p = *out;
@@ -520,6 +516,7 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
     }
     const int P = f.h * f.w;
     p.f[i] = FusedFrame{f.gbuf, f.tbuf, f.layer_count, f.out, f.latent->fold(), f.K, P, 0, 0};
+    p.f[i].w = f.w;
     tiles += (P + kTile - 1) / kTile;
     if (tiles >= (1ll << 24)) return fail(GN_EINVAL, "batch too large");
   }
@@ -554,6 +551,31 @@ void bind_plan(FusedParams& p, void* ws) {
   p.plan = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws) + kPlanHeader);
 }
 
+size_t batch_ws_bytes(const gn_model* m, const FusedParams& p) {
+  size_t b = (fused_plan_bytes(p.total_tiles) + 255) / 256 * 256;
+  if (m->wi.RK == 3)
+    for (int i = 0; i < p.nframes; ++i) b += phi_bytes(m, p.f[i].P / p.f[i].w, p.f[i].w);
+  return b;
+}
+
+void bind_batch_ws(const gn_model* m, FusedParams& p, void* ws) {
+  bind_plan(p, ws);
+  if (m->wi.RK != 3) return;
+  uint8_t* at = static_cast<uint8_t*>(ws) + (fused_plan_bytes(p.total_tiles) + 255) / 256 * 256;
+  for (int i = 0; i < p.nframes; ++i) {
+    p.f[i].phi = reinterpret_cast<uint16_t*>(at);
+    at += phi_bytes(m, p.f[i].P / p.f[i].w, p.f[i].w);
+  }
+}
+
+cudaError_t launch_render(const gn_model* m, const FusedParams& p, cudaStream_t s) {
+  cudaError_t e = launch_fused(m, p, s);
+  if (e != cudaSuccess || m->wi.RK != 3) return e;
+  for (int i = 0; i < p.nframes && e == cudaSuccess; ++i)
+    e = launch_conv_r3(m->H, m->conv, p.f[i].phi, p.f[i].out, p.f[i].P / p.f[i].w, p.f[i].w, m->err, s);
+  return e;
+}
+
 }  // namespace gn
 
 extern "C" {
@@ -583,26 +605,17 @@ int glassnet_render_ws(const gn_model* m, const gn_latent* lat, const float* gbu
   p.nframes = 1;
   p.err = m->err;
   p.f[0] = gn::FusedFrame{gbuf, tbuf, cnt, out, lat->fold(), K, P, 0, 0};
+  p.f[0].w = w;
   number_tiles(p);
-  size_t need = 0;
-  glassnet_workspace_bytes(m, K, h, w, &need);
+  const size_t need = gn::batch_ws_bytes(m, p);  // = glassnet_workspace_bytes
   if (!ws || ws_bytes < need)
     return fail(GN_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, need);
   if (reinterpret_cast<uintptr_t>(ws) & 255u)
     return fail(GN_EINVAL, "workspace must be 256-byte aligned");
-  gn::bind_plan(p, ws);
-  uint16_t* phi = nullptr;
-  if (m->wi.RK == 3) {  // the fused kernel stops at the neural buffer, the 3x3 R follows
-    phi = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(ws) + need - phi_bytes(m, h, w));
-    p.f[0].phi = phi;
-    p.f[0].w = w;
-  }
-  e = gn::launch_fused(m, p, s);
+  // the plan (and, for a 3x3 R, the neural buffer the fused kernel stops at)
+  gn::bind_batch_ws(m, p, ws);
+  e = gn::launch_render(m, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "fused launch");
-  if (phi) {
-    e = gn::launch_conv_r3(m->H, m->conv, phi, out, h, w, m->err, s);
-    if (e != cudaSuccess) return cuda_fail(e, "3x3 R launch");
-  }
   return GN_OK;
 }
 
@@ -663,10 +676,10 @@ int glassnet_render_batch(const gn_model* m, const gn_frame* frames, int n, cuda
   int rc = gn::build_batch(m, frames, n, &p);
   if (rc != GN_OK) return rc;
   gn_model* mm = const_cast<gn_model*>(m);
-  rc = grow_buffer(mm->plan, mm->plan_bytes, gn::fused_plan_bytes(p.total_tiles), "tile plan");
+  rc = grow_buffer(mm->plan, mm->plan_bytes, gn::batch_ws_bytes(m, p), "tile plan");
   if (rc != GN_OK) return rc;
-  gn::bind_plan(p, mm->plan);
-  cudaError_t e = gn::launch_fused(m, p, s);
+  gn::bind_batch_ws(m, p, mm->plan);
+  cudaError_t e = gn::launch_render(m, p, s);
   if (e != cudaSuccess) return cuda_fail(e, "batched fused launch");
   return GN_OK;
 }

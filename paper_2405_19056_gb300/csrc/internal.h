@@ -177,8 +177,8 @@ struct FusedFrame {
   int P;      // pixels
   int tile0;  // first global tile index of this frame
   int win0;   // first global plan window of this frame (set by the launcher)
-  // 3x3 R only (single-frame launches): the neural buffer the fused kernel
-  // writes, BF16 [h][H/8][w][8], and the frame width.
+  // 3x3 R: the neural buffer the fused kernel writes, BF16 [h][H/8][w][8],
+  // and the frame width.
   uint16_t* phi;
   int w;
 };
@@ -290,6 +290,12 @@ cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s
 cudaError_t prepare_fused(const gn_model* m);
 // Points the params at a plan workspace of fused_plan_bytes(p.total_tiles) bytes.
 void bind_plan(FusedParams& p, void* ws);
+// Workspace of a launch of the model's form: the plan (256-byte rounded),
+// then, for a 3x3 R, each frame's neural buffer; binding sets both.
+size_t batch_ws_bytes(const gn_model* m, const FusedParams& p);
+void bind_batch_ws(const gn_model* m, FusedParams& p, void* ws);
+// The fused launch and, for a 3x3 R, each frame's 3x3 kernel.
+cudaError_t launch_render(const gn_model* m, const FusedParams& p, cudaStream_t s);
 // Sets the calling thread's glassnet_last_error message; returns `code`.
 int set_error(int code, const char* msg);
 }  // namespace gn

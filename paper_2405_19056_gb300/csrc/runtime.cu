@@ -17,14 +17,15 @@ int cuda_err(cudaError_t e, const char* what) {
   return gn::set_error(GN_ECUDA, buf);
 }
 
-// Captures the plan + fused launch of `p` on a private stream.
+// Captures the plan + fused launch of `p` (and a 3x3 R's kernels) on a
+// private stream.
 int capture(const gn_model* m, const gn::FusedParams& p, cudaGraph_t* graph) {
   cudaStream_t cs = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_err(e, "create capture stream");
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    const cudaError_t el = gn::launch_fused(m, p, cs);
+    const cudaError_t el = gn::launch_render(m, p, cs);
     e = cudaStreamEndCapture(cs, graph);
     if (el != cudaSuccess) e = el;
   }
@@ -36,7 +37,7 @@ int capture(const gn_model* m, const gn::FusedParams& p, cudaGraph_t* graph) {
 bool same_shapes(const gn::FusedParams& a, const gn::FusedParams& b) {
   if (a.nframes != b.nframes || a.total_tiles != b.total_tiles) return false;
   for (int i = 0; i < a.nframes; ++i)
-    if (a.f[i].P != b.f[i].P || a.f[i].K != b.f[i].K) return false;
+    if (a.f[i].P != b.f[i].P || a.f[i].w != b.f[i].w || a.f[i].K != b.f[i].K) return false;
   return true;
 }
 
@@ -62,12 +63,12 @@ int glassnet_graph_create(const gn_model* m, const gn_frame* frames, int n, gn_g
   gn_graph* g = new (std::nothrow) gn_graph();
   if (!g) return gn::set_error(GN_ENOMEM, "host allocation failed");
   g->model = m;
-  const size_t bytes = gn::fused_plan_bytes(p.total_tiles);
+  const size_t bytes = gn::batch_ws_bytes(m, p);
   if ((e = cudaMalloc(&g->ws, bytes)) != cudaSuccess) {
     delete g;
     return gn::set_error(GN_ENOMEM, "cudaMalloc graph tile plan");
   }
-  gn::bind_plan(p, g->ws);
+  gn::bind_batch_ws(m, p, g->ws);
   cudaGraph_t graph = nullptr;
   if ((rc = capture(m, p, &graph)) != GN_OK) {
     glassnet_graph_free(g);
@@ -98,7 +99,7 @@ int glassnet_graph_update(gn_graph* g, const gn_frame* frames, int n) {
   if (rc != GN_OK) return rc;
   if (!same_shapes(p, g->params))
     return gn::set_error(GN_EINVAL, "frame count, sizes or K differ from the captured batch");
-  gn::bind_plan(p, g->ws);
+  gn::bind_batch_ws(g->model, p, g->ws);
   cudaGraph_t graph = nullptr;
   if ((rc = capture(g->model, p, &graph)) != GN_OK) return rc;
   cudaGraphExecUpdateResultInfo info;

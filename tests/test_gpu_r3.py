@@ -146,16 +146,41 @@ def test_r3_render_host_and_workspace(cuda_lib):
     assert n3 >= n1 + 50 * 150 * 128 * 2  # the neural buffer
 
 
+def test_r3_batch_and_graph_equal_single_renders(cuda_lib):
+    """Frames of different sizes in one batched launch (each with its own
+    neural buffer and 3x3 kernel launch), and the same batch replayed from a
+    CUDA graph, reproduce the single renders bit for bit."""
+    _, m = model()
+    specs = [(33, 47, 3, "uniform", 1), (70, 200, 8, "poisson3", 2), (5, 300, 1, "all", 3)]
+    frames, singles, outs, lats = [], [], [], []
+    for (h, w, K, cd, sd) in specs:
+        f = synth.make_frame(h, w, K, counts=cd, seed=20 + sd)
+        singles.append(render(m, synth.make_scene(sd), f))
+        lat = m.encode(synth.make_scene(sd))
+        lats.append(lat)
+        out = torch.full((3, h, w), float("nan"), device=DEV)
+        outs.append(out)
+        frames.append(dict(latent=lat.handle, gbuf=_dev(f.gbuf), tbuf=_dev(f.tbuf),
+                           layer_count=_dev(f.counts), K=K, h=h, w=w, out=out))
+    gl.glassnet_render_batch(m.handle, frames)
+    m.check()
+    for out, single in zip(outs, singles):
+        assert np.array_equal(out.cpu().numpy().astype(np.float64), single)
+        out.fill_(float("nan"))
+    g = gl.glassnet_graph_create(m.handle, frames)
+    try:
+        for _ in range(2):
+            gl.glassnet_graph_launch(g)
+            m.check()
+            for out, single in zip(outs, singles):
+                assert np.array_equal(out.cpu().numpy().astype(np.float64), single)
+                out.fill_(float("nan"))
+    finally:
+        gl.glassnet_graph_free(g)
+
+
 def test_r3_refused_where_not_built(cuda_lib):
     w, m = model()
-    lat = m.encode(synth.make_scene(0))
-    f = synth.make_frame(16, 16, 2, counts="all", seed=1)
-    out = torch.empty((3, 16, 16), device=DEV)
-    frames = [dict(latent=lat.handle, gbuf=_dev(f.gbuf), tbuf=_dev(f.tbuf), layer_count=_dev(f.counts),
-                   K=2, h=16, w=16, out=out)]
-    with pytest.raises(gl.GlassNetError) as ei:
-        gl.glassnet_render_batch(m.handle, frames)
-    assert ei.value.code == gl.GN_EUNSUPPORTED
     with pytest.raises(gl.GlassNetError) as ei:
         gl.glassnet_pool_create(m.handle, 16, 16)
     assert ei.value.code == gl.GN_EUNSUPPORTED
