@@ -103,3 +103,22 @@ def test_least_recently_used_scene_is_replaced(model):
             gl.glassnet_server_submit(srv, c, r["g"], r["t"], r["c"], 8, 64, 64, r["out"])
     finally:
         gl.glassnet_server_destroy(srv)
+
+
+@pytest.mark.parametrize("form", ["sum", "r3", "pe"])
+def test_model_options_served_equal_alone(cuda_lib, form):
+    """The serving loop with the model options (sum pooling, a 3x3 R whose
+    per-lane graphs hold a neural buffer, positional encoding at H = 64):
+    each request equals its render alone, bit for bit."""
+    if form == "pe":
+        w = synth.make_weights(synth.Widths(64, 128, 4), seed=2, bias="uniform")
+    else:
+        w = synth.make_weights(synth.Widths(128, 256, 0, 3 if form == "r3" else 1), seed=2, bias="uniform")
+    m = gl.Model(w, gl.GN_BF16_FUSED, gl.GN_POOL_SUM if form == "sum" else gl.GN_POOL_MAX_MEAN)
+    scenes = [21, 22]
+    reqs = _requests(10, seed=3, n_scenes=len(scenes))
+    _serve(m, reqs, scenes, n_streams=2, max_scenes=2, max_h=128, max_w=128, max_K=8)
+    m.check()
+    latents = [m.encode(synth.make_scene(s)) for s in scenes]
+    for i, r in enumerate(reqs):
+        assert np.array_equal(r["out"].numpy(), _alone(m, latents[r["scene"]], r)), (form, i)
