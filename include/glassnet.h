@@ -165,8 +165,9 @@ typedef struct gn_model_config {
  *   above): the fused kernel writes each frame's neural buffer (BF16, H 2
  *   bytes per pixel, in the launch's workspace, so glassnet_workspace_bytes
  *   grows by about h w H 2 bytes), then a tcgen05 kernel per frame runs the
- *   3x3 layer, R2 and the sigmoid.  Streaming calls and GN_FP8_FUSED return
- *   GN_EUNSUPPORTED.
+ *   3x3 layer, R2 and the sigmoid (streaming: the resolve writes the neural
+ *   buffer into the pool's own, then the 3x3 kernel runs).  GN_FP8_FUSED
+ *   returns GN_EUNSUPPORTED.
  * Errors: those of glassnet_load_weights, GN_EINVAL (NULL config, unknown
  * pooling, pe_freqs outside 0..10, r_kernel not 0, 1 or 3), GN_EUNSUPPORTED.
  */

@@ -417,7 +417,7 @@ template <int H, int Mode, bool Sum, bool PE, bool R3>
 __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   static_assert(!Sum || Mode != kModeAccumulate, "accumulation does not depend on the pooling");
-  static_assert(!R3 || Mode == kModeFrame, "the 3x3 R runs on whole frames");
+  static_assert(!R3 || Mode != kModeAccumulate, "accumulation does not depend on R");
   using L = FusedLayout<H, PE>;
   using T = TMap<H>;
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
@@ -1044,6 +1044,8 @@ cudaError_t prepare_all() {
   if (e == cudaSuccess) e = prepare_h<H, kModeResolve, true, PE>();
   if (e == cudaSuccess) e = prepare_h<H, kModeFrame, false, PE, true>();
   if (e == cudaSuccess) e = prepare_h<H, kModeFrame, true, PE, true>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeResolve, false, PE, true>();
+  if (e == cudaSuccess) e = prepare_h<H, kModeResolve, true, PE, true>();
   return e;
 }
 
@@ -1052,8 +1054,10 @@ cudaError_t launch_mode(int mode, const void* wimg, const FusedParams& p, cudaSt
                         int grid) {
   // accumulation is the same for both poolings (the state holds max and sum)
   if (mode == kModeAccumulate) return launch_h<H, kModeAccumulate, false, PE>(wimg, p, s, grid);
-  if (p.f[0].phi) {  // the neural buffer out, for the 3x3 R (whole frames only)
-    if (mode != kModeFrame) return cudaErrorInvalidValue;
+  if (p.f[0].phi) {  // the neural buffer out, for the 3x3 R (frames and resolves)
+    if (mode == kModeResolve)
+      return p.pool_sum ? launch_h<H, kModeResolve, true, PE, true>(wimg, p, s, grid)
+                        : launch_h<H, kModeResolve, false, PE, true>(wimg, p, s, grid);
     return p.pool_sum ? launch_h<H, kModeFrame, true, PE, true>(wimg, p, s, grid)
                       : launch_h<H, kModeFrame, false, PE, true>(wimg, p, s, grid);
   }

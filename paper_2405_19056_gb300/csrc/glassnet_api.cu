@@ -776,7 +776,8 @@ struct gn_pool {
   uint32_t* st = nullptr;
   size_t st_words = 0;
   uint8_t* cnt = nullptr;
-  void* plan = nullptr;  // tile plan of the pool's launches
+  void* plan = nullptr;  // tile plan of the pool's launches, then (3x3 R) the neural buffer
+  uint16_t* phi = nullptr;
   int layers = 0;        // accumulate calls since the last reset
 };
 
@@ -819,8 +820,8 @@ int check_pool_call(const gn_model* m, const gn_latent* lat, const gn_pool* pool
   if (!m) return fail(GN_EINVAL, "model is NULL");
   if (!lat) return fail(GN_EINVAL, "latent is NULL");
   if (!pool) return fail(GN_EINVAL, "pool is NULL");
-  if (m->precision != GN_BF16_FUSED || m->wi.RK == 3)
-    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model with a 1x1 R");
+  if (m->precision != GN_BF16_FUSED)
+    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model");
   if (lat->H != m->H || lat->Z != m->Z)
     return fail(GN_EINVAL, "latent widths (%d, %d) do not match the model (%d, %d)", lat->H,
                 lat->Z, m->H, m->Z);
@@ -834,8 +835,8 @@ extern "C" {
 int glassnet_pool_create(const gn_model* m, int h, int w, gn_pool** out) {
   if (!m || !out) return fail(GN_EINVAL, "model and out must be non-NULL");
   *out = nullptr;
-  if (m->precision != GN_BF16_FUSED || m->wi.RK == 3)
-    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model with a 1x1 R");
+  if (m->precision != GN_BF16_FUSED)
+    return fail(GN_EUNSUPPORTED, "streaming needs a GN_BF16_FUSED model");
   if (h < 1 || w < 1) return fail(GN_EINVAL, "frame %d x %d is empty", h, w);
   const long long P = static_cast<long long>(h) * w;
   if (P * gn::kTC >= (1ll << 31)) return fail(GN_EINVAL, "frame %d x %d too large", h, w);
@@ -856,11 +857,14 @@ int glassnet_pool_create(const gn_model* m, int h, int w, gn_pool** out) {
   uint8_t* base = static_cast<uint8_t*>(pool->dev);
   pool->st = reinterpret_cast<uint32_t*>(base);
   pool->cnt = base + b_st;
-  if (cudaMalloc(&pool->plan, gn::fused_plan_bytes(tiles)) != cudaSuccess) {
+  const size_t b_plan = up(gn::fused_plan_bytes(tiles));
+  const size_t b_phi = m->wi.RK == 3 ? phi_bytes(m, h, w) : 0;
+  if (cudaMalloc(&pool->plan, b_plan + b_phi) != cudaSuccess) {
     cudaFree(pool->dev);
     delete pool;
     return fail(GN_ENOMEM, "cudaMalloc pool tile plan");
   }
+  if (b_phi) pool->phi = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(pool->plan) + b_plan);
   int rc = glassnet_pool_reset(pool, nullptr);
   if (rc == GN_OK && (e = cudaStreamSynchronize(nullptr)) != cudaSuccess) rc = cuda_fail(e, "pool reset");
   if (rc != GN_OK) {
@@ -905,7 +909,13 @@ int glassnet_resolve(const gn_model* m, const gn_latent* lat, const gn_pool* poo
   if (!gbuf || !out) return fail(GN_EINVAL, "gbuf and out must be non-NULL");
   if (!aligned4(gbuf) || !aligned4(out)) return fail(GN_EINVAL, "gbuf and out must be 4-byte aligned");
   gn::FusedParams p = pool_params(m, lat, pool, gbuf, nullptr, pool->cnt, gn::kMaxK, out);
+  if (pool->phi) {  // 3x3 R: the resolve stops at the neural buffer, the 3x3 kernel follows
+    p.f[0].phi = pool->phi;
+    p.f[0].w = pool->w;
+  }
   cudaError_t e = gn::launch_fused_bf16(m->H, m->fused, p, s, 2);
+  if (e == cudaSuccess && pool->phi)
+    e = gn::launch_conv_r3(m->H, m->conv, pool->phi, out, pool->h, pool->w, m->err, s);
   if (e != cudaSuccess) return cuda_fail(e, "resolve launch");
   return GN_OK;
 }

@@ -179,11 +179,30 @@ def test_r3_batch_and_graph_equal_single_renders(cuda_lib):
         gl.glassnet_graph_free(g)
 
 
+def test_r3_streamed_equals_render(cuda_lib):
+    """Layers accumulated one at a time (any order), then the resolve writes
+    the neural buffer into the pool's own and the 3x3 kernel runs: the frame
+    equals glassnet_render bit for bit."""
+    _, m = model()
+    scene = synth.make_scene(4)
+    f = synth.make_frame(90, 260, 8, counts="poisson3", seed=12)
+    want = render(m, scene, f)
+    lat = m.encode(scene)
+    pool = gl.glassnet_pool_create(m.handle, f.h, f.w)
+    try:
+        tb, cnt = _dev(f.tbuf), _dev(f.counts)
+        for k in [2, 7, 0, 5, 3, 1, 6, 4]:
+            gl.glassnet_accumulate_layer(m.handle, lat.handle, pool, tb[k], (cnt > k).to(torch.uint8))
+        out = torch.full((3, f.h, f.w), float("nan"), device=DEV)
+        gl.glassnet_resolve(m.handle, lat.handle, pool, _dev(f.gbuf), out)
+        m.check()
+        assert np.array_equal(out.cpu().numpy().astype(np.float64), want)
+    finally:
+        gl.glassnet_pool_free(pool)
+
+
 def test_r3_refused_where_not_built(cuda_lib):
     w, m = model()
-    with pytest.raises(gl.GlassNetError) as ei:
-        gl.glassnet_pool_create(m.handle, 16, 16)
-    assert ei.value.code == gl.GN_EUNSUPPORTED
     with pytest.raises(gl.GlassNetError) as ei:
         gl.Model(w, gl.GN_FP8_FUSED)
     assert ei.value.code == gl.GN_EUNSUPPORTED
