@@ -160,14 +160,15 @@ typedef struct gn_model_config {
  * pe_freqs > 0 serves every render, batch, graph, server and streaming call
  * of GN_FP32_PLAIN / GN_BF16_FUSED models; with GN_FP8_FUSED it returns
  * GN_EUNSUPPORTED.
- * r_kernel = 3 serves every render, batch, graph and server call of
- *   GN_FP32_PLAIN and GN_BF16_FUSED models (any pooling; with pe_freqs as
+ * r_kernel = 3 serves every render, batch, graph and server call of every
+ *   precision (streaming: GN_BF16_FUSED) (any pooling; with pe_freqs as
  *   above): the fused kernel writes each frame's neural buffer (BF16, H 2
  *   bytes per pixel, in the launch's workspace, so glassnet_workspace_bytes
  *   grows by about h w H 2 bytes), then a tcgen05 kernel per frame runs the
  *   3x3 layer, R2 and the sigmoid (streaming: the resolve writes the neural
  *   buffer into the pool's own, then the 3x3 kernel runs).  GN_FP8_FUSED
- *   returns GN_EUNSUPPORTED.
+ *   models write B2's output in real units as BF16 and share the BF16 3x3
+ *   kernel.
  * Errors: those of glassnet_load_weights, GN_EINVAL (NULL config, unknown
  * pooling, pe_freqs outside 0..10, r_kernel not 0, 1 or 3), GN_EUNSUPPORTED.
  */

@@ -220,7 +220,10 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
 // fixed-point sum) goes straight to B1's r operand as codes of tau / s_g,
 // where rho's output would go; rho's GEMM and its epilogue pass are skipped
 // and the max is not kept.
-template <int H, bool Sum>
+// R3: R's first layer is a 3x3 kernel over the frame (conv_r3.cu): the tile
+// ends after B2, whose output goes to the frame's neural buffer as BF16 in
+// real units ((acc s_B2 + b_B2) s_y2, ReLU) instead of R1's E4M3 operand.
+template <int H, bool Sum, bool R3>
 __global__ void __launch_bounds__(kThreadsF, 1)
     fused_fp8_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   using L = FusedLayoutF8<H>;
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       const uint32_t Y = tbase + T::buf(p1.b == 2 ? 0 : p1.b + 1);
       const uint32_t Z = tbase + T::buf(p1.b == 0 ? 2 : p1.b - 1);
 #pragma unroll
-      for (int l = Sum ? 1 : 0; l < 4; ++l) {
+      for (int l = Sum ? 1 : 0; l < (R3 ? 3 : 4); ++l) {
         if (!wait_in()) goto done;
         if (l == 1) {
           if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
@@ -395,8 +398,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         if (l == 1) mma_commit_e(bar(B_AG_E));
         __syncwarp();
       }
-      if (!wait_in()) goto done;
-      issue_gemm_f8<16, H>(Z + H / 2, Y + H / 2, dsc_r2, id816);
+      if (!wait_in()) goto done;  // R2's operand written (3x3 R: B2's accumulator read)
+      if constexpr (!R3) issue_gemm_f8<16, H>(Z + H / 2, Y + H / 2, dsc_r2, id816);
       mma_commit_e(bar(B_DR2));
       __syncwarp();
     }
@@ -569,8 +572,23 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const uint32_t X = tl + T::buf(r3);
         const uint32_t Y = tl + T::buf(r3 == 2 ? 0 : r3 + 1);
         const uint32_t Z = tl + T::buf(r3 == 0 ? 2 : r3 - 1);
+        // 3x3 R: this row's pixel in its frame's neural buffer (chunk c of 8
+        // channels at phi_px + c w)
+        uint4* phi_px = nullptr;
+        uint32_t fw = 0;
+        if constexpr (R3) {
+          const FusedFrame& Fr = frame_of(prm, tile);
+          fw = static_cast<uint32_t>(Fr.w);
+          const uint32_t e = __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row);
+          if (e != kPlanEmpty) {
+            const uint32_t pix = e & kPlanPixelMask;
+            const uint32_t py = pix / fw;
+            phi_px = reinterpret_cast<uint4*>(Fr.phi) + static_cast<size_t>(py) * (H / 8) * fw +
+                     (pix - py * fw);
+          }
+        }
 #pragma unroll
-        for (int l = Sum ? 1 : 0; l < 4; ++l) {
+        for (int l = Sum ? 1 : 0; l < (R3 ? 3 : 4); ++l) {
           if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
           ++n_dp;
           tc_fence_after();
@@ -587,9 +605,27 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             uint32_t(&cur)[16] = (hh & 1) ? rb : ra;
             uint32_t(&nxt)[16] = (hh & 1) ? ra : rb;
             if (hh + 1 < CH / 16) tmem_ld16_async(src + (hh + 1) * 16, nxt);
-            uint32_t u[4];
-            quant16(cur, sl + hh * 16, bl ? bl + hh * 16 : nullptr, l == 0 && c == 0, u);
-            tmem_st4(dst + hh * 4, u);
+            if (R3 && l == 2) {  // y2 in real units -> the neural buffer (BF16)
+              if (phi_px) {
+                const float s_y2 = cst[L::S_Y2];
+                uint32_t v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  float y0, y1;
+                  ffma2(y0, y1, __uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]),
+                        sl[hh * 16 + 2 * i], sl[hh * 16 + 2 * i + 1], bl[hh * 16 + 2 * i],
+                        bl[hh * 16 + 2 * i + 1]);
+                  v[i] = pack_bf16_relu(y0 * s_y2, y1 * s_y2);
+                }
+                const size_t c8 = static_cast<size_t>(g * CH + hh * 16) / 8;
+                phi_px[c8 * fw] = make_uint4(v[0], v[1], v[2], v[3]);
+                phi_px[(c8 + 1) * fw] = make_uint4(v[4], v[5], v[6], v[7]);
+              }
+            } else {
+              uint32_t u[4];
+              quant16(cur, sl + hh * 16, bl ? bl + hh * 16 : nullptr, l == 0 && c == 0, u);
+              tmem_st4(dst + hh * 4, u);
+            }
             if (hh + 1 < CH / 16) tmem_wait_ld_tied(nxt);
           }
           arrive_in();
@@ -598,7 +634,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const uint32_t ent = g == 0 ? __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row)
                                     : kPlanEmpty;
         if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
-        if (g == 0) {
+        if (!R3 && g == 0) {
           tc_fence_after();
           uint32_t r[4];
           tmem_ld4(Z + H / 2, r);
@@ -625,20 +661,20 @@ done:
   }
 }
 
-template <int H, bool Sum>
+template <int H, bool Sum, bool R3>
 cudaError_t prepare_f8() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_fp8_kernel<H, Sum>,
+  cudaError_t e = cudaFuncSetAttribute(fused_fp8_kernel<H, Sum, R3>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FusedLayoutF8<H>::smem_bytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <int H, bool Sum>
+template <int H, bool Sum, bool R3>
 cudaError_t launch_f8(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
-  cudaError_t e = prepare_f8<H, Sum>();
+  cudaError_t e = prepare_f8<H, Sum, R3>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -650,15 +686,17 @@ cudaError_t launch_f8(const void* wimg, const FusedParams& p, cudaStream_t s, in
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_fp8_kernel<H, Sum>, p, static_cast<const uint8_t*>(wimg));
+  return cudaLaunchKernelEx(&cfg, fused_fp8_kernel<H, Sum, R3>, p, static_cast<const uint8_t*>(wimg));
 }
 
 }  // namespace
 
 cudaError_t prepare_fused_fp8(int H) {
   device_sm_count();
-  cudaError_t e = H == 128 ? prepare_f8<128, false>() : prepare_f8<64, false>();
-  if (e == cudaSuccess) e = H == 128 ? prepare_f8<128, true>() : prepare_f8<64, true>();
+  cudaError_t e = H == 128 ? prepare_f8<128, false, false>() : prepare_f8<64, false, false>();
+  if (e == cudaSuccess) e = H == 128 ? prepare_f8<128, true, false>() : prepare_f8<64, true, false>();
+  if (e == cudaSuccess) e = H == 128 ? prepare_f8<128, false, true>() : prepare_f8<64, false, true>();
+  if (e == cudaSuccess) e = H == 128 ? prepare_f8<128, true, true>() : prepare_f8<64, true, true>();
   return e;
 }
 
@@ -668,9 +706,18 @@ cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& params,
   cudaError_t e = launch_plan(p, s);
   if (e != cudaSuccess) return e;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
+  if (p.f[0].phi) {  // 3x3 R: the neural buffer out
+    if (p.pool_sum)
+      return H == 128 ? launch_f8<128, true, true>(wimg, p, s, grid)
+                      : launch_f8<64, true, true>(wimg, p, s, grid);
+    return H == 128 ? launch_f8<128, false, true>(wimg, p, s, grid)
+                    : launch_f8<64, false, true>(wimg, p, s, grid);
+  }
   if (p.pool_sum)
-    return H == 128 ? launch_f8<128, true>(wimg, p, s, grid) : launch_f8<64, true>(wimg, p, s, grid);
-  return H == 128 ? launch_f8<128, false>(wimg, p, s, grid) : launch_f8<64, false>(wimg, p, s, grid);
+    return H == 128 ? launch_f8<128, true, false>(wimg, p, s, grid)
+                    : launch_f8<64, true, false>(wimg, p, s, grid);
+  return H == 128 ? launch_f8<128, false, false>(wimg, p, s, grid)
+                  : launch_f8<64, false, false>(wimg, p, s, grid);
 }
 
 }  // namespace gn

@@ -225,6 +225,7 @@ std::vector<uint8_t> pack_fused_fp8(const float* w, const gn::WeightIndex& wi, c
   c[L::INV_S_T] = 1.0f / s_t;
   c[L::INV_S_G] = 1.0f / s_g;
   c[L::INV_S_POOL] = 1.0f / s_pool;
+  c[L::S_Y2] = s_y2;
   return img;
 }
 
@@ -271,8 +272,6 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_con
   const int precision = cfg->precision, pooling = cfg->pooling, pe = cfg->pe_freqs;
   const int rk = cfg->r_kernel == 0 ? 1 : cfg->r_kernel;
   if (rk != 1 && rk != 3) return fail(GN_EINVAL, "r_kernel %d is neither 1 nor 3", cfg->r_kernel);
-  if (precision == GN_FP8_FUSED && rk == 3)
-    return fail(GN_EUNSUPPORTED, "a 3x3 R is built for GN_FP32_PLAIN and GN_BF16_FUSED");
   if (precision != GN_FP32_PLAIN && precision != GN_BF16_FUSED && precision != GN_FP8_FUSED)
     return fail(GN_EINVAL, "unknown precision %d", precision);
   if (pooling != GN_POOL_MAX_MEAN && pooling != GN_POOL_SUM)
@@ -364,17 +363,16 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_con
       glassnet_free_model(m);
       return cuda_fail(e, "upload packed weights");
     }
-    if (rk == 3) {
-      std::vector<uint8_t> cimg = pack_conv_r3(w.data(), wi);
-      if ((e = cudaMalloc(&m->conv, cimg.size())) != cudaSuccess) {
-        glassnet_free_model(m);
-        return fail(GN_ENOMEM, "cudaMalloc 3x3 R weights: %s", cudaGetErrorString(e));
-      }
-      if ((e = cudaMemcpy(m->conv, cimg.data(), cimg.size(), cudaMemcpyHostToDevice)) !=
-          cudaSuccess) {
-        glassnet_free_model(m);
-        return cuda_fail(e, "upload 3x3 R weights");
-      }
+  }
+  if (rk == 3 && precision != GN_FP32_PLAIN) {  // the 3x3 R kernel's image (BF16)
+    std::vector<uint8_t> cimg = pack_conv_r3(w.data(), wi);
+    if ((e = cudaMalloc(&m->conv, cimg.size())) != cudaSuccess) {
+      glassnet_free_model(m);
+      return fail(GN_ENOMEM, "cudaMalloc 3x3 R weights: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpy(m->conv, cimg.data(), cimg.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      glassnet_free_model(m);
+      return cuda_fail(e, "upload 3x3 R weights");
     }
   }
   *out = m;
@@ -541,8 +539,7 @@ cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s
 }
 
 cudaError_t prepare_fused(const gn_model* m) {
-  if (m->precision == GN_FP8_FUSED) return prepare_fused_fp8(m->H);
-  cudaError_t e = prepare_fused_bf16(m->H);
+  cudaError_t e = m->precision == GN_FP8_FUSED ? prepare_fused_fp8(m->H) : prepare_fused_bf16(m->H);
   return e == cudaSuccess && m->wi.RK == 3 ? prepare_conv_r3(m->H) : e;
 }
 

@@ -131,8 +131,9 @@ struct FusedLayout {
 //   FP32 constants (indices in floats from `cst`): per output column a
 //   dequantisation scale (accumulator -> next layer's quantised input, or
 //   real units where the result is not re-quantised) and a bias; u_phi1 and
-//   u_b1 turn c_phi / c_B into accumulator units; then three scalars: 1/s_t,
-//   1/s_g (the scale of B1's [g ; r] input) and 1/s_pool.
+//   u_b1 turn c_phi / c_B into accumulator units; then four scalars: 1/s_t,
+//   1/s_g (the scale of B1's [g ; r] input), 1/s_pool and s_y2 (B2's output
+//   in real units, for the neural buffer of a 3x3 R).
 //   A operands: at0, at1, ag ([2][128][16] bytes each, K block 1 zero) and
 //   the constant BF16 [1, 1, 0, ...] operand of the bias MMAs.
 template <int H>
@@ -150,7 +151,8 @@ struct FusedLayoutF8 {
   enum : int {
     S_PHI1 = 0, S_PHI2 = H, B_PHI2 = 2 * H, S_RHO = 3 * H, B_RHO = 4 * H, S_B1 = 5 * H,
     S_B2 = 6 * H, B_B2 = 7 * H, S_R1 = 8 * H, B_R1 = 9 * H, U_PHI1 = 10 * H, U_B1 = 11 * H,
-    S_R2 = 12 * H, B_R2 = 12 * H + 16, INV_S_T = 12 * H + 32, INV_S_G, INV_S_POOL, N_CST = 12 * H + 36
+    S_R2 = 12 * H, B_R2 = 12 * H + 16, INV_S_T = 12 * H + 32, INV_S_G, INV_S_POOL, S_Y2,
+    N_CST = 12 * H + 36
   };
   static constexpr uint32_t bytes = cst + N_CST * 4;
   static constexpr uint32_t at0 = (bytes + 127) / 128 * 128;

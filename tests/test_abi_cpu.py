@@ -122,13 +122,13 @@ def test_pooling_arguments_checked_before_any_device_work(lib):
 
 
 def test_r_kernel_checked_on_the_host(lib):
-    """r_kernel must be 0, 1 or 3; FP8 has no 3x3 R; a 1x1 blob read as 3x3
-    has the wrong payload size.  All refused before any device work."""
+    """r_kernel must be 0, 1 or 3; a 1x1 blob read as 3x3 has the wrong
+    payload size.  All refused before any device work."""
     blob = _blob()
     out = ctypes.c_void_p()
     buf = ctypes.create_string_buffer(blob, len(blob))
     for precision, rk, code in [(gl.GN_BF16_FUSED, 2, gl.GN_EINVAL), (gl.GN_BF16_FUSED, 5, gl.GN_EINVAL),
-                                (gl.GN_FP8_FUSED, 3, gl.GN_EUNSUPPORTED), (gl.GN_BF16_FUSED, 3, gl.GN_EFORMAT),
+                                (gl.GN_FP8_FUSED, 3, gl.GN_EFORMAT), (gl.GN_BF16_FUSED, 3, gl.GN_EFORMAT),
                                 (gl.GN_FP32_PLAIN, 3, gl.GN_EFORMAT)]:
         cfg = gl.ModelConfig(precision, 0, 0, rk)
         assert lib.glassnet_load_weights_ex(buf, len(blob), ctypes.byref(cfg), ctypes.byref(out)) == code, rk
