@@ -265,8 +265,28 @@ int glassnet_load_weights(const void* blob, size_t nbytes, int precision, gn_mod
   return glassnet_load_weights_ex(blob, nbytes, &cfg, out);
 }
 
+namespace {
+int load_weights_impl(const void* blob, size_t nbytes, const gn_model_config* cfg, gn_model** out,
+                      gn_model** partial);
+}  // namespace
+
+// Host allocations (the weights' copy, the packed images) may fail with
+// std::bad_alloc; nothing is thrown across the ABI.
 int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_config* cfg,
                              gn_model** out) {
+  gn_model* partial = nullptr;
+  try {
+    return load_weights_impl(blob, nbytes, cfg, out, &partial);
+  } catch (const std::bad_alloc&) {
+    glassnet_free_model(partial);
+    if (out) *out = nullptr;
+    return fail(GN_ENOMEM, "host allocation failed");
+  }
+}
+
+namespace {
+int load_weights_impl(const void* blob, size_t nbytes, const gn_model_config* cfg, gn_model** out,
+                      gn_model** partial) {
   if (!blob || !cfg || !out) return fail(GN_EINVAL, "blob, config and out must be non-NULL");
   *out = nullptr;
   const int precision = cfg->precision, pooling = cfg->pooling, pe = cfg->pe_freqs;
@@ -319,6 +339,7 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_con
   std::memcpy(w.data(), payload, wi.total * sizeof(float));
   gn_model* m = new (std::nothrow) gn_model();
   if (!m) return fail(GN_ENOMEM, "host allocation failed");
+  *partial = m;  // freed by the caller if a host allocation throws below
   m->H = wi.H;
   m->Z = wi.Z;
   m->precision = precision;
@@ -375,9 +396,11 @@ int glassnet_load_weights_ex(const void* blob, size_t nbytes, const gn_model_con
       return cuda_fail(e, "upload 3x3 R weights");
     }
   }
+  *partial = nullptr;
   *out = m;
   return GN_OK;
 }
+}  // namespace
 
 int glassnet_model_info(const gn_model* m, int* hidden, int* latent, int* precision) {
   if (!m) return fail(GN_EINVAL, "model is NULL");
@@ -689,8 +712,23 @@ int glassnet_render_batch(const gn_model* m, const gn_frame* frames, int n, cuda
 // outliers of up to 0.12 in RGB; with it, <= 0.056).
 constexpr float kFp8Headroom = 2.0f;
 
+namespace {
+int calibrate_fp8_impl(gn_model* m, const gn_latent* lat, const float* gbuf, const float* tbuf,
+                       const uint8_t* cnt, int K, int h, int w, cudaStream_t s);
+}  // namespace
+
 int glassnet_calibrate_fp8(gn_model* m, const gn_latent* lat, const float* gbuf, const float* tbuf,
                            const uint8_t* cnt, int K, int h, int w, cudaStream_t s) {
+  try {
+    return calibrate_fp8_impl(m, lat, gbuf, tbuf, cnt, K, h, w, s);
+  } catch (const std::bad_alloc&) {
+    return fail(GN_ENOMEM, "host allocation failed");
+  }
+}
+
+namespace {
+int calibrate_fp8_impl(gn_model* m, const gn_latent* lat, const float* gbuf, const float* tbuf,
+                       const uint8_t* cnt, int K, int h, int w, cudaStream_t s) {
   if (!m) return fail(GN_EINVAL, "model is NULL");
   if (m->precision != GN_FP8_FUSED) return fail(GN_EINVAL, "model precision is not GN_FP8_FUSED");
   const int P = h * w;
@@ -733,6 +771,7 @@ int glassnet_calibrate_fp8(gn_model* m, const gn_latent* lat, const float* gbuf,
   m->fp8_ready = true;
   return GN_OK;
 }
+}  // namespace
 
 int glassnet_fp8_scales(const gn_model* m, float* scales) {
   if (!m || !scales) return fail(GN_EINVAL, "model and scales must be non-NULL");
@@ -768,7 +807,7 @@ void glassnet_free_latent(gn_latent* lat) {
 
 // ------------------------------------------------------------- streaming
 struct gn_pool {
-  int h = 0, w = 0, H = 0;
+  int h = 0, w = 0, H = 0, RK = 1;  // frame, widths and R1's kernel size of its model
   void* dev = nullptr;  // state blocks (tile-major, see FusedParams), then counts [P] u8
   uint32_t* st = nullptr;
   size_t st_words = 0;
@@ -823,6 +862,9 @@ int check_pool_call(const gn_model* m, const gn_latent* lat, const gn_pool* pool
     return fail(GN_EINVAL, "latent widths (%d, %d) do not match the model (%d, %d)", lat->H,
                 lat->Z, m->H, m->Z);
   if (pool->H != m->H) return fail(GN_EINVAL, "pool of width %d, model of width %d", pool->H, m->H);
+  if (pool->RK != m->wi.RK)
+    return fail(GN_EINVAL, "pool made for a %dx%d R, model with a %dx%d R", pool->RK, pool->RK,
+                m->wi.RK, m->wi.RK);
   return GN_OK;
 }
 }  // namespace
@@ -839,10 +881,12 @@ int glassnet_pool_create(const gn_model* m, int h, int w, gn_pool** out) {
   if (P * gn::kTC >= (1ll << 31)) return fail(GN_EINVAL, "frame %d x %d too large", h, w);
   cudaError_t e = gn::prepare_fused(m);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel attributes");
-  gn_pool* pool = new gn_pool;
+  gn_pool* pool = new (std::nothrow) gn_pool;
+  if (!pool) return fail(GN_ENOMEM, "host allocation failed");
   pool->h = h;
   pool->w = w;
   pool->H = m->H;
+  pool->RK = m->wi.RK;
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   const long long tiles = (P + gn::kTile - 1) / gn::kTile;
   pool->st_words = static_cast<size_t>(tiles) * (m->H / 2 + m->H) * gn::kTile;

@@ -237,3 +237,20 @@ def test_full_512_K8_poisson_r3_corner_and_interior(cuda_lib):
         oy, ox = y0 - ys.start, x0 - xs.start
         e = np.abs(got[:, y0:y0 + 64, x0:x0 + 64] - exp[:, oy:oy + 64, ox:ox + 64])
         assert e.max() <= BF16_MAX and e.mean() <= BF16_MEAN, ((y0, x0), e.max(), e.mean())
+
+
+def test_pool_of_another_r_kernel_is_rejected(cuda_lib):
+    """A pool holds state shaped by its model (a 3x3 R also owns a neural
+    buffer): a model with another R kernel cannot use it."""
+    _, m3 = model()
+    m1 = gl.Model(synth.make_weights(synth.DOUBLED_WIDTHS, seed=3), gl.GN_BF16_FUSED)
+    lat = m3.encode(synth.make_scene(0))
+    f = synth.make_frame(16, 16, 1, counts="all", seed=1)
+    pool = gl.glassnet_pool_create(m1.handle, 16, 16)
+    try:
+        out = torch.empty((3, 16, 16), device=DEV)
+        with pytest.raises(gl.GlassNetError) as ei:
+            gl.glassnet_resolve(m3.handle, lat.handle, pool, _dev(f.gbuf), out)
+        assert ei.value.code == gl.GN_EINVAL and "R" in str(ei.value)
+    finally:
+        gl.glassnet_pool_free(pool)
