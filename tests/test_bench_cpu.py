@@ -1,0 +1,70 @@
+"""CPU checks of bench.py's own arithmetic: the algorithmic FLOP counts the
+roofline divides by, and the rule that a DRAM-traffic record only counts for
+the kernel sources it was taken of."""
+import json
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    sys.path.insert(0, ROOT)
+    saved = sys.argv
+    sys.argv = ["bench.py"]
+    import bench as b
+    sys.argv = saved
+    return b
+
+
+def _macs(H, layer_sizes, valid_layers, pixels):
+    """Multiply-accumulates counted layer by layer from (out, in) shapes."""
+    per_layer = sum(o * i for o, i in layer_sizes["layer"])
+    per_pixel = sum(o * i for o, i in layer_sizes["pixel"])
+    return per_layer * valid_layers + per_pixel * pixels
+
+
+@pytest.mark.parametrize("H,pooling,pe,rk", [(128, "max_mean", 0, 1), (128, "sum", 0, 1), (64, "max_mean", 4, 1),
+                                             (128, "max_mean", 0, 3), (64, "sum", 2, 3)])
+def test_algorithmic_flops_match_the_folded_layer_shapes(bench, H, pooling, pe, rk):
+    """2 x the MACs of the folded network (the latent enters as per-scene
+    biases), phi on the valid layers only, rho only for [max ; mean], R1 with
+    k^2 H inputs for a k x k kernel, R2 with 3 outputs."""
+    e = 1 + 2 * pe
+    sizes = {"layer": [(H, 12 * e), (H, H)],
+             "pixel": ([] if pooling == "sum" else [(H, 2 * H)]) + [(H, 14 * e + H), (H, H), (H, rk * rk * H), (3, H)]}
+    counts = np.random.default_rng(0).integers(0, 9, size=(7, 5)).astype(np.uint8)
+    want = 2.0 * _macs(H, sizes, int(counts.sum()), counts.size)
+    assert bench.algorithmic_flops(H, counts, pooling, pe, rk) == want
+
+
+def test_headline_flops_per_frame(bench):
+    """The benchmark frame's 72.2 GFLOP (doubled widths, Poisson(3) counts)."""
+    from gen import synth
+    f = synth.make_frame(512, 512, 8, counts="poisson3", seed=0)
+    g = bench.algorithmic_flops(128, f.counts) / 1e9
+    assert 71.5 < g < 73.0, g
+
+
+def test_traffic_record_only_counts_for_its_kernel_sources(bench, tmp_path):
+    rec = {"kernel_sha256": bench.kernel_digest(), "dram_bytes_per_launch": 123}
+    p = tmp_path / "t.json"
+    p.write_text(json.dumps(rec))
+    assert bench.profiled_traffic(str(p)) == 123
+    rec["kernel_sha256"] = "0" * 64
+    p.write_text(json.dumps(rec))
+    assert bench.profiled_traffic(str(p)) is None
+    assert bench.profiled_traffic(str(tmp_path / "absent.json")) is None
+
+
+def test_committed_traffic_records_name_their_command_and_workload(bench):
+    for name in ("fused_bf16_512x512_K8", "fused_bf16_sum_512x512_K8", "fused_bf16_pe4_512x512_K8"):
+        with open(os.path.join(ROOT, "profiles", name + ".traffic.json")) as f:
+            rec = json.load(f)
+        assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
+        assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
+        assert "bench.py" in rec["command"] and rec["workload"].startswith("512x512")
