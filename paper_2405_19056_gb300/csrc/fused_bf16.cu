@@ -52,6 +52,9 @@
 //    shared-memory A operands, running up to two layer slots ahead.  With
 //    positional encoding there are four loader warps (9-12, 32 rows each)
 //    that also compute the encoded bands (13 warps).
+// The base widths without encoding (H = 64) run one epilogue warp per lane
+// quadrant instead (warps 0-3, all H columns; MMA warp 4; loaders 5-6), at
+// two CTAs per SM (128 registers a thread).
 //
 // Layer-slot pipeline.  Three TMEM accumulator buffers rotate over the global
 // sequence of layer slots: phi1(k) writes buffer k mod 3, the epilogue turns
@@ -247,12 +250,21 @@ __device__ __forceinline__ void store_slot_pe(uint32_t base, int row0, const flo
 enum : int { kModeFrame = 0, kModeAccumulate = 1, kModeResolve = 2 };
 
 // Warp counts: 2 loader warps (2 rows per lane), or 4 (1 row per lane) when
-// the loaders also encode the inputs.
-template <bool PE>
+// the loaders also encode the inputs.  The base widths (H = 64, no
+// encoding) run one epilogue warp per TMEM lane quadrant (7 warps) and two
+// CTAs per SM: each CTA holds 74 KB of shared memory and 256 TMEM columns,
+// and the SM interleaves two tiles' hand-off chains.
+template <int H, bool PE>
 struct Roles {
+  static constexpr bool kPair = H == 64 && !PE;
+  static constexpr int EW = kPair ? 1 : kEW;  // epilogue warps per lane quadrant
+  static constexpr int EPI = 4 * EW;          // epilogue warps 0 .. EPI - 1
+  static constexpr int MMA = 4 * EW;          // the MMA warp
+  static constexpr int LOAD0 = 4 * EW + 1;    // the first loader warp
   static constexpr int LW = PE ? 4 : kLoadWarps;
   static constexpr int RPL = kTile / (LW * 32);
-  static constexpr int kThreads = (4 * kEW + 1 + LW) * 32;
+  static constexpr int kThreads = (4 * EW + 1 + LW) * 32;
+  static constexpr int kCtasPerSm = kPair ? 2 : 1;
   static_assert(LW <= kMaxLoadWarps && RPL * LW * 32 == kTile, "loader rows must cover the tile");
 };
 
@@ -265,7 +277,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
                                             uint32_t bar_base, LoaderShared& ls,
                                             volatile int* abort_flag, int li, int lane) {
   using L = FusedLayout<H, PE>;
-  constexpr int RPL = Roles<PE>::RPL, LW = Roles<PE>::LW;
+  constexpr int RPL = Roles<H, PE>::RPL, LW = Roles<H, PE>::LW;
   const int nf = PE ? prm.pe_freqs : 0;  // positional-encoding frequencies
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
   const int row0 = li * (32 * RPL) + lane;
@@ -414,12 +426,14 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
 // [y][H/8][x][8], one buffer per frame of the launch) to device memory
 // instead of running R.
 template <int H, int Mode, bool Sum, bool PE, bool R3>
-__global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
+__global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPerSm)
     fused_bf16_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
   static_assert(!Sum || Mode != kModeAccumulate, "accumulation does not depend on the pooling");
   static_assert(!R3 || Mode != kModeAccumulate, "accumulation does not depend on R");
   using L = FusedLayout<H, PE>;
   using T = TMap<H>;
+  using R = Roles<H, PE>;
+  constexpr int kEW = R::EW;  // epilogue warps per lane quadrant
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
   constexpr int CHC = CH / 2;  // TMEM columns of CH bf16 values
   static_assert(CH % 16 == 0, "accumulator columns per thread must be a multiple of 16");
@@ -439,25 +453,25 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
     mbar_init(bar(B_W), 1);
     mbar_init(bar(B_DP), 1);
     mbar_init(bar(B_DR2), 1);
-    mbar_init(bar(B_AG_F), Roles<PE>::LW);
+    mbar_init(bar(B_AG_F), Roles<H, PE>::LW);
     mbar_init(bar(B_AG_E), 1);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(bar(B_IN + b), kEpiWarps);
-      mbar_init(bar(B_AT_F + b), Roles<PE>::LW);
+      mbar_init(bar(B_IN + b), R::EPI);
+      mbar_init(bar(B_AT_F + b), Roles<H, PE>::LW);
       mbar_init(bar(B_AT_E + b), 1);
-      mbar_init(bar(B_TILE + b), Roles<PE>::LW);
+      mbar_init(bar(B_TILE + b), Roles<H, PE>::LW);
       mbar_init(bar(B_SCHED + b), 1);
-      mbar_init(bar(B_H + b), kEpiWarps);
+      mbar_init(bar(B_H + b), R::EPI);
     }
     for (int b = 0; b < 3; ++b) {
       mbar_init(bar(B_D1 + b), 1);
       mbar_init(bar(B_D2 + b), 1);
-      mbar_init(bar(B_BE + b), kEpiWarps);
+      mbar_init(bar(B_BE + b), R::EPI);
     }
     s_abort = 0;
     fence_mbar_init();
   }
-  if (warp == kMmaWarp) {
+  if (warp == R::MMA) {
     tmem_alloc(smem_u32(&s_tmem), T::NCOLS);
     tmem_relinquish();
   }
@@ -466,16 +480,16 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
   tc_fence_after();
   const uint32_t tbase = s_tmem;
 
-  if (warp >= kLoadWarp0) {
+  if (warp >= R::LOAD0) {
     // the constant [1, 1, 0, ...] operand that multiplies phi2's bias rows
-    for (int r = (warp - kLoadWarp0) * 32 + lane; r < kTile; r += Roles<PE>::LW * 32) {
+    for (int r = (warp - R::LOAD0) * 32 + lane; r < kTile; r += Roles<H, PE>::LW * 32) {
       sts128(sbase + L::aone + r * 16u, pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
       sts128(sbase + L::aone + 2048u + r * 16u, 0u, 0u, 0u, 0u);
     }
     fence_proxy_async_smem();
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
-    loader_loop<H, Mode, PE>(prm, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
-  } else if (warp == kMmaWarp) {
+    loader_loop<H, Mode, PE>(prm, sbase, bar_base, s_ld, &s_abort, warp - R::LOAD0, lane);
+  } else if (warp == R::MMA) {
     // ------------------------------------------------------------ MMA warp
     if (lane == 0) {
       mbar_arrive_expect_tx(bar(B_W), L::bytes);
@@ -554,7 +568,7 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
       tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
       ns = 0;
 #pragma unroll
-      for (int w = 0; w < Roles<PE>::LW; ++w) ns = max(ns, s_ld.ns[t & 1][w]);
+      for (int w = 0; w < Roles<H, PE>::LW; ++w) ns = max(ns, s_ld.ns[t & 1][w]);
       fold = tile < total_tiles ? s_ld.fold[t & 3] : nullptr;
       return true;
     };
@@ -720,7 +734,7 @@ __global__ void __launch_bounds__(Roles<PE>::kThreads, 1)
         tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
         ns = 0;
 #pragma unroll
-      for (int w = 0; w < Roles<PE>::LW; ++w) ns = max(ns, s_ld.ns[t & 1][w]);
+      for (int w = 0; w < Roles<H, PE>::LW; ++w) ns = max(ns, s_ld.ns[t & 1][w]);
         c = s_ld.cnt[t & 1][row];
         return true;
       };
@@ -997,7 +1011,7 @@ done:
   if (s_abort && tid == 0) atomicOr(prm.err, kErrTimeout);
   tc_fence_before();
   __syncthreads();
-  if (warp == kMmaWarp) {
+  if (warp == R::MMA) {
     tc_fence_after();
     tmem_dealloc(tbase, TMap<H>::NCOLS);
   }
@@ -1023,7 +1037,7 @@ cudaError_t launch_h(const void* wimg, const FusedParams& p, cudaStream_t s, int
   // is still running; they wait on the grid dependency before the plan reads.
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(Roles<PE>::kThreads);
+  cfg.blockDim = dim3(Roles<H, PE>::kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -1083,7 +1097,10 @@ cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& params
   FusedParams p = params;
   cudaError_t e = launch_plan(p, s);
   if (e != cudaSuccess) return e;
-  const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
+  // persistent CTAs take tiles from the plan's counter: as many as fit
+  const int per_sm = (H == 64 && p.pe_freqs == 0) ? Roles<64, false>::kCtasPerSm : 1;
+  const int slots = per_sm * device_sm_count();
+  const int grid = p.total_tiles < slots ? p.total_tiles : slots;
   if (p.pe_freqs > 0) {
     // the encoded operands exist for H = 64 only (the loader refuses others)
     if (H != 64 || p.pe_freqs > kMaxPeFreqsFused) return cudaErrorInvalidValue;
