@@ -36,12 +36,13 @@ WORKLOAD = "512x512 frame, K=8 slots, counts min(Poisson(3),8), H=128 Z=256"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "fused_bf16_512x512_K8.traffic.json")
 PROFILE_TRAFFIC_SUM = os.path.join(ROOT, "profiles", "fused_bf16_sum_512x512_K8.traffic.json")
 PROFILE_TRAFFIC_PE = os.path.join(ROOT, "profiles", "fused_bf16_pe4_512x512_K8.traffic.json")
+PROFILE_TRAFFIC_H64 = os.path.join(ROOT, "profiles", "fused_bf16_h64_512x512_K8.traffic.json")
 
 
 def profiled_traffic(path: str):
     """DRAM bytes per launch from an ncu capture, if it was taken of the
     kernel sources as they are now (else None: the counters are stale)."""
-    if not os.path.exists(path):
+    if path is None or not os.path.exists(path):
         return None
     with open(path) as f:
         prof = json.load(f)
@@ -67,6 +68,9 @@ def parse():
     ap.add_argument("--r-kernel", type=int, default=1, choices=[1, 3],
                     help="R's first layer: 1x1, or a 3x3 kernel over the frame (fused kernel to "
                          "the neural buffer, then the tcgen05 3x3 kernel)")
+    ap.add_argument("--widths", default="doubled", choices=["doubled", "base"],
+                    help="network widths of the timed leg: doubled (H=128 Z=256) or base "
+                         "(H=64 Z=128)")
     ap.add_argument("--pe-freqs", type=int, default=0,
                     help="time the base widths (H=64 Z=128) with every input positionally "
                          "encoded at this many frequencies (BF16, 1..4) instead of the doubled widths")
@@ -275,7 +279,8 @@ def run_fused(args, world, rank, local):
     gl.load_library()
     pe = args.pe_freqs
     rk = args.r_kernel
-    widths = synth.Widths(64, 128, pe, rk) if pe else synth.Widths(128, 256, 0, rk)
+    base = pe > 0 or args.widths == "base"
+    widths = synth.Widths(64, 128, pe, rk) if base else synth.Widths(128, 256, 0, rk)
     weights = synth.make_weights(widths, seed=0)
     fp8 = args.precision == "fp8"
     pool_sum = args.pooling == "sum"
@@ -342,22 +347,29 @@ def run_fused(args, world, rank, local):
     if fp8:
         peak_tf *= 2
     achieved_tf = step_flops / (avg_kernel_ms * 1e-3) / 1e12
-    # the captures cover L = 4 (encoded) and the two poolings of the doubled widths
-    traffic = None if fp8 or rk == 3 or (pe and (pe != 4 or pool_sum)) else profiled_traffic(
-        PROFILE_TRAFFIC_PE if pe else PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC)
+    # the captures cover the two poolings of the doubled widths and [max ; mean]
+    # at the base widths, without encoding and at L = 4
+    traffic = None
+    if not fp8 and rk == 1 and not (base and pool_sum):
+        traffic = profiled_traffic(
+            (PROFILE_TRAFFIC_PE if pe == 4 else None) if pe else PROFILE_TRAFFIC_H64 if base else
+            PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC)
     metric = METRIC.replace("BF16", "FP8") if fp8 else METRIC
     if pool_sum:
         metric = metric.replace("BF16 fused", "BF16 fused, sum pooling")
     if pe:
         metric = metric.replace("BF16 fused", f"BF16 fused, H=64, inputs encoded at L={pe}")
+    elif base:
+        metric = metric.replace(" fused", " fused, H=64", 1)
     if rk == 3:
         metric = metric.replace("BF16 fused", "BF16 fused, 3x3 R")
     result = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if fp8 else "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD if not pe else
-                   WORKLOAD.replace("H=128 Z=256", f"H=64 Z=128, positional encoding L={pe}"),
+        "config": {"workload": WORKLOAD if not base else
+                   WORKLOAD.replace("H=128 Z=256", "H=64 Z=128" +
+                                    (f", positional encoding L={pe}" if pe else "")),
                    "frames_rotated": N_ROTATE,
                    "l2": "inputs rotate over 3 frames of 115 MB (> 129 MB L2 in total)",
                    "parallelism": f"replicas{world}", "weights": "Xavier-normal seed 0, zero bias"},
@@ -368,7 +380,7 @@ def run_fused(args, world, rank, local):
         "gpu_launches": (3 if rk == 3 else 2) * args.steps,
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
-                     "kernel": "fused_fp8_kernel<128>" if fp8 else
+                     "kernel": f"fused_fp8_kernel<{widths.hidden}>" if fp8 else
                                f"fused_bf16_kernel<{widths.hidden}, frame, sum={int(pool_sum)}, "
                                f"pe={int(pe > 0)}>" + (" + conv_r3_kernel" if rk == 3 else ""),
                      "duration": "CUDA events around the render call (plan kernel + fused kernel)",
