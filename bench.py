@@ -49,6 +49,19 @@ def profiled_traffic(path: str):
     return prof.get("dram_bytes_per_launch") if prof.get("kernel_sha256") == kernel_digest() else None
 
 
+def traffic_record(fp8: bool, r_kernel: int, pe: int, base: bool, pool_sum: bool):
+    """The committed capture of the timed leg's fused kernel, if there is one:
+    both poolings at the doubled widths, [max ; mean] at the base widths
+    without encoding and at L = 4 (BF16, 1x1 R)."""
+    if fp8 or r_kernel != 1 or (base and pool_sum):
+        return None
+    if pe:
+        return PROFILE_TRAFFIC_PE if pe == 4 else None
+    if base:
+        return PROFILE_TRAFFIC_H64
+    return PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,13 +360,7 @@ def run_fused(args, world, rank, local):
     if fp8:
         peak_tf *= 2
     achieved_tf = step_flops / (avg_kernel_ms * 1e-3) / 1e12
-    # the captures cover the two poolings of the doubled widths and [max ; mean]
-    # at the base widths, without encoding and at L = 4
-    traffic = None
-    if not fp8 and rk == 1 and not (base and pool_sum):
-        traffic = profiled_traffic(
-            (PROFILE_TRAFFIC_PE if pe == 4 else None) if pe else PROFILE_TRAFFIC_H64 if base else
-            PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC)
+    traffic = profiled_traffic(traffic_record(fp8, rk, pe, base, pool_sum))
     metric = METRIC.replace("BF16", "FP8") if fp8 else METRIC
     if pool_sum:
         metric = metric.replace("BF16 fused", "BF16 fused, sum pooling")

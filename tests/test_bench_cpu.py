@@ -69,3 +69,15 @@ def test_committed_traffic_records_name_their_command_and_workload(bench):
         assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
         assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
         assert "bench.py" in rec["command"] and rec["workload"].startswith("512x512")
+
+
+def test_each_leg_takes_the_capture_of_its_own_kernel(bench):
+    """(fp8, r_kernel, pe, base widths, sum pooling) -> the record taken of
+    that fused kernel, or none."""
+    assert bench.traffic_record(False, 1, 0, False, False) == bench.PROFILE_TRAFFIC
+    assert bench.traffic_record(False, 1, 0, False, True) == bench.PROFILE_TRAFFIC_SUM
+    assert bench.traffic_record(False, 1, 0, True, False) == bench.PROFILE_TRAFFIC_H64
+    assert bench.traffic_record(False, 1, 4, True, False) == bench.PROFILE_TRAFFIC_PE
+    for args in [(True, 1, 0, False, False), (False, 3, 0, False, False), (False, 1, 2, True, False),
+                 (False, 1, 4, True, True), (False, 1, 0, True, True)]:
+        assert bench.traffic_record(*args) is None, args
