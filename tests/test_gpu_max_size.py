@@ -1,0 +1,90 @@
+"""The largest frames the C ABI accepts, and the first ones it refuses.
+
+glassnet_render takes a frame when 12 max(K, 1) h w < 2^31.  At the edge the
+fused kernel's 32-bit plane offsets reach their largest values: at K = 8 the
+last slot's last channel plane ends just below 2^31 floats, and at K = 0 the
+G-buffer's 14 planes hold 2.5 x 10^9 floats, past the signed 32-bit range.
+
+Each accepted frame is a small seeded synthetic frame repeated down the rows
+(on the device), so every output pixel has an oracle value: the whole frame
+is compared with the FP64 oracle of the small frame (BF16 tolerances: max
+|err| <= 2e-2, mean <= 3e-3), and pixels with equal inputs must come out
+bit-identical wherever their tiles fall.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gen import synth
+from paper_2405_19056_gb300 import glassnet as gl
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+BF16_MAX = 2e-2
+BF16_MEAN = 3e-3
+LIMIT = 1 << 31
+
+# (K, h, w, rows of the repeated small frame)
+EDGE_CASES = [(8, 4729, 4730, 11), (0, 13377, 13377, 7)]
+
+
+def test_edge_sizes_are_the_documented_limit():
+    for K, h, w, _ in EDGE_CASES:
+        assert 12 * max(K, 1) * h * w < LIMIT
+        assert 12 * max(K, 1) * h * (w + 1) >= LIMIT
+
+
+@pytest.fixture(scope="module")
+def doubled(cuda_lib):
+    w = synth.make_weights(synth.DOUBLED_WIDTHS, seed=9, bias="uniform")
+    return w, gl.Model(w, gl.GN_BF16_FUSED)
+
+
+@pytest.mark.parametrize("K,h,w,rows", EDGE_CASES, ids=["K8", "K0"])
+def test_one_column_more_is_refused(doubled, K, h, w, rows):
+    """Refused before any launch: the buffers passed are far too small to be
+    read at all."""
+    _, m = doubled
+    lat = m.encode(synth.make_scene(2))
+    g = torch.zeros(16, device=DEV)
+    t = torch.zeros(16, device=DEV) if K else None
+    c = torch.zeros(16, dtype=torch.uint8, device=DEV)
+    out = torch.zeros(16, device=DEV)
+    with pytest.raises(gl.GlassNetError) as e:
+        gl.glassnet_render(m.handle, lat.handle, g, t, c, K, h, w + 1, out)
+    assert e.value.code == gl.GN_EINVAL
+    m.check()
+
+
+@pytest.mark.parametrize("K,h,w,rows", EDGE_CASES, ids=["K8", "K0"])
+def test_largest_frame_matches_the_oracle(doubled, K, h, w, rows):
+    weights, m = doubled
+    scene = synth.make_scene(2)
+    f = synth.make_frame(rows, w, K, counts="poisson3", seed=21)
+    exp = oracle.render_frame(weights, scene, f.gbuf, f.tbuf, f.counts)  # [3][rows][w]
+    idx = torch.arange(h, device=DEV) % rows  # row y of the frame is row y mod rows
+    g = torch.from_numpy(f.gbuf).to(DEV).index_select(1, idx)
+    t = torch.from_numpy(f.tbuf).to(DEV).index_select(2, idx) if K else None
+    c = torch.from_numpy(f.counts).to(DEV).index_select(0, idx)
+    out = torch.full((3, h, w), float("nan"), device=DEV)
+    lat = m.encode(scene)
+    m.render(lat, g, t, c, out)
+    m.check()
+    torch.cuda.synchronize()
+    del g, t, c
+    assert bool(torch.isfinite(out).all())
+    # equal inputs, equal bits: each row against the row `rows` further down
+    assert torch.equal(out[:, rows:], out[:, :-rows])
+    ref = torch.from_numpy(exp.astype(np.float32)).to(DEV)
+    err_max, err_sum = 0.0, 0.0
+    for y0 in range(0, h, 1024):  # in bands, to bound the temporaries
+        ys = idx[y0:y0 + 1024]
+        d = (out[:, y0:y0 + 1024] - ref.index_select(1, ys)).abs()
+        err_max = max(err_max, float(d.max()))
+        err_sum += float(d.double().sum())
+    err_mean = err_sum / (3 * h * w)
+    assert err_max <= BF16_MAX and err_mean <= BF16_MEAN, (err_max, err_mean)
+    del out
+    torch.cuda.empty_cache()
