@@ -88,3 +88,60 @@ def test_largest_frame_matches_the_oracle(doubled, K, h, w, rows):
     assert err_max <= BF16_MAX and err_mean <= BF16_MEAN, (err_max, err_mean)
     del out
     torch.cuda.empty_cache()
+
+
+def _stack_rows(f, rows_idx):
+    """The frame whose row j is row rows_idx[j] of f."""
+    return synth.Frame(gbuf=np.ascontiguousarray(f.gbuf[:, rows_idx]),
+                       tbuf=np.ascontiguousarray(f.tbuf[:, :, rows_idx]),
+                       counts=np.ascontiguousarray(f.counts[rows_idx]))
+
+
+@pytest.mark.parametrize("K,h,w,rows", [(8, 4729, 4730, 5), (0, 13377, 13377, 7)], ids=["K8", "K0"])
+def test_largest_frame_with_the_3x3_R(cuda_lib, K, h, w, rows):
+    """The 3x3 R at the edge sizes: the neural buffer is 5.7 GB (K = 8) or
+    45.8 GB (K = 0), past 32-bit byte offsets.  With the rows repeating,
+    a pixel away from the top and bottom edges sees a periodic 3x3
+    neighbourhood, i.e. the middle block of three stacked copies; the top and
+    bottom rows see the zero padding."""
+    weights = synth.make_weights(synth.Widths(128, 256, 0, 3), seed=4, bias="uniform")
+    m = gl.Model(weights, gl.GN_BF16_FUSED)
+    scene = synth.make_scene(3)
+    f = synth.make_frame(rows, w, K, counts="poisson3", seed=22)
+    r = np.arange(rows)
+    mid = oracle.render_frame(weights, scene, *_fields(_stack_rows(f, np.concatenate([r, r, r]))))
+    top = oracle.render_frame(weights, scene, *_fields(f))[:, 0]
+    rb = (h - 1) % rows
+    bot = oracle.render_frame(weights, scene, *_fields(_stack_rows(f, np.array([(rb - 1) % rows, rb]))))[:, 1]
+    idx = torch.arange(h, device=DEV) % rows
+    g = torch.from_numpy(f.gbuf).to(DEV).index_select(1, idx)
+    t = torch.from_numpy(f.tbuf).to(DEV).index_select(2, idx) if K else None
+    c = torch.from_numpy(f.counts).to(DEV).index_select(0, idx)
+    out = torch.full((3, h, w), float("nan"), device=DEV)
+    lat = m.encode(scene)
+    m.render(lat, g, t, c, out)
+    m.check()
+    torch.cuda.synchronize()
+    del g, t, c
+    m.close()  # frees the neural buffer
+    assert bool(torch.isfinite(out).all())
+    assert torch.equal(out[:, 1 + rows:h - 1], out[:, 1:h - 1 - rows])
+    ref = torch.from_numpy(mid[:, rows:2 * rows].astype(np.float32)).to(DEV)
+    err_max, err_sum = 0.0, 0.0
+    for y0 in range(1, h - 1, 1024):
+        y1 = min(y0 + 1024, h - 1)
+        d = (out[:, y0:y1] - ref.index_select(1, idx[y0:y1])).abs()
+        err_max = max(err_max, float(d.max()))
+        err_sum += float(d.double().sum())
+    for y, e in ((0, top), (h - 1, bot)):
+        d = (out[:, y].double().cpu().numpy() - e)
+        err_max = max(err_max, float(np.abs(d).max()))
+        err_sum += float(np.abs(d).sum())
+    err_mean = err_sum / (3 * h * w)
+    assert err_max <= BF16_MAX and err_mean <= BF16_MEAN, (err_max, err_mean)
+    del out
+    torch.cuda.empty_cache()
+
+
+def _fields(f):
+    return f.gbuf, f.tbuf, f.counts
