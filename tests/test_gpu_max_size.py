@@ -7,9 +7,10 @@ G-buffer's 14 planes hold 2.5 x 10^9 floats, past the signed 32-bit range.
 
 Each accepted frame is a small seeded synthetic frame repeated down the rows
 (on the device), so every output pixel has an oracle value: the whole frame
-is compared with the FP64 oracle of the small frame (BF16 tolerances: max
-|err| <= 2e-2, mean <= 3e-3), and pixels with equal inputs must come out
-bit-identical wherever their tiles fall.
+is compared with the FP64 oracle of the small frame (BF16: max |err| <=
+2e-2, mean <= 3e-3; FP8, calibrated on a seed-1 128x128 K=8 frame: 6e-2 and
+1e-2), and pixels with equal inputs must come out bit-identical wherever
+their tiles fall.
 """
 import numpy as np
 import pytest
@@ -24,6 +25,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 BF16_MAX = 2e-2
 BF16_MEAN = 3e-3
+TOL = {"bf16": (BF16_MAX, BF16_MEAN), "fp8": (6e-2, 1e-2)}
 LIMIT = 1 << 31
 
 # (K, h, w, rows of the repeated small frame)
@@ -42,6 +44,21 @@ def doubled(cuda_lib):
     return w, gl.Model(w, gl.GN_BF16_FUSED)
 
 
+@pytest.fixture(scope="module")
+def doubled_fp8(doubled):
+    w, _ = doubled
+    m = gl.Model(w, gl.GN_FP8_FUSED)
+    cal = synth.make_frame(128, 128, 8, counts="poisson3", seed=1)
+    lat = m.encode(synth.make_scene(0))
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+    gl.glassnet_calibrate_fp8(m.handle, lat.handle, dev(cal.gbuf), dev(cal.tbuf), dev(cal.counts),
+                              8, 128, 128)
+    return w, m
+
+
 @pytest.mark.parametrize("K,h,w,rows", EDGE_CASES, ids=["K8", "K0"])
 def test_one_column_more_is_refused(doubled, K, h, w, rows):
     """Refused before any launch: the buffers passed are far too small to be
@@ -58,9 +75,10 @@ def test_one_column_more_is_refused(doubled, K, h, w, rows):
     m.check()
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
 @pytest.mark.parametrize("K,h,w,rows", EDGE_CASES, ids=["K8", "K0"])
-def test_largest_frame_matches_the_oracle(doubled, K, h, w, rows):
-    weights, m = doubled
+def test_largest_frame_matches_the_oracle(request, K, h, w, rows, precision):
+    weights, m = request.getfixturevalue("doubled" if precision == "bf16" else "doubled_fp8")
     scene = synth.make_scene(2)
     f = synth.make_frame(rows, w, K, counts="poisson3", seed=21)
     exp = oracle.render_frame(weights, scene, f.gbuf, f.tbuf, f.counts)  # [3][rows][w]
@@ -85,7 +103,8 @@ def test_largest_frame_matches_the_oracle(doubled, K, h, w, rows):
         err_max = max(err_max, float(d.max()))
         err_sum += float(d.double().sum())
     err_mean = err_sum / (3 * h * w)
-    assert err_max <= BF16_MAX and err_mean <= BF16_MEAN, (err_max, err_mean)
+    tol_max, tol_mean = TOL[precision]
+    assert err_max <= tol_max and err_mean <= tol_mean, (err_max, err_mean)
     del out
     torch.cuda.empty_cache()
 
