@@ -201,3 +201,11 @@ def test_product_package_never_imports_the_oracle():
         text = f.read_text()
         assert "import oracle" not in text and "from oracle" not in text, f
         assert "glassnet_oracle" not in text, f
+
+
+def test_edge_frame_sizes_of_the_gpu_tests_are_the_documented_limit():
+    """The frames of test_gpu_max_size.py sit at glassnet_render's limit
+    12 max(K, 1) h w < 2^31: accepted as they are, refused one column wider."""
+    for K, h, w in ((8, 4729, 4730), (0, 13377, 13377)):
+        assert 12 * max(K, 1) * h * w < 1 << 31
+        assert 12 * max(K, 1) * h * (w + 1) >= 1 << 31
