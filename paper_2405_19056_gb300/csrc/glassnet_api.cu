@@ -709,7 +709,9 @@ int glassnet_render_batch(const gn_model* m, const gn_frame* frames, int n, cuda
 // of headroom costs precision only for values in the lowest binade, while it
 // keeps inputs up to twice the calibration maximum from saturating (measured:
 // with no headroom, frames other than the calibration frame showed clipped
-// outliers of up to 0.12 in RGB; with it, <= 0.056).
+// outliers of up to 0.12 in RGB; with it, <= 0.056 on 64x64 crops, while a
+// 52,030-pixel frame with no activation beyond 1.55x its calibration maximum
+// reached 0.085 through E4M3 rounding alone).
 constexpr float kFp8Headroom = 2.0f;
 
 namespace {
