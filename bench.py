@@ -106,10 +106,14 @@ def algorithmic_flops(H: int, counts: np.ndarray, pooling: str = "max_mean", pe:
     return 2.0 * (per_layer * float(counts.sum()) + per_pixel * counts.size)
 
 
+# the sources of the fused and plan kernels whose DRAM traffic is recorded
+KERNEL_SOURCES = ("fused_bf16.cu", "fused_common.cuh", "plan.cu", "tc_ptx.cuh", "internal.h")
+
+
 def kernel_digest() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2405_19056_gb300", "csrc")
-    for name in ("fused_bf16.cu", "fused_common.cuh", "plan.cu", "tc_ptx.cuh", "internal.h"):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()

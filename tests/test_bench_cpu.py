@@ -3,6 +3,7 @@ roofline divides by, and the rule that a DRAM-traffic record only counts for
 the kernel sources it was taken of."""
 import json
 import os
+import re
 import sys
 
 import numpy as np
@@ -81,3 +82,22 @@ def test_each_leg_takes_the_capture_of_its_own_kernel(bench):
     for args in [(True, 1, 0, False, False), (False, 3, 0, False, False), (False, 1, 2, True, False),
                  (False, 1, 4, True, True), (False, 1, 0, True, True)]:
         assert bench.traffic_record(*args) is None, args
+
+
+def test_kernel_digest_covers_every_source_of_the_captured_kernels(bench):
+    """The traffic records are keyed by a hash of the fused kernel's and the
+    plan kernel's sources: every repository file they include, transitively,
+    is hashed, except the public C header (declarations and enum values the
+    kernels never branch on at compile time)."""
+    csrc = os.path.join(ROOT, "paper_2405_19056_gb300", "csrc")
+    seen, todo = set(), ["fused_bf16.cu", "plan.cu"]
+    while todo:
+        name = todo.pop()
+        if name in seen:
+            continue
+        seen.add(name)
+        with open(os.path.join(csrc, name)) as f:
+            for inc in re.findall(r'^#include "([^"]+)"', f.read(), flags=re.M):
+                if not inc.endswith("include/glassnet.h"):
+                    todo.append(inc)
+    assert seen == set(bench.KERNEL_SOURCES)
