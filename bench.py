@@ -62,6 +62,10 @@ def traffic_record(fp8: bool, r_kernel: int, pe: int, base: bool, pool_sum: bool
     return PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC
 
 
+EXTRA_LEGS = ("fp32_plain", "e2e", "batch_16_frames", "streaming", "fp8", "sum_pooling",
+              "positional_encoding", "spatial_r3", "serving", "cpu_baseline")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -70,6 +74,9 @@ def parse():
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e, FP32-plain, batched, FP8 and CPU-baseline legs")
+    ap.add_argument("--legs", default=None,
+                    help="comma-separated extra legs to run (default: all of them unless "
+                         "--no-extras): " + ",".join(EXTRA_LEGS))
     ap.add_argument("--serving-full", action="store_true",
                     help="serving leg at 50, 200 and 800 req/s with 2000 requests each "
                          "(default: 200 and 800 req/s, 300 requests each)")
@@ -88,6 +95,18 @@ def parse():
                     help="time the base widths (H=64 Z=128) with every input positionally "
                          "encoded at this many frequencies (BF16, 1..4) instead of the doubled widths")
     return ap.parse_args()
+
+
+def selected_legs(args) -> set:
+    """The extra legs this run measures: ``--legs`` if given, else all of
+    them unless ``--no-extras``."""
+    if args.legs is not None:
+        legs = {x.strip() for x in args.legs.split(",") if x.strip()}
+        unknown = legs - set(EXTRA_LEGS)
+        if unknown:
+            raise SystemExit(f"unknown legs {sorted(unknown)}; known: {', '.join(EXTRA_LEGS)}")
+        return legs
+    return set() if args.no_extras else set(EXTRA_LEGS)
 
 
 def algorithmic_flops(H: int, counts: np.ndarray, pooling: str = "max_mean", pe: int = 0,
@@ -129,55 +148,156 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """SM clock and clock-event reasons, read through NVML (the driver's
+    libnvidia-ml, by ctypes; reading only) every 2 ms on a thread while
+    running, with nvidia-smi's 200 ms loop as the fallback.  Samples carry
+    their host time, so the timed region's own samples can be told apart from
+    those of the same load continued after it (``extend``)."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReason bits that bench rules name
+    REASON_BITS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+                   0x4: "sw_power_cap"}
 
-    def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.path = None
+    def __init__(self, index: int, uuid: str | None = None, period_s: float = 0.002):
+        self.index, self.uuid, self.period = index, uuid, period_s
+        self.samples = []  # (host time, sm MHz, max MHz, reason bits)
+        self.why = None
+        self.source = None
+        self._stop = None
+        self._thread = None
+        self._proc = None
+        self.t_begin = self.t_end = None
+
+    # NVML through ctypes
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit_v2 failed")
+        h = ctypes.c_void_p()
+        rc = 1
+        if self.uuid:
+            rc = lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(h))
+        if rc != 0:
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h))
+        if rc != 0:
+            raise OSError(f"no NVML handle for GPU {self.uuid or self.index} (rc {rc})")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
+
+    def _nvml_loop(self, lib, h, reasons):
+        import ctypes
+        mhz, mx, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # NVML_CLOCK_SM = 1
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and \
+                    reasons(h, ctypes.byref(bits)) == 0:
+                self.samples.append((time.perf_counter(), float(mhz.value), float(mx.value),
+                                     int(bits.value)))
+            self._stop.wait(self.period)
+
+    def _smi_loop(self):
+        sel = self.uuid or str(self.index)
+        self._proc = subprocess.Popen(
+            ["nvidia-smi", "-i", sel, f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+             "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+        for ln in self._proc.stdout:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm, mx = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            bits = sum(b for b, name in ((0x8, 5), (0x40, 6), (0x20, 7), (0x4, 8))
+                       if parts[name].lower() == "active")
+            self.samples.append((time.perf_counter(), sm, mx, bits))
 
     def __enter__(self):
+        import threading
+        self._stop = threading.Event()
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
-            self.proc = None
+            lib, h, reasons = self._nvml_handle()
+            self.source = "nvml (libnvidia-ml via ctypes, 2 ms period)"
+            self._thread = threading.Thread(target=self._nvml_loop, args=(lib, h, reasons), daemon=True)
+        except (OSError, AttributeError) as e:
+            self.why = f"NVML unavailable ({e}); nvidia-smi 200 ms loop used"
+            self.source = "nvidia-smi"
+            self._thread = threading.Thread(target=self._smi_loop, daemon=True)
+        self._thread.start()
+        t0 = time.perf_counter()  # the sampler is running before the timed region starts
+        while not self.samples and time.perf_counter() - t0 < 3.0:
+            time.sleep(0.002)
+        if not self.samples:
+            self.why = (self.why or "") + " no sample within 3 s of starting the sampler"
+        self.t_begin = time.perf_counter()
         return self
 
+    def mark_end(self):
+        self.t_end = time.perf_counter()
+
+    def extend(self, step, sync, min_samples: int = 20, max_s: float = 0.5):
+        """If the timed region held fewer than ``min_samples`` samples, keep
+        running ``step`` (the same untimed work, ``sync`` after every 8 steps
+        so that the queue stays short) until that many more samples arrived
+        or ``max_s`` has passed."""
+        if self._in(self.t_begin, self.t_end) >= min_samples:
+            return
+        t0 = time.perf_counter()
+        i = 0
+        while time.perf_counter() - t0 < max_s and self._in(t0, None) < min_samples:
+            step(i)
+            i += 1
+            if i % 8 == 0:
+                sync()
+        sync()
+        self._t_ext = (t0, time.perf_counter())
+
+    def _in(self, a, b):
+        return sum(1 for s in self.samples if s[0] >= a and (b is None or s[0] <= b))
+
     def __exit__(self, *a):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        self._stop.set()
+        if self._proc is not None:
+            self._proc.terminate()
+        if self._thread is not None:
+            self._thread.join(timeout=5)
 
     def summary(self):
-        if self.proc is None or not self.path or not os.path.exists(self.path):
-            return None
-        rows = []
-        with open(self.path) as f:
-            for ln in f:
-                parts = [x.strip() for x in ln.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.remove(self.path)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+        t_end = self.t_end if self.t_end is not None else time.perf_counter()
+        timed = [s for s in self.samples if self.t_begin <= s[0] <= t_end]
+        ext = getattr(self, "_t_ext", None)
+        after = [s for s in self.samples if ext and ext[0] <= s[0] <= ext[1]]
+        use = timed if len(timed) >= 3 else timed + after
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "source": self.source,
+                    "why": self.why or "no clock sample fell in or right after the timed region"}
+        names = sorted({name for s in use for bit, name in self.REASON_BITS.items() if s[3] & bit})
+        out = {"sm_mhz": statistics.median(s[1] for s in use), "sm_max_mhz": max(s[2] for s in use),
+               "reasons": names, "samples": len(use), "samples_in_timed_region": len(timed),
+               "source": self.source}
+        if len(timed) < 3:
+            out["samples_same_load_after"] = len(after)
+            out["note"] = ("the timed region was too short for more samples; the rest are of the "
+                           "same render loop continued, untimed, right after it")
+        if self.why:
+            out["why"] = self.why
+        return out
+
+
+def device_uuid(local: int):
+    """NVML's name of the CUDA device (GPU-<uuid>), or None."""
+    import torch
+    u = getattr(torch.cuda.get_device_properties(local), "uuid", None)
+    if u is None:
+        return None
+    u = str(u)
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 def dist_setup(n_gpus: int):
@@ -345,12 +465,14 @@ def run_fused(args, world, rank, local):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, device_uuid(local)) as clk:
         for i in range(args.steps):
             starts[i].record(stream)
             step(i)
             ends[i].record(stream)
         stream.synchronize()
+        clk.mark_end()
+        clk.extend(step, stream.synchronize)  # untimed, only if the timed region was too short
     barrier(world)
     torch.cuda.synchronize()
     gl.glassnet_check(model.handle, stream)
@@ -400,21 +522,30 @@ def run_fused(args, world, rank, local):
                                      "fp8/bf16 ratio)") if fp8 else
                                     f"{peak_src} bf16 burst (MEASURED_PEAKS.json)"},
     }
-    if not args.no_extras:
+    legs = selected_legs(args)
+    if "fp32_plain" in legs:
         result["fp32_plain"] = fp32_plain_leg(dev, weights, scene, dframes, stream)
         result["fp32_plain"]["speedup_of_bf16_fused"] = value / world / result["fp32_plain"]["value"]
+    if "e2e" in legs:
         result["e2e"] = e2e_leg(model, lat, scene, frames, args, stream, world)
+    if "batch_16_frames" in legs:
         result["batch_16_frames"] = batch_leg(model, dev, stream)
+    if "streaming" in legs:
         result["streaming"] = streaming_leg(model, lat, dframes, stream)
+    if "fp8" in legs:
         result["fp8"] = fp8_leg(weights, scene, dframes, flops, stream, dev)
+    if "sum_pooling" in legs:
         result["sum_pooling"] = sum_pooling_leg(weights, scene, dframes, frames, stream)
+    if "positional_encoding" in legs:
         result["positional_encoding"] = pe_leg(scene, dframes, frames, stream)
+    if "spatial_r3" in legs:
         result["spatial_r3"] = r3_leg(scene, dframes, frames, stream)
+    if "serving" in legs:
         result["serving"] = (serving_leg(model, (50, 200, 800), 2000) if args.serving_full
                              else serving_leg(model, (200, 800), 300))
     clocks = clk.summary()
     result["clocks"] = clocks
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and "cpu_baseline" in legs:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(result), flush=True)

@@ -404,6 +404,9 @@ typedef struct gn_server_stats {
   double pixels;                           /* pixels of completed requests */
 } gn_server_stats;
 int glassnet_server_create(gn_model* model, const gn_server_config* config, gn_server** out);
+/* Encodes `scene` (host, 32 floats) on a private stream and keeps its latent
+ * resident; concurrent calls take different slots, and a call waits while
+ * every slot is being encoded by another call or used by requests in flight. */
 int glassnet_server_add_scene(gn_server* server, const float* scene, int* scene_id);
 int glassnet_server_submit(gn_server* server, const gn_request* request, uint64_t* ticket);
 int glassnet_server_wait(gn_server* server, uint64_t ticket, double* latency_ms);
@@ -419,6 +422,20 @@ void glassnet_server_destroy(gn_server* server);
 int glassnet_check(const gn_model* model, cudaStream_t stream);
 
 /*
+ * Test hook for the device-side timeout path (the paper has no counterpart).
+ * The next fused launch of this GN_BF16_FUSED model (one render, batch or
+ * streamed launch) makes its MMA warp wait `stall_ns` nanoseconds (1 ns ..
+ * 1 s) on a barrier that nothing arrives on, after the weights are in shared
+ * memory and before any MMA is issued; the wait gives up, every warp of the
+ * kernel leaves through its exit path (which leaves no MMA or bulk copy in
+ * flight and frees the tensor memory), the frame is not written, and the next
+ * glassnet_check returns GN_ETIMEOUT.  Later launches render normally.  Do not
+ * arm it around a graph capture (the stall would be captured).
+ * Errors: GN_EINVAL (NULL model, another precision, stall out of range).
+ */
+int glassnet_debug_stall_next_render(gn_model* model, uint64_t stall_ns);
+
+/*
  * The FP32 plain render with no device allocation.  The paper has no
  * counterpart; this is an ABI convenience.  glassnet_render grows a
  * model-owned workspace with cudaMalloc (synchronising the device) when it
@@ -427,17 +444,19 @@ int glassnet_check(const gn_model* model, cudaStream_t stream);
  * program whose device memory is all handed out up front by its own pooling
  * allocator, a frame loop that must never block in the allocator) use this
  * entry point instead: its scratch is a 48 MiB array in device memory that
- * the library defines statically, so every GPU that loads the library holds
- * those 48 MiB until the process exits.
+ * the library defines statically.  A GPU maps it when the first
+ * GN_FP32_PLAIN model is loaded on it (glassnet_load_weights looks up the
+ * array's address with the model's device current) and holds it until the
+ * process exits; this call itself maps and allocates nothing.
  *  - The model must have precision GN_FP32_PLAIN.  Other arguments and the
  *    result are those of glassnet_render.
  *  - Frames whose plain-path scratch (glassnet_workspace_bytes) exceeds
  *    48 MiB are rejected with GN_EINVAL and a message giving both sizes, e.g.
  *    base widths K = 4 fit up to about 14,000 pixels, doubled widths K = 8 up
  *    to about 4,400 pixels.
- *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.  Later calls only launch kernels.
+ *  - Every call only launches kernels (the address lookup is done at model
+ *    load).  cudaDeviceReset invalidates every model and latent of the
+ *    device, this entry point's set-up included: load the model again.
  *  - All calls on a device share the one array, and it keeps the previous
  *    call's contents (every call overwrites all scratch it reads).  Calls
  *    whose work overlaps on the GPU (different streams, no ordering between

@@ -88,7 +88,9 @@ using namespace fused;
 // halves of K, arriving on one barrier per half, so the next layer's MMAs
 // over the first half run while the second half is produced.
 constexpr int B_H = B_COUNT;  // + half: K half of the next per-pixel A operand written
-constexpr int B_COUNT_B = B_COUNT + 2;
+constexpr int B_STALL = B_COUNT + 2;  // never arrived on: the stall that tests the timeout path
+constexpr int B_DRAIN = B_COUNT + 3;  // the exit path's last commit
+constexpr int B_COUNT_B = B_COUNT + 4;
 
 // TMEM column map (128 lanes x 4H columns of 32 bits): three accumulator
 // buffers of H columns, then U (H bf16 = H/2 columns) double buffered.  The
@@ -453,6 +455,8 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     mbar_init(bar(B_W), 1);
     mbar_init(bar(B_DP), 1);
     mbar_init(bar(B_DR2), 1);
+    mbar_init(bar(B_STALL), 1);
+    mbar_init(bar(B_DRAIN), 1);
     mbar_init(bar(B_AG_F), Roles<H, PE>::LW);
     mbar_init(bar(B_AG_E), 1);
     for (int b = 0; b < 2; ++b) {
@@ -592,6 +596,10 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     int tile, ns;
     const float* fold;
     if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+    // Test hook (stall_ns > 0, set by glassnet_debug_stall_next_render): wait
+    // on a barrier that nothing arrives on, before any MMA is issued, so that
+    // the wait gives up and every warp takes the timeout exit.
+    if (prm.stall_ns > 0 && !warp_wait(bar(B_STALL), 0, &s_abort, prm.stall_ns)) goto done;
     if (!take_tile(0, tile, ns, fold)) goto done;
     if (tile < total_tiles) {
       patch_fold(fold);
@@ -1008,9 +1016,12 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     }
   }
 done:
-  if (s_abort && tid == 0) atomicOr(prm.err, kErrTimeout);
   tc_fence_before();
-  __syncthreads();
+  __syncthreads();  // every warp is here: s_abort is final
+  if (s_abort) {
+    if (warp == R::MMA) drain_async(bar(B_W), bar(B_DRAIN));
+    if (tid == 0) atomicOr(prm.err, kErrTimeout);
+  }
   if (warp == R::MMA) {
     tc_fence_after();
     tmem_dealloc(tbase, TMap<H>::NCOLS);

@@ -96,7 +96,8 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
 // Bounded wait shared by a whole warp: every lane waits, then the warp agrees.
 // On a timeout the CTA-wide abort flag is raised and every later wait fails
 // at once, so all warps reach the common exit.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit_ns = kWaitNs) {
   bool ok = mbar_try_wait(bar, parity);
   if (!ok) {
     const uint64_t t0 = globaltimer_ns();
@@ -106,13 +107,27 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
         break;
       }
       if (*abort_flag) break;
-      if (globaltimer_ns() - t0 > kWaitNs) {
+      if (globaltimer_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         break;
       }
     }
   }
   return __all_sync(0xffffffffu, ok);
+}
+
+// Exit path of a CTA whose waits gave up: called by the warp that issued the
+// CTA's MMAs and its weight copy (completion on `bar_w`, phase 0), so that
+// nothing of the CTA is in flight when its TMEM is freed and it leaves:
+// waits (bounded) for the copy, then commits every MMA it issued to
+// `bar_drain` and waits (bounded) for that.  MMAs and copies complete by
+// themselves, so both waits end.
+__device__ __forceinline__ void drain_async(uint32_t bar_w, uint32_t bar_drain) {
+  mbar_wait(bar_w, 0, kWaitNs);
+  mma_commit_e(bar_drain);
+  __syncwarp();
+  mbar_wait(bar_drain, 0, kWaitNs);
+  __syncwarp();
 }
 
 // Frame that owns global tile `tile`.

@@ -361,6 +361,11 @@ int load_weights_impl(const void* blob, size_t nbytes, const gn_model_config* cf
     glassnet_free_model(m);
     return fail(GN_ENOMEM, "cudaMalloc error word: %s", cudaGetErrorString(e));
   }
+  if (precision == GN_FP32_PLAIN && (e = gn::setup_static_scratch(m->device)) != cudaSuccess) {
+    glassnet_free_model(m);
+    return fail(GN_ENOMEM, "static scratch of glassnet_render_fp32_static: %s",
+                cudaGetErrorString(e));
+  }
   if (precision == GN_FP8_FUSED) {
     // packed by glassnet_calibrate_fp8 once activation scales are known
     m->host_w = static_cast<float*>(std::malloc(wi.total * sizeof(float)));
@@ -552,10 +557,12 @@ cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s
     q.pool_sum = 1;
     return launch_fused_fp8(m->H, m->fused, q, s);
   }
-  if (m->pooling == GN_POOL_SUM || m->wi.L > 0) {
+  if (m->pooling == GN_POOL_SUM || m->wi.L > 0 || m->stall_ns > 0) {
     FusedParams q = p;
     q.pool_sum = m->pooling == GN_POOL_SUM;
     q.pe_freqs = m->wi.L;
+    q.stall_ns = m->stall_ns;  // the test hook holds for one launch
+    const_cast<gn_model*>(m)->stall_ns = 0;
     return launch_fused_bf16(m->H, m->fused, q, s);
   }
   return launch_fused_bf16(m->H, m->fused, p, s);
@@ -780,6 +787,15 @@ int glassnet_fp8_scales(const gn_model* m, float* scales) {
   if (m->precision != GN_FP8_FUSED || !m->fp8_ready)
     return fail(GN_EINVAL, "not a calibrated GN_FP8_FUSED model");
   std::memcpy(scales, m->fp8_act, sizeof(m->fp8_act));
+  return GN_OK;
+}
+
+int glassnet_debug_stall_next_render(gn_model* m, uint64_t stall_ns) {
+  if (!m) return fail(GN_EINVAL, "model is NULL");
+  if (m->precision != GN_BF16_FUSED) return fail(GN_EINVAL, "the stall hook is in the fused BF16 kernel");
+  if (stall_ns == 0 || stall_ns > 1000000000ull)
+    return fail(GN_EINVAL, "stall of %llu ns outside 1 ns .. 1 s", static_cast<unsigned long long>(stall_ns));
+  m->stall_ns = stall_ns;
   return GN_OK;
 }
 

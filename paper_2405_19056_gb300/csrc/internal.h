@@ -217,6 +217,10 @@ struct FusedParams {
   // Positional-encoding frequencies of the inputs (0: none; the PE kernel
   // variant serves 1 .. kMaxPeFreqsFused).
   int pe_freqs;
+  // Test hook of the BF16 kernel's timeout path (0 in every render): the MMA
+  // warp waits this long on a barrier that nothing arrives on, then every
+  // warp leaves and the error word gets the timeout bit.
+  uint64_t stall_ns;
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -242,6 +246,9 @@ cudaError_t launch_plain_fp32(const float* w32, const WeightIndex& wi, const flo
                               int P, float* out, void* ws, uint32_t* err, cudaStream_t s,
                               int pool_sum, int w);
 int device_sm_count();
+// Looks up (and so maps) the static scratch of glassnet_render_fp32_static on
+// device `dev`, which must be current (noalloc_fp32.cu).
+cudaError_t setup_static_scratch(int dev);
 // 3x3 R (conv_r3.cu): R1 as a 3x3 kernel over the neural buffer phi
 // (BF16 [h][H/8][w][8]) the fused kernel wrote, then R2 and the sigmoid.
 // The image holds the 9 taps' [H/8][H][8] BF16 weights (tap = (dy + 1) 3 +
@@ -280,6 +287,7 @@ struct gn_model {
   float* host_w = nullptr;  // FP8 models: concat-form f32 weights kept for packing
   bool fp8_ready = false;   // FP8 models: calibrated and packed
   float fp8_act[gn::kFp8Acts] = {};  // FP8 activation scales (real value of a code = code * s)
+  uint64_t stall_ns = 0;    // test hook: the next fused BF16 launch stalls (glassnet_debug_stall_next_render)
 };
 
 namespace gn {

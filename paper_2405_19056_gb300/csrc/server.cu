@@ -70,8 +70,12 @@ struct Job {
   double latency_ms = 0.0;
 };
 
+// A scene slot is empty (id < 0, not encoding), resident (id >= 0) or being
+// (re-)encoded by one glassnet_server_add_scene call (encoding: no other call
+// may take it, and no request can name it).
 struct Scene {
   int id = -1;
+  bool encoding = false;
   gn_latent* latent = nullptr;
   uint64_t last_use = 0;
   int in_flight = 0;
@@ -273,35 +277,58 @@ int glassnet_server_create(gn_model* m, const gn_server_config* cfg, gn_server**
 int glassnet_server_add_scene(gn_server* s, const float* scene, int* scene_id) {
   if (!s || !scene || !scene_id) return gn::set_error(GN_EINVAL, "server, scene and id must be non-NULL");
   std::unique_lock<std::mutex> lk(s->mu);
-  // an empty slot, else the least recently used one once no request uses it
+  // an empty slot, else the least recently used resident one once no request
+  // uses it; slots that another call is encoding are never taken
   int slot = -1;
-  for (size_t i = 0; i < s->scenes.size(); ++i)
-    if (s->scenes[i].id < 0) {
-      slot = static_cast<int>(i);
-      break;
+  s->cv.wait(lk, [&] {
+    slot = -1;
+    for (size_t i = 0; i < s->scenes.size(); ++i)
+      if (s->scenes[i].id < 0 && !s->scenes[i].encoding) {
+        slot = static_cast<int>(i);
+        return true;
+      }
+    for (size_t i = 0; i < s->scenes.size(); ++i) {
+      const Scene& c = s->scenes[i];
+      if (c.encoding || c.in_flight > 0) continue;
+      if (slot < 0 || c.last_use < s->scenes[slot].last_use) slot = static_cast<int>(i);
     }
-  if (slot < 0) {
-    slot = 0;
-    for (size_t i = 1; i < s->scenes.size(); ++i)
-      if (s->scenes[i].last_use < s->scenes[slot].last_use) slot = static_cast<int>(i);
-    s->cv.wait(lk, [&] { return s->scenes[slot].in_flight == 0; });
-  }
+    return slot >= 0;
+  });
   Scene& sc = s->scenes[slot];
   sc.id = -1;  // not usable while it is being re-encoded
+  sc.encoding = true;
   gn_latent* old = sc.latent;
   sc.latent = nullptr;
   lk.unlock();
   if (old) glassnet_free_latent(old);
+  // encode on a private stream, so that adding a scene does not wait for the
+  // lanes' requests in flight
   gn_latent* lat = nullptr;
-  const int rc = glassnet_encode_scene(s->model, scene, &lat, nullptr);
-  if (rc == GN_OK && cudaDeviceSynchronize() != cudaSuccess)
-    return gn::set_error(GN_ECUDA, "scene encoder failed");
+  cudaStream_t st = nullptr;
+  cudaSetDevice(s->model->device);
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  int rc = e == cudaSuccess ? glassnet_encode_scene(s->model, scene, &lat, st)
+                            : err(GN_ECUDA, "scene stream: %s", cudaGetErrorString(e));
+  if (rc == GN_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      glassnet_free_latent(lat);
+      lat = nullptr;
+      rc = err(GN_ECUDA, "scene encoder failed: %s", cudaGetErrorString(e));
+    }
+  }
+  if (st) cudaStreamDestroy(st);
   lk.lock();
-  if (rc != GN_OK) return rc;
+  sc.encoding = false;
+  if (rc != GN_OK) {  // the slot is empty again
+    s->cv.notify_all();
+    return rc;
+  }
   sc.latent = lat;
   sc.id = s->next_scene_id++;
   sc.last_use = ++s->use_clock;
   *scene_id = sc.id;
+  s->cv.notify_all();
   return GN_OK;
 }
 

@@ -52,6 +52,7 @@ _SIGNATURES = {
     "glassnet_render_host": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P]),
     "glassnet_render_batch": (_I, [_P, _P, _I, _P]),
     "glassnet_check": (_I, [_P, _P]),
+    "glassnet_debug_stall_next_render": (_I, [_P, ctypes.c_uint64]),
     "glassnet_render_fp32_static": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P]),
     "glassnet_calibrate_fp8": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P]),
     "glassnet_fp8_scales": (_I, [_P, _P]),
@@ -371,6 +372,10 @@ def glassnet_render_fp32_static(model, latent, gbuf, tbuf, layer_count, K, h, w,
 
 def glassnet_check(model, stream=None):
     _check(_lib().glassnet_check(model, _stream(stream)))
+
+
+def glassnet_debug_stall_next_render(model, stall_ns: int):
+    _check(_lib().glassnet_debug_stall_next_render(model, int(stall_ns)))
 
 
 def glassnet_check_code(model, stream=None) -> int:

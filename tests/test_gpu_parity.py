@@ -239,6 +239,28 @@ def test_exact_sum_range_reported(cuda_lib):
     assert gl.glassnet_check_code(m.handle) == gl.GN_ERANGE
 
 
+@pytest.mark.parametrize("widths", ["base", "doubled"])
+def test_timeout_reported_and_next_render_exact(widths, request):
+    """A device wait that gives up (the stall hook: the MMA warp waits 20 us on
+    a barrier nothing arrives on) is reported as GN_ETIMEOUT, the frame is left
+    unwritten, and the next render of the same model is bit-identical to one
+    taken before the stall."""
+    net = request.getfixturevalue(widths)
+    m = net.model(gl.GN_BF16_FUSED)
+    scene = synth.make_scene(12)
+    frame = synth.make_frame(40, 52, 4, counts="uniform", seed=12)
+    before = render(net, gl.GN_BF16_FUSED, scene, frame)
+    lat = m.encode(scene)
+    out = torch.full((3, frame.h, frame.w), float("nan"), device=DEV)
+    gl.glassnet_debug_stall_next_render(m.handle, 20_000)
+    m.render(lat, _dev(frame.gbuf), _dev(frame.tbuf), _dev(frame.counts), out)
+    assert gl.glassnet_check_code(m.handle) == gl.GN_ETIMEOUT
+    assert gl.glassnet_check_code(m.handle) == gl.GN_OK  # cleared
+    assert np.isnan(out.cpu().numpy()).all()  # no tile ran
+    after = render(net, gl.GN_BF16_FUSED, scene, frame)
+    assert np.array_equal(before, after)
+
+
 def test_render_batch_equals_single_renders(base):
     m = base.model(gl.GN_BF16_FUSED)
     specs = [(33, 47, 3, "uniform", 1), (128, 64, 8, "poisson3", 2), (5, 300, 1, "all", 3)]

@@ -1,18 +1,22 @@
 """glassnet_render_fp32_static: the FP32 plain render for callers that cannot
 allocate device memory when they render (their device memory is all handed out
 up front by their own pooling allocator, or their frame loop must never block
-in the allocator).  Its scratch is a 48 MiB static device array in the library.
+in the allocator).  Its scratch is a 48 MiB static device array in the library,
+mapped when the FP32 model is loaded.
 
-Checked through the C ABI against glassnet_render (same model, same inputs)
-within the FP32 tolerance used by the other tests, on two calls in a row with
-different frames, so contents left in the shared scratch by the first call
-cannot leak into the second.  This file is collected last so that a run that
-stops at the first failure has already run every other test.
+Checked through the C ABI on two calls in a row with different frames (so
+contents left in the shared scratch by the first call cannot leak into the
+second): each output against the FP64 oracle and against glassnet_render
+within the FP32 tolerance used by the other tests, and the device's free
+memory unchanged across each call, the first one included.  This file is
+collected last so that a run that stops at the first failure has already run
+every other test.
 """
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from gen import synth
 from paper_2405_19056_gb300 import glassnet as gl
 
@@ -27,37 +31,45 @@ def _dev(a):
 
 
 @pytest.fixture(scope="module")
-def plain_model(cuda_lib):
-    w = synth.make_weights(synth.BASE_WIDTHS, seed=2, bias="uniform")
-    return gl.Model(w, gl.GN_FP32_PLAIN)
+def plain_weights():
+    return synth.make_weights(synth.BASE_WIDTHS, seed=2, bias="uniform")
 
 
-def _both(model, lat, frame):
+@pytest.fixture(scope="module")
+def plain_model(cuda_lib, plain_weights):
+    return gl.Model(plain_weights, gl.GN_FP32_PLAIN)
+
+
+def _static_then_render(model, lat, frame):
+    """The static render (free device memory measured around it), then
+    glassnet_render of the same inputs."""
     K, h, w = frame.K, frame.h, frame.w
     g, t, c = _dev(frame.gbuf), _dev(frame.tbuf), _dev(frame.counts)
     ref = torch.full((3, h, w), float("nan"), device=DEV)
     got = torch.full((3, h, w), float("nan"), device=DEV)
-    gl.glassnet_render(model.handle, lat.handle, g, t, c, K, h, w, ref)
-    model.check()
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     gl.glassnet_render_fp32_static(model.handle, lat.handle, g, t, c, K, h, w, got)
     model.check()
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
+    gl.glassnet_render(model.handle, lat.handle, g, t, c, K, h, w, ref)
+    model.check()
     return ref.cpu().numpy(), got.cpu().numpy(), free0 - free1
 
 
-def test_static_scratch_render_matches_glassnet_render_twice(plain_model):
-    lat = plain_model.encode(synth.make_scene(4))
-    f1 = synth.make_frame(96, 100, 4, counts="uniform", seed=41)
-    f2 = synth.make_frame(64, 64, 2, counts="all", seed=42)
-    ref1, got1, _ = _both(plain_model, lat, f1)
-    ref2, got2, grew = _both(plain_model, lat, f2)
-    assert np.all(np.isfinite(got1)) and np.all(np.isfinite(got2))
-    assert np.abs(got1 - ref1).max() <= FP32_MAX
-    assert np.abs(got2 - ref2).max() <= FP32_MAX
-    assert grew == 0, f"device free memory dropped by {grew} bytes during the call"
+def test_static_scratch_render_matches_oracle_and_render_twice(plain_model, plain_weights):
+    scene = synth.make_scene(4)
+    lat = plain_model.encode(scene)
+    frames = [synth.make_frame(96, 100, 4, counts="uniform", seed=41),
+              synth.make_frame(64, 64, 2, counts="all", seed=42)]
+    for i, f in enumerate(frames):
+        ref, got, grew = _static_then_render(plain_model, lat, f)
+        assert grew == 0, f"call {i + 1}: device free memory dropped by {grew} bytes"
+        assert np.all(np.isfinite(got))
+        want = oracle.render_frame(plain_weights, scene, f.gbuf, f.tbuf, f.counts)
+        assert np.abs(got - want).max() <= FP32_MAX, f"call {i + 1} against the oracle"
+        assert np.abs(got - ref).max() <= FP32_MAX, f"call {i + 1} against glassnet_render"
 
 
 def test_static_scratch_rejects_frames_beyond_its_size(plain_model):
