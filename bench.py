@@ -77,9 +77,9 @@ def parse():
     ap.add_argument("--legs", default=None,
                     help="comma-separated extra legs to run (default: all of them unless "
                          "--no-extras): " + ",".join(EXTRA_LEGS))
-    ap.add_argument("--serving-full", action="store_true",
-                    help="serving leg at 50, 200 and 800 req/s with 2000 requests each "
-                         "(default: 200 and 800 req/s, 300 requests each)")
+    ap.add_argument("--serving-quick", action="store_true",
+                    help="serving leg at 200 and 800 req/s with 300 requests each (default: the "
+                         "serving workload as stated, 2000 requests at each of 50, 200, 800 req/s)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8"],
                     help="precision of the timed fused leg (fp8: calibrated on a seed-1 frame)")
     ap.add_argument("--pooling", default="max_mean", choices=["max_mean", "sum"],
@@ -541,8 +541,8 @@ def run_fused(args, world, rank, local):
     if "spatial_r3" in legs:
         result["spatial_r3"] = r3_leg(scene, dframes, frames, stream)
     if "serving" in legs:
-        result["serving"] = (serving_leg(model, (50, 200, 800), 2000) if args.serving_full
-                             else serving_leg(model, (200, 800), 300))
+        result["serving"] = (serving_leg(model, weights, (200, 800), 300) if args.serving_quick
+                             else serving_leg(model, weights, (50, 200, 800), 2000))
     clocks = clk.summary()
     result["clocks"] = clocks
     if rank == 0 and "cpu_baseline" in legs:
@@ -734,74 +734,144 @@ def pe_leg(scene, dframes, frames, stream, L=4, steps=200):
     return out
 
 
-def serving_leg(model, rates, n_requests, n_streams=4, seed=0):
-    """Requests arriving as a Poisson process (rate per second), resolution
-    256, 512 or 1024 squared with probabilities 0.5 / 0.35 / 0.15, K ~ U{1..8}
-    with every slot valid, 8 resident scenes, host buffers (page-locked) in
-    and out, through glassnet_server_*: p50 / p99 latency from submission to
-    the image in host memory, and the throughput achieved."""
-    import time
+P99_TARGET_MS = 10.0  # the serving loop's stated p99 target (derivation in the leg's docstring)
+
+
+def serving_stream(rate, n_requests, seed=0):
+    """The serving workload's request stream at one rate: Poisson arrival
+    times (s), resolutions 256/512/1024 squared w.p. 0.5/0.35/0.15, K ~
+    U{1..8} and a scene index among 32, all from one seeded generator."""
+    rng = np.random.default_rng([seed, rate])
+    res = rng.choice((256, 512, 1024), size=n_requests, p=(0.5, 0.35, 0.15))
+    Ks = rng.integers(1, 9, size=n_requests)
+    arrive = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    scenes = rng.integers(0, 32, size=n_requests)
+    return res, Ks, arrive, scenes
+
+
+def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
+    """The serving workload: n_requests render requests per rate arriving as a
+    Poisson process; resolution 256, 512 or 1024 squared w.p. 0.5 / 0.35 /
+    0.15; K ~ U{1..8} with every slot valid; 32 resident scene latents; host
+    buffers (page-locked) in and out; admission by a 40 GB device-memory
+    budget, through glassnet_server_*.  Open loop: the generator submits each
+    request at its arrival time and never waits for a result (each size's
+    outputs rotate over 32 host buffers, which the generator does not read);
+    every request is waited for at the end.  Latency runs from submission to
+    the image in host memory.
+
+    Beside it, the FP32 plain path served one request at a time
+    (glassnet_render_host, synchronous) on the same request streams: its
+    latency runs from the request's arrival time, so it includes the time
+    the request queued behind earlier ones.
+
+    p99 target: 10 ms.  A request's latency alone is its host->device copy
+    (up to 461 MB for 1024^2 at K = 8, ~2.3 ms at the ~200 GB/s measured host
+    link), the render (~0.5 ms) and the 12.6 MB read-back; with up to 4 lanes
+    in flight and ~30 % of the link busy at 800 req/s, a request can queue
+    behind up to three others, so 10 ms bounds the tail at every rate."""
     import torch
     from gen import synth
     from paper_2405_19056_gb300 import glassnet as gl
 
-    sizes, probs = (256, 512, 1024), (0.5, 0.35, 0.15)
+    sizes = (256, 512, 1024)
     pool = {}
-    for r in sizes:  # one K = 8 frame per size; the first K slots are a K-slot buffer
+    for r in sizes:  # one K = 8 frame per size; its first K slots are a K-slot buffer
         f = synth.make_frame(r, r, 8, counts="all", seed=10 + r)
         pool[r] = dict(g=torch.from_numpy(f.gbuf).pin_memory(), t=torch.from_numpy(f.tbuf).pin_memory(),
                        c={K: torch.full((r, r), K, dtype=torch.uint8).pin_memory() for K in range(1, 9)},
-                       outs=[torch.empty((3, r, r)).pin_memory() for _ in range(16)])
+                       outs=[torch.empty((3, r, r)).pin_memory() for _ in range(32)])
+    scenes = [synth.make_scene(200 + i) for i in range(32)]
     results = []
-    srv = gl.glassnet_server_create(model.handle, n_streams=n_streams, max_scenes=32)
-    try:
-        ids = [gl.glassnet_server_add_scene(srv, synth.make_scene(200 + i)) for i in range(8)]
-        for rate in rates:
-            rng = np.random.default_rng([seed, rate])
-            res = rng.choice(sizes, size=n_requests, p=probs)
-            Ks = rng.integers(1, 9, size=n_requests)
-            arrive = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
-            before = gl.glassnet_server_stats(srv)
-            ring = {r: [None] * 16 for r in sizes}
+    for rate in rates:
+        res, Ks, arrive, sc = serving_stream(rate, n_requests, seed)
+        srv = gl.glassnet_server_create(model.handle, n_streams=n_streams, max_scenes=32,
+                                        budget_bytes=40 * 10 ** 9)
+        try:
+            ids = [gl.glassnet_server_add_scene(srv, x) for x in scenes]
             used = {r: 0 for r in sizes}
-            tickets = []
+            # warm-up: per (size, K) bucket, one request on each lane (submitted
+            # together while every lane is free) captures the lanes' graphs
+            for r in sizes:
+                for K in range(1, 9):
+                    p = pool[r]
+                    warm = [gl.glassnet_server_submit(srv, ids[0], p["g"], p["t"], p["c"][K], K, r, r,
+                                                      p["outs"][j]) for j in range(n_streams)]
+                    for t in warm:
+                        gl.glassnet_server_wait(srv, t)
+            before = gl.glassnet_server_stats(srv)
+            tickets, lag = [], 0.0
             t0 = time.perf_counter()
             for i in range(n_requests):
                 while time.perf_counter() - t0 < arrive[i]:
                     pass
+                lag = max(lag, time.perf_counter() - t0 - arrive[i])
                 r, K = int(res[i]), int(Ks[i])
-                slot = used[r] % 16
-                used[r] += 1
-                if ring[r][slot] is not None:  # the output buffer's previous request
-                    gl.glassnet_server_wait(srv, ring[r][slot])
-                    ring[r][slot] = None
                 p = pool[r]
-                t = gl.glassnet_server_submit(srv, ids[i % 8], p["g"], p["t"], p["c"][K], K, r, r,
-                                              p["outs"][slot])
-                ring[r][slot] = t
-                tickets.append(t)
-            for r in sizes:
-                for t in ring[r]:
-                    if t is not None:
-                        gl.glassnet_server_wait(srv, t)
+                out = p["outs"][used[r] % 32]
+                used[r] += 1
+                tickets.append(gl.glassnet_server_submit(srv, ids[int(sc[i])], p["g"], p["t"],
+                                                         p["c"][K], K, r, r, out))
+            lats = [gl.glassnet_server_wait(srv, t) for t in tickets]
             wall = time.perf_counter() - t0
             st = gl.glassnet_server_stats(srv)
-            px = st["pixels"] - before["pixels"]
-            mean_px = float(np.mean(res.astype(np.float64) ** 2))
-            results.append({"rate_per_s": rate, "requests": n_requests,
-                            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                            "throughput_mpx_s": px / wall / 1e6,
-                            "demand_mpx_s": rate * mean_px / 1e6})
-            # latencies are cumulative in the server: restart it per rate
+        finally:
             gl.glassnet_server_destroy(srv)
-            srv = gl.glassnet_server_create(model.handle, n_streams=n_streams, max_scenes=32)
-            ids = [gl.glassnet_server_add_scene(srv, synth.make_scene(200 + i)) for i in range(8)]
-        gl.glassnet_check(model.handle)
-    finally:
-        gl.glassnet_server_destroy(srv)
-    return {"workload": "Poisson arrivals; 256/512/1024 squared w.p. 0.5/0.35/0.15; K~U{1..8}, "
-                        "all slots valid; 8 scenes; host buffers in and out; "
-                        f"{n_streams} lanes", "rates": results}
+        px = st["pixels"] - before["pixels"]
+        mean_px = float(np.mean(res.astype(np.float64) ** 2))
+        p50, p99 = (float(np.percentile(lats, q)) for q in (50, 99))
+        results.append({"rate_per_s": rate, "requests": n_requests, "p50_ms": p50, "p99_ms": p99,
+                        "max_ms": float(np.max(lats)), "p99_target_ms": P99_TARGET_MS,
+                        "p99_met": p99 <= P99_TARGET_MS,
+                        "throughput_mpx_s": px / wall / 1e6, "demand_mpx_s": rate * mean_px / 1e6,
+                        "wall_s": wall, "generator_lag_max_ms": lag * 1e3})
+    gl.glassnet_check(model.handle)
+    plain = fp32_plain_serving(weights, rates, n_requests, pool, scenes, seed)
+    for r_bf, r_fp in zip(results, plain):
+        r_bf["speedup_of_fp32_plain_served"] = r_bf["throughput_mpx_s"] / r_fp["throughput_mpx_s"]
+    return {"workload": f"{n_requests} requests per rate, Poisson arrivals; 256/512/1024 squared "
+                        "w.p. 0.5/0.35/0.15; K~U{1..8}, all slots valid; 32 resident scenes; "
+                        "40 GB admission budget; host buffers in and out; "
+                        f"{n_streams} lanes; open-loop generator",
+            "api": "glassnet_server_submit / _wait", "rates": results,
+            "fp32_plain_served_one_at_a_time": plain}
+
+
+def fp32_plain_serving(weights, rates, n_requests, pool, scenes, seed=0):
+    """The FP32 plain path on the same request streams, one request at a time
+    (glassnet_render_host: copies in, render, copy out, wait); latency from
+    each request's arrival time."""
+    import torch
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    m = gl.Model(weights, gl.GN_FP32_PLAIN)
+    lats_ = [m.encode(x) for x in scenes]
+    stream = torch.cuda.Stream()
+    out = []
+    for r in (256, 512, 1024):  # warm-up: workspace and staging at the largest size
+        p = pool[r]
+        gl.glassnet_render_host(m.handle, lats_[0].handle, p["g"], p["t"], p["c"][8], 8, r, r,
+                                p["outs"][0], stream)
+    for rate in rates:
+        res, Ks, arrive, sc = serving_stream(rate, n_requests, seed)
+        lat_ms = []
+        t0 = time.perf_counter()
+        for i in range(n_requests):
+            while time.perf_counter() - t0 < arrive[i]:
+                pass
+            r, K = int(res[i]), int(Ks[i])
+            p = pool[r]
+            gl.glassnet_render_host(m.handle, lats_[int(sc[i])].handle, p["g"], p["t"], p["c"][K], K,
+                                    r, r, p["outs"][0], stream)
+            lat_ms.append((time.perf_counter() - t0 - arrive[i]) * 1e3)
+        wall = time.perf_counter() - t0
+        px = float(np.sum(res.astype(np.float64) ** 2))
+        out.append({"rate_per_s": rate, "requests": n_requests,
+                    "p50_ms": float(np.percentile(lat_ms, 50)),
+                    "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(np.max(lat_ms)),
+                    "throughput_mpx_s": px / wall / 1e6, "wall_s": wall})
+    m.check(stream)
+    return out
 
 
 def streaming_leg(model, lat, dframes, stream, steps=20):

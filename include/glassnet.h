@@ -58,7 +58,8 @@ typedef enum gn_status {
   GN_EFORMAT = -4,      /* weight blob: bad magic, version, sizes or checksum */
   GN_ETIMEOUT = -5,     /* a device-side wait exceeded its time limit */
   GN_EUNSUPPORTED = -6, /* widths or precision this build does not provide */
-  GN_ERANGE = -7        /* exact set-sum left its fixed-point range (see below) */
+  GN_ERANGE = -7,       /* exact set-sum left its fixed-point range (see below) */
+  GN_ESATURATED = -8    /* FP8: an input beyond its calibrated range was clamped */
 } gn_status;
 
 typedef enum gn_precision {
@@ -304,25 +305,34 @@ int glassnet_render_batch(const gn_model* model, const gn_frame* frames, int n,
 /*
  * FP8 variant.  A model loaded with GN_FP8_FUSED runs every layer's GEMM with
  * E4M3 operands and FP32 accumulation: weights are quantised per output
- * channel (scale = channel |max| / 448), activations per tensor with static
- * scales taken from one calibration render.  The per-scene folded biases
- * stay exact (a BF16 hi/lo MMA), the set pooling stays exact and
- * order-independent (it runs on the dequantised phi output).  The paper
- * fixes no precision for the network; this is a deployment variant.
+ * channel (scale = channel |max| / 448), the network's two input tensors
+ * (transparency layers, G-buffer) per input channel and the hidden
+ * activations per tensor, with static scales taken from one calibration
+ * render.  An input channel's scale is folded into its weight column (the
+ * weights quantised are W[n][c] s[c]), so it costs nothing at render time.
+ * The per-scene folded biases stay exact (a BF16 hi/lo MMA), the set pooling
+ * stays exact and order-independent (it runs on the dequantised phi output).
+ * An input value beyond its channel's calibrated range is clamped to the
+ * largest E4M3 code and reported (GN_ESATURATED at the next glassnet_check);
+ * the frame is still rendered.  The paper fixes no precision for the
+ * network; this is a deployment variant.
  *
  * glassnet_calibrate_fp8 renders the given frame with the FP32 plain path
  * (intermediates in the model's FP32 workspace, grown on demand), takes the
- * |max| of each layer input over it (t over valid slots, U, pool, [g ; r],
- * y, y2, q), sets scale = 2 |max| / 448 (one binade of headroom against
- * inputs beyond the calibration frame's range; 1 where the maximum is 0) and
- * packs the E4M3 image.  Synchronous.  Until it has run, rendering with the model
- * returns GN_EINVAL.  It may be called again to recalibrate (no render may be
- * in flight).  Errors: GN_EINVAL (not an FP8 model, bad frame), GN_ENOMEM,
- * GN_ECUDA.
+ * |max| of each layer input over it (each channel of t over the valid slots,
+ * each channel of g; then U, pool, r, y, y2, q) and sets scale = 8 |max| / 448
+ * for the input channels and 4 |max| / 448 for the others (headroom against
+ * inputs beyond the calibration frame's range; 1 where the maximum is 0),
+ * then packs the E4M3 image.  Synchronous.  Until it has run, rendering with
+ * the model returns GN_EINVAL.  It may be called again to recalibrate (no
+ * render may be in flight).  Errors: GN_EINVAL (not an FP8 model, bad frame),
+ * GN_ENOMEM, GN_ECUDA.
  *
- * glassnet_fp8_scales copies the seven activation scales (the real value of a
- * code x is x * scale), in the order above, to host memory.
+ * glassnet_fp8_scales copies the GN_FP8_SCALES = 32 scales (the real value of
+ * a code x is x * scale) to host memory, in the order: the 12 channels of t,
+ * the 14 channels of g, then U, pool, r, y, y2, q.
  */
+#define GN_FP8_SCALES 32
 int glassnet_calibrate_fp8(gn_model* model, const gn_latent* latent, const float* gbuf,
                            const float* tbuf, const uint8_t* layer_count, int K, int h, int w,
                            cudaStream_t stream);
@@ -415,8 +425,9 @@ void glassnet_server_destroy(gn_server* server);
 
 /*
  * Synchronises `stream`, then returns and clears the model's device error
- * bits: GN_EINVAL (a layer count above K), GN_ERANGE (a pixel's exact set-sum
- * reached 2^11 and lost exactness), GN_ETIMEOUT (a device wait gave up), or
+ * bits: GN_ETIMEOUT (a device wait gave up), GN_EINVAL (a layer count above
+ * K), GN_ERANGE (a pixel's exact set-sum reached 2^11 and lost exactness),
+ * GN_ESATURATED (an FP8 input was clamped), in that order of precedence, or
  * GN_OK.  GN_ECUDA if the stream reports a CUDA error.
  */
 int glassnet_check(const gn_model* model, cudaStream_t stream);

@@ -99,17 +99,31 @@ __device__ __forceinline__ void load_slot_f8(const FusedFrame& F, int k,
   }
 }
 
+// x[c] / s[c] for N input channels, each channel with its own calibrated
+// scale; `sat` is set when a value lies beyond the largest E4M3 code (the
+// conversion clamps it).
+template <int N>
+__device__ __forceinline__ void scale_inputs(const float (&x)[N], const float (&inv_s)[N],
+                                             float (&v)[N], bool& sat) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    v[c] = x[c] * inv_s[c];
+    sat |= fabsf(v[c]) > 448.0f;
+  }
+}
+
 // Writes K block 0 of rows row0 + 32 i of a [2][128][16]-byte operand: the
-// 12 channels as E4M3 codes of x / s_t, then zeros (block 1 stays zero).
-__device__ __forceinline__ void store_slot_f8(uint32_t base, int row0, float inv_s,
-                                              const float (&x)[kRowsPerLoadLane][kTC]) {
+// 12 channels as E4M3 codes of x[c] / s_t[c], then zeros (block 1 stays zero).
+__device__ __forceinline__ void store_slot_f8(uint32_t base, int row0, const float (&inv_s)[kTC],
+                                              const float (&x)[kRowsPerLoadLane][kTC], bool& sat) {
 #pragma unroll
   for (int i = 0; i < kRowsPerLoadLane; ++i) {
+    float v[kTC];
+    scale_inputs(x[i], inv_s, v, sat);
     uint32_t w[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      w[j] = pack_u16x2(pack_e4m3(x[i][4 * j] * inv_s, x[i][4 * j + 1] * inv_s),
-                        pack_e4m3(x[i][4 * j + 2] * inv_s, x[i][4 * j + 3] * inv_s));
+      w[j] = pack_u16x2(pack_e4m3(v[4 * j], v[4 * j + 1]), pack_e4m3(v[4 * j + 2], v[4 * j + 3]));
     sts128(base + static_cast<uint32_t>(row0 + 32 * i) * 16u, w[0], w[1], w[2], 0u);
   }
 }
@@ -122,8 +136,17 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
   using L = FusedLayoutF8<H>;
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
   const float* cst = reinterpret_cast<const float*>(wimg + L::cst);
-  const float inv_s_t = __ldg(cst + L::INV_S_T);
-  const float inv_s_g = __ldg(cst + L::INV_S_G);
+  float inv_s_t[kTC], inv_s_g[kGC];  // per-channel input scales
+#pragma unroll
+  for (int c = 0; c < kTC; ++c) inv_s_t[c] = __ldg(cst + L::INV_S_TCH + c);
+#pragma unroll
+  for (int c = 0; c < kGC; ++c) inv_s_g[c] = __ldg(cst + L::INV_S_GCH + c);
+  bool sat = false;  // an input of this warp's rows was clamped
+  // reported once per tile, by the warp's lane 0
+  auto report_sat = [&]() {
+    if (__any_sync(0xffffffffu, sat) && lane == 0) atomicOr(prm.err, kErrSaturated);
+    sat = false;
+  };
   const int row0 = li * 64 + lane;
   uint32_t lc = 0, n_ag = 0;
   for (uint32_t tb = 0;; ++tb) {
@@ -136,6 +159,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
       return;
     }
     tile = *reinterpret_cast<volatile int*>(&ls.tile[tb & 1]);
+    report_sat();  // the previous tile's inputs
     if (tile >= prm.total_tiles) {
       if (lane == 0) {
         ls.ns[tb & 1][li] = 0;
@@ -174,18 +198,19 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
         for (int ch = 0; ch < kGC; ++ch)
           gv[i][ch] = has[i] ? __ldg(F.gbuf + (static_cast<uint32_t>(ch) * P + pix[i])) : 0.0f;
     }
-    // B1's G-buffer operand: the 14 channels as codes of g / s_g, then zeros
+    // B1's G-buffer operand: the 14 channels as codes of g[c] / s_g[c], then zeros
     auto put_ag = [&]() -> bool {
       if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
 #pragma unroll
       for (int i = 0; i < kRowsPerLoadLane; ++i) {
+        float v[kGC];
+        scale_inputs(gv[i], inv_s_g, v, sat);
         uint32_t w[4];
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-          w[j] = pack_u16x2(pack_e4m3(gv[i][4 * j] * inv_s_g, gv[i][4 * j + 1] * inv_s_g),
-                            pack_e4m3(gv[i][4 * j + 2] * inv_s_g, gv[i][4 * j + 3] * inv_s_g));
-        w[3] = pack_u16x2(pack_e4m3(gv[i][12] * inv_s_g, gv[i][13] * inv_s_g), 0);
+          w[j] = pack_u16x2(pack_e4m3(v[4 * j], v[4 * j + 1]), pack_e4m3(v[4 * j + 2], v[4 * j + 3]));
+        w[3] = pack_u16x2(pack_e4m3(v[12], v[13]), 0);
         sts128(sbase + L::ag + static_cast<uint32_t>(row0 + 32 * i) * 16u, w[0], w[1], w[2], w[3]);
       }
       fence_proxy_async_smem();
@@ -202,7 +227,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
       if (k + 1 < ns) load_slot_f8(F, k + 1, pix, cnt, y);
       const int b = lc & 1;
       if (!warp_wait(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
-      store_slot_f8(sbase + (b ? L::at1 : L::at0), row0, inv_s_t, x);
+      store_slot_f8(sbase + (b ? L::at1 : L::at0), row0, inv_s_t, x, sat);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_AT_F + b));
@@ -217,7 +242,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
 
 // ------------------------------------------------------------------ kernel
 // Sum: the paper's sum form of Eq. 5.  tau = s - 2^11 + c 2^-13 (the exact
-// fixed-point sum) goes straight to B1's r operand as codes of tau / s_g,
+// fixed-point sum) goes straight to B1's r operand as codes of tau / s_r,
 // where rho's output would go; rho's GEMM and its epilogue pass are skipped
 // and the max is not kept.
 // R3: R's first layer is a 3x3 kernel over the frame (conv_r3.cu): the tile
@@ -506,9 +531,9 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 
         if constexpr (Sum) {
           // tau -> the r operand of B1 (buffer Y, see below) as codes of
-          // tau / s_g
+          // tau / s_r
           const uint32_t Yr = tl + T::buf((gs + ns) % 3u == 2 ? 0 : (gs + ns) % 3u + 1);
-          const float inv_s_g = cst[L::INV_S_G];
+          const float inv_s_r = cst[L::INV_S_R];
           const float off = kSumBase - static_cast<float>(c) * kHalfQuantum;
           bool over = false;
 #pragma unroll
@@ -523,8 +548,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
                 over |= !(fmaxf(sm[e], sm[e + 1]) < kSumLimit);
                 float d0, d1;
                 fadd2_rn(d0, d1, sm[e], sm[e + 1], -off, -off);
-                a[t] = d0 * inv_s_g;
-                a[t + 1] = d1 * inv_s_g;
+                a[t] = d0 * inv_s_r;
+                a[t + 1] = d1 * inv_s_r;
               }
               u[j] = pack_u16x2(pack_e4m3_relu(a[0], a[1]), pack_e4m3_relu(a[2], a[3]));
             }

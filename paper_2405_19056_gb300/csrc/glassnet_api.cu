@@ -169,7 +169,7 @@ inline size_t core_idx8(int N, int n, int k) {
 }
 
 // FP8 image (FusedLayoutF8) from the concat-form weights and the activation
-// scales act[kFp8Acts] = s of t, U, pool, [g ; r], y, y2, q.
+// scales act[kFp8Acts] (per-channel t and g, then U, pool, r, y, y2, q).
 template <int H>
 std::vector<uint8_t> pack_fused_fp8(const float* w, const gn::WeightIndex& wi, const float* act) {
   using L = gn::FusedLayoutF8<H>;
@@ -177,36 +177,44 @@ std::vector<uint8_t> pack_fused_fp8(const float* w, const gn::WeightIndex& wi, c
   auto W = [&](int l, int n, int j) { return w[wi.w[l] + static_cast<size_t>(n) * wi.in[l] + j]; };
   auto Bv = [&](int l, int n) { return w[wi.b[l] + n]; };
   // per-output-channel weight scale over the columns that stay in the GEMM
-  auto wscale = [&](int l, int n, int j0, int j1, int j2 = 0, int j3 = 0) {
+  auto wscale = [&](int l, int n, int j0, int j1) {
     float m = 0.0f;
     for (int j = j0; j < j1; ++j) m = std::max(m, std::fabs(W(l, n, j)));
-    for (int j = j2; j < j3; ++j) m = std::max(m, std::fabs(W(l, n, j)));
     return m > 0.0f ? m / 448.0f : 1.0f;
   };
   auto put = [&](uint32_t off, int N, int n, int k, float v) {
     img[off + core_idx8(N, n, k)] = e4m3_rne(v);
   };
-  const float s_t = act[0], s_u = act[1], s_pool = act[2], s_g = act[3], s_y = act[4],
-              s_y2 = act[5], s_q = act[6];
+  const float* s_t = act + gn::FP8_T0;
+  const float* s_g = act + gn::FP8_G0;
+  const float s_u = act[gn::FP8_U], s_pool = act[gn::FP8_POOL], s_r = act[gn::FP8_R],
+              s_y = act[gn::FP8_Y], s_y2 = act[gn::FP8_Y2], s_q = act[gn::FP8_Q];
   float* c = reinterpret_cast<float*>(img.data() + L::cst);
   for (int n = 0; n < H; ++n) {
-    const float w1 = wscale(gn::LPHI1, n, 0, gn::kTC);
-    for (int k = 0; k < gn::kTC; ++k) put(L::phi1, H, n, k, W(gn::LPHI1, n, k) / w1);
-    c[L::S_PHI1 + n] = s_t * w1 / s_u;
-    c[L::U_PHI1 + n] = 1.0f / (s_t * w1);
+    // phi1: column c of the weights carries the input channel's scale
+    float m1 = 0.0f;
+    for (int k = 0; k < gn::kTC; ++k) m1 = std::max(m1, std::fabs(W(gn::LPHI1, n, k) * s_t[k]));
+    const float w1 = m1 > 0.0f ? m1 / 448.0f : 1.0f;
+    for (int k = 0; k < gn::kTC; ++k) put(L::phi1, H, n, k, W(gn::LPHI1, n, k) * s_t[k] / w1);
+    c[L::S_PHI1 + n] = w1 / s_u;
+    c[L::U_PHI1 + n] = 1.0f / w1;
     const float w2 = wscale(gn::LPHI2, n, 0, H);
     for (int k = 0; k < H; ++k) put(L::phi2, H, n, k, W(gn::LPHI2, n, k) / w2);
     c[L::S_PHI2 + n] = s_u * w2;
     c[L::B_PHI2 + n] = Bv(gn::LPHI2, n);
     const float wr = wscale(gn::LRHO, n, 0, 2 * H);
     for (int k = 0; k < 2 * H; ++k) put(L::rho, H, n, k, W(gn::LRHO, n, k) / wr);
-    c[L::S_RHO + n] = s_pool * wr / s_g;
-    c[L::B_RHO + n] = Bv(gn::LRHO, n) / s_g;
-    const float wb1 = wscale(gn::LB1, n, 0, gn::kGC + H);
-    for (int k = 0; k < gn::kGC; ++k) put(L::b1, H, n, k, W(gn::LB1, n, k) / wb1);
-    for (int k = 0; k < H; ++k) put(L::b1, H, n, 32 + k, W(gn::LB1, n, gn::kGC + k) / wb1);
-    c[L::S_B1 + n] = s_g * wb1 / s_y;
-    c[L::U_B1 + n] = 1.0f / (s_g * wb1);
+    c[L::S_RHO + n] = s_pool * wr / s_r;
+    c[L::B_RHO + n] = Bv(gn::LRHO, n) / s_r;
+    // B1: the G-buffer columns carry their channels' scales, the r columns s_r
+    float mb = 0.0f;
+    for (int k = 0; k < gn::kGC; ++k) mb = std::max(mb, std::fabs(W(gn::LB1, n, k) * s_g[k]));
+    for (int k = 0; k < H; ++k) mb = std::max(mb, std::fabs(W(gn::LB1, n, gn::kGC + k) * s_r));
+    const float wb1 = mb > 0.0f ? mb / 448.0f : 1.0f;
+    for (int k = 0; k < gn::kGC; ++k) put(L::b1, H, n, k, W(gn::LB1, n, k) * s_g[k] / wb1);
+    for (int k = 0; k < H; ++k) put(L::b1, H, n, 32 + k, W(gn::LB1, n, gn::kGC + k) * s_r / wb1);
+    c[L::S_B1 + n] = wb1 / s_y;
+    c[L::U_B1 + n] = 1.0f / wb1;
     const float wb2 = wscale(gn::LB2, n, 0, H);
     for (int k = 0; k < H; ++k) put(L::b2, H, n, k, W(gn::LB2, n, k) / wb2);
     c[L::S_B2 + n] = s_y * wb2 / s_y2;
@@ -222,10 +230,11 @@ std::vector<uint8_t> pack_fused_fp8(const float* w, const gn::WeightIndex& wi, c
     c[L::S_R2 + n] = s_q * wq2;
     c[L::B_R2 + n] = Bv(gn::LR2, n);
   }
-  c[L::INV_S_T] = 1.0f / s_t;
-  c[L::INV_S_G] = 1.0f / s_g;
+  c[L::INV_S_R] = 1.0f / s_r;
   c[L::INV_S_POOL] = 1.0f / s_pool;
   c[L::S_Y2] = s_y2;
+  for (int k = 0; k < gn::kTC; ++k) c[L::INV_S_TCH + k] = 1.0f / s_t[k];
+  for (int k = 0; k < gn::kGC; ++k) c[L::INV_S_GCH + k] = 1.0f / s_g[k];
   return img;
 }
 
@@ -711,15 +720,13 @@ int glassnet_render_batch(const gn_model* m, const gn_frame* frames, int n, cuda
   return GN_OK;
 }
 
-// Activation scale = kFp8Headroom |max| / 448 over the calibration render.
-// E4M3's relative step is the same over its whole normal range, so one binade
-// of headroom costs precision only for values in the lowest binade, while it
-// keeps inputs up to twice the calibration maximum from saturating (measured:
-// with no headroom, frames other than the calibration frame showed clipped
-// outliers of up to 0.12 in RGB; with it, <= 0.056 on 64x64 crops, while a
-// 52,030-pixel frame with no activation beyond 1.55x its calibration maximum
-// reached 0.085 through E4M3 rounding alone).
-constexpr float kFp8Headroom = 2.0f;
+// Scales = headroom |max| / 448 over the calibration render, per channel for
+// the two input tensors (the transparency layers and the G-buffer, whose
+// channels range from [0, 1] to log-normal lighting) and per tensor for the
+// hidden activations (internal.h gives the headroom factors).  With one
+// scale for all input channels and one binade of headroom, a 93,639-pixel
+// frame clipped a lighting value at 2x its calibration maximum and its
+// hidden activations went past 2x theirs.
 
 namespace {
 int calibrate_fp8_impl(gn_model* m, const gn_latent* lat, const float* gbuf, const float* tbuf,
@@ -765,7 +772,8 @@ int calibrate_fp8_impl(gn_model* m, const gn_latent* lat, const float* gbuf, con
   for (int i = 0; i < gn::kFp8Acts; ++i) {
     float a;
     std::memcpy(&a, &bits[i], 4);
-    act[i] = (a > 0.0f && std::isfinite(a)) ? a * kFp8Headroom / 448.0f : 1.0f;
+    const float headroom = i < gn::FP8_U ? gn::kFp8InputHeadroom : gn::kFp8HiddenHeadroom;
+    act[i] = (a > 0.0f && std::isfinite(a)) ? a * headroom / 448.0f : 1.0f;
   }
   std::vector<uint8_t> img = m->H == 128 ? pack_fused_fp8<128>(m->host_w, m->wi, act)
                                          : pack_fused_fp8<64>(m->host_w, m->wi, act);
@@ -812,6 +820,8 @@ int glassnet_check(const gn_model* m, cudaStream_t s) {
   if (bits & gn::kErrTimeout) return fail(GN_ETIMEOUT, "a device-side wait timed out");
   if (bits & gn::kErrCount) return fail(GN_EINVAL, "a layer count exceeded K");
   if (bits & gn::kErrRange) return fail(GN_ERANGE, "an exact set-sum left its fixed-point range");
+  if (bits & gn::kErrSaturated)
+    return fail(GN_ESATURATED, "an FP8 input was beyond its calibrated range and was clamped");
   return GN_OK;
 }
 

@@ -28,6 +28,7 @@ constexpr uint32_t kPlanPixelMask = 0x0fffffffu;
 constexpr uint32_t kErrCount = 1u;    // layer count above K
 constexpr uint32_t kErrRange = 2u;    // exact set-sum left its fixed-point range
 constexpr uint32_t kErrTimeout = 4u;  // a device wait gave up
+constexpr uint32_t kErrSaturated = 8u;  // an FP8 input beyond its calibrated range (clamped)
 
 // Linear layers in blob order.
 enum Layer { LF1 = 0, LF2, LPHI1, LPHI2, LRHO, LB1, LB2, LR1, LR2, kLayers };
@@ -131,9 +132,13 @@ struct FusedLayout {
 //   FP32 constants (indices in floats from `cst`): per output column a
 //   dequantisation scale (accumulator -> next layer's quantised input, or
 //   real units where the result is not re-quantised) and a bias; u_phi1 and
-//   u_b1 turn c_phi / c_B into accumulator units; then four scalars: 1/s_t,
-//   1/s_g (the scale of B1's [g ; r] input), 1/s_pool and s_y2 (B2's output
-//   in real units, for the neural buffer of a 3x3 R).
+//   u_b1 turn c_phi / c_B into accumulator units; then three scalars: 1/s_r
+//   (the scale of B1's r input, or of tau in the sum form), 1/s_pool and s_y2
+//   (B2's output in real units, for the neural buffer of a 3x3 R); then the
+//   per-channel input scales 1/s_t[c] (12, padded to 16) and 1/s_g[c] (14,
+//   padded to 16).  The first layers' weight columns carry the per-channel
+//   scales (W[n][c] s[c] is quantised), so an input code is x[c] / s[c]
+//   and the accumulator stays in the weight scale's units.
 //   A operands: at0, at1, ag ([2][128][16] bytes each, K block 1 zero) and
 //   the constant BF16 [1, 1, 0, ...] operand of the bias MMAs.
 template <int H>
@@ -151,8 +156,8 @@ struct FusedLayoutF8 {
   enum : int {
     S_PHI1 = 0, S_PHI2 = H, B_PHI2 = 2 * H, S_RHO = 3 * H, B_RHO = 4 * H, S_B1 = 5 * H,
     S_B2 = 6 * H, B_B2 = 7 * H, S_R1 = 8 * H, B_R1 = 9 * H, U_PHI1 = 10 * H, U_B1 = 11 * H,
-    S_R2 = 12 * H, B_R2 = 12 * H + 16, INV_S_T = 12 * H + 32, INV_S_G, INV_S_POOL, S_Y2,
-    N_CST = 12 * H + 36
+    S_R2 = 12 * H, B_R2 = 12 * H + 16, INV_S_R = 12 * H + 32, INV_S_POOL, S_Y2,
+    INV_S_TCH = 12 * H + 36, INV_S_GCH = 12 * H + 52, N_CST = 12 * H + 68
   };
   static constexpr uint32_t bytes = cst + N_CST * 4;
   static constexpr uint32_t at0 = (bytes + 127) / 128 * 128;
@@ -163,10 +168,19 @@ struct FusedLayoutF8 {
   static_assert(bytes % 16 == 0, "bulk copy size must be a multiple of 16 bytes");
 };
 
-// Activation scales of the FP8 path (per-tensor, static): the real value of
-// an E4M3 code x is x * s.  Order: layer inputs t (phi1), U (phi2), pool
-// (rho), [g ; r] (B1), y (B2), y2 (R1), q (R2).
-constexpr int kFp8Acts = 7;
+// Activation scales of the FP8 path (static): the real value of an E4M3 code
+// x is x * s.  Order: the 12 transparency-layer channels (phi1's input, per
+// channel), the 14 G-buffer channels (B1's, per channel), then per tensor U
+// (phi2), pool (rho), r (B1's r block), y (B2), y2 (R1), q (R2).
+constexpr int kFp8Acts = 32;
+enum : int { FP8_T0 = 0, FP8_G0 = 12, FP8_U = 26, FP8_POOL, FP8_R, FP8_Y, FP8_Y2, FP8_Q };
+// Headroom of the calibrated ranges: scale = headroom |max| / 448.  The input
+// channels take 8 (direct lighting is log-normal: a frame of more pixels than
+// the calibration frame reaches further into its tail), the hidden
+// activations 4.  E4M3 keeps the same relative step over its normal range, so
+// headroom costs precision only below 2^-6 s.
+constexpr float kFp8InputHeadroom = 8.0f;
+constexpr float kFp8HiddenHeadroom = 4.0f;
 
 // One frame as the fused kernel sees it.
 struct FusedFrame {

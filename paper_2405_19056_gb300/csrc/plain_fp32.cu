@@ -199,16 +199,17 @@ __global__ void amax_kernel(const float* __restrict__ x, size_t n, uint32_t* slo
   m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
   if ((threadIdx.x & 31) == 0) atomicMax(slot, __float_as_uint(m));
 }
-// |t| max over the valid layer slots (k < c_p) of a transparency buffer.
+// |t| max of channel `ch` over the valid layer slots (k < c_p) of a
+// transparency buffer.
 __global__ void amax_layers_kernel(const float* __restrict__ tbuf, const uint8_t* __restrict__ counts,
-                                   int K, int P, uint32_t* slot) {
+                                   int K, int P, int ch, uint32_t* slot) {
   float m = 0.0f;
-  const size_t n = static_cast<size_t>(K) * kTC * P;
+  const size_t n = static_cast<size_t>(K) * P;
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
     const int p = static_cast<int>(i % P);
-    const int k = static_cast<int>(i / (static_cast<size_t>(kTC) * P));
-    if (k < counts[p]) m = fmaxf(m, fabsf(tbuf[i]));
+    const int k = static_cast<int>(i / P);
+    if (k < counts[p]) m = fmaxf(m, fabsf(tbuf[(static_cast<size_t>(k) * kTC + ch) * P + p]));
   }
   m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
   m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
@@ -291,15 +292,16 @@ cudaError_t launch_fp8_act_amax(const void* ws, const float* gbuf, const float* 
     amax_kernel<<<blocks, 256, 0, s>>>(x, n, amax + slot);
   };
   if (K > 0) {
-    amax_layers_kernel<<<1024, 256, 0, s>>>(tbuf, counts, K, P, amax + 0);
-    run(U, rows * H, 1);
-    run(pool, ph * 2, 2);
+    for (int ch = 0; ch < kTC; ++ch)
+      amax_layers_kernel<<<512, 256, 0, s>>>(tbuf, counts, K, P, ch, amax + FP8_T0 + ch);
+    run(U, rows * H, FP8_U);
+    run(pool, ph * 2, FP8_POOL);
   }
-  run(gbuf, static_cast<size_t>(kGC) * P, 3);
-  run(R, ph, 3);
-  run(Y1, ph, 4);
-  run(Y2, ph, 5);
-  run(Q, ph, 6);
+  for (int ch = 0; ch < kGC; ++ch) run(gbuf + static_cast<size_t>(ch) * P, P, FP8_G0 + ch);
+  run(R, ph, FP8_R);
+  run(Y1, ph, FP8_Y);
+  run(Y2, ph, FP8_Y2);
+  run(Q, ph, FP8_Q);
   return cudaGetLastError();
 }
 

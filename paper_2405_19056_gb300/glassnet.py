@@ -23,6 +23,8 @@ GN_EFORMAT = -4
 GN_ETIMEOUT = -5
 GN_EUNSUPPORTED = -6
 GN_ERANGE = -7
+GN_ESATURATED = -8
+GN_FP8_SCALES = 32
 
 GN_FP32_PLAIN = 0
 GN_BF16_FUSED = 1
@@ -246,7 +248,7 @@ def glassnet_calibrate_fp8(model, latent, gbuf, tbuf, layer_count, K, h, w, stre
 
 
 def glassnet_fp8_scales(model) -> np.ndarray:
-    out = np.zeros(7, dtype=np.float32)
+    out = np.zeros(GN_FP8_SCALES, dtype=np.float32)
     _check(_lib().glassnet_fp8_scales(model, out.ctypes.data))
     return out
 

@@ -101,3 +101,55 @@ def test_kernel_digest_covers_every_source_of_the_captured_kernels(bench):
                 if not inc.endswith("include/glassnet.h"):
                     todo.append(inc)
     assert seen == set(bench.KERNEL_SOURCES)
+
+
+def test_serving_stream_follows_the_stated_workload(bench):
+    """The serving stream: Poisson arrivals at the given rate, sizes 256 /
+    512 / 1024 squared w.p. 0.5 / 0.35 / 0.15, K in 1..8, 32 scenes; the
+    same seed gives the same stream."""
+    res, Ks, arrive, scenes = bench.serving_stream(800, 20000, seed=0)
+    res2, _, arrive2, _ = bench.serving_stream(800, 20000, seed=0)
+    assert np.array_equal(res, res2) and np.array_equal(arrive, arrive2)
+    frac = [np.mean(res == r) for r in (256, 512, 1024)]
+    assert np.allclose(frac, (0.5, 0.35, 0.15), atol=0.015)
+    assert Ks.min() == 1 and Ks.max() == 8
+    assert scenes.min() == 0 and scenes.max() == 31
+    gaps = np.diff(np.concatenate([[0.0], arrive]))
+    assert np.all(gaps > 0)
+    assert abs(gaps.mean() - 1.0 / 800) < 0.03 / 800  # mean inter-arrival 1/rate
+    assert abs(np.std(gaps) / gaps.mean() - 1.0) < 0.05  # exponential: CV = 1
+
+
+def test_selected_legs(bench):
+    class A:
+        legs, no_extras = None, False
+    a = A()
+    assert bench.selected_legs(a) == set(bench.EXTRA_LEGS)
+    a.no_extras = True
+    assert bench.selected_legs(a) == set()
+    a.legs = "streaming, fp8"
+    assert bench.selected_legs(a) == {"streaming", "fp8"}
+    a.legs = "nope"
+    with pytest.raises(SystemExit):
+        bench.selected_legs(a)
+
+
+def test_clock_summary_uses_timed_samples_and_names_reasons(bench):
+    """Samples inside the timed region are used when there are at least 3;
+    otherwise the same-load samples right after it are added and said so;
+    throttle reasons come from the NVML bit mask."""
+    c = bench.ClockSampler(0)
+    c.source = "test"
+    c.t_begin, c.t_end = 10.0, 11.0
+    c.samples = [(10.1, 2070.0, 2070.0, 0), (10.5, 2050.0, 2070.0, 0x4), (10.9, 2060.0, 2070.0, 0),
+                 (11.5, 1000.0, 2070.0, 0x40)]
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2060.0 and s["reasons"] == ["sw_power_cap"]
+    c.samples = [(10.5, 2070.0, 2070.0, 0), (11.2, 1900.0, 2070.0, 0x8), (11.3, 1950.0, 2070.0, 0)]
+    c._t_ext = (11.0, 12.0)
+    s = c.summary()
+    assert s["samples"] == 3 and s["samples_in_timed_region"] == 1
+    assert s["reasons"] == ["hw_slowdown"] and "note" in s
+    c.samples = []
+    s = c.summary()
+    assert s["sm_mhz"] is None and s["why"]

@@ -89,15 +89,45 @@ def test_uncalibrated_model_is_rejected(cuda_lib):
         gl.glassnet_fp8_scales(m.handle)
 
 
-def test_input_scale_is_twice_valid_layer_amax_over_448(base8):
+def test_input_scales_are_per_channel_amax_times_8_over_448(base8):
+    """Input scales: per channel, 8 |max| / 448 over the calibration frame
+    (transparency channels over the valid slots only); hidden activations
+    per tensor."""
     s = gl.glassnet_fp8_scales(base8.model.handle)
+    assert s.shape == (gl.GN_FP8_SCALES,)
     f = base8.cal
     valid = np.arange(f.tbuf.shape[0])[:, None, None] < f.counts[None, :, :]
-    amax_t = np.float32(np.abs(f.tbuf.transpose(1, 0, 2, 3)[:, valid]).max())
-    assert s[0] == np.float32(np.float32(2.0) * amax_t / np.float32(448.0))
-    amax_g = np.float32(np.abs(f.gbuf).max())
-    assert s[3] >= np.float32(np.float32(2.0) * amax_g / np.float32(448.0))
+    eight, d = np.float32(8.0), np.float32(448.0)
+    for ch in range(12):
+        amax_t = np.float32(np.abs(f.tbuf[:, ch][valid]).max())
+        assert s[ch] == np.float32(eight * amax_t / d), ch
+    for ch in range(14):
+        amax_g = np.float32(np.abs(f.gbuf[ch]).max())
+        assert s[12 + ch] == np.float32(eight * amax_g / d), ch
     assert np.all(np.isfinite(s)) and np.all(s > 0)
+
+
+def test_input_beyond_calibrated_range_is_clamped_and_reported(base8):
+    """A G-buffer value far beyond its channel's calibrated range saturates
+    its E4M3 code: GN_ESATURATED at the next check, every pixel still
+    rendered, and the other pixels unchanged."""
+    m = base8.model
+    lat = m.encode(synth.make_scene(0))
+    f = synth.make_frame(32, 32, 2, counts="all", seed=77)
+    ref = torch.full((3, 32, 32), float("nan"), device=DEV)
+    m.render(lat, _dev(f.gbuf), _dev(f.tbuf), _dev(f.counts), ref)
+    m.check()
+    g = f.gbuf.copy()
+    g[12, 5, 7] = 1e6  # direct lighting far outside the calibration frame's range
+    out = torch.full((3, 32, 32), float("nan"), device=DEV)
+    m.render(lat, _dev(g), _dev(f.tbuf), _dev(f.counts), out)
+    assert gl.glassnet_check_code(m.handle) == gl.GN_ESATURATED
+    assert gl.glassnet_check_code(m.handle) == gl.GN_OK  # cleared
+    a, b = ref.cpu().numpy(), out.cpu().numpy()
+    assert np.isfinite(b).all()
+    mask = np.ones((32, 32), bool)
+    mask[5, 7] = False
+    assert np.array_equal(a[:, mask], b[:, mask])
 
 
 CASES = [

@@ -10,11 +10,22 @@ Each accepted frame is a small seeded synthetic frame repeated down the rows
 to the same pixel rendered in the small frame by itself (per-pixel results do
 not depend on where the tile falls, nor on the frame size), and the small
 frame's render is compared with the FP64 oracle: BF16 max |err| <= 2e-2,
-mean <= 3e-3; FP8 (calibrated on a seed-1 128x128 K=8 frame) mean <= 1e-2
-and at most 1 in 10^3 values above 6e-2.  The small frames hold 52,030 and
-93,639 distinct pixels, and FP8's largest error grows with the extremes of
-that many inputs (E4M3 rounds each operand to a relative 2^-4), so it is
-reported, not bounded.
+mean <= 3e-3; FP8 (calibrated on a seed-1 128x128 K=8 frame) max <= 0.1,
+mean <= 1e-2 and at most 1 in 10^4 values above 6e-2.
+
+The FP8 bound for these populations (52,030 and 93,639 distinct pixels, where
+the 64x64 crops of test_gpu_fp8.py hold 4,096) comes from E4M3's rounding,
+with no saturation: the input channels have per-channel scales at 8x and the
+hidden activations 4x their calibrated range, and a CPU emulation of every
+quantisation point of the kernel (E4M3 round-to-nearest-even of each
+operand, per-channel weight scales, exact pooling of BF16-rounded phi
+outputs) gives at most 0.053 (K = 8) and 0.060 (K = 0) on these frames, at
+mean 0.0031 and 0.0030, with no value above 6e-2 at K = 8 and 1 in 2.8 x 10^5
+at K = 0.  The kernel measured up to 1.3x its emulation's largest error
+before (0.085 against 0.066 with the per-tensor scales): the bound takes
+that factor with some room, 0.1.  E4M3 keeps 3 mantissa bits (a relative
+step of 2^-3) in every operand of seven GEMMs, so the largest error of a
+population grows with its size while the mean does not.
 """
 import numpy as np
 import pytest
@@ -30,7 +41,7 @@ DEV = "cuda:0"
 BF16_MAX = 2e-2
 BF16_MEAN = 3e-3
 # max, mean, and (threshold, largest fraction of values above it)
-TOL = {"bf16": (BF16_MAX, BF16_MEAN, None), "fp8": (float("inf"), 1e-2, (6e-2, 1e-3))}
+TOL = {"bf16": (BF16_MAX, BF16_MEAN, None), "fp8": (0.1, 1e-2, (6e-2, 1e-4))}
 
 # (K, h, w, rows of the repeated small frame): 12 max(K, 1) h w < 2^31, and
 # one more column reaches it (checked on the CPU in test_abi_cpu.py)
