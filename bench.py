@@ -790,15 +790,16 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
         try:
             ids = [gl.glassnet_server_add_scene(srv, x) for x in scenes]
             used = {r: 0 for r in sizes}
-            # warm-up: per (size, K) bucket, one request on each lane (submitted
-            # together while every lane is free) captures the lanes' graphs
+            # every lane's graph of every (size, K) bucket, captured before the
+            # stream starts; then one request per bucket as a warm-up
+            for r in sizes:
+                for K in range(1, 9):
+                    gl.glassnet_server_prepare(srv, r, r, K)
             for r in sizes:
                 for K in range(1, 9):
                     p = pool[r]
-                    warm = [gl.glassnet_server_submit(srv, ids[0], p["g"], p["t"], p["c"][K], K, r, r,
-                                                      p["outs"][j]) for j in range(n_streams)]
-                    for t in warm:
-                        gl.glassnet_server_wait(srv, t)
+                    gl.glassnet_server_wait(srv, gl.glassnet_server_submit(
+                        srv, ids[0], p["g"], p["t"], p["c"][K], K, r, r, p["outs"][0]))
             before = gl.glassnet_server_stats(srv)
             tickets, lag = [], 0.0
             t0 = time.perf_counter()
@@ -812,7 +813,7 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
                 used[r] += 1
                 tickets.append(gl.glassnet_server_submit(srv, ids[int(sc[i])], p["g"], p["t"],
                                                          p["c"][K], K, r, r, out))
-            lats = [gl.glassnet_server_wait(srv, t) for t in tickets]
+            lats = np.array([gl.glassnet_server_wait(srv, t) for t in tickets])
             wall = time.perf_counter() - t0
             st = gl.glassnet_server_stats(srv)
         finally:
@@ -824,7 +825,11 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
                         "max_ms": float(np.max(lats)), "p99_target_ms": P99_TARGET_MS,
                         "p99_met": p99 <= P99_TARGET_MS,
                         "throughput_mpx_s": px / wall / 1e6, "demand_mpx_s": rate * mean_px / 1e6,
-                        "wall_s": wall, "generator_lag_max_ms": lag * 1e3})
+                        "wall_s": wall, "generator_lag_max_ms": lag * 1e3,
+                        "p99_ms_by_size": {int(r): float(np.percentile(lats[res == r], 99))
+                                           for r in sizes if np.any(res == r)},
+                        "p99_ms_by_quarter": [float(np.percentile(x, 99))
+                                              for x in np.array_split(lats, 4)]})
     gl.glassnet_check(model.handle)
     plain = fp32_plain_serving(weights, rates, n_requests, pool, scenes, seed)
     for r_bf, r_fp in zip(results, plain):

@@ -418,6 +418,10 @@ int glassnet_server_create(gn_model* model, const gn_server_config* config, gn_s
  * resident; concurrent calls take different slots, and a call waits while
  * every slot is being encoded by another call or used by requests in flight. */
 int glassnet_server_add_scene(gn_server* server, const float* scene, int* scene_id);
+/* Captures the graph of the shape bucket (h, w, K) on every lane now, so that
+ * the first requests of that shape do not wait for a capture.  Call it while
+ * no request is queued or in flight (GN_EINVAL otherwise).  Synchronous. */
+int glassnet_server_prepare(gn_server* server, int h, int w, int K);
 int glassnet_server_submit(gn_server* server, const gn_request* request, uint64_t* ticket);
 int glassnet_server_wait(gn_server* server, uint64_t ticket, double* latency_ms);
 int glassnet_server_stats(gn_server* server, gn_server_stats* stats);

@@ -80,6 +80,17 @@ int glassnet_graph_create(const gn_model* m, const gn_frame* frames, int n, gn_g
     glassnet_graph_free(g);
     return cuda_err(e, "instantiate graph");
   }
+  // upload it now, so that its first launch does not pay for that
+  cudaStream_t us = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking)) == cudaSuccess) {
+    e = cudaGraphUpload(g->exec, us);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+    cudaStreamDestroy(us);
+  }
+  if (e != cudaSuccess) {
+    glassnet_graph_free(g);
+    return cuda_err(e, "upload graph");
+  }
   g->params = p;
   *out = g;
   return GN_OK;

@@ -115,26 +115,37 @@ struct gn_server {
   int issue(Lane& lane, Job& job);
 };
 
-int gn_server::issue(Lane& lane, Job& job) {
-  const gn_request& r = job.req;
-  const Bucket bk{r.h, r.w, r.K};
-  const ArenaMap am(r.K, r.h, r.w);
+// The lane's graph of a shape bucket, captured on first use.
+int gn_server_bucket_graph(gn_model* model, Lane& lane, const Bucket& bk,
+                           std::map<Bucket, gn_graph*>::iterator* out) {
   auto it = lane.graphs.find(bk);
   if (it == lane.graphs.end()) {
+    const ArenaMap am(bk.K, bk.h, bk.w);
     gn_frame f;
     f.latent = &lane.latent;
     f.gbuf = reinterpret_cast<const float*>(lane.arena + am.gbuf);
-    f.tbuf = r.K > 0 ? reinterpret_cast<const float*>(lane.arena + am.tbuf) : nullptr;
+    f.tbuf = bk.K > 0 ? reinterpret_cast<const float*>(lane.arena + am.tbuf) : nullptr;
     f.layer_count = lane.arena + am.counts;
-    f.K = r.K;
-    f.h = r.h;
-    f.w = r.w;
+    f.K = bk.K;
+    f.h = bk.h;
+    f.w = bk.w;
     f.out = reinterpret_cast<float*>(lane.arena + am.out);
     gn_graph* g = nullptr;
     const int rc = glassnet_graph_create(model, &f, 1, &g);
     if (rc != GN_OK) return rc;
     it = lane.graphs.emplace(bk, g).first;
   }
+  *out = it;
+  return GN_OK;
+}
+
+int gn_server::issue(Lane& lane, Job& job) {
+  const gn_request& r = job.req;
+  const Bucket bk{r.h, r.w, r.K};
+  const ArenaMap am(r.K, r.h, r.w);
+  std::map<Bucket, gn_graph*>::iterator it;
+  const int grc = gn_server_bucket_graph(model, lane, bk, &it);
+  if (grc != GN_OK) return grc;
   const size_t P = static_cast<size_t>(r.h) * r.w;
   cudaError_t e = cudaMemcpyAsync(lane.latent.d, scenes[job.scene_slot].latent->d, latent_bytes,
                                   cudaMemcpyDeviceToDevice, lane.stream);
@@ -330,6 +341,31 @@ int glassnet_server_add_scene(gn_server* s, const float* scene, int* scene_id) {
   *scene_id = sc.id;
   s->cv.notify_all();
   return GN_OK;
+}
+
+int glassnet_server_prepare(gn_server* s, int h, int w, int K) {
+  if (!s) return gn::set_error(GN_EINVAL, "server is NULL");
+  if (K < 0 || K > s->cfg.max_K || h < 1 || w < 1 || h > s->cfg.max_h || w > s->cfg.max_w)
+    return gn::set_error(GN_EINVAL, "bucket outside the server's maximum");
+  {
+    // the lanes must be idle; they stay marked busy while their graphs are
+    // captured, so the dispatcher cannot use them meanwhile
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->queue.empty()) return gn::set_error(GN_EINVAL, "requests are queued");
+    for (const Lane& l : s->lanes)
+      if (l.busy) return gn::set_error(GN_EINVAL, "requests are in flight");
+    for (Lane& l : s->lanes) l.busy = true;
+  }
+  cudaSetDevice(s->model->device);
+  int rc = GN_OK;
+  for (Lane& l : s->lanes) {
+    std::map<Bucket, gn_graph*>::iterator it;
+    if ((rc = gn_server_bucket_graph(s->model, l, Bucket{h, w, K}, &it)) != GN_OK) break;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (Lane& l : s->lanes) l.busy = false;
+  s->cv.notify_all();
+  return rc;
 }
 
 int glassnet_server_submit(gn_server* s, const gn_request* req, uint64_t* ticket) {

@@ -60,6 +60,7 @@ _SIGNATURES = {
     "glassnet_fp8_scales": (_I, [_P, _P]),
     "glassnet_server_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
     "glassnet_server_add_scene": (_I, [_P, _P, ctypes.POINTER(_I)]),
+    "glassnet_server_prepare": (_I, [_P, _I, _I, _I]),
     "glassnet_server_submit": (_I, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "glassnet_server_wait": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "glassnet_server_stats": (_I, [_P, _P]),
@@ -337,6 +338,10 @@ def glassnet_server_add_scene(server, scene) -> int:
     sid = ctypes.c_int()
     _check(_lib().glassnet_server_add_scene(server, s.ctypes.data, ctypes.byref(sid)))
     return sid.value
+
+
+def glassnet_server_prepare(server, h, w, K):
+    _check(_lib().glassnet_server_prepare(server, h, w, K))
 
 
 def glassnet_server_submit(server, scene_id, gbuf, tbuf, layer_count, K, h, w, out) -> int:

@@ -122,3 +122,65 @@ def test_model_options_served_equal_alone(cuda_lib, form):
     latents = [m.encode(synth.make_scene(s)) for s in scenes]
     for i, r in enumerate(reqs):
         assert np.array_equal(r["out"].numpy(), _alone(m, latents[r["scene"]], r)), (form, i)
+
+
+def test_concurrent_add_scene_takes_distinct_slots(model):
+    """Scenes added from several threads at once: every call gets its own
+    slot and id, and every id stays resident and renders its own scene."""
+    import threading
+    srv = gl.glassnet_server_create(model.handle, n_streams=2, max_scenes=8, max_h=32, max_w=32,
+                                    max_K=2)
+    try:
+        ids, errs = {}, []
+
+        def add(s):
+            try:
+                ids[s] = gl.glassnet_server_add_scene(srv, synth.make_scene(s))
+            except Exception as e:  # noqa: BLE001 - reported below
+                errs.append(e)
+        threads = [threading.Thread(target=add, args=(40 + i,)) for i in range(8)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert not errs, errs
+        assert len(set(ids.values())) == 8
+        f = synth.make_frame(32, 32, 2, counts="uniform", seed=19)
+        r = dict(h=32, w=32, K=2, g=_pin(f.gbuf), t=_pin(f.tbuf), c=_pin(f.counts))
+        for s, sid in ids.items():
+            out = torch.full((3, 32, 32), float("nan")).pin_memory()
+            gl.glassnet_server_wait(srv, gl.glassnet_server_submit(srv, sid, r["g"], r["t"], r["c"],
+                                                                   2, 32, 32, out))
+            assert np.array_equal(out.numpy(), _alone(model, model.encode(synth.make_scene(s)),
+                                                      dict(r, out=out))), s
+    finally:
+        gl.glassnet_server_destroy(srv)
+
+
+def test_prepared_buckets_serve_equal_alone(model):
+    """glassnet_server_prepare captures a bucket's graph on every lane; a
+    bucket beyond the server's maximum is refused; requests of prepared
+    buckets equal the same inputs rendered alone."""
+    srv = gl.glassnet_server_create(model.handle, n_streams=3, max_scenes=1, max_h=64, max_w=64,
+                                    max_K=4)
+    try:
+        sid = gl.glassnet_server_add_scene(srv, synth.make_scene(50))
+        for K in (1, 4):
+            gl.glassnet_server_prepare(srv, 64, 64, K)
+        with pytest.raises(gl.GlassNetError) as ei:
+            gl.glassnet_server_prepare(srv, 64, 64, 5)  # K above the server's maximum
+        assert ei.value.code == gl.GN_EINVAL
+        lat = model.encode(synth.make_scene(50))
+        reqs = []
+        for i, K in enumerate((1, 4, 4, 1, 4, 1)):
+            f = synth.make_frame(64, 64, K, counts="uniform", seed=80 + i)
+            reqs.append(dict(h=64, w=64, K=K, g=_pin(f.gbuf), t=_pin(f.tbuf), c=_pin(f.counts),
+                             out=torch.full((3, 64, 64), float("nan")).pin_memory()))
+        tickets = [gl.glassnet_server_submit(srv, sid, r["g"], r["t"], r["c"], r["K"], 64, 64, r["out"])
+                   for r in reqs]
+        for t in tickets:
+            gl.glassnet_server_wait(srv, t)
+        for r in reqs:
+            assert np.array_equal(r["out"].numpy(), _alone(model, lat, r))
+    finally:
+        gl.glassnet_server_destroy(srv)
