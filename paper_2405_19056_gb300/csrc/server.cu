@@ -108,6 +108,7 @@ struct gn_server {
   uint64_t submitted = 0, completed = 0;
   double pixels_done = 0.0;
   bool stop = false;
+  bool preparing = false;  // glassnet_server_prepare is capturing graphs: no dispatch
   std::thread dispatcher, completer;
 
   void dispatch_loop();
@@ -175,7 +176,7 @@ void gn_server::dispatch_loop() {
     int free_lane = -1;
     cv.wait(lk, [&] {
       if (stop) return true;
-      if (queue.empty()) return false;
+      if (queue.empty() || preparing) return false;
       const Job& j = jobs[queue.front()];
       if (bytes_in_flight + j.bytes > cfg.budget_bytes) return false;
       for (size_t i = 0; i < lanes.size(); ++i)
@@ -348,13 +349,15 @@ int glassnet_server_prepare(gn_server* s, int h, int w, int K) {
   if (K < 0 || K > s->cfg.max_K || h < 1 || w < 1 || h > s->cfg.max_h || w > s->cfg.max_w)
     return gn::set_error(GN_EINVAL, "bucket outside the server's maximum");
   {
-    // the lanes must be idle; they stay marked busy while their graphs are
-    // captured, so the dispatcher cannot use them meanwhile
+    // the lanes must be idle; the dispatcher admits nothing while their
+    // graphs are captured (a lane's `busy` means a request in flight, which
+    // the completion thread would look for)
     std::lock_guard<std::mutex> lk(s->mu);
+    if (s->preparing) return gn::set_error(GN_EINVAL, "another prepare is running");
     if (!s->queue.empty()) return gn::set_error(GN_EINVAL, "requests are queued");
     for (const Lane& l : s->lanes)
       if (l.busy) return gn::set_error(GN_EINVAL, "requests are in flight");
-    for (Lane& l : s->lanes) l.busy = true;
+    s->preparing = true;
   }
   cudaSetDevice(s->model->device);
   int rc = GN_OK;
@@ -363,7 +366,7 @@ int glassnet_server_prepare(gn_server* s, int h, int w, int K) {
     if ((rc = gn_server_bucket_graph(s->model, l, Bucket{h, w, K}, &it)) != GN_OK) break;
   }
   std::lock_guard<std::mutex> lk(s->mu);
-  for (Lane& l : s->lanes) l.busy = false;
+  s->preparing = false;
   s->cv.notify_all();
   return rc;
 }
