@@ -37,16 +37,18 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "fused_bf16_512x512_K8.traffic.
 PROFILE_TRAFFIC_SUM = os.path.join(ROOT, "profiles", "fused_bf16_sum_512x512_K8.traffic.json")
 PROFILE_TRAFFIC_PE = os.path.join(ROOT, "profiles", "fused_bf16_pe4_512x512_K8.traffic.json")
 PROFILE_TRAFFIC_H64 = os.path.join(ROOT, "profiles", "fused_bf16_h64_512x512_K8.traffic.json")
+PROFILE_TRAFFIC_COMPACT = os.path.join(ROOT, "profiles", "fused_compact_h64_512x512_K8.traffic.json")
 
 
-def profiled_traffic(path: str):
+def profiled_traffic(path: str, sources=None):
     """DRAM bytes per launch from an ncu capture, if it was taken of the
     kernel sources as they are now (else None: the counters are stale)."""
     if path is None or not os.path.exists(path):
         return None
     with open(path) as f:
         prof = json.load(f)
-    return prof.get("dram_bytes_per_launch") if prof.get("kernel_sha256") == kernel_digest() else None
+    digest = kernel_digest(sources or KERNEL_SOURCES)
+    return prof.get("dram_bytes_per_launch") if prof.get("kernel_sha256") == digest else None
 
 
 def traffic_record(fp8: bool, r_kernel: int, pe: int, base: bool, pool_sum: bool):
@@ -63,7 +65,7 @@ def traffic_record(fp8: bool, r_kernel: int, pe: int, base: bool, pool_sum: bool
 
 
 EXTRA_LEGS = ("fp32_plain", "e2e", "batch_16_frames", "streaming", "fp8", "sum_pooling",
-              "positional_encoding", "spatial_r3", "serving", "cpu_baseline")
+              "positional_encoding", "spatial_r3", "compact_schedule", "serving", "cpu_baseline")
 
 
 def parse():
@@ -127,12 +129,13 @@ def algorithmic_flops(H: int, counts: np.ndarray, pooling: str = "max_mean", pe:
 
 # the sources of the fused and plan kernels whose DRAM traffic is recorded
 KERNEL_SOURCES = ("fused_bf16.cu", "fused_common.cuh", "plan.cu", "tc_ptx.cuh", "internal.h")
+COMPACT_SOURCES = ("fused_compact.cu", "fused_common.cuh", "plan.cu", "tc_ptx.cuh", "internal.h")
 
 
-def kernel_digest() -> str:
+def kernel_digest(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2405_19056_gb300", "csrc")
-    for name in KERNEL_SOURCES:
+    for name in sources:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -540,6 +543,8 @@ def run_fused(args, world, rank, local):
         result["positional_encoding"] = pe_leg(scene, dframes, frames, stream)
     if "spatial_r3" in legs:
         result["spatial_r3"] = r3_leg(scene, dframes, frames, stream)
+    if "compact_schedule" in legs:
+        result["compact_schedule"] = compact_leg(scene, dframes, frames, stream)
     if "serving" in legs:
         result["serving"] = (serving_leg(model, weights, (200, 800), 300) if args.serving_quick
                              else serving_leg(model, weights, (50, 200, 800), 2000))
@@ -734,6 +739,59 @@ def pe_leg(scene, dframes, frames, stream, L=4, steps=200):
     return out
 
 
+def layer_rows(counts: np.ndarray, schedule: str) -> tuple[int, int]:
+    """(executed, valid) (pixel, layer) rows of one frame's layer work.
+    sorted: windows of 4 tiles (512 pixels) sorted by count, each 128-pixel
+    tile runs its largest count in slots; compact: per 256-pixel block (half
+    a window, pixel order) the valid rows packed into 128-row tiles."""
+    c = counts.reshape(-1).astype(np.int64)
+    valid = int(c.sum())
+    executed = 0
+    if schedule == "sorted":
+        for w0 in range(0, c.size, 512):
+            win = np.sort(c[w0:w0 + 512])[::-1]
+            executed += sum(128 * int(win[t0:t0 + 128].max()) for t0 in range(0, win.size, 128))
+    else:
+        for b0 in range(0, c.size, 256):
+            executed += 128 * -(-int(c[b0:b0 + 256].sum()) // 128)
+    return executed, valid
+
+
+def compact_leg(scene, dframes, frames, stream, steps=200):
+    """The compacted ragged-layer schedule (GN_SCHEDULE_COMPACT) against the
+    count-sorted one on the same frames at the base widths (H=64, Z=128; the
+    compacted kernel's pool takes 128 KB of shared memory, which fits beside
+    the H = 64 operands only).  Reports both timings, the executed / valid
+    layer-row ratio of each, and the compacted kernel's roofline."""
+    from gen import synth
+    from paper_2405_19056_gb300 import glassnet as gl
+
+    peak_bf16, _, _ = measured_peaks()
+    w = synth.make_weights(synth.BASE_WIDTHS, seed=0)
+    flops = sum(algorithmic_flops(64, frames[i % N_ROTATE].counts) for i in range(steps)) / steps
+    out = {"widths": "H=64 Z=128", "pooling": "max_mean"}
+    for sched in ("sorted", "compact"):
+        m = gl.Model(w, gl.GN_BF16_FUSED)
+        if sched == "compact":
+            gl.glassnet_set_layer_schedule(m.handle, gl.GN_SCHEDULE_COMPACT)
+        lat = m.encode(scene, stream)
+        ms = _time_renders(m, lat, dframes, stream, steps)
+        ex, va = (sum(x) for x in zip(*(layer_rows(f.counts, sched) for f in frames)))
+        achieved = flops / (ms * 1e-3) / 1e12
+        kernel = "fused_compact_kernel<sum=0>" if sched == "compact" else \
+            "fused_bf16_kernel<64, frame, sum=0, pe=0>"
+        out[sched] = {"value": H_IMG * W_IMG / (ms * 1e-3) / 1e6, "unit": "Mpixel/s",
+                      "ms_per_step": ms, "steps": steps, "layer_rows_executed_per_valid": ex / va,
+                      "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16,
+                                   "unit": "TFLOP/s", "frac": achieved / peak_bf16,
+                                   "traffic": profiled_traffic(PROFILE_TRAFFIC_COMPACT,
+                                                               COMPACT_SOURCES)
+                                   if sched == "compact" else profiled_traffic(PROFILE_TRAFFIC_H64),
+                                   "kernel": kernel, "peak_source": "measured bf16 burst"}}
+    out["speedup_of_sorted"] = out["compact"]["value"] / out["sorted"]["value"]
+    return out
+
+
 P99_TARGET_MS = 10.0  # the serving loop's stated p99 target (derivation in the leg's docstring)
 
 
@@ -782,6 +840,20 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
                        c={K: torch.full((r, r), K, dtype=torch.uint8).pin_memory() for K in range(1, 9)},
                        outs=[torch.empty((3, r, r)).pin_memory() for _ in range(32)])
     scenes = [synth.make_scene(200 + i) for i in range(32)]
+    # the host link as this process sees it: the 1024^2 K = 8 layer buffer
+    # (402 MB, page-locked) copied to the device, best of 3
+    big = pool[1024]["t"]
+    dst = torch.empty(big.shape, dtype=big.dtype, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best_ms = float("inf")
+    for _ in range(3):
+        e0.record()
+        dst.copy_(big, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        best_ms = min(best_ms, e0.elapsed_time(e1))
+    h2d_gbs = big.numel() * 4 / (best_ms * 1e-3) / 1e9
+    del dst
     results = []
     for rate in rates:
         res, Ks, arrive, sc = serving_stream(rate, n_requests, seed)
@@ -839,6 +911,7 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
                         "40 GB admission budget; host buffers in and out; "
                         f"{n_streams} lanes; open-loop generator",
             "api": "glassnet_server_submit / _wait", "rates": results,
+            "h2d_gbs": h2d_gbs, "h2d_pinned": bool(big.is_pinned()),
             "fp32_plain_served_one_at_a_time": plain}
 
 

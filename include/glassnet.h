@@ -450,6 +450,34 @@ int glassnet_check(const gn_model* model, cudaStream_t stream);
  */
 int glassnet_debug_stall_next_render(gn_model* model, uint64_t stall_ns);
 
+/* How the fused BF16 kernel runs the ragged layer work of Eq. 5 (each pixel
+ * pools over its own c_p <= K layers).
+ * GN_SCHEDULE_SORTED (default): 128-pixel tiles whose pixels are sorted by
+ *   layer count within windows of 512 pixels; a tile runs as many layer slots
+ *   as its largest count (1.42 executed rows per valid (pixel, layer) row at
+ *   Poisson(3) counts).
+ * GN_SCHEDULE_COMPACT: the valid (pixel, layer) rows of 256 pixels are packed
+ *   slot-major into 128-row layer tiles (about 1.08 executed rows per valid
+ *   row) and each pixel's pool is kept in shared memory.  Built for H = 64
+ *   without positional encoding and with the 1x1 R (the pool of 256 pixels
+ *   takes 128 KB of shared memory beside the operands). */
+typedef enum gn_schedule {
+  GN_SCHEDULE_SORTED = 0,
+  GN_SCHEDULE_COMPACT = 1
+} gn_schedule;
+
+/*
+ * Selects the layer schedule of a GN_BF16_FUSED model's frame renders
+ * (glassnet_render*, the server).  Both schedules give bit-identical frames;
+ * streamed layers (glassnet_accumulate_layer / glassnet_resolve) always use
+ * the sorted kernel.  Call it outside stream capture (it sets the kernel's
+ * attributes) and not while a render of the model is being enqueued.
+ * Errors: GN_EINVAL (NULL model, unknown schedule), GN_EUNSUPPORTED
+ * (GN_SCHEDULE_COMPACT for another precision, H != 64, positional encoding
+ * or a 3x3 R), GN_ECUDA.
+ */
+int glassnet_set_layer_schedule(gn_model* model, int schedule);
+
 /*
  * The FP32 plain render with no device allocation.  The paper has no
  * counterpart; this is an ABI convenience.  glassnet_render grows a

@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libglassnet.so"
 SOURCES = ["glassnet_api.cu", "encode.cu", "plain_fp32.cu", "fused_bf16.cu", "noalloc_fp32.cu",
-           "runtime.cu", "plan.cu", "fused_fp8.cu", "server.cu", "conv_r3.cu"]
+           "runtime.cu", "plan.cu", "fused_fp8.cu", "server.cu", "conv_r3.cu",
+           "fused_compact.cu"]
 HEADERS = ["internal.h", "tc_ptx.cuh", "fused_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -566,12 +566,14 @@ cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s
     q.pool_sum = 1;
     return launch_fused_fp8(m->H, m->fused, q, s);
   }
-  if (m->pooling == GN_POOL_SUM || m->wi.L > 0 || m->stall_ns > 0) {
+  if (m->pooling == GN_POOL_SUM || m->wi.L > 0 || m->stall_ns > 0 ||
+      m->schedule == GN_SCHEDULE_COMPACT) {
     FusedParams q = p;
     q.pool_sum = m->pooling == GN_POOL_SUM;
     q.pe_freqs = m->wi.L;
     q.stall_ns = m->stall_ns;  // the test hook holds for one launch
     const_cast<gn_model*>(m)->stall_ns = 0;
+    if (m->schedule == GN_SCHEDULE_COMPACT) return launch_fused_compact(m->fused, q, s);
     return launch_fused_bf16(m->H, m->fused, q, s);
   }
   return launch_fused_bf16(m->H, m->fused, p, s);
@@ -579,6 +581,7 @@ cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s
 
 cudaError_t prepare_fused(const gn_model* m) {
   cudaError_t e = m->precision == GN_FP8_FUSED ? prepare_fused_fp8(m->H) : prepare_fused_bf16(m->H);
+  if (e == cudaSuccess && m->schedule == GN_SCHEDULE_COMPACT) e = prepare_fused_compact();
   return e == cudaSuccess && m->wi.RK == 3 ? prepare_conv_r3(m->H) : e;
 }
 
@@ -804,6 +807,22 @@ int glassnet_debug_stall_next_render(gn_model* m, uint64_t stall_ns) {
   if (stall_ns == 0 || stall_ns > 1000000000ull)
     return fail(GN_EINVAL, "stall of %llu ns outside 1 ns .. 1 s", static_cast<unsigned long long>(stall_ns));
   m->stall_ns = stall_ns;
+  return GN_OK;
+}
+
+int glassnet_set_layer_schedule(gn_model* m, int schedule) {
+  if (!m) return fail(GN_EINVAL, "model is NULL");
+  if (schedule != GN_SCHEDULE_SORTED && schedule != GN_SCHEDULE_COMPACT)
+    return fail(GN_EINVAL, "unknown schedule %d", schedule);
+  if (schedule == GN_SCHEDULE_COMPACT) {
+    if (m->precision != GN_BF16_FUSED || m->H != 64 || m->wi.L > 0 || m->wi.RK != 1)
+      return fail(GN_EUNSUPPORTED,
+                  "the compacted layer schedule is built for GN_BF16_FUSED at H = 64 without "
+                  "positional encoding and with a 1x1 R");
+    const cudaError_t e = gn::prepare_fused_compact();
+    if (e != cudaSuccess) return cuda_fail(e, "compacted kernel attributes");
+  }
+  m->schedule = schedule;
   return GN_OK;
 }
 

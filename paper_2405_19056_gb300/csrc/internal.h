@@ -274,6 +274,10 @@ cudaError_t launch_conv_r3(int H, const void* img, const uint16_t* phi, float* o
 // FP8 fused path (fused_fp8.cu): plan kernel, then the fused E4M3 kernel.
 cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& p, cudaStream_t s);
 cudaError_t prepare_fused_fp8(int H);
+// Compacted ragged-layer kernel (fused_compact.cu, BF16, H = 64, whole frames,
+// no encoding, 1x1 R): plan kernel (identity order), then the fused kernel.
+cudaError_t launch_fused_compact(const void* wimg, const FusedParams& p, cudaStream_t s);
+cudaError_t prepare_fused_compact();
 // Per-layer |activation| maxima of an FP32 plain render held in `ws` (the
 // workspace launch_plain_fp32 filled for the same frame), in the order of
 // the FP8 activation scales, as FP32 bit patterns in amax[kFp8Acts].
@@ -302,6 +306,7 @@ struct gn_model {
   bool fp8_ready = false;   // FP8 models: calibrated and packed
   float fp8_act[gn::kFp8Acts] = {};  // FP8 activation scales (real value of a code = code * s)
   uint64_t stall_ns = 0;    // test hook: the next fused BF16 launch stalls (glassnet_debug_stall_next_render)
+  int schedule = GN_SCHEDULE_SORTED;  // gn_schedule of the fused BF16 frame renders
 };
 
 namespace gn {

@@ -25,6 +25,8 @@ GN_EUNSUPPORTED = -6
 GN_ERANGE = -7
 GN_ESATURATED = -8
 GN_FP8_SCALES = 32
+GN_SCHEDULE_SORTED = 0
+GN_SCHEDULE_COMPACT = 1
 
 GN_FP32_PLAIN = 0
 GN_BF16_FUSED = 1
@@ -55,6 +57,7 @@ _SIGNATURES = {
     "glassnet_render_batch": (_I, [_P, _P, _I, _P]),
     "glassnet_check": (_I, [_P, _P]),
     "glassnet_debug_stall_next_render": (_I, [_P, ctypes.c_uint64]),
+    "glassnet_set_layer_schedule": (_I, [_P, _I]),
     "glassnet_render_fp32_static": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P, _P]),
     "glassnet_calibrate_fp8": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _P]),
     "glassnet_fp8_scales": (_I, [_P, _P]),
@@ -383,6 +386,10 @@ def glassnet_check(model, stream=None):
 
 def glassnet_debug_stall_next_render(model, stall_ns: int):
     _check(_lib().glassnet_debug_stall_next_render(model, int(stall_ns)))
+
+
+def glassnet_set_layer_schedule(model, schedule: int):
+    _check(_lib().glassnet_set_layer_schedule(model, int(schedule)))
 
 
 def glassnet_check_code(model, stream=None) -> int:

@@ -84,13 +84,15 @@ def test_each_leg_takes_the_capture_of_its_own_kernel(bench):
         assert bench.traffic_record(*args) is None, args
 
 
-def test_kernel_digest_covers_every_source_of_the_captured_kernels(bench):
+@pytest.mark.parametrize("root,attr", [("fused_bf16.cu", "KERNEL_SOURCES"),
+                                       ("fused_compact.cu", "COMPACT_SOURCES")])
+def test_kernel_digest_covers_every_source_of_the_captured_kernels(bench, root, attr):
     """The traffic records are keyed by a hash of the fused kernel's and the
     plan kernel's sources: every repository file they include, transitively,
     is hashed, except the public C header (declarations and enum values the
     kernels never branch on at compile time)."""
     csrc = os.path.join(ROOT, "paper_2405_19056_gb300", "csrc")
-    seen, todo = set(), ["fused_bf16.cu", "plan.cu"]
+    seen, todo = set(), [root, "plan.cu"]
     while todo:
         name = todo.pop()
         if name in seen:
@@ -100,7 +102,25 @@ def test_kernel_digest_covers_every_source_of_the_captured_kernels(bench):
             for inc in re.findall(r'^#include "([^"]+)"', f.read(), flags=re.M):
                 if not inc.endswith("include/glassnet.h"):
                     todo.append(inc)
-    assert seen == set(bench.KERNEL_SOURCES)
+    assert seen == set(getattr(bench, attr))
+
+
+def test_layer_rows_of_both_schedules(bench):
+    """Executed / valid (pixel, layer) rows.  Every pixel with K layers: both
+    schedules run exactly the valid rows.  One pixel with 8 layers in a
+    512-pixel window of empty pixels: the sorted tile runs 8 slots of 128
+    rows, the compacted block one 128-row tile."""
+    full = np.full((16, 64), 5, dtype=np.uint8)
+    assert bench.layer_rows(full, "sorted") == (5 * 1024, 5 * 1024)
+    assert bench.layer_rows(full, "compact") == (5 * 1024, 5 * 1024)
+    one = np.zeros((8, 64), dtype=np.uint8)
+    one[3, 7] = 8
+    assert bench.layer_rows(one, "sorted") == (8 * 128, 8)
+    assert bench.layer_rows(one, "compact") == (128, 8)
+    # a ragged frame: 300 pixels of count 1 -> blocks of 256 and 44 pixels
+    rag = np.ones((1, 300), dtype=np.uint8)
+    assert bench.layer_rows(rag, "compact") == (128 * 2 + 128, 300)
+    assert bench.layer_rows(rag, "sorted") == (128 * 3, 300)
 
 
 def test_serving_stream_follows_the_stated_workload(bench):
