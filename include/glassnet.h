@@ -438,15 +438,16 @@ int glassnet_check(const gn_model* model, cudaStream_t stream);
 
 /*
  * Test hook for the device-side timeout path (the paper has no counterpart).
- * The next fused launch of this GN_BF16_FUSED model (one render, batch or
- * streamed launch) makes its MMA warp wait `stall_ns` nanoseconds (1 ns ..
- * 1 s) on a barrier that nothing arrives on, after the weights are in shared
- * memory and before any MMA is issued; the wait gives up, every warp of the
- * kernel leaves through its exit path (which leaves no MMA or bulk copy in
- * flight and frees the tensor memory), the frame is not written, and the next
- * glassnet_check returns GN_ETIMEOUT.  Later launches render normally.  Do not
- * arm it around a graph capture (the stall would be captured).
- * Errors: GN_EINVAL (NULL model, another precision, stall out of range).
+ * The next fused launch of this GN_BF16_FUSED or GN_FP8_FUSED model (one
+ * render, batch or streamed launch; either layer schedule) makes its MMA warp
+ * wait `stall_ns` nanoseconds (1 ns .. 1 s) on a barrier that nothing arrives
+ * on, after the weights are in shared memory and before any MMA is issued;
+ * the wait gives up, every warp of the kernel leaves through its exit path
+ * (which leaves no MMA or bulk copy in flight and frees the tensor memory),
+ * the frame is not written, and the next glassnet_check returns GN_ETIMEOUT.
+ * Later launches render normally.  Do not arm it around a graph capture (the
+ * stall would be captured).
+ * Errors: GN_EINVAL (NULL model, GN_FP32_PLAIN, stall out of range).
  */
 int glassnet_debug_stall_next_render(gn_model* model, uint64_t stall_ns);
 

@@ -24,6 +24,10 @@ namespace gn {
 namespace {
 using namespace fused;
 
+constexpr int B_STALL8 = B_COUNT;      // never arrived on: the stall that tests the timeout path
+constexpr int B_DRAIN8 = B_COUNT + 1;  // the exit path's last commit
+constexpr int B_COUNT_F8 = B_COUNT + 2;
+
 // TMEM column map (128 lanes x 4H columns): three accumulator buffers of H
 // columns, then U (H e4m3 = H/4 columns) double buffered; the pooled
 // [max ; mean] (2H e4m3 = H/2 columns) reuses the U region.  The per-pixel
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
   static_assert(CH % 16 == 0, "accumulator columns per thread must be a multiple of 16");
 
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[B_COUNT];
+  __shared__ __align__(8) uint64_t bars[B_COUNT_F8];
   __shared__ uint32_t s_tmem;
   __shared__ LoaderShared s_ld;
   __shared__ volatile int s_abort;
@@ -276,6 +280,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     mbar_init(bar(B_DR2), 1);
     mbar_init(bar(B_AG_F), kLoadWarps);
     mbar_init(bar(B_AG_E), 1);
+    mbar_init(bar(B_STALL8), 1);
+    mbar_init(bar(B_DRAIN8), 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(bar(B_IN + b), kEpiWarps);
       mbar_init(bar(B_AT_F + b), kLoadWarps);
@@ -367,6 +373,9 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       return true;
     };
     if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+    // Test hook (stall_ns > 0, set by glassnet_debug_stall_next_render): a
+    // wait on a barrier that nothing arrives on, before any MMA is issued.
+    if (prm.stall_ns > 0 && !warp_wait(bar(B_STALL8), 0, &s_abort, prm.stall_ns)) goto done;
     for (;; ++tb) {
       if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
       const int tile = *reinterpret_cast<volatile int*>(&s_ld.tile[tb & 1]);
@@ -677,9 +686,13 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     }
   }
 done:
-  if (s_abort && tid == 0) atomicOr(prm.err, kErrTimeout);
   tc_fence_before();
-  __syncthreads();
+  __syncthreads();  // every warp is here: s_abort is final
+  if (s_abort) {
+    // nothing of this CTA may be in flight when its TMEM is freed
+    if (warp == kMmaWarp) drain_async(bar(B_W), bar(B_DRAIN8));
+    if (tid == 0) atomicOr(prm.err, kErrTimeout);
+  }
   if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tbase, TMapF8<H>::NCOLS);

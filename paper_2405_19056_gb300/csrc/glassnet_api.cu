@@ -561,9 +561,11 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
 
 cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s) {
   if (m->precision == GN_FP8_FUSED) {
-    if (m->pooling != GN_POOL_SUM) return launch_fused_fp8(m->H, m->fused, p, s);
+    if (m->pooling != GN_POOL_SUM && m->stall_ns == 0) return launch_fused_fp8(m->H, m->fused, p, s);
     FusedParams q = p;
-    q.pool_sum = 1;
+    q.pool_sum = m->pooling == GN_POOL_SUM;
+    q.stall_ns = m->stall_ns;  // the test hook holds for one launch
+    const_cast<gn_model*>(m)->stall_ns = 0;
     return launch_fused_fp8(m->H, m->fused, q, s);
   }
   if (m->pooling == GN_POOL_SUM || m->wi.L > 0 || m->stall_ns > 0 ||
@@ -803,7 +805,8 @@ int glassnet_fp8_scales(const gn_model* m, float* scales) {
 
 int glassnet_debug_stall_next_render(gn_model* m, uint64_t stall_ns) {
   if (!m) return fail(GN_EINVAL, "model is NULL");
-  if (m->precision != GN_BF16_FUSED) return fail(GN_EINVAL, "the stall hook is in the fused BF16 kernel");
+  if (m->precision == GN_FP32_PLAIN)
+    return fail(GN_EINVAL, "the stall hook is in the fused kernels (BF16, FP8)");
   if (stall_ns == 0 || stall_ns > 1000000000ull)
     return fail(GN_EINVAL, "stall of %llu ns outside 1 ns .. 1 s", static_cast<unsigned long long>(stall_ns));
   m->stall_ns = stall_ns;

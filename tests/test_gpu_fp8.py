@@ -205,6 +205,25 @@ def test_fp8_batch_and_graph_equal_single(doubled8):
         gl.glassnet_graph_free(g)
 
 
+@pytest.mark.parametrize("widths", ["base8", "doubled8"])
+def test_fp8_timeout_reported_and_next_render_exact(widths, request):
+    """The stall hook in the FP8 kernel: the MMA warp's wait gives up, every
+    warp leaves (nothing left in flight), GN_ETIMEOUT is reported, the frame
+    is left unwritten, and the next render is bit-identical to one taken
+    before the stall."""
+    net = request.getfixturevalue(widths)
+    m = net.model
+    frame = synth.make_frame(40, 52, 4, counts="uniform", seed=12)
+    before = net.render(frame, scene_seed=12)
+    out = torch.full((3, frame.h, frame.w), float("nan"), device=DEV)
+    gl.glassnet_debug_stall_next_render(m.handle, 20_000)
+    m.render(net.latent(12), _dev(frame.gbuf), _dev(frame.tbuf), _dev(frame.counts), out)
+    assert gl.glassnet_check_code(m.handle) == gl.GN_ETIMEOUT
+    assert gl.glassnet_check_code(m.handle) == gl.GN_OK
+    assert np.isnan(out.cpu().numpy()).all()
+    assert np.array_equal(net.render(frame, scene_seed=12), before)
+
+
 def test_fp8_full_512_K8_poisson_sampled(doubled8):
     """The benchmark workload with the FP8 model: the 64x64 crop at rows and
     columns 0..63 and 1024 sampled pixels against the oracle."""
