@@ -152,15 +152,19 @@ typedef struct gn_model_config {
  *   pixel's layers.
  * Positional encoding: pe_freqs 0..10 for GN_FP32_PLAIN; 0..4 at H = 64 for
  *   GN_BF16_FUSED (the encoded operands fill the fused kernel's shared
- *   memory; H = 128 with pe_freqs > 0 is GN_EUNSUPPORTED).  The fused kernel
- *   computes sin(pi x) and cos(pi x) of each input channel with exact
- *   argument reduction and the higher bands by the double-angle identities
- *   in FP32, then rounds every band to BF16.
+ *   memory; H = 128 with pe_freqs > 0 is GN_EUNSUPPORTED); 0..4 at H = 64
+ *   and H = 128 for GN_FP8_FUSED with the 1x1 R (E4M3 operands take half the
+ *   bytes).  The fused kernels compute sin(pi x) and cos(pi x) of each input
+ *   channel with exact argument reduction and the higher bands by the
+ *   double-angle identities in FP32, then round every band to BF16, or to
+ *   E4M3: band 0 as codes of its channel's calibrated scale, the sine and
+ *   cosine bands as codes of 256 v (|v| <= 1).
  * GN_POOL_SUM serves every precision (for GN_FP8_FUSED the sum enters B1 as
  * codes of B1's input scale, calibrated on the FP32 path's sum form).
  * pe_freqs > 0 serves every render, batch, graph, server and streaming call
- * of GN_FP32_PLAIN / GN_BF16_FUSED models; with GN_FP8_FUSED it returns
- * GN_EUNSUPPORTED.
+ * of GN_FP32_PLAIN / GN_BF16_FUSED models and every render, batch, graph and
+ * server call of GN_FP8_FUSED models (pe_freqs above 4, or with r_kernel = 3,
+ * returns GN_EUNSUPPORTED there).
  * r_kernel = 3 serves every render, batch, graph and server call of every
  *   precision (streaming: GN_BF16_FUSED) (any pooling; with pe_freqs as
  *   above): the fused kernel writes each frame's neural buffer (BF16, H 2

@@ -93,6 +93,40 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
                : "memory");
 }
 
+// Positional encoding (Sec. 3.4), shared by the BF16 and FP8 loaders: each
+// input channel x enters as the bands
+// [x ; sin(2^0 pi x) ; cos(2^0 pi x) ; ... ; cos(2^(L-1) pi x)].
+// First band: x = n + r with n = rint(x) and r = x - n exact, |r| <= 1/2, so
+// sin(pi x) = (-1)^n sin(pi r) and cos(pi x) = (-1)^n cos(pi r) with
+// |pi r| <= pi/2, where the hardware sine and cosine (__sinf, __cosf) are
+// accurate to about 2^-21 absolute.  Every next band follows from the
+// double-angle identities sin 2a = 2 sin a cos a and cos 2a = 1 - 2 sin^2 a
+// in FP32; each doubling at most quadruples the error, so band f is within
+// about 4^f 2^-21 of the exact value (3e-5 at f = 3), far below the rounding
+// of the operand it feeds (2^-9 relative in BF16, 2^-4 in E4M3).
+__device__ __forceinline__ void sincospi_reduced(float x, float& sn, float& cs) {
+  const float n = rintf(x);
+  const float a = (x - n) * 3.14159265358979f;
+  const float h = 0.5f * n;
+  const float sign = rintf(h) == h ? 1.0f : -1.0f;  // (-1)^n, also for |n| >= 2^24 (even)
+  sn = sign * __sinf(a);
+  cs = sign * __cosf(a);
+}
+template <int N>
+__device__ __forceinline__ void pe_first(const float (&x)[N], float (&sn)[N], float (&cs)[N]) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) sincospi_reduced(x[j], sn[j], cs[j]);
+}
+template <int N>
+__device__ __forceinline__ void pe_double(float (&sn)[N], float (&cs)[N]) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const float a = sn[j];
+    sn[j] = 2.0f * a * cs[j];
+    cs[j] = fmaf(-2.0f * a, a, 1.0f);
+  }
+}
+
 // Bounded wait shared by a whole warp: every lane waits, then the warp agrees.
 // On a timeout the CTA-wide abort flag is raised and every later wait fails
 // at once, so all warps reach the common exit.

@@ -132,19 +132,79 @@ __device__ __forceinline__ void store_slot_f8(uint32_t base, int row0, const flo
   }
 }
 
-template <int H>
+// Positional encoding (Sec. 3.4) of one row of N input channels (12 for a
+// layer, 14 for the G-buffer) as a K = 128 E4M3 operand row: band-major, code
+// k = N t + c of band t; band 0 the code of x[c] / s[c] (calibrated channel
+// scale), bands 2f + 1 and 2f + 2 the codes of sin and cos(2^f pi x[c]) times
+// kFp8BandCode; zeros from k = N (1 + 2 nf) on.  Channel pairs fill 16-bit
+// halves (N t + c is even for even c).
+// The channel scales 1 / s[c] are read from shared memory at `inv_s` (a
+// volatile load per use: the encoder's registers go to the bands).
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+template <int N>
+__device__ __forceinline__ void encode_row_f8(const float (&x)[N], uint32_t inv_s, int nf,
+                                              uint32_t (&w)[32], bool& sat) {
+  static_assert(N % 2 == 0 && N * (1 + 2 * kMaxPeFreqsFused) <= 128, "bands must fit K = 128");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) w[j] = 0u;
+  auto put = [&](int h, uint16_t v) {  // codes 2h and 2h + 1 of the row
+    w[h >> 1] |= (h & 1) ? static_cast<uint32_t>(v) << 16 : static_cast<uint32_t>(v);
+  };
+#pragma unroll
+  for (int p = 0; p < N / 2; ++p) {
+    const float x0 = x[2 * p], x1 = x[2 * p + 1];
+    const float v0 = x0 * lds_f32(inv_s + 8u * p), v1 = x1 * lds_f32(inv_s + 8u * p + 4u);
+    sat |= fabsf(v0) > 448.0f || fabsf(v1) > 448.0f;
+    put(p, pack_e4m3(v0, v1));
+    float sn[2], cs[2];
+    const float xs[2] = {x0, x1};
+    pe_first(xs, sn, cs);
+#pragma unroll
+    for (int f = 0; f < kMaxPeFreqsFused; ++f) {
+      if (f < nf) {
+        if (f > 0) pe_double(sn, cs);
+        put((N / 2) * (2 * f + 1) + p, pack_e4m3(kFp8BandCode * sn[0], kFp8BandCode * sn[1]));
+        put((N / 2) * (2 * f + 2) + p, pack_e4m3(kFp8BandCode * cs[0], kFp8BandCode * cs[1]));
+      }
+    }
+  }
+}
+
+// The 8 core-matrix columns (16 codes each) of row `row` of a [8][128][16]
+// operand.
+__device__ __forceinline__ void store_row_k128(uint32_t base, int row, const uint32_t (&w)[32]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    sts128(base + static_cast<uint32_t>(j) * 2048u + static_cast<uint32_t>(row) * 16u, w[4 * j],
+           w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+}
+
+template <int H, bool PE>
 __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uint8_t* wimg,
                                                uint32_t sbase, uint32_t bar_base,
                                                LoaderShared& ls, volatile int* abort_flag, int li,
                                                int lane) {
-  using L = FusedLayoutF8<H>;
+  using L = FusedLayoutF8<H, PE>;
+  const int nf = PE ? prm.pe_freqs : 0;  // positional-encoding frequencies
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
   const float* cst = reinterpret_cast<const float*>(wimg + L::cst);
-  float inv_s_t[kTC], inv_s_g[kGC];  // per-channel input scales
+  float inv_s_t[kTC], inv_s_g[kGC];  // per-channel input scales (inputs as given)
+  // encoded inputs: the scales stay in the shared-memory copy of the
+  // constants, which is there once the weights have landed
+  const uint32_t inv_s_t_sm = sbase + L::cst + 4u * L::INV_S_TCH;
+  const uint32_t inv_s_g_sm = sbase + L::cst + 4u * L::INV_S_GCH;
+  if constexpr (PE) {
+    if (!warp_wait(bar(B_W), 0, abort_flag)) return;
+  } else {
 #pragma unroll
-  for (int c = 0; c < kTC; ++c) inv_s_t[c] = __ldg(cst + L::INV_S_TCH + c);
+    for (int c = 0; c < kTC; ++c) inv_s_t[c] = __ldg(cst + L::INV_S_TCH + c);
 #pragma unroll
-  for (int c = 0; c < kGC; ++c) inv_s_g[c] = __ldg(cst + L::INV_S_GCH + c);
+    for (int c = 0; c < kGC; ++c) inv_s_g[c] = __ldg(cst + L::INV_S_GCH + c);
+  }
   bool sat = false;  // an input of this warp's rows was clamped
   // reported once per tile, by the warp's lane 0
   auto report_sat = [&]() {
@@ -193,29 +253,39 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
     if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
     const int ns = max(ls.ns[tb & 1][0], ls.ns[tb & 1][1]);
 
+    // the G-buffer rows, loads in flight now (encoded inputs: loaded when
+    // B1's operand is written, which keeps the slot loop's registers free)
     float gv[kRowsPerLoadLane][kGC];
-    {
+    auto load_g = [&]() {
       const uint32_t P = static_cast<uint32_t>(F.P);
 #pragma unroll
       for (int i = 0; i < kRowsPerLoadLane; ++i)
 #pragma unroll
         for (int ch = 0; ch < kGC; ++ch)
           gv[i][ch] = has[i] ? __ldg(F.gbuf + (static_cast<uint32_t>(ch) * P + pix[i])) : 0.0f;
-    }
+    };
+    if constexpr (!PE) load_g();
     // B1's G-buffer operand: the 14 channels as codes of g[c] / s_g[c], then zeros
     auto put_ag = [&]() -> bool {
+      if constexpr (PE) load_g();
       if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
 #pragma unroll
       for (int i = 0; i < kRowsPerLoadLane; ++i) {
-        float v[kGC];
-        scale_inputs(gv[i], inv_s_g, v, sat);
-        uint32_t w[4];
+        if constexpr (PE) {
+          uint32_t w[32];
+          encode_row_f8(gv[i], inv_s_g_sm, nf, w, sat);
+          store_row_k128(sbase + L::ag, row0 + 32 * i, w);
+        } else {
+          float v[kGC];
+          scale_inputs(gv[i], inv_s_g, v, sat);
+          uint32_t w[4];
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-          w[j] = pack_u16x2(pack_e4m3(v[4 * j], v[4 * j + 1]), pack_e4m3(v[4 * j + 2], v[4 * j + 3]));
-        w[3] = pack_u16x2(pack_e4m3(v[12], v[13]), 0);
-        sts128(sbase + L::ag + static_cast<uint32_t>(row0 + 32 * i) * 16u, w[0], w[1], w[2], w[3]);
+          for (int j = 0; j < 3; ++j)
+            w[j] = pack_u16x2(pack_e4m3(v[4 * j], v[4 * j + 1]), pack_e4m3(v[4 * j + 2], v[4 * j + 3]));
+          w[3] = pack_u16x2(pack_e4m3(v[12], v[13]), 0);
+          sts128(sbase + L::ag + static_cast<uint32_t>(row0 + 32 * i) * 16u, w[0], w[1], w[2], w[3]);
+        }
       }
       fence_proxy_async_smem();
       __syncwarp();
@@ -231,7 +301,16 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
       if (k + 1 < ns) load_slot_f8(F, k + 1, pix, cnt, y);
       const int b = lc & 1;
       if (!warp_wait(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
-      store_slot_f8(sbase + (b ? L::at1 : L::at0), row0, inv_s_t, x, sat);
+      if constexpr (PE) {
+#pragma unroll
+        for (int i = 0; i < kRowsPerLoadLane; ++i) {
+          uint32_t w[32];
+          encode_row_f8(x[i], inv_s_t_sm, nf, w, sat);
+          store_row_k128(sbase + (b ? L::at1 : L::at0), row0 + 32 * i, w);
+        }
+      } else {
+        store_slot_f8(sbase + (b ? L::at1 : L::at0), row0, inv_s_t, x, sat);
+      }
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_AT_F + b));
@@ -252,10 +331,11 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
 // R3: R's first layer is a 3x3 kernel over the frame (conv_r3.cu): the tile
 // ends after B2, whose output goes to the frame's neural buffer as BF16 in
 // real units ((acc s_B2 + b_B2) s_y2, ReLU) instead of R1's E4M3 operand.
-template <int H, bool Sum, bool R3>
+template <int H, bool Sum, bool R3, bool PE>
 __global__ void __launch_bounds__(kThreadsF, 1)
     fused_fp8_kernel(const __grid_constant__ FusedParams prm, const uint8_t* __restrict__ wimg) {
-  using L = FusedLayoutF8<H>;
+  static_assert(!(PE && R3), "the encoded inputs are built with the 1x1 R");
+  using L = FusedLayoutF8<H, PE>;
   using T = TMapF8<H>;
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
   constexpr int CHQ = CH / 4;  // TMEM columns of CH e4m3 values
@@ -318,7 +398,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     }
     fence_proxy_async_smem();
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
-    loader_loop_f8<H>(prm, wimg, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
+    loader_loop_f8<H, PE>(prm, wimg, sbase, bar_base, s_ld, &s_abort, warp - kLoadWarp0, lane);
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA warp
     if (lane == 0) {
@@ -347,7 +427,15 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     const uint64_t dsc_one = make_sdesc(sbase + L::aone, 128 * 16, 128);
     const uint64_t dsc_ag = make_sdesc(sbase + L::ag, 128 * 16, 128);
     // B1's weights for r start after its 32-wide G-buffer block
-    const uint64_t dsc_b1r = dsc_b1 + static_cast<uint64_t>((2 * H * 16) >> 4);
+    const uint64_t dsc_b1r = dsc_b1 + static_cast<uint64_t>(L::KG / 32) * ((2 * H * 16) >> 4);
+    // D (+)= A (shared memory, K codes) x B^T: K / 32 steps, each advancing A
+    // by two core-matrix columns of 128 rows (4096 bytes) and B by two of N
+    // rows
+    auto mma_ss_k = [&](uint32_t d, uint64_t a0, uint64_t b0, int K, uint32_t acc) {
+      for (int t = 0; t < K / 32; ++t)
+        mma_f8_ss_e(d, a0 + static_cast<uint64_t>(t) * (4096u >> 4),
+                    b0 + static_cast<uint64_t>(t) * ((2 * H * 16) >> 4), id8, (t > 0 || acc) ? 1u : 0u);
+    };
     SlotPos p1, p2;
     uint32_t g1 = 0, n_in = 0, n_agf = 0, tb = 0;
     const float* cur_fold = nullptr;
@@ -357,7 +445,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       if (!warp_wait(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
       tc_fence_after();
       const uint32_t d = tbase + T::buf(p1.b);
-      mma_f8_ss_e(d, a ? dsc_at1 : dsc_at0, dsc_phi1, id8, 0u);
+      mma_ss_k(d, a ? dsc_at1 : dsc_at0, dsc_phi1, L::KT, 0u);
       mma_f16_ss_e(d, dsc_one, dsc_phi1b, idb, 1u);
       mma_commit_e(bar(B_D1 + p1.b));
       mma_commit_e(bar(B_AT_E + a));
@@ -422,7 +510,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         }
         if (l == 0) issue_gemm_f8<H, 2 * H>(X, tbase + T::APOOL, dsc_rho, id8);
         if (l == 1) {
-          mma_f8_ss_e(X, dsc_ag, dsc_b1, id8, 0u);
+          mma_ss_k(X, dsc_ag, dsc_b1, L::KG, 0u);
           issue_gemm_f8<H, H>(X, Y, dsc_b1r, id8, true);
           mma_f16_ss_e(X, dsc_one, dsc_b1b, idb, 1u);
         }
@@ -699,43 +787,65 @@ done:
   }
 }
 
-template <int H, bool Sum, bool R3>
+template <int H, bool Sum, bool R3, bool PE = false>
 cudaError_t prepare_f8() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_fp8_kernel<H, Sum, R3>,
+  cudaError_t e = cudaFuncSetAttribute(fused_fp8_kernel<H, Sum, R3, PE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       FusedLayoutF8<H>::smem_bytes);
+                                       FusedLayoutF8<H, PE>::smem_bytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <int H, bool Sum, bool R3>
+template <int H, bool Sum, bool R3, bool PE = false>
 cudaError_t launch_f8(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
-  cudaError_t e = prepare_f8<H, Sum, R3>();
+  cudaError_t e = prepare_f8<H, Sum, R3, PE>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kThreadsF);
-  cfg.dynamicSmemBytes = FusedLayoutF8<H>::smem_bytes;
+  cfg.dynamicSmemBytes = FusedLayoutF8<H, PE>::smem_bytes;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fused_fp8_kernel<H, Sum, R3>, p, static_cast<const uint8_t*>(wimg));
+  return cudaLaunchKernelEx(&cfg, fused_fp8_kernel<H, Sum, R3, PE>, p,
+                            static_cast<const uint8_t*>(wimg));
+}
+
+template <int H>
+cudaError_t prepare_all_f8() {
+  cudaError_t e = prepare_f8<H, false, false>();
+  if (e == cudaSuccess) e = prepare_f8<H, true, false>();
+  if (e == cudaSuccess) e = prepare_f8<H, false, true>();
+  if (e == cudaSuccess) e = prepare_f8<H, true, true>();
+  if (e == cudaSuccess) e = prepare_f8<H, false, false, true>();
+  if (e == cudaSuccess) e = prepare_f8<H, true, false, true>();
+  return e;
+}
+
+template <int H>
+cudaError_t launch_h_f8(const void* wimg, const FusedParams& p, cudaStream_t s, int grid) {
+  if (p.pe_freqs > 0) {  // encoded inputs (1x1 R only; the loader encodes up to 4 frequencies)
+    if (p.f[0].phi || p.pe_freqs > kMaxPeFreqsFused) return cudaErrorInvalidValue;
+    return p.pool_sum ? launch_f8<H, true, false, true>(wimg, p, s, grid)
+                      : launch_f8<H, false, false, true>(wimg, p, s, grid);
+  }
+  if (p.f[0].phi)  // 3x3 R: the neural buffer out
+    return p.pool_sum ? launch_f8<H, true, true>(wimg, p, s, grid)
+                      : launch_f8<H, false, true>(wimg, p, s, grid);
+  return p.pool_sum ? launch_f8<H, true, false>(wimg, p, s, grid)
+                    : launch_f8<H, false, false>(wimg, p, s, grid);
 }
 
 }  // namespace
 
 cudaError_t prepare_fused_fp8(int H) {
   device_sm_count();
-  cudaError_t e = H == 128 ? prepare_f8<128, false, false>() : prepare_f8<64, false, false>();
-  if (e == cudaSuccess) e = H == 128 ? prepare_f8<128, true, false>() : prepare_f8<64, true, false>();
-  if (e == cudaSuccess) e = H == 128 ? prepare_f8<128, false, true>() : prepare_f8<64, false, true>();
-  if (e == cudaSuccess) e = H == 128 ? prepare_f8<128, true, true>() : prepare_f8<64, true, true>();
-  return e;
+  return H == 128 ? prepare_all_f8<128>() : prepare_all_f8<64>();
 }
 
 cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& params, cudaStream_t s) {
@@ -744,18 +854,7 @@ cudaError_t launch_fused_fp8(int H, const void* wimg, const FusedParams& params,
   cudaError_t e = launch_plan(p, s);
   if (e != cudaSuccess) return e;
   const int grid = p.total_tiles < device_sm_count() ? p.total_tiles : device_sm_count();
-  if (p.f[0].phi) {  // 3x3 R: the neural buffer out
-    if (p.pool_sum)
-      return H == 128 ? launch_f8<128, true, true>(wimg, p, s, grid)
-                      : launch_f8<64, true, true>(wimg, p, s, grid);
-    return H == 128 ? launch_f8<128, false, true>(wimg, p, s, grid)
-                    : launch_f8<64, false, true>(wimg, p, s, grid);
-  }
-  if (p.pool_sum)
-    return H == 128 ? launch_f8<128, true, false>(wimg, p, s, grid)
-                    : launch_f8<64, true, false>(wimg, p, s, grid);
-  return H == 128 ? launch_f8<128, false, false>(wimg, p, s, grid)
-                  : launch_f8<64, false, false>(wimg, p, s, grid);
+  return H == 128 ? launch_h_f8<128>(wimg, p, s, grid) : launch_h_f8<64>(wimg, p, s, grid);
 }
 
 }  // namespace gn

@@ -170,9 +170,9 @@ inline size_t core_idx8(int N, int n, int k) {
 
 // FP8 image (FusedLayoutF8) from the concat-form weights and the activation
 // scales act[kFp8Acts] (per-channel t and g, then U, pool, r, y, y2, q).
-template <int H>
+template <int H, bool PE = false>
 std::vector<uint8_t> pack_fused_fp8(const float* w, const gn::WeightIndex& wi, const float* act) {
-  using L = gn::FusedLayoutF8<H>;
+  using L = gn::FusedLayoutF8<H, PE>;
   std::vector<uint8_t> img(L::bytes, 0);
   auto W = [&](int l, int n, int j) { return w[wi.w[l] + static_cast<size_t>(n) * wi.in[l] + j]; };
   auto Bv = [&](int l, int n) { return w[wi.b[l] + n]; };
@@ -190,12 +190,18 @@ std::vector<uint8_t> pack_fused_fp8(const float* w, const gn::WeightIndex& wi, c
   const float s_u = act[gn::FP8_U], s_pool = act[gn::FP8_POOL], s_r = act[gn::FP8_R],
               s_y = act[gn::FP8_Y], s_y2 = act[gn::FP8_Y2], s_q = act[gn::FP8_Q];
   float* c = reinterpret_cast<float*>(img.data() + L::cst);
+  // Input column k of phi1's (B1's) first block is channel k % 12 (k % 14) of
+  // band k / 12 (k / 14): band 0 enters as x / s[c], the sine and cosine bands
+  // as v kFp8BandCode, so the column carries s[c] or 1 / kFp8BandCode.
+  const int tce = wi.tc_enc(), gce = wi.gc_enc();
+  auto col_t = [&](int k) { return k < gn::kTC ? s_t[k] : 1.0f / gn::kFp8BandCode; };
+  auto col_g = [&](int k) { return k < gn::kGC ? s_g[k] : 1.0f / gn::kFp8BandCode; };
   for (int n = 0; n < H; ++n) {
     // phi1: column c of the weights carries the input channel's scale
     float m1 = 0.0f;
-    for (int k = 0; k < gn::kTC; ++k) m1 = std::max(m1, std::fabs(W(gn::LPHI1, n, k) * s_t[k]));
+    for (int k = 0; k < tce; ++k) m1 = std::max(m1, std::fabs(W(gn::LPHI1, n, k) * col_t(k)));
     const float w1 = m1 > 0.0f ? m1 / 448.0f : 1.0f;
-    for (int k = 0; k < gn::kTC; ++k) put(L::phi1, H, n, k, W(gn::LPHI1, n, k) * s_t[k] / w1);
+    for (int k = 0; k < tce; ++k) put(L::phi1, H, n, k, W(gn::LPHI1, n, k) * col_t(k) / w1);
     c[L::S_PHI1 + n] = w1 / s_u;
     c[L::U_PHI1 + n] = 1.0f / w1;
     const float w2 = wscale(gn::LPHI2, n, 0, H);
@@ -208,11 +214,11 @@ std::vector<uint8_t> pack_fused_fp8(const float* w, const gn::WeightIndex& wi, c
     c[L::B_RHO + n] = Bv(gn::LRHO, n) / s_r;
     // B1: the G-buffer columns carry their channels' scales, the r columns s_r
     float mb = 0.0f;
-    for (int k = 0; k < gn::kGC; ++k) mb = std::max(mb, std::fabs(W(gn::LB1, n, k) * s_g[k]));
-    for (int k = 0; k < H; ++k) mb = std::max(mb, std::fabs(W(gn::LB1, n, gn::kGC + k) * s_r));
+    for (int k = 0; k < gce; ++k) mb = std::max(mb, std::fabs(W(gn::LB1, n, k) * col_g(k)));
+    for (int k = 0; k < H; ++k) mb = std::max(mb, std::fabs(W(gn::LB1, n, gce + k) * s_r));
     const float wb1 = mb > 0.0f ? mb / 448.0f : 1.0f;
-    for (int k = 0; k < gn::kGC; ++k) put(L::b1, H, n, k, W(gn::LB1, n, k) * s_g[k] / wb1);
-    for (int k = 0; k < H; ++k) put(L::b1, H, n, 32 + k, W(gn::LB1, n, gn::kGC + k) * s_r / wb1);
+    for (int k = 0; k < gce; ++k) put(L::b1, H, n, k, W(gn::LB1, n, k) * col_g(k) / wb1);
+    for (int k = 0; k < H; ++k) put(L::b1, H, n, L::KG + k, W(gn::LB1, n, gce + k) * s_r / wb1);
     c[L::S_B1 + n] = wb1 / s_y;
     c[L::U_B1 + n] = 1.0f / wb1;
     const float wb2 = wscale(gn::LB2, n, 0, H);
@@ -307,9 +313,10 @@ int load_weights_impl(const void* blob, size_t nbytes, const gn_model_config* cf
     return fail(GN_EINVAL, "unknown pooling %d", pooling);
   if (pe < 0 || pe > gn::kMaxPeFreqs)
     return fail(GN_EINVAL, "pe_freqs %d outside 0..%d", pe, gn::kMaxPeFreqs);
-  if (precision == GN_FP8_FUSED && pe > 0)
+  if (precision == GN_FP8_FUSED && pe > 0 && (pe > gn::kMaxPeFreqsFused || rk != 1))
     return fail(GN_EUNSUPPORTED,
-                "positional encoding is built for GN_FP32_PLAIN and GN_BF16_FUSED");
+                "positional encoding in the FP8 kernel is built for pe_freqs 1..%d with a 1x1 R; "
+                "pe_freqs = %d, r_kernel = %d", gn::kMaxPeFreqsFused, pe, rk);
   if (nbytes < sizeof(gn_blob_header))
     return fail(GN_EFORMAT, "blob of %zu bytes is shorter than its header", nbytes);
   gn_blob_header hd;
@@ -561,9 +568,9 @@ int build_batch(const gn_model* m, const gn_frame* frames, int n, FusedParams* o
 
 cudaError_t launch_fused(const gn_model* m, const FusedParams& p, cudaStream_t s) {
   if (m->precision == GN_FP8_FUSED) {
-    if (m->pooling != GN_POOL_SUM && m->stall_ns == 0) return launch_fused_fp8(m->H, m->fused, p, s);
     FusedParams q = p;
     q.pool_sum = m->pooling == GN_POOL_SUM;
+    q.pe_freqs = m->wi.L;
     q.stall_ns = m->stall_ns;  // the test hook holds for one launch
     const_cast<gn_model*>(m)->stall_ns = 0;
     return launch_fused_fp8(m->H, m->fused, q, s);
@@ -780,8 +787,11 @@ int calibrate_fp8_impl(gn_model* m, const gn_latent* lat, const float* gbuf, con
     const float headroom = i < gn::FP8_U ? gn::kFp8InputHeadroom : gn::kFp8HiddenHeadroom;
     act[i] = (a > 0.0f && std::isfinite(a)) ? a * headroom / 448.0f : 1.0f;
   }
-  std::vector<uint8_t> img = m->H == 128 ? pack_fused_fp8<128>(m->host_w, m->wi, act)
-                                         : pack_fused_fp8<64>(m->host_w, m->wi, act);
+  const bool pe = m->wi.L > 0;
+  std::vector<uint8_t> img = m->H == 128 ? (pe ? pack_fused_fp8<128, true>(m->host_w, m->wi, act)
+                                                : pack_fused_fp8<128>(m->host_w, m->wi, act))
+                                         : (pe ? pack_fused_fp8<64, true>(m->host_w, m->wi, act)
+                                                : pack_fused_fp8<64>(m->host_w, m->wi, act));
   if (!m->fused) {
     if ((e = cudaMalloc(&m->fused, img.size())) != cudaSuccess)
       return fail(GN_ENOMEM, "cudaMalloc packed weights: %s", cudaGetErrorString(e));

@@ -141,14 +141,23 @@ struct FusedLayout {
 //   and the accumulator stays in the weight scale's units.
 //   A operands: at0, at1, ag ([2][128][16] bytes each, K block 1 zero) and
 //   the constant BF16 [1, 1, 0, ...] operand of the bias MMAs.
-template <int H>
+// With positional encoding (PE, up to kMaxPeFreqsFused frequencies) phi1's
+// input and B1's G-buffer block are K = 128 wide: the bands of the 12 (14)
+// channels band-major, code k = 12 t + c (14 t + c) for band t, zeros after
+// the last band (108 and 126 codes at L = 4); band 0 carries the channels'
+// calibrated scales, the sine and cosine bands the fixed code scale
+// kFp8BandCode; B1's r block starts at k = 128.  at0, at1 and ag are then
+// [8][128][16] bytes each.
+template <int H, bool PE = false>
 struct FusedLayoutF8 {
+  static constexpr int KT = PE ? 128 : 32;  // phi1's K (E4M3 codes)
+  static constexpr int KG = PE ? 128 : 32;  // B1's G-buffer block
   static constexpr uint32_t phi1 = 0;
-  static constexpr uint32_t phi1b = phi1 + 32 * H;
+  static constexpr uint32_t phi1b = phi1 + KT * H;
   static constexpr uint32_t phi2 = phi1b + 16 * H * 2;
   static constexpr uint32_t rho = phi2 + H * H;
   static constexpr uint32_t b1 = rho + 2 * H * H;
-  static constexpr uint32_t b1b = b1 + (32 + H) * H;
+  static constexpr uint32_t b1b = b1 + (KG + H) * H;
   static constexpr uint32_t b2 = b1b + 16 * H * 2;
   static constexpr uint32_t r1 = b2 + H * H;
   static constexpr uint32_t r2 = r1 + H * H;
@@ -161,12 +170,16 @@ struct FusedLayoutF8 {
   };
   static constexpr uint32_t bytes = cst + N_CST * 4;
   static constexpr uint32_t at0 = (bytes + 127) / 128 * 128;
-  static constexpr uint32_t at1 = at0 + 4096;
-  static constexpr uint32_t ag = at1 + 4096;
-  static constexpr uint32_t aone = ag + 4096;
+  static constexpr uint32_t at1 = at0 + 128 * KT;
+  static constexpr uint32_t ag = at1 + 128 * KT;
+  static constexpr uint32_t aone = ag + 128 * KG;
   static constexpr uint32_t smem_bytes = aone + 4096;
   static_assert(bytes % 16 == 0, "bulk copy size must be a multiple of 16 bytes");
+  static_assert(smem_bytes + 2048 <= 232448, "operands exceed the shared memory per CTA");
 };
+// Code scale of the sine and cosine bands in the FP8 kernel: a band value
+// v in [-1, 1] enters as the E4M3 code v * 256 (at most 256 of 448).
+constexpr float kFp8BandCode = 256.0f;
 
 // Activation scales of the FP8 path (static): the real value of an E4M3 code
 // x is x * s.  Order: the 12 transparency-layer channels (phi1's input, per

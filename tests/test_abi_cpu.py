@@ -97,9 +97,9 @@ def test_unknown_precision_rejected(lib):
 
 
 def test_pooling_arguments_checked_before_any_device_work(lib):
-    """Unknown pooling or frequency count -> EINVAL; positional encoding with
-    FP8 -> EUNSUPPORTED; all rejected on the host, before the blob reaches
-    the device."""
+    """Unknown pooling or frequency count -> EINVAL; positional encoding in
+    FP8 beyond the 4 frequencies its operands hold -> EUNSUPPORTED; all
+    rejected on the host, before the blob reaches the device."""
     blob = _blob()
     out = ctypes.c_void_p()
     buf = ctypes.create_string_buffer(blob, len(blob))
@@ -111,8 +111,9 @@ def test_pooling_arguments_checked_before_any_device_work(lib):
     assert load(gl.GN_BF16_FUSED, 2, 0) == gl.GN_EINVAL
     assert load(gl.GN_BF16_FUSED, 0, -1) == gl.GN_EINVAL
     assert load(gl.GN_BF16_FUSED, 0, 11) == gl.GN_EINVAL
-    assert load(gl.GN_FP8_FUSED, 0, 2) == gl.GN_EUNSUPPORTED
+    assert load(gl.GN_FP8_FUSED, 0, 5) == gl.GN_EUNSUPPORTED
     assert "positional encoding" in gl.glassnet_last_error()
+    assert load(gl.GN_FP8_FUSED, 0, 2) == gl.GN_EFORMAT  # a plain blob read as L = 2
     # a plain (L = 0) blob read as L = 1 has the wrong payload size
     assert load(gl.GN_BF16_FUSED, 0, 1) == gl.GN_EFORMAT
     assert "pe_freqs 1" in gl.glassnet_last_error()
