@@ -160,15 +160,32 @@ __device__ __forceinline__ void encode_row_f8(const float (&x)[N], uint32_t inv_
     const float v0 = x0 * lds_f32(inv_s + 8u * p), v1 = x1 * lds_f32(inv_s + 8u * p + 4u);
     sat |= fabsf(v0) > 448.0f || fabsf(v1) > 448.0f;
     put(p, pack_e4m3(v0, v1));
+    // the bands times kFp8BandCode = 2^8 throughout: the double-angle steps
+    // on scaled values (2 s c = (2 / 2^8) s' c', 1 - 2 s^2 = 2^8 - (2 / 2^8)
+    // s'^2 in units of 2^-8) differ from the unscaled ones only by the
+    // exact power-of-two factors
     float sn[2], cs[2];
     const float xs[2] = {x0, x1};
     pe_first(xs, sn, cs);
 #pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      sn[j] *= kFp8BandCode;
+      cs[j] *= kFp8BandCode;
+    }
+    constexpr float k2 = 2.0f / kFp8BandCode;
+#pragma unroll
     for (int f = 0; f < kMaxPeFreqsFused; ++f) {
       if (f < nf) {
-        if (f > 0) pe_double(sn, cs);
-        put((N / 2) * (2 * f + 1) + p, pack_e4m3(kFp8BandCode * sn[0], kFp8BandCode * sn[1]));
-        put((N / 2) * (2 * f + 2) + p, pack_e4m3(kFp8BandCode * cs[0], kFp8BandCode * cs[1]));
+        if (f > 0) {
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const float a = sn[j];
+            sn[j] = k2 * a * cs[j];
+            cs[j] = fmaf(-k2 * a, a, kFp8BandCode);
+          }
+        }
+        put((N / 2) * (2 * f + 1) + p, pack_e4m3(sn[0], sn[1]));
+        put((N / 2) * (2 * f + 2) + p, pack_e4m3(cs[0], cs[1]));
       }
     }
   }
@@ -305,7 +322,12 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
 #pragma unroll
         for (int i = 0; i < kRowsPerLoadLane; ++i) {
           uint32_t w[32];
-          encode_row_f8(x[i], inv_s_t_sm, nf, w, sat);
+          if (__any_sync(0xffffffffu, k < cnt[i])) {
+            encode_row_f8(x[i], inv_s_t_sm, nf, w, sat);
+          } else {  // no row of this warp has slot k: zeros (the loaded values are zeros)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) w[j] = 0u;
+          }
           store_row_k128(sbase + (b ? L::at1 : L::at0), row0 + 32 * i, w);
         }
       } else {
