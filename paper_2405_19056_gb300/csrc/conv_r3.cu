@@ -81,7 +81,8 @@ enum : int {
   C_WEMPTY = C_WFULL + kStagesC,  // + stage: weights consumed (commit)
   C_DFULL = C_WEMPTY + kStagesC,  // + buffer: accumulator pair ready (commit)
   C_DFREE = C_DFULL + 2,          // + buffer: accumulator pair read (epilogue warps)
-  C_COUNT = C_DFREE + 2
+  C_DRAIN = C_DFREE + 2,          // the exit path's last commit
+  C_COUNT = C_DRAIN + 1
 };
 
 constexpr int kConvEpi = 4, kConvMma = 4, kConvWLoad = 5, kConvRLoad = 6, kConvThreads = 7 * 32;
@@ -136,9 +137,15 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       mbar_init(bar(C_DFULL + i), 1);
       mbar_init(bar(C_DFREE + i), kConvEpi);
     }
+    mbar_init(bar(C_DRAIN), 1);
     s_abort = 0;
     fence_mbar_init();
   }
+  // the last copy each loader warp issued per weight stage / halo slot (the
+  // exit path waits for them)
+  int last_wg[kStagesC], last_l[kSlotsC];
+  for (int i = 0; i < kStagesC; ++i) last_wg[i] = -1;
+  for (int i = 0; i < kSlotsC; ++i) last_l[i] = -1;
   if (warp == kConvMma) {
     tmem_alloc(smem_u32(&s_tmem), L::tcols);
     tmem_relinquish();
@@ -164,6 +171,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         for (int q = 0; q < L::kStagesPerTap; ++q) {
           const int g = (j * 9 + tap) * L::kStagesPerTap + q, st = g % kStagesC, u = g / kStagesC;
           if (u > 0 && !warp_wait(bar(C_WEMPTY + st), (u - 1) & 1, &s_abort)) goto done;
+          last_wg[st] = g;
           if (lane == 0) {
             mbar_arrive_expect_tx(bar(C_WFULL + st), L::kStageBytes);
             bulk_g2s(sbase + L::wst + static_cast<uint32_t>(st) * L::kStageBytes,
@@ -181,6 +189,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       if (l >= kSlotsC && !warp_wait(bar(C_FREE + sl), ((l / kSlotsC) - 1) & 1, &s_abort))
         return false;
       const uint32_t dst = slot_addr(l);
+      last_l[sl] = l;
       if (yy < 0 || yy >= h) {  // outside the frame: zeros
         for (uint32_t o = static_cast<uint32_t>(lane) * 16u; o < L::kRowBytes; o += 32u * 16u)
           sts128(dst + o, 0u, 0u, 0u, 0u);
@@ -325,9 +334,29 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     }
   }
 done:
-  if (s_abort && tid == 0) atomicOr(prm.err, kErrTimeout);
   tc_fence_before();
-  __syncthreads();
+  __syncthreads();  // every warp is here: s_abort is final
+  if (s_abort) {
+    // nothing of this CTA may be in flight when it leaves: each loader warp
+    // waits (bounded) for the last copy it issued per stage or slot, the MMA
+    // warp commits every MMA it issued and waits for that
+    if (warp == kConvWLoad && lane == 0) {
+      mbar_wait(bar(C_TAIL), 0, kWaitNs);
+      for (int st = 0; st < kStagesC; ++st)
+        if (last_wg[st] >= 0) mbar_wait(bar(C_WFULL + st), (last_wg[st] / kStagesC) & 1, kWaitNs);
+    }
+    if (warp == kConvRLoad && lane == 0)
+      for (int sl = 0; sl < kSlotsC; ++sl)
+        if (last_l[sl] >= 0) mbar_wait(bar(C_FULL + sl), (last_l[sl] / kSlotsC) & 1, kWaitNs);
+    if (warp == kConvMma) {
+      mma_commit_e(bar(C_DRAIN));
+      __syncwarp();
+      mbar_wait(bar(C_DRAIN), 0, kWaitNs);
+      __syncwarp();
+    }
+    if (tid == 0) report_timeout(prm.err, s_abort, bar_base, kKernelConvR3, 0);
+    __syncthreads();
+  }
   if (warp == kConvMma) {
     tc_fence_after();
     tmem_dealloc(tbase, L::tcols);

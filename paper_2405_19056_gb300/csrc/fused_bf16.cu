@@ -987,7 +987,7 @@ done:
   __syncthreads();  // every warp is here: s_abort is final
   if (s_abort) {
     if (warp == R::MMA) drain_async(bar(B_W), bar(B_DRAIN));
-    if (tid == 0) atomicOr(prm.err, kErrTimeout);
+    if (tid == 0) report_timeout(prm.err, s_abort, bar_base, kKernelFusedBf16, Mode);
   }
   if (warp == R::MMA) {
     tc_fence_after();

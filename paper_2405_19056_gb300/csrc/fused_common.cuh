@@ -128,21 +128,22 @@ __device__ __forceinline__ void pe_double(float (&sn)[N], float (&cs)[N]) {
 }
 
 // Bounded wait shared by a whole warp: every lane waits, then the warp agrees.
-// On a timeout the CTA-wide abort flag is raised and every later wait fails
-// at once, so all warps reach the common exit.
+// On a timeout the CTA-wide abort flag is raised (to the shared-memory
+// address of the barrier that gave up, bit 0 set so that it is never 0) and
+// every later wait fails at once, so all warps reach the common exit.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           uint64_t limit_ns = kWaitNs) {
   bool ok = mbar_try_wait(bar, parity);
   if (!ok) {
-    const uint64_t t0 = globaltimer_ns();
+    const WaitClock clk;
     while (true) {
       if (mbar_try_wait(bar, parity)) {
         ok = true;
         break;
       }
       if (*abort_flag) break;
-      if (globaltimer_ns() - t0 > limit_ns) {
-        *abort_flag = 1;
+      if (clk.expired(limit_ns)) {
+        *abort_flag = static_cast<int>(bar | 1u);
         break;
       }
     }
@@ -162,6 +163,19 @@ __device__ __forceinline__ void drain_async(uint32_t bar_w, uint32_t bar_drain) 
   __syncwarp();
   mbar_wait(bar_drain, 0, kWaitNs);
   __syncwarp();
+}
+
+// Exit-path report of a CTA whose wait gave up: the timeout bit of the error
+// word, and in the second word (the first reporting CTA of an error epoch
+// wins) the kernel, its launch mode and the mbarrier slot that gave up:
+// 1 << 31 | kernel << 16 | mode << 8 | slot.  `abort_val` is the CTA's
+// abort flag, `bar_base` the address of its barrier array.
+__device__ __forceinline__ void report_timeout(uint32_t* err, int abort_val, uint32_t bar_base,
+                                               uint32_t kernel, uint32_t mode) {
+  const uint32_t a = static_cast<uint32_t>(abort_val) & ~1u;
+  const uint32_t slot = a >= bar_base ? (a - bar_base) / 8u : 0xffu;
+  atomicCAS(err + 1, 0u, 0x80000000u | (kernel << 16) | (mode << 8) | (slot & 0xffu));
+  atomicOr(err, kErrTimeout);
 }
 
 // Frame that owns global tile `tile`.

@@ -776,7 +776,7 @@ done:
   __syncthreads();  // every warp is here: s_abort is final
   if (s_abort) {
     if (warp == kMmaC) drain_async(bar(B_W), bar(B_DRAINC));
-    if (tid == 0) atomicOr(prm.err, kErrTimeout);
+    if (tid == 0) report_timeout(prm.err, s_abort, bar_base, kKernelCompact, 0);
   }
   if (warp == kMmaC) {
     tc_fence_after();

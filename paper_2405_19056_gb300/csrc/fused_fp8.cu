@@ -801,7 +801,7 @@ done:
   if (s_abort) {
     // nothing of this CTA may be in flight when its TMEM is freed
     if (warp == kMmaWarp) drain_async(bar(B_W), bar(B_DRAIN8));
-    if (tid == 0) atomicOr(prm.err, kErrTimeout);
+    if (tid == 0) report_timeout(prm.err, s_abort, bar_base, kKernelFusedFp8, 0);
   }
   if (warp == kMmaWarp) {
     tc_fence_after();

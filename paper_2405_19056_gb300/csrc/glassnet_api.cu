@@ -843,13 +843,22 @@ int glassnet_check(const gn_model* m, cudaStream_t s) {
   if (!m) return fail(GN_EINVAL, "model is NULL");
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream");
-  uint32_t bits = 0;
-  if ((e = cudaMemcpy(&bits, m->err, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+  uint32_t words[2] = {0, 0};  // error bits; which wait timed out (report_timeout)
+  if ((e = cudaMemcpy(words, m->err, 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "read error word");
-  if (bits) {
-    if ((e = cudaMemset(m->err, 0, 4)) != cudaSuccess) return cuda_fail(e, "clear error word");
+  const uint32_t bits = words[0];
+  if (bits || words[1]) {
+    if ((e = cudaMemset(m->err, 0, 8)) != cudaSuccess) return cuda_fail(e, "clear error word");
   }
-  if (bits & gn::kErrTimeout) return fail(GN_ETIMEOUT, "a device-side wait timed out");
+  if (bits & gn::kErrTimeout) {
+    const uint32_t w = words[1];
+    if (!(w >> 31)) return fail(GN_ETIMEOUT, "a device-side wait timed out");
+    static const char* const kernels[] = {"?", "fused BF16", "fused FP8", "compacted", "3x3 R"};
+    static const char* const modes[] = {"frame", "accumulate", "resolve"};
+    const uint32_t k = (w >> 16) & 0x7fffu, md = (w >> 8) & 0xffu, slot = w & 0xffu;
+    return fail(GN_ETIMEOUT, "a device-side wait timed out (%s kernel, %s launch, mbarrier slot %u)",
+                k < 5 ? kernels[k] : "?", md < 3 ? modes[md] : "?", slot);
+  }
   if (bits & gn::kErrCount) return fail(GN_EINVAL, "a layer count exceeded K");
   if (bits & gn::kErrRange) return fail(GN_ERANGE, "an exact set-sum left its fixed-point range");
   if (bits & gn::kErrSaturated)

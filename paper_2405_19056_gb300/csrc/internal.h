@@ -29,6 +29,8 @@ constexpr uint32_t kErrCount = 1u;    // layer count above K
 constexpr uint32_t kErrRange = 2u;    // exact set-sum left its fixed-point range
 constexpr uint32_t kErrTimeout = 4u;  // a device wait gave up
 constexpr uint32_t kErrSaturated = 8u;  // an FP8 input beyond its calibrated range (clamped)
+// Kernels named by the second error word after a timeout (report_timeout).
+enum : uint32_t { kKernelFusedBf16 = 1, kKernelFusedFp8 = 2, kKernelCompact = 3, kKernelConvR3 = 4 };
 
 // Linear layers in blob order.
 enum Layer { LF1 = 0, LF2, LPHI1, LPHI2, LRHO, LB1, LB2, LR1, LR2, kLayers };

@@ -168,6 +168,9 @@ def test_compact_timeout_reported_and_next_render_exact(pair):
     gl.glassnet_debug_stall_next_render(m.handle, 20_000)
     m.render(lat, _dev(frame.gbuf), _dev(frame.tbuf), _dev(frame.counts), out)
     assert gl.glassnet_check_code(m.handle) == gl.GN_ETIMEOUT
+    # the report names the kernel, its launch mode and the barrier that gave up
+    # (the stall hook's slot)
+    assert "compacted kernel, frame launch, mbarrier slot 28)" in gl.glassnet_last_error()
     assert gl.glassnet_check_code(m.handle) == gl.GN_OK
     assert np.isnan(out.cpu().numpy()).all()
     assert np.array_equal(render(m, scene, frame), before)

@@ -255,6 +255,9 @@ def test_timeout_reported_and_next_render_exact(widths, request):
     gl.glassnet_debug_stall_next_render(m.handle, 20_000)
     m.render(lat, _dev(frame.gbuf), _dev(frame.tbuf), _dev(frame.counts), out)
     assert gl.glassnet_check_code(m.handle) == gl.GN_ETIMEOUT
+    # the report names the kernel, its launch mode and the barrier that gave up
+    # (the stall hook's slot)
+    assert "fused BF16 kernel, frame launch, mbarrier slot 26)" in gl.glassnet_last_error()
     assert gl.glassnet_check_code(m.handle) == gl.GN_OK  # cleared
     assert np.isnan(out.cpu().numpy()).all()  # no tile ran
     after = render(net, gl.GN_BF16_FUSED, scene, frame)
