@@ -331,12 +331,21 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     if constexpr (Mode != kModeAccumulate) load_g();
     // The operand's release (B_AG_E) also paces the loaders: they are at most
     // one tile ahead, as the two tile-publication barriers need.  Accumulate
-    // launches run no B1: there the MMA warp commits B_AG_E once per tile
-    // after phi2 and no operand is written.
+    // launches run no B1 and write no operand: the loaders still arrive on
+    // B_AG_F once per tile after their wait, and the MMA warp waits for that
+    // arrival before it commits B_AG_E for the tile.  Each commit then follows
+    // the loaders' wait for the previous one, so B_AG_E never completes two
+    // phases ahead of the loaders' parity wait (without the arrival a tile
+    // with no covered pixel let the MMA warp commit two tiles in a row before
+    // the loaders looked, and their wait then missed the phase).
     auto put_ag = [&]() -> bool {
       if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
-      if constexpr (Mode == kModeAccumulate) return true;
+      if constexpr (Mode == kModeAccumulate) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_AG_F));
+        return true;
+      }
       const uint32_t one = pack_bf16(1.0f, 1.0f);
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
@@ -593,10 +602,13 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // B_AG_E paces the loaders (see loader_loop), once every epilogue
         // warp has taken this tile (a tile without covered pixels involves
         // no epilogue work, and the loaders must not get two tiles ahead of
-        // the epilogue either)
+        // the epilogue either) and the loaders have passed their wait for
+        // the previous commit (B_AG_F)
         // (two alternating barriers: the epilogue cannot take tile tb + 2
         // before this commit, so neither runs two phases ahead)
         if (!warp_wait(bar(B_H + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
+        if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        ++n_agf;
         mma_commit_e(bar(B_AG_E));
         __syncwarp();
         if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;

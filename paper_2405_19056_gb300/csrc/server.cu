@@ -56,7 +56,9 @@ struct Lane {
   uint8_t* arena = nullptr;
   gn_latent latent;  // lane-private latent (device)
   std::map<Bucket, gn_graph*> graphs;
-  bool busy = false;
+  bool busy = false;    // holds a job (set by the dispatcher before it enqueues the job's work)
+  bool issued = false;  // the job's work and its `done` event are enqueued: only then is the
+                        // event the job's own (before, it still holds the previous job's)
   uint64_t ticket = 0;
 };
 
@@ -203,6 +205,8 @@ void gn_server::dispatch_loop() {
       lane.busy = false;
       bytes_in_flight -= job.bytes;
       scenes[job.scene_slot].in_flight--;
+    } else {
+      lane.issued = true;  // the completer may query the lane's event from now on
     }
     cv.notify_all();
   }
@@ -217,12 +221,12 @@ void gn_server::complete_loop() {
       cv.wait(lk, [&] {
         if (stop) return true;
         for (const Lane& l : lanes)
-          if (l.busy) return true;
+          if (l.busy && l.issued) return true;
         return false;
       });
       if (stop) return;
       for (size_t i = 0; i < lanes.size(); ++i)
-        if (lanes[i].busy) busy.push_back(static_cast<int>(i));
+        if (lanes[i].busy && lanes[i].issued) busy.push_back(static_cast<int>(i));
     }
     bool any = false;
     for (int i : busy) {
@@ -242,6 +246,7 @@ void gn_server::complete_loop() {
       bytes_in_flight -= job.bytes;
       scenes[job.scene_slot].in_flight--;
       lane.busy = false;
+      lane.issued = false;
       cv.notify_all();
     }
     if (!any) std::this_thread::sleep_for(std::chrono::microseconds(20));

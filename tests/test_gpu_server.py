@@ -71,6 +71,33 @@ def test_mixed_requests_equal_alone(model):
         assert np.array_equal(r["out"].numpy(), _alone(model, latents[r["scene"]], r)), i
 
 
+def test_many_requests_in_flight_each_equal_alone(model):
+    """300 requests of one size submitted at once, K alternating 8 and 1, four
+    lanes: a lane's arena then holds a K = 8 layer buffer where the next
+    K = 1 request keeps its counts, so a lane handed a new request before its
+    previous one had finished would mix them (and report a count above K).
+    A lane is free again only after its own request's event completed: every
+    image equals its request rendered alone and no device error is set."""
+    scene = 21
+    reqs = []
+    for i in range(300):
+        K = 8 if i % 2 == 0 else 1
+        f = synth.make_frame(96, 96, K, counts="all", seed=900 + i % 6)
+        reqs.append(dict(scene=0, h=96, w=96, K=K, g=_pin(f.gbuf), t=_pin(f.tbuf), c=_pin(f.counts),
+                         out=torch.full((3, 96, 96), float("nan")).pin_memory()))
+    lats, stats = _serve(model, reqs, [scene], n_streams=4, max_scenes=2, max_h=96, max_w=96,
+                         max_K=8)
+    model.check()
+    assert stats["completed"] == 300
+    lat = model.encode(synth.make_scene(scene))
+    alone = {}
+    for i, r in enumerate(reqs):
+        key = (r["K"], i % 6)
+        if key not in alone:
+            alone[key] = _alone(model, lat, r)
+        assert np.array_equal(r["out"].numpy(), alone[key]), i
+
+
 def test_budget_of_one_request_serialises_admission(model):
     reqs = _requests(10, seed=2, n_scenes=1)
     one = 128 * 128 * (14 * 4 + 12 * 4 * 8 + 1 + 3 * 4) + 4 * 256  # the largest request, padded

@@ -144,6 +144,31 @@ def test_layer_limit_and_reset(net):
         gl.glassnet_pool_free(pool)
 
 
+def test_accumulates_over_alternating_empty_tiles(net):
+    """Accumulate launches whose tiles alternate between a few covered pixels
+    and none (the tiles without covered pixels involve no MMA): 30 streamed
+    frames of 8 layers at 512x512, each resolved and checked.  The loaders'
+    pacing barrier must never complete two phases ahead of their wait, however
+    fast the empty tiles go by (a device wait that gives up is reported as
+    GN_ETIMEOUT by the check); every frame equals the one-shot render."""
+    _, m, lat = net
+    h = w = 512
+    f = synth.make_frame(h, w, 8, counts="all", seed=56)
+    cnt = np.zeros((h, w), dtype=np.uint8)
+    flat = cnt.reshape(-1)
+    for t0 in range(0, h * w, 256):  # even 128-pixel tiles: 3 covered pixels, odd tiles: none
+        flat[t0 + 5] = flat[t0 + 60] = flat[t0 + 127] = 8
+    f = synth.Frame(gbuf=f.gbuf, tbuf=f.tbuf, counts=cnt)
+    want = _render(m, lat, f)
+    pool = gl.glassnet_pool_create(m.handle, h, w)
+    try:
+        for _ in range(30):
+            gl.glassnet_pool_reset(pool)
+            assert np.array_equal(_stream(m, lat, f, range(8), pool=pool), want)
+    finally:
+        gl.glassnet_pool_free(pool)
+
+
 def test_coverage_above_one_is_reported(net):
     _, m, lat = net
     f = synth.make_frame(16, 16, 1, counts="all", seed=55)
