@@ -914,7 +914,8 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
                 used[r] += 1
                 tickets.append(gl.glassnet_server_submit(srv, ids[int(sc[i])], p["g"], p["t"],
                                                          p["c"][K], K, r, r, out))
-            lats = np.array([gl.glassnet_server_wait(srv, t) for t in tickets])
+            parts = [gl.glassnet_server_wait_times(srv, t) for t in tickets]
+            lats = np.array([p["total_ms"] for p in parts])
             wall = time.perf_counter() - t0
             st = gl.glassnet_server_stats(srv)
         finally:
@@ -930,7 +931,13 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
                         "p99_ms_by_size": {int(r): float(np.percentile(lats[res == r], 99))
                                            for r in sizes if np.any(res == r)},
                         "p99_ms_by_quarter": [float(np.percentile(x, 99))
-                                              for x in np.array_split(lats, 4)]})
+                                              for x in np.array_split(lats, 4)],
+                        # the latency's parts: queue (lane and budget), enqueue of
+                        # copies and graph, device (copies, kernels, read-back, polling)
+                        "parts_ms": {k: {"p50": float(np.percentile([p[k] for p in parts], 50)),
+                                         "p99": float(np.percentile([p[k] for p in parts], 99))}
+                                     for k in ("queue_ms", "enqueue_ms", "device_ms", "copy_in_ms",
+                                               "render_ms", "copy_out_ms")}})
     gl.glassnet_check(model.handle)
     plain = fp32_plain_serving(weights, rates, n_requests, pool, scenes, seed)
     for r_bf, r_fp in zip(results, plain):

@@ -428,6 +428,20 @@ int glassnet_server_add_scene(gn_server* server, const float* scene, int* scene_
 int glassnet_server_prepare(gn_server* server, int h, int w, int K);
 int glassnet_server_submit(gn_server* server, const gn_request* request, uint64_t* ticket);
 int glassnet_server_wait(gn_server* server, uint64_t ticket, double* latency_ms);
+/* Where a request's latency went (milliseconds).  Host clock: waiting in
+ * the queue for a lane and the budget, enqueueing its copies and graph on
+ * the lane's stream, and from then until the completion thread saw the
+ * lane's event (device_ms); total = the sum, as glassnet_server_wait reports
+ * it.  Device clock (CUDA events on the lane's stream), the parts of
+ * device_ms: copies of the latent and the inputs (including any wait for a
+ * copy engine), the plan and fused kernels (including any wait for SMs) and
+ * the read-back of the image. */
+typedef struct gn_request_times {
+  double queue_ms, enqueue_ms, device_ms, total_ms;
+  double copy_in_ms, render_ms, copy_out_ms;
+} gn_request_times;
+/* As glassnet_server_wait, with the latency's parts. */
+int glassnet_server_wait_times(gn_server* server, uint64_t ticket, gn_request_times* times);
 int glassnet_server_stats(gn_server* server, gn_server_stats* stats);
 void glassnet_server_destroy(gn_server* server);
 

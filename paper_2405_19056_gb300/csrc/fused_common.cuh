@@ -135,14 +135,14 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
                                           uint64_t limit_ns = kWaitNs) {
   bool ok = mbar_try_wait(bar, parity);
   if (!ok) {
-    const WaitClock clk;
+    const uint64_t t0 = globaltimer_ns();
     while (true) {
       if (mbar_try_wait(bar, parity)) {
         ok = true;
         break;
       }
       if (*abort_flag) break;
-      if (clk.expired(limit_ns)) {
+      if (globaltimer_ns() - t0 > limit_ns) {
         *abort_flag = static_cast<int>(bar | 1u);
         break;
       }

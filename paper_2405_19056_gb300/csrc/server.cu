@@ -53,6 +53,9 @@ struct ArenaMap {
 struct Lane {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
+  // timing marks of the request in flight: work started, inputs on the
+  // device, image rendered (`done`: image in host memory)
+  cudaEvent_t t_start = nullptr, t_in = nullptr, t_kern = nullptr;
   uint8_t* arena = nullptr;
   gn_latent latent;  // lane-private latent (device)
   std::map<Bucket, gn_graph*> graphs;
@@ -64,12 +67,13 @@ struct Lane {
 
 struct Job {
   gn_request req;
-  Clock::time_point t_submit;
+  Clock::time_point t_submit, t_dispatch, t_issued;  // submitted, taken by the dispatcher, enqueued
   size_t bytes = 0;
   int scene_slot = -1;
   bool done = false;
   int status = GN_OK;
   double latency_ms = 0.0;
+  gn_request_times times = {};
 };
 
 // A scene slot is empty (id < 0, not encoding), resident (id >= 0) or being
@@ -150,8 +154,10 @@ int gn_server::issue(Lane& lane, Job& job) {
   const int grc = gn_server_bucket_graph(model, lane, bk, &it);
   if (grc != GN_OK) return grc;
   const size_t P = static_cast<size_t>(r.h) * r.w;
-  cudaError_t e = cudaMemcpyAsync(lane.latent.d, scenes[job.scene_slot].latent->d, latent_bytes,
-                                  cudaMemcpyDeviceToDevice, lane.stream);
+  cudaError_t e = cudaEventRecord(lane.t_start, lane.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(lane.latent.d, scenes[job.scene_slot].latent->d, latent_bytes,
+                        cudaMemcpyDeviceToDevice, lane.stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(lane.arena + am.gbuf, r.gbuf, P * gn::kGC * 4, cudaMemcpyHostToDevice,
                         lane.stream);
@@ -161,11 +167,14 @@ int gn_server::issue(Lane& lane, Job& job) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(lane.arena + am.counts, r.layer_count, P, cudaMemcpyHostToDevice,
                         lane.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(lane.t_in, lane.stream);
   if (e != cudaSuccess) return err(GN_ECUDA, "request copies: %s", cudaGetErrorString(e));
   int rc = glassnet_graph_launch(it->second, lane.stream);
   if (rc != GN_OK) return rc;
-  e = cudaMemcpyAsync(r.out, lane.arena + am.out, P * gn::kOut * 4, cudaMemcpyDeviceToHost,
-                      lane.stream);
+  e = cudaEventRecord(lane.t_kern, lane.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(r.out, lane.arena + am.out, P * gn::kOut * 4, cudaMemcpyDeviceToHost,
+                        lane.stream);
   if (e == cudaSuccess) e = cudaEventRecord(lane.done, lane.stream);
   if (e != cudaSuccess) return err(GN_ECUDA, "result copy: %s", cudaGetErrorString(e));
   return GN_OK;
@@ -192,6 +201,7 @@ void gn_server::dispatch_loop() {
     const uint64_t t = queue.front();
     queue.pop_front();
     Job& job = jobs[t];
+    job.t_dispatch = Clock::now();
     Lane& lane = lanes[free_lane];
     lane.busy = true;
     lane.ticket = t;
@@ -206,6 +216,7 @@ void gn_server::dispatch_loop() {
       bytes_in_flight -= job.bytes;
       scenes[job.scene_slot].in_flight--;
     } else {
+      job.t_issued = Clock::now();
       lane.issued = true;  // the completer may query the lane's event from now on
     }
     cv.notify_all();
@@ -238,7 +249,22 @@ void gn_server::complete_loop() {
       Lane& lane = lanes[i];
       Job& job = jobs[lane.ticket];
       job.status = q == cudaSuccess ? GN_OK : GN_ECUDA;
-      job.latency_ms = std::chrono::duration<double, std::milli>(now - job.t_submit).count();
+      auto ms = [](Clock::time_point a, Clock::time_point b) {
+        return std::chrono::duration<double, std::milli>(b - a).count();
+      };
+      job.latency_ms = ms(job.t_submit, now);
+      job.times.queue_ms = ms(job.t_submit, job.t_dispatch);
+      job.times.enqueue_ms = ms(job.t_dispatch, job.t_issued);
+      job.times.device_ms = ms(job.t_issued, now);
+      job.times.total_ms = job.latency_ms;
+      float a = 0.0f, b = 0.0f, c = 0.0f;  // device timeline of the lane's stream
+      if (q == cudaSuccess && cudaEventElapsedTime(&a, lane.t_start, lane.t_in) == cudaSuccess &&
+          cudaEventElapsedTime(&b, lane.t_in, lane.t_kern) == cudaSuccess &&
+          cudaEventElapsedTime(&c, lane.t_kern, lane.done) == cudaSuccess) {
+        job.times.copy_in_ms = a;
+        job.times.render_ms = b;
+        job.times.copy_out_ms = c;
+      }
       job.done = true;
       latencies.push_back(job.latency_ms);
       ++completed;
@@ -277,7 +303,8 @@ int glassnet_server_create(gn_model* m, const gn_server_config* cfg, gn_server**
     l.latent.H = m->H;
     l.latent.Z = m->Z;
     if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&l.done) != cudaSuccess || cudaEventCreate(&l.t_start) != cudaSuccess ||
+        cudaEventCreate(&l.t_in) != cudaSuccess || cudaEventCreate(&l.t_kern) != cudaSuccess ||
         cudaMalloc(&l.arena, arena) != cudaSuccess ||
         cudaMalloc(&l.latent.d, s->latent_bytes) != cudaSuccess) {
       glassnet_server_destroy(s);
@@ -407,7 +434,7 @@ int glassnet_server_submit(gn_server* s, const gn_request* req, uint64_t* ticket
   return GN_OK;
 }
 
-int glassnet_server_wait(gn_server* s, uint64_t ticket, double* latency_ms) {
+int glassnet_server_wait_times(gn_server* s, uint64_t ticket, gn_request_times* times) {
   if (!s) return gn::set_error(GN_EINVAL, "server is NULL");
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->jobs.find(ticket);
@@ -415,10 +442,17 @@ int glassnet_server_wait(gn_server* s, uint64_t ticket, double* latency_ms) {
   s->cv.wait(lk, [&] { return it->second.done || s->stop; });
   if (!it->second.done) return gn::set_error(GN_EINVAL, "server stopped");
   const int rc = it->second.status;
-  if (latency_ms) *latency_ms = it->second.latency_ms;
+  if (times) *times = it->second.times;
   s->jobs.erase(it);
   if (rc != GN_OK) return gn::set_error(rc, "request failed on the device");
   return GN_OK;
+}
+
+int glassnet_server_wait(gn_server* s, uint64_t ticket, double* latency_ms) {
+  gn_request_times t;
+  const int rc = glassnet_server_wait_times(s, ticket, &t);
+  if (rc == GN_OK && latency_ms) *latency_ms = t.total_ms;
+  return rc;
 }
 
 int glassnet_server_stats(gn_server* s, gn_server_stats* out) {
@@ -468,6 +502,9 @@ void glassnet_server_destroy(gn_server* s) {
     if (l.arena) cudaFree(l.arena);
     if (l.latent.d) cudaFree(l.latent.d);
     if (l.done) cudaEventDestroy(l.done);
+    if (l.t_start) cudaEventDestroy(l.t_start);
+    if (l.t_in) cudaEventDestroy(l.t_in);
+    if (l.t_kern) cudaEventDestroy(l.t_kern);
     if (l.stream) cudaStreamDestroy(l.stream);
   }
   for (Scene& sc : s->scenes)

@@ -48,31 +48,15 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ uint64_t sm_cycles() {
-  uint64_t c;
-  asm volatile("mov.u64 %0, %%clock64;" : "=l"(c));
-  return c;
-}
-// Deadline of a bounded wait: `limit_ns` has passed on the global nanosecond
-// timer AND `limit_ns` cycles on this SM's own counter (at most 2.07 GHz, so
-// at least half the limit in wall time), so that a step of the global timer
-// cannot end a wait early.
-struct WaitClock {
-  uint64_t t0, c0;
-  __device__ __forceinline__ WaitClock() : t0(globaltimer_ns()), c0(sm_cycles()) {}
-  __device__ __forceinline__ bool expired(uint64_t limit_ns) const {
-    return globaltimer_ns() - t0 > limit_ns && sm_cycles() - c0 > limit_ns;
-  }
-};
 // Waits for the phase with the given parity to complete.  Gives up after
-// `timeout_ns` (WaitClock) and returns false; the caller records the error
+// `timeout_ns` of wall time and returns false; the caller records the error
 // and leaves the kernel without issuing further work.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
   if (mbar_try_wait(bar, parity)) return true;
-  const WaitClock clk;
+  const uint64_t t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (clk.expired(timeout_ns)) return false;
+    if (globaltimer_ns() - t0 > timeout_ns) return false;
   }
 }
 

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "glassnet_server_prepare": (_I, [_P, _I, _I, _I]),
     "glassnet_server_submit": (_I, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "glassnet_server_wait": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "glassnet_server_wait_times": (_I, [_P, ctypes.c_uint64, _P]),
     "glassnet_server_stats": (_I, [_P, _P]),
     "glassnet_server_destroy": (None, [_P]),
     "glassnet_pool_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
@@ -360,6 +361,20 @@ def glassnet_server_wait(server, ticket) -> float:
     lat = ctypes.c_double()
     _check(_lib().glassnet_server_wait(server, ticket, ctypes.byref(lat)))
     return lat.value
+
+
+class GnRequestTimes(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("enqueue_ms", ctypes.c_double),
+                ("device_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("copy_in_ms", ctypes.c_double), ("render_ms", ctypes.c_double),
+                ("copy_out_ms", ctypes.c_double)]
+
+
+def glassnet_server_wait_times(server, ticket) -> dict:
+    """As glassnet_server_wait, returning the latency's parts (milliseconds)."""
+    t = GnRequestTimes()
+    _check(_lib().glassnet_server_wait_times(server, ticket, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in GnRequestTimes._fields_}
 
 
 def glassnet_server_stats(server) -> dict:
