@@ -882,6 +882,16 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
         e1.synchronize()
         best_ms = min(best_ms, e0.elapsed_time(e1))
     h2d_gbs = big.numel() * 4 / (best_ms * 1e-3) / 1e9
+    # the same copy alone, 100 times 20 ms apart (no server): the link's own
+    # latency distribution for the largest request's inputs
+    alone_ms = []
+    for _ in range(100):
+        e0.record()
+        dst.copy_(big, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        alone_ms.append(e0.elapsed_time(e1))
+        time.sleep(0.02)
     del dst
     results = []
     for rate in rates:
@@ -948,6 +958,9 @@ def serving_leg(model, weights, rates, n_requests, n_streams=4, seed=0):
                         f"{n_streams} lanes; open-loop generator",
             "api": "glassnet_server_submit / _wait", "rates": results,
             "h2d_gbs": h2d_gbs, "h2d_pinned": bool(big.is_pinned()),
+            "h2d_alone_402MB_ms": {"p50": float(np.percentile(alone_ms, 50)),
+                                   "p99": float(np.percentile(alone_ms, 99)),
+                                   "max": float(np.max(alone_ms)), "copies": len(alone_ms)},
             "fp32_plain_served_one_at_a_time": plain}
 
 
