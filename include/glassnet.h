@@ -150,11 +150,13 @@ typedef struct gn_model_config {
  *   accumulator as the mean (range [0, 2^11) per pixel-channel, GN_ERANGE
  *   beyond it), so the BF16 result is bit-identical under any order of a
  *   pixel's layers.
- * Positional encoding: pe_freqs 0..10 for GN_FP32_PLAIN; 0..4 at H = 64 for
- *   GN_BF16_FUSED (the encoded operands fill the fused kernel's shared
- *   memory; H = 128 with pe_freqs > 0 is GN_EUNSUPPORTED); 0..4 at H = 64
- *   and H = 128 for GN_FP8_FUSED with the 1x1 R (E4M3 operands take half the
- *   bytes).  The fused kernels compute sin(pi x) and cos(pi x) of each input
+ * Positional encoding: pe_freqs 0..10 for GN_FP32_PLAIN; 0..4 at H = 64 and
+ *   H = 128 for GN_BF16_FUSED (the encoded operands are sized for 4; at
+ *   H = 128 they and the resident weights fill the shared memory, so the
+ *   per-pixel weights stream from device memory through a two-stage ring
+ *   in each CTA, with the same arithmetic); 0..4 at H = 64 and H = 128 for
+ *   GN_FP8_FUSED with the 1x1 R (E4M3 operands take half the bytes).
+ *   The fused kernels compute sin(pi x) and cos(pi x) of each input
  *   channel with exact argument reduction and the higher bands by the
  *   double-angle identities in FP32, then round every band to BF16, or to
  *   E4M3: band 0 as codes of its channel's calibrated scale, the sine and

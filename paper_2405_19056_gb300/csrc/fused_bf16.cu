@@ -90,7 +90,10 @@ using namespace fused;
 constexpr int B_H = B_COUNT;  // + half: K half of the next per-pixel A operand written
 constexpr int B_STALL = B_COUNT + 2;  // never arrived on: the stall that tests the timeout path
 constexpr int B_DRAIN = B_COUNT + 3;  // the exit path's last commit
-constexpr int B_COUNT_B = B_COUNT + 4;
+// Streamed per-pixel weights (doubled widths with encoding): + stage (2).
+constexpr int B_WF = B_COUNT + 4;  // ring stage filled (transaction count)
+constexpr int B_WE = B_COUNT + 6;  // ring stage read by its MMAs (commit)
+constexpr int B_COUNT_B = B_COUNT + 8;
 
 // TMEM column map (128 lanes x 4H columns of 32 bits): three accumulator
 // buffers of H columns, then U (H bf16 = H/2 columns) double buffered.  The
@@ -187,23 +190,26 @@ __device__ __forceinline__ void pe_chunks(uint32_t a, const float (&v)[N], int n
 
 // Encoded layer operand: band 0 as store_slot writes it (channels 0-7, then
 // 8-11 and the constant-one pair), then the nf frequencies' sine and cosine
-// bands, one core-matrix column of channels at a time.  With one row per
-// lane the encoding's code stays small enough that the loaders do not evict
-// the epilogue's loops from the instruction cache (the same code unrolled
-// over two rows per lane measured 40 % slower), and four loader warps, one
-// per SM sub-partition, share the encoding work.
+// bands, one core-matrix column of channels at a time.  The encoding's code
+// is kept small, so that the loaders do not evict the epilogue's loops from
+// the instruction cache (the same code unrolled over two rows per lane
+// measured 40 % slower at H = 64): one row per lane there, with four loader
+// warps, one per SM sub-partition, sharing the encoding work; with two rows
+// per lane (the doubled widths) a loop over the rows, each row's values
+// picked by selects (an indexed register array would go to local memory).
 template <int RPL>
 __device__ __forceinline__ void store_slot_pe(uint32_t base, int row0, const float (&x)[RPL][kTC],
                                               int nf) {
-  static_assert(RPL == 1, "one row per loader lane with positional encoding");
+  static_assert(RPL == 1 || RPL == 2, "one or two rows per loader lane with encoding");
   const uint32_t one = pack_bf16(1.0f, 1.0f);
-  {
-    const uint32_t r = base + static_cast<uint32_t>(row0) * 16u;
+#pragma unroll 1
+  for (int i = 0; i < RPL; ++i) {
+    const uint32_t r = base + static_cast<uint32_t>(row0 + 32 * i) * 16u;
     float lo[8], hi[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) lo[j] = x[0][j];
+    for (int j = 0; j < 8; ++j) lo[j] = i == 0 ? x[0][j] : x[RPL - 1][j];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) hi[j] = x[0][8 + j];
+    for (int j = 0; j < 4; ++j) hi[j] = i == 0 ? x[0][8 + j] : x[RPL - 1][8 + j];
     sts_chunk(r, lo);
     sts128(r + 2048u, pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), one, 0u);
     pe_chunks(r, lo, nf);
@@ -223,16 +229,24 @@ enum : int { kModeFrame = 0, kModeAccumulate = 1, kModeResolve = 2 };
 // encoding) run one epilogue warp per TMEM lane quadrant (7 warps) and two
 // CTAs per SM: each CTA holds 74 KB of shared memory and 256 TMEM columns,
 // and the SM interleaves two tiles' hand-off chains.
+//
+// The doubled widths with encoding stream their per-pixel weights (kStream,
+// FusedLayout<128, true>): two loader warps that also encode (two rows per
+// lane), and one more warp that fills the weight ring (12 warps, three per
+// SM sub-partition, as the pool state of two epilogue warps per lane
+// quadrant needs).
 template <int H, bool PE>
 struct Roles {
   static constexpr bool kPair = H == 64 && !PE;
+  static constexpr bool kStream = FusedLayout<H, PE>::kStream;
   static constexpr int EW = kPair ? 1 : kEW;  // epilogue warps per lane quadrant
   static constexpr int EPI = 4 * EW;          // epilogue warps 0 .. EPI - 1
   static constexpr int MMA = 4 * EW;          // the MMA warp
   static constexpr int LOAD0 = 4 * EW + 1;    // the first loader warp
-  static constexpr int LW = PE ? 4 : kLoadWarps;
+  static constexpr int LW = PE && !kStream ? 4 : kLoadWarps;
+  static constexpr int PROD = kStream ? LOAD0 + LW : -1;  // the weight-ring warp
   static constexpr int RPL = kTile / (LW * 32);
-  static constexpr int kThreads = (4 * EW + 1 + LW) * 32;
+  static constexpr int kThreads = (4 * EW + 1 + LW + (kStream ? 1 : 0)) * 32;
   static constexpr int kCtasPerSm = kPair ? 2 : 1;
   static_assert(LW <= kMaxLoadWarps && RPL * LW * 32 == kTile, "loader rows must cover the tile");
 };
@@ -392,6 +406,64 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
   }
 }
 
+// Ring stage s of the streamed per-pixel weights (FusedLayout<128, true>).
+template <class L>
+__device__ __forceinline__ uint32_t ring_stage(int s) {
+  if constexpr (L::kStream) return s ? L::ring1 : L::ring0;
+  else return 0;
+}
+
+// Weight-ring warp of the streamed layout: per tile, the per-pixel weight
+// chunks in the order the MMA warp consumes them (rho's four K = 64 chunks
+// unless Sum; B1's G-buffer bands 1.. (four bands a chunk) and its two r
+// chunks; B2's two; R1's two and R2 unless R3), each into the next of the two
+// stages once the MMAs that read that stage's previous chunk have completed.
+// It follows the tiles the loaders publish and ends with the last; every
+// copy it issued has landed before it leaves, so none is in flight when the
+// CTA exits.
+template <int H, bool Sum, bool R3>
+__device__ __forceinline__ void ring_loop(const FusedParams& prm, const uint8_t* wimg,
+                                          uint32_t sbase, uint32_t bar_base, LoaderShared& ls,
+                                          volatile int* abort_flag, int lane) {
+  using L = FusedLayout<H, true>;
+  auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
+  const int nb = 1 + 2 * prm.pe_freqs;
+  uint32_t n = 0, last[2] = {0, 0};
+  bool used[2] = {false, false};
+  auto fill = [&](uint32_t off, uint32_t bytes) -> bool {
+    const uint32_t st = n & 1;
+    if (!warp_wait(bar(B_WE + st), ((n >> 1) & 1) ^ 1, abort_flag)) return false;
+    if (lane == 0) {
+      mbar_arrive_expect_tx(bar(B_WF + st), bytes);
+      bulk_g2s(sbase + ring_stage<L>(st), wimg + off, bytes, bar(B_WF + st));
+    }
+    __syncwarp();
+    last[st] = n;
+    used[st] = true;
+    ++n;
+    return true;
+  };
+  bool ok = true;
+  for (uint32_t tb = 0; ok; ++tb) {
+    if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) break;
+    if (*reinterpret_cast<volatile int*>(&ls.tile[tb & 1]) >= prm.total_tiles) break;
+    if constexpr (!Sum)
+      for (uint32_t q = 0; ok && q < 4; ++q) ok = fill(L::img_rho + q * L::kChunk, L::kChunk);
+    for (int t0 = 1; ok && t0 < nb; t0 += 4)
+      ok = fill(L::img_b1g + static_cast<uint32_t>((t0 - 1) / 4) * L::kChunk,
+                static_cast<uint32_t>(min(4, nb - t0)) * 4096u);
+    for (uint32_t q = 0; ok && q < 2; ++q) ok = fill(L::img_b1r + q * L::kChunk, L::kChunk);
+    for (uint32_t q = 0; ok && q < 2; ++q) ok = fill(L::img_b2 + q * L::kChunk, L::kChunk);
+    if constexpr (!R3) {
+      for (uint32_t q = 0; ok && q < 2; ++q) ok = fill(L::img_r1 + q * L::kChunk, L::kChunk);
+      if (ok) ok = fill(L::img_r2, H * L::NR2 * 2);
+    }
+  }
+  for (int st = 0; st < 2; ++st)
+    if (used[st]) mbar_wait(bar(B_WF + st), (last[st] >> 1) & 1, kWaitNs);
+  __syncwarp();
+}
+
 // ------------------------------------------------------------------ kernel
 // Sum: the paper's own form of Eq. 5, tau = sum of the valid layers' phi
 // outputs entering B1 directly (no rho).  tau is the same fixed-point sum as
@@ -433,6 +505,10 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     mbar_init(bar(B_DR2), 1);
     mbar_init(bar(B_STALL), 1);
     mbar_init(bar(B_DRAIN), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(B_WF + b), 1);
+      mbar_init(bar(B_WE + b), 1);
+    }
     mbar_init(bar(B_AG_F), Roles<H, PE>::LW);
     mbar_init(bar(B_AG_E), 1);
     for (int b = 0; b < 2; ++b) {
@@ -460,7 +536,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
   tc_fence_after();
   const uint32_t tbase = s_tmem;
 
-  if (warp >= R::LOAD0) {
+  if (warp >= R::LOAD0 && warp < R::LOAD0 + R::LW) {
     // the constant [1, 1, 0, ...] operand that multiplies phi2's bias rows
     for (int r = (warp - R::LOAD0) * 32 + lane; r < kTile; r += Roles<H, PE>::LW * 32) {
       sts128(sbase + L::aone + r * 16u, pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
@@ -469,6 +545,10 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     fence_proxy_async_smem();
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
     loader_loop<H, Mode, PE>(prm, sbase, bar_base, s_ld, &s_abort, warp - R::LOAD0, lane);
+  } else if (R::kStream && warp == R::PROD) {
+    // ------------------------------------------------------ weight-ring warp
+    if constexpr (R::kStream && Mode != kModeAccumulate)
+      ring_loop<H, Sum, R3>(prm, wimg, sbase, bar_base, s_ld, &s_abort, lane);
   } else if (warp == R::MMA) {
     // ------------------------------------------------------------ MMA warp
     if (lane == 0) {
@@ -485,11 +565,33 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     const uint64_t dsc_phi1 = make_sdesc(sbase + L::phi1, H * 16, 128);
     const uint64_t dsc_phi2 = make_sdesc(sbase + L::phi2, H * 16, 128);
     const uint64_t dsc_phi2b = make_sdesc(sbase + L::phi2b, H * 16, 128);
-    const uint64_t dsc_rho = make_sdesc(sbase + L::rho, H * 16, 128);
     const uint64_t dsc_b1 = make_sdesc(sbase + L::b1, H * 16, 128);
-    const uint64_t dsc_b2 = make_sdesc(sbase + L::b2, H * 16, 128);
-    const uint64_t dsc_r1 = make_sdesc(sbase + L::r1, H * 16, 128);
-    const uint64_t dsc_r2 = make_sdesc(sbase + L::r2, 16 * 16, 128);
+    // per-pixel weights: resident, or (streamed layout) the ring's two stages
+    uint64_t dsc_rho = 0, dsc_b2 = 0, dsc_r1 = 0, dsc_r2 = 0;
+    if constexpr (!L::kStream) {
+      dsc_rho = make_sdesc(sbase + L::rho, H * 16, 128);
+      dsc_b2 = make_sdesc(sbase + L::b2, H * 16, 128);
+      dsc_r1 = make_sdesc(sbase + L::r1, H * 16, 128);
+      dsc_r2 = make_sdesc(sbase + L::r2, 16 * 16, 128);
+    }
+    const uint64_t dsc_ring[2] = {make_sdesc(sbase + ring_stage<L>(0), H * 16, 128),
+                                  make_sdesc(sbase + ring_stage<L>(1), H * 16, 128)};
+    const uint64_t dsc_ring16[2] = {make_sdesc(sbase + ring_stage<L>(0), 16 * 16, 128),
+                                    make_sdesc(sbase + ring_stage<L>(1), 16 * 16, 128)};
+    uint32_t n_ck = 0;  // ring chunks taken
+    // the next chunk is in its stage: its descriptor (N = H, or N = 16 for R2)
+    auto ck_wait = [&](uint64_t& d, bool n16) -> bool {
+      const uint32_t st = n_ck & 1;
+      if (!warp_wait(bar(B_WF + st), (n_ck >> 1) & 1, &s_abort)) return false;
+      d = n16 ? dsc_ring16[st] : dsc_ring[st];
+      return true;
+    };
+    // its MMAs are issued: the stage is free once they complete
+    auto ck_done = [&]() {
+      mma_commit_e(bar(B_WE + (n_ck & 1)));
+      __syncwarp();
+      ++n_ck;
+    };
     const uint64_t dsc_at0 = make_sdesc(sbase + L::at0, 128 * 16, 128);
     const uint64_t dsc_at1 = make_sdesc(sbase + L::at1, 128 * 16, 128);
     const uint64_t dsc_one = make_sdesc(sbase + L::aone, 128 * 16, 128);
@@ -626,6 +728,63 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         const uint32_t Z = tbase + T::buf(p1.b == 0 ? 2 : p1.b - 1);
         const uint32_t A_LO = tbase + T::APOOL, A_HI = tbase + T::APOOL + H / 2;
         constexpr uint64_t kHalfK = static_cast<uint64_t>(H / 32) * ((2 * H * 16) >> 4);
+        if constexpr (L::kStream) {
+        // The same GEMMs with the weights from the ring, one K = 64 chunk per
+        // half of a K half (the producer's order, ring_loop).  B1's G-buffer
+        // band 0 (with the folded bias) is resident.
+        auto half = [&](uint32_t acc, uint32_t a, bool accum) -> bool {
+          uint64_t d;
+          if (!ck_wait(d, false)) return false;
+          issue_gemm<H, H / 2>(acc, a, d, idH, accum);
+          ck_done();
+          return true;
+        };
+        if constexpr (!Sum) {
+          if (!wait_h(0) || !half(X, A_LO, false) || !half(X, A_LO + H / 4, true)) goto done;
+          if (!wait_h(1) || !half(X, A_HI, true) || !half(X, A_HI + H / 4, true)) goto done;
+          mma_commit_e(bar(B_DP));
+          __syncwarp();
+        }
+        if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
+        if (!wait_h(0)) goto done;
+        if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        ++n_agf;
+        tc_fence_after();
+        mma_f16_ss_e(Y, dsc_ag, dsc_b1, idH, 0u);
+        for (int t0 = 1; t0 < nb; t0 += 4) {
+          uint64_t d;
+          if (!ck_wait(d, false)) goto done;
+          for (int t = t0; t < nb && t < t0 + 4; ++t)
+            mma_f16_ss_e(Y, dsc_ag + static_cast<uint64_t>(t) * 256u,
+                         d + static_cast<uint64_t>(t - t0) * ((2 * H * 16) >> 4), idH, 1u);
+          ck_done();
+        }
+        if (!half(Y, A_LO, true) || !wait_h(1) || !half(Y, A_LO + H / 4, true)) goto done;
+        mma_commit_e(bar(B_DP));
+        mma_commit_e(bar(B_AG_E));
+        __syncwarp();
+        if (!wait_h(0) || !half(X, A_HI, false) || !wait_h(1) || !half(X, A_HI + H / 4, true))
+          goto done;
+        mma_commit_e(bar(B_DP));
+        __syncwarp();
+        if constexpr (R3) {
+          if (!wait_h(0) || !wait_h(1)) goto done;
+          mma_commit_e(bar(B_DR2));
+          __syncwarp();
+        } else {
+          if (!wait_h(0) || !half(Y, A_LO, false) || !wait_h(1) || !half(Y, A_LO + H / 4, true))
+            goto done;
+          mma_commit_e(bar(B_DP));
+          __syncwarp();
+          if (!wait_h(0) || !wait_h(1)) goto done;
+          uint64_t d;
+          if (!ck_wait(d, true)) goto done;
+          issue_gemm<16, H>(Z, A_HI, d, id16);
+          ck_done();
+          mma_commit_e(bar(B_DR2));
+          __syncwarp();
+        }
+        } else {
         if constexpr (!Sum) {
           if (!wait_h(0)) goto done;
           issue_gemm<H, H>(X, A_LO, dsc_rho, idH);
@@ -672,6 +831,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         mma_commit_e(bar(B_DR2));
         __syncwarp();
         }  // R1, R2
+        }  // resident per-pixel weights
       }
       // the next tile's first two phi1 right behind R2 (they write X and Y)
       tile = next_tile;
@@ -1076,7 +1236,10 @@ cudaError_t launch_mode(int mode, const void* wimg, const FusedParams& p, cudaSt
 
 cudaError_t prepare_fused_bf16(int H) {
   device_sm_count();
-  if (H == 128) return prepare_all<128, false>();
+  if (H == 128) {
+    cudaError_t e = prepare_all<128, false>();
+    return e == cudaSuccess ? prepare_all<128, true>() : e;
+  }
   cudaError_t e = prepare_all<64, false>();
   return e == cudaSuccess ? prepare_all<64, true>() : e;
 }
@@ -1092,9 +1255,10 @@ cudaError_t launch_fused_bf16(int H, const void* wimg, const FusedParams& params
   const int slots = per_sm * device_sm_count();
   const int grid = p.total_tiles < slots ? p.total_tiles : slots;
   if (p.pe_freqs > 0) {
-    // the encoded operands exist for H = 64 only (the loader refuses others)
-    if (H != 64 || p.pe_freqs > kMaxPeFreqsFused) return cudaErrorInvalidValue;
-    return launch_mode<64, true>(mode, wimg, p, s, grid);
+    // the encoded operands are sized for kMaxPeFreqsFused (the loader refuses more)
+    if (p.pe_freqs > kMaxPeFreqsFused) return cudaErrorInvalidValue;
+    return H == 128 ? launch_mode<128, true>(mode, wimg, p, s, grid)
+                    : launch_mode<64, true>(mode, wimg, p, s, grid);
   }
   return H == 128 ? launch_mode<128, false>(mode, wimg, p, s, grid)
                   : launch_mode<64, false>(mode, wimg, p, s, grid);

@@ -106,6 +106,60 @@ std::vector<uint8_t> pack_fused_bf16(const float* w, const gn::WeightIndex& wi) 
   return img;
 }
 
+// Image of the doubled widths with positional encoding (FusedLayout<128,
+// true>): the resident block (phi1 with every band, phi2, band 0 of B1's
+// G-buffer block, phi2b, the biases), then the per-pixel weights in chunks of
+// K = 64 rows, each chunk the slice [8 k0 / 64 ...][N][8] of the layer's
+// [K/8][N][8] operand, streamed through the kernel's shared-memory ring.
+std::vector<uint8_t> pack_fused_bf16_stream(const float* w, const gn::WeightIndex& wi) {
+  using L = gn::FusedLayout<128, true>;
+  constexpr int H = 128;
+  const int nb = wi.bands();
+  std::vector<uint8_t> img(L::img_bytes, 0);
+  auto put = [&](uint32_t off, int N, int n, int k, float v) {
+    uint16_t b = bf16_rne(v);
+    std::memcpy(img.data() + off + core_idx(N, n, k) * 2, &b, 2);
+  };
+  // K row k of a chunked operand starting at `base`
+  auto put_chunked = [&](uint32_t base, int n, int k, float v) {
+    put(base + static_cast<uint32_t>(k / 64) * L::kChunk, H, n, k % 64, v);
+  };
+  auto W = [&](int l, int n, int j) { return w[wi.w[l] + static_cast<size_t>(n) * wi.in[l] + j]; };
+  for (int n = 0; n < H; ++n) {
+    for (int t = 0; t < nb; ++t)
+      for (int k = 0; k < gn::kTC; ++k) put(L::phi1, H, n, 16 * t + k, W(gn::LPHI1, n, t * gn::kTC + k));
+    for (int k = 0; k < H; ++k) put(L::phi2, H, n, k, W(gn::LPHI2, n, k));
+    for (int k = 0; k < gn::kGC; ++k) put(L::b1, H, n, k, W(gn::LB1, n, k));
+    for (int k = 0; k < 2 * H; ++k) put_chunked(L::img_rho, n, k, W(gn::LRHO, n, k));
+    for (int t = 1; t < nb; ++t)  // band t at K 16 (t - 1) of the bands' chunks
+      for (int k = 0; k < gn::kGC; ++k)
+        put_chunked(L::img_b1g, n, 16 * (t - 1) + k, W(gn::LB1, n, t * gn::kGC + k));
+    for (int k = 0; k < H; ++k) put_chunked(L::img_b1r, n, k, W(gn::LB1, n, wi.gc_enc() + k));
+    for (int k = 0; k < H; ++k) put_chunked(L::img_b2, n, k, W(gn::LB2, n, k));
+    for (int k = 0; k < H; ++k) put_chunked(L::img_r1, n, k, W(gn::LR1, n, k));
+  }
+  for (int n = 0; n < gn::kOut; ++n)
+    for (int k = 0; k < H; ++k) put(L::img_r2, 16, n, k, W(gn::LR2, n, k));
+  for (int n = 0; n < H; ++n) {  // phi2 bias as hi + lo BF16 rows of a K = 16 operand
+    const float b = w[wi.b[gn::LPHI2] + n];
+    uint16_t hb = bf16_rne(b);
+    uint32_t hu = static_cast<uint32_t>(hb) << 16;
+    float hf;
+    std::memcpy(&hf, &hu, 4);
+    put(L::phi2b, H, n, 0, hf);
+    put(L::phi2b, H, n, 1, b - hf);
+  }
+  float* bias = reinterpret_cast<float*>(img.data() + L::bias);
+  for (int n = 0; n < H; ++n) {
+    bias[n] = w[wi.b[gn::LPHI2] + n];
+    bias[H + n] = w[wi.b[gn::LRHO] + n];
+    bias[2 * H + n] = w[wi.b[gn::LB2] + n];
+    bias[3 * H + n] = w[wi.b[gn::LR1] + n];
+  }
+  for (int n = 0; n < gn::kOut; ++n) bias[4 * H + n] = w[wi.b[gn::LR2] + n];
+  return img;
+}
+
 // Image of the 3x3 R kernel (conv_r3.cu): per tap t = (dy + 1) 3 + dx + 1
 // the [H/8][H][8] BF16 B operand of W_R1[:, :, dy + 1, dx + 1] (the blob
 // stores R1 as [H][H 9], column k 9 + t), then in FP32 b_R1 [H], W_R2 [3][H]
@@ -345,11 +399,11 @@ int load_weights_impl(const void* blob, size_t nbytes, const gn_model_config* cf
   if (!ok_widths)
     return fail(GN_EUNSUPPORTED, "widths (H, Z) = (%u, %u); this build has (64, 128), (128, 256)",
                 hd.hidden, hd.latent);
-  if (precision == GN_BF16_FUSED && pe > 0 && (hd.hidden != 64 || pe > gn::kMaxPeFreqsFused))
+  if (precision == GN_BF16_FUSED && pe > gn::kMaxPeFreqsFused)
     return fail(GN_EUNSUPPORTED,
-                "positional encoding in the fused BF16 kernel is built for H = 64 and pe_freqs "
-                "1..%d (its operands fill the shared memory); H = %u, pe_freqs = %d",
-                gn::kMaxPeFreqsFused, hd.hidden, pe);
+                "positional encoding in the fused BF16 kernel is built for pe_freqs 1..%d (its "
+                "encoded operands are sized for them); pe_freqs = %d",
+                gn::kMaxPeFreqsFused, pe);
 
   std::vector<float> w(wi.total);
   std::memcpy(w.data(), payload, wi.total * sizeof(float));
@@ -392,7 +446,8 @@ int load_weights_impl(const void* blob, size_t nbytes, const gn_model_config* cf
     std::memcpy(m->host_w, w.data(), wi.total * sizeof(float));
   }
   if (precision == GN_BF16_FUSED) {
-    std::vector<uint8_t> img = wi.H == 128 ? pack_fused_bf16<128, false>(w.data(), wi)
+    std::vector<uint8_t> img = wi.H == 128 ? (wi.L > 0 ? pack_fused_bf16_stream(w.data(), wi)
+                                                       : pack_fused_bf16<128, false>(w.data(), wi))
                                : wi.L > 0  ? pack_fused_bf16<64, true>(w.data(), wi)
                                            : pack_fused_bf16<64, false>(w.data(), wi);
     m->fused_bytes = img.size();

@@ -39,7 +39,7 @@ enum Layer { LF1 = 0, LF2, LPHI1, LPHI2, LRHO, LB1, LB2, LR1, LR2, kLayers };
 // enters as n (1 + 2L) values, the blocks [x ; sin(2^0 pi x) ; cos(2^0 pi x) ;
 // ... ; sin(2^(L-1) pi x) ; cos(2^(L-1) pi x)].  Band t of an input is block t.
 constexpr int kMaxPeFreqs = 10;       // any precision's limit
-constexpr int kMaxPeFreqsFused = 4;   // the fused BF16 kernel at H = 64
+constexpr int kMaxPeFreqsFused = 4;   // the fused BF16 and FP8 kernels
 
 // Offsets (in floats) of each W and b inside the concat-form f32 weights.
 struct WeightIndex {
@@ -79,13 +79,13 @@ __device__ __forceinline__ float pe_band_value(float x, int t) {
 //                   GEMM multiplies it by a constant [1, 1, 0, ...] A column
 //   bias f32: phi2[H], rho[H], B2[H], R1[H], R2[16]
 //
-// With positional encoding (PE, H = 64 only) every band of phi1's input and
-// of B1's G-buffer block takes 16 K columns (12 or 14 values, then zeros),
+// With positional encoding (PE) every band of phi1's input and of B1's
+// G-buffer block takes 16 K columns (12 or 14 values, then zeros),
 // for up to kMaxPeFreqsFused frequencies: band 0 keeps the layout above
 // (constant-one columns at k = 12, 13 of phi1 and k = 14, 15 of B1), band t
 // sits at k = 16 t, and B1's r block starts after the last band.  The
 // operands are sized for the largest L; a model with fewer frequencies uses
-// the first 1 + 2L bands.
+// the first 1 + 2L bands.  At H = 128 the per-pixel weights stream (below).
 template <int H, bool PE = false>
 struct FusedLayout {
   static constexpr int kBands = PE ? 1 + 2 * kMaxPeFreqsFused : 1;
@@ -118,6 +118,61 @@ struct FusedLayout {
   static constexpr uint32_t ag = aone + 4096;
   static constexpr uint32_t smem_bytes = ag + KG * 256;
   static_assert(smem_bytes <= 232448, "operands exceed the 227 KB of shared memory per CTA");
+  static constexpr bool kStream = false;
+};
+
+// Doubled widths with positional encoding: the encoded operands and weights
+// (phi1 and B1's G-buffer block at K = 16 (1 + 2 kMaxPeFreqsFused)) do not
+// fit beside every weight, so the per-pixel weights stream from device
+// memory (through L2) into a ring of two 16 KB shared-memory stages, one
+// chunk of K = 64 rows at a time, while phi1, phi2, phi2b, the biases and
+// band 0 of B1 (which carries the folded per-scene bias) stay resident.
+// The image starts with the resident block, copied verbatim at offset 0:
+//   phi1 [KT][H] | phi2 [H][H] | B1 band 0 [16][H] | phi2b [16][H] | bias f32
+// then the chunks, each a contiguous [64/8][N][8] (or smaller) block:
+//   rho      4 chunks (K = [max ; mean], 64 rows each)
+//   B1 bands 2 chunks (bands 1-4 and 5-8 of the G-buffer block, 16 K each;
+//            a model with fewer frequencies copies the bands it uses)
+//   B1 r     2 chunks    B2  2 chunks    R1  2 chunks    R2  1 chunk [H][16]
+template <>
+struct FusedLayout<128, true> {
+  static constexpr int H = 128;
+  static constexpr int kBands = 1 + 2 * kMaxPeFreqsFused;
+  static constexpr int KT = 16 * kBands;
+  static constexpr int KG = 16 * kBands;
+  static constexpr int NR2 = 16;
+  static constexpr uint32_t kChunk = 64 * H * 2;  // one ring stage: K = 64 rows of an N = H operand
+  // resident block (smem offset = image offset)
+  static constexpr uint32_t phi1 = 0;
+  static constexpr uint32_t phi2 = phi1 + KT * H * 2;
+  static constexpr uint32_t b1 = phi2 + H * H * 2;  // band 0 of B1's G-buffer block only
+  static constexpr uint32_t phi2b = b1 + 16 * H * 2;
+  static constexpr uint32_t bias = phi2b + 16 * H * 2;
+  static constexpr uint32_t bias_phi2 = bias;
+  static constexpr uint32_t bias_rho = bias + H * 4;
+  static constexpr uint32_t bias_b2 = bias + 2 * H * 4;
+  static constexpr uint32_t bias_r1 = bias + 3 * H * 4;
+  static constexpr uint32_t bias_r2 = bias + 4 * H * 4;
+  static constexpr uint32_t bytes = bias + (4 * H + 16) * 4;  // resident bytes
+  // chunks in the image
+  static constexpr uint32_t img_rho = (bytes + 127) / 128 * 128;
+  static constexpr uint32_t img_b1g = img_rho + 4 * kChunk;
+  static constexpr uint32_t img_b1r = img_b1g + 2 * kChunk;
+  static constexpr uint32_t img_b2 = img_b1r + 2 * kChunk;
+  static constexpr uint32_t img_r1 = img_b2 + 2 * kChunk;
+  static constexpr uint32_t img_r2 = img_r1 + 2 * kChunk;
+  static constexpr uint32_t img_bytes = img_r2 + H * NR2 * 2;
+  // shared memory beyond the resident block: the ring, then the A operands
+  // as in the general layout
+  static constexpr uint32_t ring0 = (bytes + 127) / 128 * 128;
+  static constexpr uint32_t ring1 = ring0 + kChunk;
+  static constexpr uint32_t at0 = ring1 + kChunk;
+  static constexpr uint32_t at1 = at0 + KT * 256;
+  static constexpr uint32_t aone = at1 + KT * 256;
+  static constexpr uint32_t ag = aone + 4096;
+  static constexpr uint32_t smem_bytes = ag + KG * 256;
+  static_assert(smem_bytes + 1024 <= 232448, "operands exceed the 227 KB of shared memory per CTA");
+  static constexpr bool kStream = true;
 };
 
 // Packed operand image of the FP8 fused kernel (E4M3 operands, FP32

@@ -137,16 +137,17 @@ def test_r_kernel_checked_on_the_host(lib):
 
 
 def test_positional_encoding_limits_checked_on_the_host(lib):
-    """The fused kernel's PE variant exists for H = 64, L <= 4 only: larger
-    forms are refused before the blob reaches the device."""
+    """The fused kernel's encoded operands hold L <= 4 frequencies at both
+    widths: larger forms are refused before the blob reaches the device."""
     out = ctypes.c_void_p()
-    for widths, pe, code in [(synth.Widths(hidden=128, latent=256, pe_freqs=1), 1, gl.GN_EUNSUPPORTED),
+    for widths, pe, code in [(synth.Widths(hidden=128, latent=256, pe_freqs=5), 5, gl.GN_EUNSUPPORTED),
                              (synth.Widths(hidden=64, latent=128, pe_freqs=5), 5, gl.GN_EUNSUPPORTED)]:
         blob = gl.pack_blob(synth.make_weights(widths, seed=0))
         buf = ctypes.create_string_buffer(blob, len(blob))
         cfg = gl.ModelConfig(gl.GN_BF16_FUSED, 0, pe)
         assert lib.glassnet_load_weights_ex(buf, len(blob), ctypes.byref(cfg), ctypes.byref(out)) == code
-        assert "H = 64" in gl.glassnet_last_error()
+        assert "pe_freqs 1..4" in gl.glassnet_last_error()
+        assert not out.value
 
 
 def test_null_arguments_rejected(lib):
