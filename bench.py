@@ -58,7 +58,7 @@ def traffic_record(fp8: bool, r_kernel: int, pe: int, base: bool, pool_sum: bool
     if fp8 or r_kernel != 1 or (base and pool_sum):
         return None
     if pe:
-        return PROFILE_TRAFFIC_PE if pe == 4 else None
+        return PROFILE_TRAFFIC_PE if pe == 4 and base else None
     if base:
         return PROFILE_TRAFFIC_H64
     return PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC
@@ -90,12 +90,12 @@ def parse():
     ap.add_argument("--r-kernel", type=int, default=1, choices=[1, 3],
                     help="R's first layer: 1x1, or a 3x3 kernel over the frame (fused kernel to "
                          "the neural buffer, then the tcgen05 3x3 kernel)")
-    ap.add_argument("--widths", default="doubled", choices=["doubled", "base"],
-                    help="network widths of the timed leg: doubled (H=128 Z=256) or base "
-                         "(H=64 Z=128)")
+    ap.add_argument("--widths", default=None, choices=["doubled", "base"],
+                    help="network widths of the timed leg: doubled (H=128 Z=256, the default "
+                         "without encoding) or base (H=64 Z=128, the default with --pe-freqs)")
     ap.add_argument("--pe-freqs", type=int, default=0,
-                    help="time the base widths (H=64 Z=128) with every input positionally "
-                         "encoded at this many frequencies (BF16, 1..4) instead of the doubled widths")
+                    help="time a model with every input positionally encoded at this many "
+                         "frequencies (BF16, 1..4); base widths unless --widths doubled")
     return ap.parse_args()
 
 
@@ -419,8 +419,8 @@ def run_fused(args, world, rank, local):
     gl.load_library()
     pe = args.pe_freqs
     rk = args.r_kernel
-    base = pe > 0 or args.widths == "base"
-    widths = synth.Widths(64, 128, pe, rk) if base else synth.Widths(128, 256, 0, rk)
+    base = args.widths == "base" or (args.widths is None and pe > 0)
+    widths = synth.Widths(64, 128, pe, rk) if base else synth.Widths(128, 256, pe, rk)
     weights = synth.make_weights(widths, seed=0)
     fp8 = args.precision == "fp8"
     pool_sum = args.pooling == "sum"
@@ -718,7 +718,8 @@ def r3_leg(scene, dframes, frames, stream, steps=200):
 def pe_leg(scene, dframes, frames, stream, L=4, steps=200):
     """The same frames through the base widths (H=64, Z=128) with every input
     positionally encoded at L frequencies (Sec. 3.4), BF16 fused; the same
-    widths without encoding are timed beside it."""
+    widths without encoding are timed beside it, and the doubled widths
+    (H=128, Z=256) encoded at L frequencies in BF16 and in FP8."""
     from gen import synth
     from paper_2405_19056_gb300 import glassnet as gl
 
@@ -742,9 +743,25 @@ def pe_leg(scene, dframes, frames, stream, L=4, steps=200):
             out.update(leg)
         else:
             out["no_pe"] = leg
-    # the doubled widths (H=128 Z=256) encoded at L frequencies in the FP8
-    # kernel (the BF16 H = 128 operands leave no shared memory for the bands),
-    # calibrated on one frame of seed 1 that is not a timed frame
+    # the doubled widths (H=128 Z=256) encoded at L frequencies, BF16 fused:
+    # the per-pixel weights stream through each CTA's shared-memory ring
+    wd = synth.make_weights(synth.Widths(128, 256, L), seed=0)
+    md = gl.Model(wd, gl.GN_BF16_FUSED)
+    latd = md.encode(scene, stream)
+    ms = _time_renders(md, latd, dframes, stream, steps)
+    flops = sum(algorithmic_flops(128, frames[i % N_ROTATE].counts, "max_mean", L)
+                for i in range(steps)) / steps
+    achieved = flops / (ms * 1e-3) / 1e12
+    out["bf16_h128"] = {"value": H_IMG * W_IMG / (ms * 1e-3) / 1e6, "unit": "Mpixel/s",
+                        "ms_per_step": ms, "steps": steps, "gflop_per_step": flops / 1e9,
+                        "widths": f"H=128 Z=256, pe_freqs={L}",
+                        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16,
+                                     "unit": "TFLOP/s", "frac": achieved / peak_bf16,
+                                     "kernel": "fused_bf16_kernel<128, frame, sum=0, pe=1> "
+                                               "(per-pixel weights streamed)",
+                                     "peak_source": "measured bf16 burst"}}
+    # the same in the FP8 kernel, calibrated on one frame of seed 1 that is
+    # not a timed frame
     import torch
     w8 = synth.make_weights(synth.Widths(128, 256, L), seed=0)
     m8 = gl.Model(w8, gl.GN_FP8_FUSED)
