@@ -37,6 +37,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "fused_bf16_512x512_K8.traffic.
 PROFILE_TRAFFIC_SUM = os.path.join(ROOT, "profiles", "fused_bf16_sum_512x512_K8.traffic.json")
 PROFILE_TRAFFIC_PE = os.path.join(ROOT, "profiles", "fused_bf16_pe4_512x512_K8.traffic.json")
 PROFILE_TRAFFIC_H64 = os.path.join(ROOT, "profiles", "fused_bf16_h64_512x512_K8.traffic.json")
+PROFILE_TRAFFIC_PE128 = os.path.join(ROOT, "profiles", "fused_bf16_pe4_h128_512x512_K8.traffic.json")
 PROFILE_TRAFFIC_COMPACT = os.path.join(ROOT, "profiles", "fused_compact_h64_512x512_K8.traffic.json")
 
 
@@ -54,11 +55,13 @@ def profiled_traffic(path: str, sources=None):
 def traffic_record(fp8: bool, r_kernel: int, pe: int, base: bool, pool_sum: bool):
     """The committed capture of the timed leg's fused kernel, if there is one:
     both poolings at the doubled widths, [max ; mean] at the base widths
-    without encoding and at L = 4 (BF16, 1x1 R)."""
+    without encoding and at both widths with L = 4 (BF16, 1x1 R)."""
     if fp8 or r_kernel != 1 or (base and pool_sum):
         return None
     if pe:
-        return PROFILE_TRAFFIC_PE if pe == 4 and base else None
+        if pe != 4 or pool_sum:
+            return None
+        return PROFILE_TRAFFIC_PE if base else PROFILE_TRAFFIC_PE128
     if base:
         return PROFILE_TRAFFIC_H64
     return PROFILE_TRAFFIC_SUM if pool_sum else PROFILE_TRAFFIC

@@ -79,8 +79,10 @@ def test_each_leg_takes_the_capture_of_its_own_kernel(bench):
     assert bench.traffic_record(False, 1, 0, False, True) == bench.PROFILE_TRAFFIC_SUM
     assert bench.traffic_record(False, 1, 0, True, False) == bench.PROFILE_TRAFFIC_H64
     assert bench.traffic_record(False, 1, 4, True, False) == bench.PROFILE_TRAFFIC_PE
+    assert bench.traffic_record(False, 1, 4, False, False) == bench.PROFILE_TRAFFIC_PE128
     for args in [(True, 1, 0, False, False), (False, 3, 0, False, False), (False, 1, 2, True, False),
-                 (False, 1, 4, True, True), (False, 1, 0, True, True), (False, 1, 4, False, False)]:
+                 (False, 1, 4, True, True), (False, 1, 0, True, True), (False, 1, 4, False, True),
+                 (False, 1, 2, False, False)]:
         assert bench.traffic_record(*args) is None, args
 
 
