@@ -64,7 +64,8 @@ def test_traffic_record_only_counts_for_its_kernel_sources(bench, tmp_path):
 
 def test_committed_traffic_records_name_their_command_and_workload(bench):
     for name in ("fused_bf16_512x512_K8", "fused_bf16_sum_512x512_K8", "fused_bf16_pe4_512x512_K8",
-                 "fused_bf16_h64_512x512_K8", "fused_compact_h64_512x512_K8"):
+                 "fused_bf16_h64_512x512_K8", "fused_compact_h64_512x512_K8",
+                 "fused_bf16_pe4_h128_512x512_K8"):
         with open(os.path.join(ROOT, "profiles", name + ".traffic.json")) as f:
             rec = json.load(f)
         assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
