@@ -132,13 +132,16 @@ def test_least_recently_used_scene_is_replaced(model):
         gl.glassnet_server_destroy(srv)
 
 
-@pytest.mark.parametrize("form", ["sum", "r3", "pe"])
+@pytest.mark.parametrize("form", ["sum", "r3", "pe", "pe128"])
 def test_model_options_served_equal_alone(cuda_lib, form):
     """The serving loop with the model options (sum pooling, a 3x3 R whose
-    per-lane graphs hold a neural buffer, positional encoding at H = 64):
-    each request equals its render alone, bit for bit."""
+    per-lane graphs hold a neural buffer, positional encoding at H = 64 and
+    at H = 128, where the per-pixel weights stream): each request equals its
+    render alone, bit for bit."""
     if form == "pe":
         w = synth.make_weights(synth.Widths(64, 128, 4), seed=2, bias="uniform")
+    elif form == "pe128":
+        w = synth.make_weights(synth.Widths(128, 256, 3), seed=2, bias="uniform")
     else:
         w = synth.make_weights(synth.Widths(128, 256, 0, 3 if form == "r3" else 1), seed=2, bias="uniform")
     m = gl.Model(w, gl.GN_BF16_FUSED, gl.GN_POOL_SUM if form == "sum" else gl.GN_POOL_MAX_MEAN)
