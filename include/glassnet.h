@@ -57,7 +57,7 @@ typedef enum gn_status {
   GN_ECUDA = -3,        /* a CUDA runtime call failed */
   GN_EFORMAT = -4,      /* weight blob: bad magic, version, sizes or checksum */
   GN_ETIMEOUT = -5,     /* a device-side wait exceeded its time limit */
-  GN_EUNSUPPORTED = -6, /* widths or precision this build does not provide */
+  GN_EUNSUPPORTED = -6, /* widths or precision the library does not provide */
   GN_ERANGE = -7,       /* exact set-sum left its fixed-point range (see below) */
   GN_ESATURATED = -8    /* FP8: an input beyond its calibrated range was clamped */
 } gn_status;

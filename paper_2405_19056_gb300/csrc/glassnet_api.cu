@@ -397,7 +397,7 @@ int load_weights_impl(const void* blob, size_t nbytes, const gn_model_config* cf
     return fail(GN_EFORMAT, "payload checksum mismatch");
   const bool ok_widths = (hd.hidden == 64 && hd.latent == 128) || (hd.hidden == 128 && hd.latent == 256);
   if (!ok_widths)
-    return fail(GN_EUNSUPPORTED, "widths (H, Z) = (%u, %u); this build has (64, 128), (128, 256)",
+    return fail(GN_EUNSUPPORTED, "widths (H, Z) = (%u, %u); the library provides (64, 128) and (128, 256)",
                 hd.hidden, hd.latent);
   if (precision == GN_BF16_FUSED && pe > gn::kMaxPeFreqsFused)
     return fail(GN_EUNSUPPORTED,
