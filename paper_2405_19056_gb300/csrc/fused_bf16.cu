@@ -46,12 +46,14 @@
 //    They run every epilogue (ReLU, pooling, biases, sigmoid) and hold the
 //    pool state (H/2 sums and H/4 packed maxima per thread) in registers.
 //  - warp 8 (MMA): allocates TMEM, patches the per-scene bias rows, issues
-//    every tcgen05.mma from lane 0.
+//    every tcgen05.mma (one elected lane of the converged warp).
 //  - warps 9-10 (loaders, 64 pixel rows each): read each tile's plan entries,
 //    gather its G-buffer and layers, convert them to BF16 and write the
 //    shared-memory A operands, running up to two layer slots ahead.  With
-//    positional encoding there are four loader warps (9-12, 32 rows each)
-//    that also compute the encoded bands (13 warps).
+//    positional encoding at H = 64 there are four loader warps (9-12, 32
+//    rows each) that also compute the encoded bands (13 warps); at H = 128
+//    the two loader warps encode, and warp 11 fills the ring through which
+//    the per-pixel weights stream (12 warps, FusedLayout<128, true>).
 // The base widths without encoding (H = 64) run one epilogue warp per lane
 // quadrant instead (warps 0-3, all H columns; MMA warp 4; loaders 5-6), at
 // two CTAs per SM (128 registers a thread).
