@@ -888,6 +888,22 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         return true;
       };
       if (!take_tile(0)) goto done;
+      // R2's output of the previous tile, read from TMEM but not yet stored:
+      // the column-group-0 warps store it after their first phi1 epilogue of
+      // the next tile, so that the sigmoid and the global stores are not
+      // between that tile's first phi2 and the previous tile's R2.
+      float pend_y[kOut] = {};
+      float* pend_out = nullptr;
+      size_t pend_P = 0;
+      uint32_t pend_pix = 0;
+      auto flush_store = [&]() {
+        if (pend_out) {
+#pragma unroll
+          for (int j = 0; j < kOut; ++j)
+            pend_out[j * pend_P + pend_pix] = 1.0f / (1.0f + expf(-pend_y[j]));
+          pend_out = nullptr;
+        }
+      };
       for (; tile < total_tiles; ++tb) {
         uint32_t mx[CHC];  // running max, bf16 pairs
         float sm[CH];      // fixed-point sums
@@ -977,6 +993,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // epi1(k + 1) runs ahead of epi2(k); one call site each
         for (int k = -1; k < ns; ++k) {
           if (k + 1 < ns && !epi1(k + 1)) goto done;
+          if (k < 0) flush_store();  // the previous tile's RGB
           if (k >= 0 && !epi2(k)) goto done;
         }
         if constexpr (Mode == kModeAccumulate) {
@@ -1131,10 +1148,11 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
             arrive_h(h);
           }
         }
-        // R2 + sigmoid -> out (column group 0 stores).  Every warp waits for R2:
-        // the next tile's phi1 for its third slot writes Z, and it is issued
-        // only after every warp's first phi1 epilogue of that tile.  The next
-        // tile is taken first.
+        // R2 -> registers (column group 0), stored by flush_store after the
+        // next tile's first phi1 epilogue (or after the last tile).  Every warp
+        // waits for R2: the next tile's phi1 for its third slot writes Z, and
+        // it is issued only after every warp's first phi1 epilogue of that
+        // tile, which follows this TMEM read.  The next tile is taken first.
         if (!take_tile(tb + 1)) goto done;
         if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
         if (!R3 && g == 0) {
@@ -1142,18 +1160,16 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
           uint32_t r[4];
           tmem_ld4(Z, r);
           if (ent != kPlanEmpty) {
-            float* const out = s_ld.out[tb & 3];
-            const size_t P = static_cast<size_t>(s_ld.P[tb & 3]);
-            const uint32_t pix = ent & kPlanPixelMask;
+            pend_out = s_ld.out[tb & 3];
+            pend_P = static_cast<size_t>(s_ld.P[tb & 3]);
+            pend_pix = ent & kPlanPixelMask;
 #pragma unroll
-            for (int j = 0; j < kOut; ++j) {
-              const float y = __uint_as_float(r[j]) + b_r2[j];
-              out[j * P + pix] = 1.0f / (1.0f + expf(-y));
-            }
+            for (int j = 0; j < kOut; ++j) pend_y[j] = __uint_as_float(r[j]) + b_r2[j];
           }
         }
         }  // frame and resolve launches: the per-pixel layers
       }
+      flush_store();  // the last tile's RGB
     }
   }
 done:
