@@ -85,6 +85,10 @@ def parse():
     ap.add_argument("--serving-quick", action="store_true",
                     help="serving leg at 200 and 800 req/s with 300 requests each (default: the "
                          "serving workload as stated, 2000 requests at each of 50, 200, 800 req/s)")
+    ap.add_argument("--serving-lanes", type=int, default=4,
+                    help="lanes (streams) of the serving leg's server")
+    ap.add_argument("--serving-rates", default=None,
+                    help="comma-separated arrival rates of the serving leg (default 50,200,800)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8"],
                     help="precision of the timed fused leg (fp8: calibrated on a seed-1 frame)")
     ap.add_argument("--pooling", default="max_mean", choices=["max_mean", "sum"],
@@ -555,8 +559,10 @@ def run_fused(args, world, rank, local):
     leg("positional_encoding", lambda: pe_leg(scene, dframes, frames, stream))
     leg("spatial_r3", lambda: r3_leg(scene, dframes, frames, stream))
     leg("compact_schedule", lambda: compact_leg(scene, dframes, frames, stream))
-    leg("serving", lambda: serving_leg(model, weights, (200, 800), 300) if args.serving_quick
-        else serving_leg(model, weights, (50, 200, 800), 2000))
+    rates = (tuple(int(r) for r in args.serving_rates.split(",")) if args.serving_rates
+             else (200, 800) if args.serving_quick else (50, 200, 800))
+    leg("serving", lambda: serving_leg(model, weights, rates, 300 if args.serving_quick else 2000,
+                                       n_streams=args.serving_lanes))
     clocks = clk.summary()
     result["clocks"] = clocks
     if rank == 0 and "cpu_baseline" in legs:
