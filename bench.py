@@ -501,7 +501,7 @@ def run_fused(args, world, rank, local):
     if pool_sum:
         metric = metric.replace("BF16 fused", "BF16 fused, sum pooling")
     if pe:
-        metric = metric.replace("BF16 fused", f"BF16 fused, H=64, inputs encoded at L={pe}")
+        metric = metric.replace("BF16 fused", f"BF16 fused, H={widths.hidden}, inputs encoded at L={pe}")
     elif base:
         metric = metric.replace(" fused", " fused, H=64", 1)
     if rk == 3:

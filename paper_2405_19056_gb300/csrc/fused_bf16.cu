@@ -363,19 +363,34 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
         return true;
       }
       const uint32_t one = pack_bf16(1.0f, 1.0f);
+      if constexpr (PE) {
+        // a loop over the rows, each row's values picked by selects, as in
+        // store_slot_pe: one copy of the encoding code
+        static_assert(RPL == 1 || RPL == 2, "one or two rows per loader lane with encoding");
+#pragma unroll 1
+        for (int i = 0; i < RPL; ++i) {
+          const uint32_t r = sbase + L::ag + static_cast<uint32_t>(row0 + 32 * i) * 16u;
+          float g[kGC];
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const uint32_t r = sbase + L::ag + static_cast<uint32_t>(row0 + 32 * i) * 16u;
-        const float (&g)[kGC] = gv[i];
-        sts128(r, pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
-               pack_bf16(g[6], g[7]));
-        sts128(r + 2048u, pack_bf16(g[8], g[9]), pack_bf16(g[10], g[11]), pack_bf16(g[12], g[13]),
-               one);
-        if constexpr (PE) {
+          for (int c = 0; c < kGC; ++c) g[c] = i == 0 ? gv[0][c] : gv[RPL - 1][c];
+          sts128(r, pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
+                 pack_bf16(g[6], g[7]));
+          sts128(r + 2048u, pack_bf16(g[8], g[9]), pack_bf16(g[10], g[11]),
+                 pack_bf16(g[12], g[13]), one);
           const float lo[8] = {g[0], g[1], g[2], g[3], g[4], g[5], g[6], g[7]};
           const float hi[6] = {g[8], g[9], g[10], g[11], g[12], g[13]};
           pe_chunks(r, lo, nf);
           pe_chunks(r + 2048u, hi, nf);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          const uint32_t r = sbase + L::ag + static_cast<uint32_t>(row0 + 32 * i) * 16u;
+          const float (&g)[kGC] = gv[i];
+          sts128(r, pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
+                 pack_bf16(g[6], g[7]));
+          sts128(r + 2048u, pack_bf16(g[8], g[9]), pack_bf16(g[10], g[11]),
+                 pack_bf16(g[12], g[13]), one);
         }
       }
       fence_proxy_async_smem();
