@@ -287,13 +287,24 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
       if constexpr (PE) load_g();
       if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
+      // with encoding a loop over the rows, each row's values picked by
+      // selects: one copy of the (long) encoding code, which keeps the
+      // loaders from evicting the other warps' loops from the instruction
+      // cache (an indexed register array would go to local memory)
+      static_assert(kRowsPerLoadLane == 2, "the row selects below assume two rows per lane");
+      if constexpr (PE) {
+#pragma unroll 1
+        for (int i = 0; i < kRowsPerLoadLane; ++i) {
+          float g[kGC];
 #pragma unroll
-      for (int i = 0; i < kRowsPerLoadLane; ++i) {
-        if constexpr (PE) {
+          for (int c = 0; c < kGC; ++c) g[c] = i == 0 ? gv[0][c] : gv[1][c];
           uint32_t w[32];
-          encode_row_f8(gv[i], inv_s_g_sm, nf, w, sat);
+          encode_row_f8(g, inv_s_g_sm, nf, w, sat);
           store_row_k128(sbase + L::ag, row0 + 32 * i, w);
-        } else {
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kRowsPerLoadLane; ++i) {
           float v[kGC];
           scale_inputs(gv[i], inv_s_g, v, sat);
           uint32_t w[4];
@@ -319,11 +330,14 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
       const int b = lc & 1;
       if (!warp_wait(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
       if constexpr (PE) {
-#pragma unroll
-        for (int i = 0; i < kRowsPerLoadLane; ++i) {
+#pragma unroll 1
+        for (int i = 0; i < kRowsPerLoadLane; ++i) {  // one copy of the code (see put_ag)
           uint32_t w[32];
-          if (__any_sync(0xffffffffu, k < cnt[i])) {
-            encode_row_f8(x[i], inv_s_t_sm, nf, w, sat);
+          if (__any_sync(0xffffffffu, k < (i == 0 ? cnt[0] : cnt[1]))) {
+            float xr[kTC];
+#pragma unroll
+            for (int c = 0; c < kTC; ++c) xr[c] = i == 0 ? x[0][c] : x[1][c];
+            encode_row_f8(xr, inv_s_t_sm, nf, w, sat);
           } else {  // no row of this warp has slot k: zeros (the loaded values are zeros)
 #pragma unroll
             for (int j = 0; j < 32; ++j) w[j] = 0u;
