@@ -1124,7 +1124,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
           const float* bl = l == 0 ? b_rho : (l == 2 ? b_b2 : b_r1);
           const uint32_t acc = (l & 1) ? Y : X;
           const uint32_t dst = (l & 1) ? A_HI : A_LO;
-#pragma unroll
+#pragma unroll 1
           for (int h = 0; h < 2; ++h) {
             const int c0 = h * (H / 2) + g * PC;  // first accumulator column of this pass
             uint32_t ra[16], rb[16];
