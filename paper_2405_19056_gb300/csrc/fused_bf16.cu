@@ -263,6 +263,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
                                             volatile int* abort_flag, int li, int lane) {
   using L = FusedLayout<H, PE>;
   constexpr int RPL = Roles<H, PE>::RPL, LW = Roles<H, PE>::LW;
+  constexpr bool kOol = Roles<H, PE>::kPair;  // waits' polling loop out of line (warp_wait)
   const int nf = PE ? prm.pe_freqs : 0;  // positional-encoding frequencies
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
   const int row0 = li * (32 * RPL) + lane;
@@ -276,7 +277,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
       if (lane == 0) ls.tile[tb & 1] = schedule_tile(prm, atomicAdd(prm.next_tile, 1u));
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_SCHED + (tb & 1)));
-    } else if (!warp_wait(bar(B_SCHED + (tb & 1)), (tb >> 1) & 1, abort_flag)) {
+    } else if (!warp_wait<kOol>(bar(B_SCHED + (tb & 1)), (tb >> 1) & 1, abort_flag)) {
       return;
     }
     tile = *reinterpret_cast<volatile int*>(&ls.tile[tb & 1]);
@@ -314,7 +315,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     __syncwarp();
     if (lane == 0) mbar_arrive(bar(B_TILE + (tb & 1)));
     // the tile's slot count is the max over both loader warps
-    if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
+    if (!warp_wait<kOol>(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
     int ns = 0;
 #pragma unroll
     for (int w = 0; w < LW; ++w) ns = max(ns, ls.ns[tb & 1][w]);
@@ -355,7 +356,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     // with no covered pixel let the MMA warp commit two tiles in a row before
     // the loaders looked, and their wait then missed the phase).
     auto put_ag = [&]() -> bool {
-      if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
+      if (!warp_wait<kOol>(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
       if constexpr (Mode == kModeAccumulate) {
         __syncwarp();
@@ -406,7 +407,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
     for (int k = 0; k < ns; ++k, ++lc) {
       if (k + 1 < ns) load_slot(F, k + 1, pix, cnt, y);
       const int b = lc & 1;
-      if (!warp_wait(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
+      if (!warp_wait<kOol>(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
       if constexpr (PE)
         store_slot_pe(sbase + (b ? L::at1 : L::at0), row0, x, nf);
       else
@@ -500,6 +501,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
   using L = FusedLayout<H, PE>;
   using T = TMap<H>;
   using R = Roles<H, PE>;
+  constexpr bool kOol = R::kPair;  // waits' polling loop out of line (warp_wait)
   constexpr int kEW = R::EW;  // epilogue warps per lane quadrant
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
   constexpr int CHC = CH / 2;  // TMEM columns of CH bf16 values
@@ -599,7 +601,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     // the next chunk is in its stage: its descriptor (N = H, or N = 16 for R2)
     auto ck_wait = [&](uint64_t& d, bool n16) -> bool {
       const uint32_t st = n_ck & 1;
-      if (!warp_wait(bar(B_WF + st), (n_ck >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<kOol>(bar(B_WF + st), (n_ck >> 1) & 1, &s_abort)) return false;
       d = n16 ? dsc_ring16[st] : dsc_ring[st];
       return true;
     };
@@ -634,9 +636,9 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     // phi1 for the next global layer slot, into its rotating buffer
     auto phi1 = [&]() -> bool {
       // the buffer's previous phi2 accumulator has been read
-      if (!warp_wait(bar(B_BE + p1.b), (p1.u & 1) ^ 1, &s_abort)) return false;
+      if (!warp_wait<kOol>(bar(B_BE + p1.b), (p1.u & 1) ^ 1, &s_abort)) return false;
       const int a = g1 & 1;
-      if (!warp_wait(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<kOol>(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
       tc_fence_after();
       mma_bands(tbase + T::buf(p1.b), a ? dsc_at1 : dsc_at0, dsc_phi1);
       mma_commit_e(bar(B_D1 + p1.b));
@@ -649,13 +651,13 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     // the epilogue warps have written the next A operand in TMEM
     uint32_t n_h[2] = {0, 0};
     auto wait_h = [&](int h) -> bool {
-      if (!warp_wait(bar(B_H + h), n_h[h] & 1, &s_abort)) return false;
+      if (!warp_wait<kOol>(bar(B_H + h), n_h[h] & 1, &s_abort)) return false;
       ++n_h[h];
       tc_fence_after();
       return true;
     };
     auto wait_in = [&]() -> bool {
-      if (!warp_wait(bar(B_IN + (n_in & 1)), (n_in >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<kOol>(bar(B_IN + (n_in & 1)), (n_in >> 1) & 1, &s_abort)) return false;
       ++n_in;
       tc_fence_after();
       return true;
@@ -663,7 +665,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     // Tile number t of this CTA as the loaders published it: global index
     // (>= total_tiles ends the loop), slot count and the frame's biases.
     auto take_tile = [&](uint32_t t, int& tile, int& ns, const float*& fold) -> bool {
-      if (!warp_wait(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<kOol>(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
       tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
       ns = 0;
 #pragma unroll
@@ -690,11 +692,11 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     };
     int tile, ns;
     const float* fold;
-    if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+    if (!warp_wait<kOol>(bar(B_W), 0, &s_abort)) goto done;
     // Test hook (stall_ns > 0, set by glassnet_debug_stall_next_render): wait
     // on a barrier that nothing arrives on, before any MMA is issued, so that
     // the wait gives up and every warp takes the timeout exit.
-    if (prm.stall_ns > 0 && !warp_wait(bar(B_STALL), 0, &s_abort, prm.stall_ns)) goto done;
+    if (prm.stall_ns > 0 && !warp_wait<kOol>(bar(B_STALL), 0, &s_abort, prm.stall_ns)) goto done;
     if (!take_tile(0, tile, ns, fold)) goto done;
     if (tile < total_tiles) {
       patch_fold(fold);
@@ -725,8 +727,8 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // the previous commit (B_AG_F)
         // (two alternating barriers: the epilogue cannot take tile tb + 2
         // before this commit, so neither runs two phases ahead)
-        if (!warp_wait(bar(B_H + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
-        if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        if (!warp_wait<kOol>(bar(B_H + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
+        if (!warp_wait<kOol>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
         ++n_agf;
         mma_commit_e(bar(B_AG_E));
         __syncwarp();
@@ -764,7 +766,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         }
         if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
         if (!wait_h(0)) goto done;
-        if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        if (!warp_wait<kOol>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
         ++n_agf;
         tc_fence_after();
         mma_f16_ss_e(Y, dsc_ag, dsc_b1, idH, 0u);
@@ -814,7 +816,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // publish it once this tile's layer operands are written)
         if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
         if (!wait_h(0)) goto done;
-        if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        if (!warp_wait<kOol>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
         ++n_agf;
         tc_fence_after();
         mma_bands(Y, dsc_ag, dsc_b1);
@@ -856,7 +858,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
       if (tile < total_tiles) {
         if (next_fold != cur_fold) {
           // every MMA of this tile (B1 reads the old bias rows) has completed
-          if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
+          if (!warp_wait<kOol>(bar(B_DR2), tb & 1, &s_abort)) goto done;
           patch_fold(next_fold);
         }
         for (int k = 0; k < ns && k < 2; ++k)
@@ -888,13 +890,13 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
       ++n_in;
     };
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
-    if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+    if (!warp_wait<kOol>(bar(B_W), 0, &s_abort)) goto done;
     {
       const int total_tiles = prm.total_tiles;
       // Tile number t of this CTA as the loaders published it.
       int tile, ns, c;
       auto take_tile = [&](uint32_t t) -> bool {
-        if (!warp_wait(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
+        if (!warp_wait<kOol>(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
         tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
         ns = 0;
 #pragma unroll
@@ -947,7 +949,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // are double buffered: block hh + 1 is in flight while hh is packed.
         auto epi1 = [&](int k) -> bool {
           const uint32_t gk = gs + k, b = gk % 3u;
-          if (!warp_wait(bar(B_D1 + b), (gk / 3u) & 1, &s_abort)) return false;
+          if (!warp_wait<kOol>(bar(B_D1 + b), (gk / 3u) & 1, &s_abort)) return false;
           tc_fence_after();
           const uint32_t src = tl + T::buf(b) + g * CH;
           const uint32_t dst = tl + (k & 1 ? T::AU1 : T::AU0) + g * CHC;
@@ -972,7 +974,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // phi2(k) accumulator -> pool update for pixels with k < c.
         auto epi2 = [&](int k) -> bool {
           const uint32_t gk = gs + k, b = gk % 3u;
-          if (!warp_wait(bar(B_D2 + b), (gk / 3u) & 1, &s_abort)) return false;
+          if (!warp_wait<kOol>(bar(B_D2 + b), (gk / 3u) & 1, &s_abort)) return false;
           tc_fence_after();
           const uint32_t src = tl + T::buf(b) + g * CH;
           uint32_t ra[16], rb[16];
@@ -1118,7 +1120,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         static_assert(PC % 16 == 0, "per-pixel passes load 16 accumulator columns at a time");
 #pragma unroll
         for (int l = Sum ? 1 : 0; l < (R3 ? 3 : 4); ++l) {
-          if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
+          if (!warp_wait<kOol>(bar(B_DP), n_dp & 1, &s_abort)) goto done;
           ++n_dp;
           tc_fence_after();
           const float* bl = l == 0 ? b_rho : (l == 2 ? b_b2 : b_r1);
@@ -1169,7 +1171,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // it is issued only after every warp's first phi1 epilogue of that
         // tile, which follows this TMEM read.  The next tile is taken first.
         if (!take_tile(tb + 1)) goto done;
-        if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
+        if (!warp_wait<kOol>(bar(B_DR2), tb & 1, &s_abort)) goto done;
         if (!R3 && g == 0) {
           tc_fence_after();
           uint32_t r[4];

@@ -131,23 +131,36 @@ __device__ __forceinline__ void pe_double(float (&sn)[N], float (&cs)[N]) {
 // On a timeout the CTA-wide abort flag is raised (to the shared-memory
 // address of the barrier that gave up, bit 0 set so that it is never 0) and
 // every later wait fails at once, so all warps reach the common exit.
+// Polling loop of a wait whose first test failed.
+__device__ __forceinline__ bool wait_poll_inl(uint32_t bar, uint32_t parity,
+                                              volatile int* abort_flag, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer_ns() - t0 > limit_ns) {
+      *abort_flag = static_cast<int>(bar | 1u);
+      return false;
+    }
+  }
+}
+// The same loop out of line: only the first test of each wait is on the hot
+// path, so with many inlined waits the loop's code would otherwise sit in the
+// instruction-cache lines of the hot loops.  Worth it where that cache is
+// contended (two CTAs of the base widths per SM: 0.0906 against 0.0942 ms
+// per frame); at H = 128 the call's register convention costs more than it
+// saves (0.1231 against 0.1153 ms), so that kernel keeps the loop inline.
+static __device__ __noinline__ bool wait_poll_ool(uint32_t bar, uint32_t parity,
+                                                  volatile int* abort_flag, uint64_t limit_ns) {
+  return wait_poll_inl(bar, parity, abort_flag, limit_ns);
+}
+template <bool kOutOfLine = false>
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           uint64_t limit_ns = kWaitNs) {
   bool ok = mbar_try_wait(bar, parity);
-  if (!ok) {
-    const uint64_t t0 = globaltimer_ns();
-    while (true) {
-      if (mbar_try_wait(bar, parity)) {
-        ok = true;
-        break;
-      }
-      if (*abort_flag) break;
-      if (globaltimer_ns() - t0 > limit_ns) {
-        *abort_flag = static_cast<int>(bar | 1u);
-        break;
-      }
-    }
-  }
+  if (!ok)
+    ok = kOutOfLine ? wait_poll_ool(bar, parity, abort_flag, limit_ns)
+                    : wait_poll_inl(bar, parity, abort_flag, limit_ns);
   return __all_sync(0xffffffffu, ok);
 }
 
