@@ -263,7 +263,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
                                             volatile int* abort_flag, int li, int lane) {
   using L = FusedLayout<H, PE>;
   constexpr int RPL = Roles<H, PE>::RPL, LW = Roles<H, PE>::LW;
-  constexpr bool kOol = Roles<H, PE>::kPair;  // waits' polling loop out of line (warp_wait)
+  constexpr bool kOol = Roles<H, PE>::kPair || PE;  // waits' polling loop out of line (warp_wait)
   const int nf = PE ? prm.pe_freqs : 0;  // positional-encoding frequencies
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
   const int row0 = li * (32 * RPL) + lane;
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
   using L = FusedLayout<H, PE>;
   using T = TMap<H>;
   using R = Roles<H, PE>;
-  constexpr bool kOol = R::kPair;  // waits' polling loop out of line (warp_wait)
+  constexpr bool kOol = R::kPair || PE;  // waits' polling loop out of line (warp_wait)
   constexpr int kEW = R::EW;  // epilogue warps per lane quadrant
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
   constexpr int CHC = CH / 2;  // TMEM columns of CH bf16 values
