@@ -263,7 +263,7 @@ __device__ __forceinline__ void loader_loop(const FusedParams& prm, uint32_t sba
                                             volatile int* abort_flag, int li, int lane) {
   using L = FusedLayout<H, PE>;
   constexpr int RPL = Roles<H, PE>::RPL, LW = Roles<H, PE>::LW;
-  constexpr bool kOol = Roles<H, PE>::kPair || PE;  // waits' polling loop out of line (warp_wait)
+  constexpr bool kOol = true;  // the waits' polling loop out of line (warp_wait)
   const int nf = PE ? prm.pe_freqs : 0;  // positional-encoding frequencies
   auto bar = [&](int i) { return bar_base + static_cast<uint32_t>(i) * 8u; };
   const int row0 = li * (32 * RPL) + lane;
@@ -501,7 +501,9 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
   using L = FusedLayout<H, PE>;
   using T = TMap<H>;
   using R = Roles<H, PE>;
-  constexpr bool kOol = R::kPair || PE;  // waits' polling loop out of line (warp_wait)
+  // the epilogue waits' polling loop out of line (warp_wait); the MMA warp's
+  // always
+  constexpr bool kOol = R::kPair || PE;
   constexpr int kEW = R::EW;  // epilogue warps per lane quadrant
   constexpr int CH = H / kEW;  // accumulator columns per epilogue thread
   constexpr int CHC = CH / 2;  // TMEM columns of CH bf16 values
@@ -601,7 +603,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     // the next chunk is in its stage: its descriptor (N = H, or N = 16 for R2)
     auto ck_wait = [&](uint64_t& d, bool n16) -> bool {
       const uint32_t st = n_ck & 1;
-      if (!warp_wait<kOol>(bar(B_WF + st), (n_ck >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_WF + st), (n_ck >> 1) & 1, &s_abort)) return false;
       d = n16 ? dsc_ring16[st] : dsc_ring[st];
       return true;
     };
@@ -636,9 +638,9 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     // phi1 for the next global layer slot, into its rotating buffer
     auto phi1 = [&]() -> bool {
       // the buffer's previous phi2 accumulator has been read
-      if (!warp_wait<kOol>(bar(B_BE + p1.b), (p1.u & 1) ^ 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_BE + p1.b), (p1.u & 1) ^ 1, &s_abort)) return false;
       const int a = g1 & 1;
-      if (!warp_wait<kOol>(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
       tc_fence_after();
       mma_bands(tbase + T::buf(p1.b), a ? dsc_at1 : dsc_at0, dsc_phi1);
       mma_commit_e(bar(B_D1 + p1.b));
@@ -651,13 +653,13 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     // the epilogue warps have written the next A operand in TMEM
     uint32_t n_h[2] = {0, 0};
     auto wait_h = [&](int h) -> bool {
-      if (!warp_wait<kOol>(bar(B_H + h), n_h[h] & 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_H + h), n_h[h] & 1, &s_abort)) return false;
       ++n_h[h];
       tc_fence_after();
       return true;
     };
     auto wait_in = [&]() -> bool {
-      if (!warp_wait<kOol>(bar(B_IN + (n_in & 1)), (n_in >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_IN + (n_in & 1)), (n_in >> 1) & 1, &s_abort)) return false;
       ++n_in;
       tc_fence_after();
       return true;
@@ -665,7 +667,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     // Tile number t of this CTA as the loaders published it: global index
     // (>= total_tiles ends the loop), slot count and the frame's biases.
     auto take_tile = [&](uint32_t t, int& tile, int& ns, const float*& fold) -> bool {
-      if (!warp_wait<kOol>(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_TILE + (t & 1)), (t >> 1) & 1, &s_abort)) return false;
       tile = *reinterpret_cast<volatile int*>(&s_ld.tile[t & 1]);
       ns = 0;
 #pragma unroll
@@ -692,11 +694,11 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
     };
     int tile, ns;
     const float* fold;
-    if (!warp_wait<kOol>(bar(B_W), 0, &s_abort)) goto done;
+    if (!warp_wait<true>(bar(B_W), 0, &s_abort)) goto done;
     // Test hook (stall_ns > 0, set by glassnet_debug_stall_next_render): wait
     // on a barrier that nothing arrives on, before any MMA is issued, so that
     // the wait gives up and every warp takes the timeout exit.
-    if (prm.stall_ns > 0 && !warp_wait<kOol>(bar(B_STALL), 0, &s_abort, prm.stall_ns)) goto done;
+    if (prm.stall_ns > 0 && !warp_wait<true>(bar(B_STALL), 0, &s_abort, prm.stall_ns)) goto done;
     if (!take_tile(0, tile, ns, fold)) goto done;
     if (tile < total_tiles) {
       patch_fold(fold);
@@ -727,8 +729,8 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // the previous commit (B_AG_F)
         // (two alternating barriers: the epilogue cannot take tile tb + 2
         // before this commit, so neither runs two phases ahead)
-        if (!warp_wait<kOol>(bar(B_H + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
-        if (!warp_wait<kOol>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        if (!warp_wait<true>(bar(B_H + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
+        if (!warp_wait<true>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
         ++n_agf;
         mma_commit_e(bar(B_AG_E));
         __syncwarp();
@@ -766,7 +768,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         }
         if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
         if (!wait_h(0)) goto done;
-        if (!warp_wait<kOol>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        if (!warp_wait<true>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
         ++n_agf;
         tc_fence_after();
         mma_f16_ss_e(Y, dsc_ag, dsc_b1, idH, 0u);
@@ -816,7 +818,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
         // publish it once this tile's layer operands are written)
         if (!take_tile(tb + 1, next_tile, next_ns, next_fold)) goto done;
         if (!wait_h(0)) goto done;
-        if (!warp_wait<kOol>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+        if (!warp_wait<true>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
         ++n_agf;
         tc_fence_after();
         mma_bands(Y, dsc_ag, dsc_b1);
@@ -858,7 +860,7 @@ __global__ void __launch_bounds__(Roles<H, PE>::kThreads, Roles<H, PE>::kCtasPer
       if (tile < total_tiles) {
         if (next_fold != cur_fold) {
           // every MMA of this tile (B1 reads the old bias rows) has completed
-          if (!warp_wait<kOol>(bar(B_DR2), tb & 1, &s_abort)) goto done;
+          if (!warp_wait<true>(bar(B_DR2), tb & 1, &s_abort)) goto done;
           patch_fold(next_fold);
         }
         for (int k = 0; k < ns && k < 2; ++k)

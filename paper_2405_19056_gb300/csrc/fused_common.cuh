@@ -146,12 +146,14 @@ __device__ __forceinline__ bool wait_poll_inl(uint32_t bar, uint32_t parity,
 }
 // The same loop out of line: only the first test of each wait is on the hot
 // path, so with many inlined waits the loop's code would otherwise sit in the
-// instruction-cache lines of the hot loops.  Worth it where that cache is
-// contended: two CTAs of the base widths per SM (0.0906 against 0.0942 ms
-// per frame) and the kernels whose loaders encode their inputs (0.2725
-// against 0.2848 ms at H = 128, 0.1386 against 0.1404 at H = 64); in the
-// unencoded H = 128 kernel the call's register convention costs more than it
-// saves (0.1231 against 0.1153 ms), so that kernel keeps the loop inline.
+// instruction-cache lines of the hot loops.  Measured per frame (A/B in one
+// call each): two CTAs of the base widths per SM 0.0906 against 0.0942 ms;
+// the kernels whose loaders encode their inputs 0.2725 against 0.2848 ms at
+// H = 128 and 0.1386 against 0.1404 at H = 64; the FP8 kernel 0.1327
+// against 0.1372 ms.  In the unencoded H = 128 BF16 kernel the epilogue
+// warps' waits stay inline (their 96 registers of pool state would cross
+// the call: 0.1231 against 0.1153 ms with every wait out of line), and
+// its MMA and loader warps' waits go out of line (0.1136 against 0.1150).
 static __device__ __noinline__ bool wait_poll_ool(uint32_t bar, uint32_t parity,
                                                   volatile int* abort_flag, uint64_t limit_ns) {
   return wait_poll_inl(bar, parity, abort_flag, limit_ns);

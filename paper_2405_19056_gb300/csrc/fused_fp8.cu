@@ -215,7 +215,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
   const uint32_t inv_s_t_sm = sbase + L::cst + 4u * L::INV_S_TCH;
   const uint32_t inv_s_g_sm = sbase + L::cst + 4u * L::INV_S_GCH;
   if constexpr (PE) {
-    if (!warp_wait(bar(B_W), 0, abort_flag)) return;
+    if (!warp_wait<true>(bar(B_W), 0, abort_flag)) return;
   } else {
 #pragma unroll
     for (int c = 0; c < kTC; ++c) inv_s_t[c] = __ldg(cst + L::INV_S_TCH + c);
@@ -236,7 +236,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
       if (lane == 0) ls.tile[tb & 1] = schedule_tile(prm, atomicAdd(prm.next_tile, 1u));
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_SCHED + (tb & 1)));
-    } else if (!warp_wait(bar(B_SCHED + (tb & 1)), (tb >> 1) & 1, abort_flag)) {
+    } else if (!warp_wait<true>(bar(B_SCHED + (tb & 1)), (tb >> 1) & 1, abort_flag)) {
       return;
     }
     tile = *reinterpret_cast<volatile int*>(&ls.tile[tb & 1]);
@@ -267,7 +267,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
     if (lane == 0) ls.ns[tb & 1][li] = wmax;
     __syncwarp();
     if (lane == 0) mbar_arrive(bar(B_TILE + (tb & 1)));
-    if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
+    if (!warp_wait<true>(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, abort_flag)) return;
     const int ns = max(ls.ns[tb & 1][0], ls.ns[tb & 1][1]);
 
     // the G-buffer rows, loads in flight now (encoded inputs: loaded when
@@ -285,7 +285,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
     // B1's G-buffer operand: the 14 channels as codes of g[c] / s_g[c], then zeros
     auto put_ag = [&]() -> bool {
       if constexpr (PE) load_g();
-      if (!warp_wait(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
+      if (!warp_wait<true>(bar(B_AG_E), (n_ag & 1) ^ 1, abort_flag)) return false;
       ++n_ag;
       // with encoding a loop over the rows, each row's values picked by
       // selects: one copy of the (long) encoding code, which keeps the
@@ -328,7 +328,7 @@ __device__ __forceinline__ void loader_loop_f8(const FusedParams& prm, const uin
     for (int k = 0; k < ns; ++k, ++lc) {
       if (k + 1 < ns) load_slot_f8(F, k + 1, pix, cnt, y);
       const int b = lc & 1;
-      if (!warp_wait(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
+      if (!warp_wait<true>(bar(B_AT_E + b), ((lc >> 1) & 1) ^ 1, abort_flag)) return;
       if constexpr (PE) {
 #pragma unroll 1
         for (int i = 0; i < kRowsPerLoadLane; ++i) {  // one copy of the code (see put_ag)
@@ -476,9 +476,9 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     uint32_t g1 = 0, n_in = 0, n_agf = 0, tb = 0;
     const float* cur_fold = nullptr;
     auto phi1 = [&]() -> bool {
-      if (!warp_wait(bar(B_BE + p1.b), (p1.u & 1) ^ 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_BE + p1.b), (p1.u & 1) ^ 1, &s_abort)) return false;
       const int a = g1 & 1;
-      if (!warp_wait(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_AT_F + a), (g1 >> 1) & 1, &s_abort)) return false;
       tc_fence_after();
       const uint32_t d = tbase + T::buf(p1.b);
       mma_ss_k(d, a ? dsc_at1 : dsc_at0, dsc_phi1, L::KT, 0u);
@@ -491,17 +491,17 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       return true;
     };
     auto wait_in = [&]() -> bool {
-      if (!warp_wait(bar(B_IN + (n_in & 1)), (n_in >> 1) & 1, &s_abort)) return false;
+      if (!warp_wait<true>(bar(B_IN + (n_in & 1)), (n_in >> 1) & 1, &s_abort)) return false;
       ++n_in;
       tc_fence_after();
       return true;
     };
-    if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+    if (!warp_wait<true>(bar(B_W), 0, &s_abort)) goto done;
     // Test hook (stall_ns > 0, set by glassnet_debug_stall_next_render): a
     // wait on a barrier that nothing arrives on, before any MMA is issued.
-    if (prm.stall_ns > 0 && !warp_wait(bar(B_STALL8), 0, &s_abort, prm.stall_ns)) goto done;
+    if (prm.stall_ns > 0 && !warp_wait<true>(bar(B_STALL8), 0, &s_abort, prm.stall_ns)) goto done;
     for (;; ++tb) {
-      if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
+      if (!warp_wait<true>(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
       const int tile = *reinterpret_cast<volatile int*>(&s_ld.tile[tb & 1]);
       if (tile >= prm.total_tiles) break;
       const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       if (F.fold != cur_fold) {
         // Per-scene biases in accumulator units -> the BF16 bias operands,
         // once no MMA of the previous tile can still read them.
-        if (tb > 0 && !warp_wait(bar(B_DR2), (tb - 1) & 1, &s_abort)) goto done;
+        if (tb > 0 && !warp_wait<true>(bar(B_DR2), (tb - 1) & 1, &s_abort)) goto done;
         for (int i = lane; i < 2 * H; i += 32) {
           const int n = i < H ? i : i - H;
           const float cv = F.fold[i] * cst[(i < H ? L::U_PHI1 : L::U_B1) + n];
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       for (int l = Sum ? 1 : 0; l < (R3 ? 3 : 4); ++l) {
         if (!wait_in()) goto done;
         if (l == 1) {
-          if (!warp_wait(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
+          if (!warp_wait<true>(bar(B_AG_F), n_agf & 1, &s_abort)) goto done;
           ++n_agf;
           tc_fence_after();
         }
@@ -579,11 +579,11 @@ __global__ void __launch_bounds__(kThreadsF, 1)
       ++n_in;
     };
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the tile plan is complete
-    if (!warp_wait(bar(B_W), 0, &s_abort)) goto done;
+    if (!warp_wait<true>(bar(B_W), 0, &s_abort)) goto done;
     {
       const float inv_s_pool = cst[L::INV_S_POOL];
       for (;; ++tb) {
-        if (!warp_wait(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
+        if (!warp_wait<true>(bar(B_TILE + (tb & 1)), (tb >> 1) & 1, &s_abort)) goto done;
         const int tile = *reinterpret_cast<volatile int*>(&s_ld.tile[tb & 1]);
         if (tile >= prm.total_tiles) break;
         const int ns = max(s_ld.ns[tb & 1][0], s_ld.ns[tb & 1][1]);
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         // phi1(k) accumulator -> U(k) codes (the bias is in the accumulator)
         auto epi1 = [&](int k) -> bool {
           const uint32_t gk = gs + k, b = gk % 3u;
-          if (!warp_wait(bar(B_D1 + b), (gk / 3u) & 1, &s_abort)) return false;
+          if (!warp_wait<true>(bar(B_D1 + b), (gk / 3u) & 1, &s_abort)) return false;
           tc_fence_after();
           const uint32_t src = tl + T::buf(b) + g * CH;
           const uint32_t dst = tl + (k & 1 ? T::AU1 : T::AU0) + g * CHQ;
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         // phi2(k) accumulator -> v = acc s + b (real units) -> pool update
         auto epi2 = [&](int k) -> bool {
           const uint32_t gk = gs + k, b = gk % 3u;
-          if (!warp_wait(bar(B_D2 + b), (gk / 3u) & 1, &s_abort)) return false;
+          if (!warp_wait<true>(bar(B_D2 + b), (gk / 3u) & 1, &s_abort)) return false;
           tc_fence_after();
           const uint32_t src = tl + T::buf(b) + g * CH;
           uint32_t ra[16], rb[16];
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         }
 #pragma unroll
         for (int l = Sum ? 1 : 0; l < (R3 ? 3 : 4); ++l) {
-          if (!warp_wait(bar(B_DP), n_dp & 1, &s_abort)) goto done;
+          if (!warp_wait<true>(bar(B_DP), n_dp & 1, &s_abort)) goto done;
           ++n_dp;
           tc_fence_after();
           const float* sl = cst + (l == 0 ? L::S_RHO : l == 1 ? L::S_B1 : l == 2 ? L::S_B2 : L::S_R1) + g * CH;
@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         // R2 + sigmoid -> out (column group 0 stores)
         const uint32_t ent = g == 0 ? __ldg(prm.plan + static_cast<size_t>(tile) * kTile + row)
                                     : kPlanEmpty;
-        if (!warp_wait(bar(B_DR2), tb & 1, &s_abort)) goto done;
+        if (!warp_wait<true>(bar(B_DR2), tb & 1, &s_abort)) goto done;
         if (!R3 && g == 0) {
           tc_fence_after();
           uint32_t r[4];
